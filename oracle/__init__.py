@@ -1,0 +1,162 @@
+"""FP64 CPU oracle for the softened direct-sum n-body path (ctypes shim).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
+benchmark's CPU-baseline leg may call this module; the product path never
+does.  The arithmetic lives in ``nbody_oracle.c`` (plain C, FP64, OpenMP over
+bodies), which shares nothing with the CUDA library.
+
+Every function takes and returns float64 numpy arrays: positions and
+velocities (n, 3), masses (n,).  Function-level citations are in the C file:
+the force sum is the exact form of the paper's force calculation (Sec. IV-A,
+IV-B); the leapfrog is the reading of "Move_bodies" (Sec. IV-B pseudo-code);
+the diagnostics and adjoints have no counterpart in the paper and follow from
+the same formulas.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nbody_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, dbl = ctypes.c_int64, ctypes.c_double
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_accel.argtypes = [i64, _D, _D, dbl, dbl, _D]
+        lib.oracle_accel_rows.argtypes = [i64, _D, _D, dbl, dbl, i64, _I, _D]
+        lib.oracle_energy.argtypes = [i64, _D, _D, _D, dbl, dbl, _D]
+        lib.oracle_kdk.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64, _D]
+        lib.oracle_force_vjp.argtypes = [i64, _D, _D, dbl, dbl, _D, _D, _D]
+        lib.oracle_kdk_grad.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64,
+                                        _D, _D, _D, _D, _D]
+        lib.oracle_kdk_grad.restype = ctypes.c_int
+        for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
+                  lib.oracle_kdk, lib.oracle_force_vjp):
+            f.restype = None
+        _lib = lib
+        return lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(_D)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_threads())
+
+
+def accel(pos, mass, G=1.0, eps=0.0):
+    """a_i = G sum_{j != i} m_j d_ij / (|d_ij|^2 + eps^2)^{3/2}, (n, 3)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    out = np.zeros((n, 3))
+    _load().oracle_accel(n, _p(x), _p(m), float(G), float(eps), _p(out))
+    return out
+
+
+def accel_rows(pos, mass, rows, G=1.0, eps=0.0):
+    """Accelerations of the bodies listed in ``rows`` only, (len(rows), 3)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    if r.size and (r.min() < 0 or r.max() >= n):
+        raise IndexError("row index out of range")
+    out = np.zeros((r.size, 3))
+    _load().oracle_accel_rows(n, _p(x), _p(m), float(G), float(eps), r.size,
+                              r.ctypes.data_as(_I), _p(out))
+    return out
+
+
+def energy(pos, vel, mass, G=1.0, eps=0.0):
+    """[E_kin, E_pot, E_tot, Px, Py, Pz, Fx, Fy, Fz] (F = sum m a)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    v = _f64(vel, (n, 3))
+    out = np.zeros(9)
+    _load().oracle_energy(n, _p(x), _p(v), _p(m), float(G), float(eps), _p(out))
+    return out
+
+
+def kdk(pos, vel, mass, G, eps, dt, nsteps):
+    """nsteps KDK leapfrog steps; returns (pos, vel, acc) at the end."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3)).copy()
+    v = _f64(vel, (n, 3)).copy()
+    a = np.zeros((n, 3))
+    _load().oracle_kdk(n, _p(x), _p(v), _p(m), float(G), float(eps), float(dt),
+                       int(nsteps), _p(a))
+    return x, v, a
+
+
+def force_vjp(pos, mass, lam, G=1.0, eps=0.0):
+    """(dL/dx, dL/dm) of L through a = F(x, m), given lam = dL/da."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    l = _f64(lam, (n, 3))
+    gx = np.zeros((n, 3))
+    gm = np.zeros(n)
+    _load().oracle_force_vjp(n, _p(x), _p(m), float(G), float(eps), _p(l),
+                             _p(gx), _p(gm))
+    return gx, gm
+
+
+def kdk_grad(pos, vel, mass, G, eps, dt, nsteps, gxT, gvT):
+    """Gradients (dL/dx0, dL/dv0, dL/dm) through nsteps KDK steps."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    v = _f64(vel, (n, 3))
+    gx = _f64(gxT, (n, 3))
+    gv = _f64(gvT, (n, 3))
+    ox = np.zeros((n, 3)); ov = np.zeros((n, 3)); om = np.zeros(n)
+    rc = _load().oracle_kdk_grad(n, _p(x), _p(v), _p(m), float(G), float(eps),
+                                 float(dt), int(nsteps), _p(gx), _p(gv),
+                                 _p(ox), _p(ov), _p(om))
+    if rc != 0:
+        raise MemoryError("oracle_kdk_grad: allocation failed")
+    return ox, ov, om

@@ -1,0 +1,250 @@
+/*
+ * FP64 CPU oracle for the softened direct-sum n-body force path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package's smoke check and
+ * the benchmark's CPU-baseline leg may load this file's library.  It shares
+ * no code, header or constant with the CUDA library and must never be used
+ * as a fallback for it.
+ *
+ * What it computes (the paper's n-body step, Sec. IV and the hybrid
+ * pseudo-code of Sec. IV-B):
+ *   - the force calculation, which the paper says takes upwards of 90% of the
+ *     cycles (Sec. IV-B), done here as the exact all-pairs sum that the
+ *     paper's tree code approximates (Sec. IV-A);
+ *   - "Move_bodies": the position/velocity update of Sec. IV-A, read as a
+ *     kick-drift-kick leapfrog with cached forces;
+ *   - energy and momentum diagnostics, and the adjoint (vector-Jacobian
+ *     product) of the force and of the leapfrog, which the paper does not
+ *     have; they follow from differentiating the same formulas.
+ *
+ * Readings where the paper is silent (Sec. IV names only "mutual gravitation
+ * field"): Plummer-softened Newtonian gravity with constant G and softening
+ * eps,   a_i = G sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2},
+ * self pair excluded; potential energy -G sum_{i<j} m_i m_j / sqrt(r^2+eps^2).
+ *
+ * The loops follow the plain definition: i outer, j ascending inner, no
+ * blocking.  The i loop is shared among OpenMP threads with a dynamic
+ * schedule, the intra-node scheme the paper uses for its force loop
+ * (Sec. IV-B pseudo-code, Sec. V-C / Table VI).  Each i is independent, so
+ * the result does not depend on the thread count.
+ *
+ * Arrays: positions/velocities/accelerations are row-major (n,3) doubles,
+ * masses (n) doubles; all caller-owned host memory.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_CHUNK 32
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Acceleration of body i (softened direct sum, self pair skipped). */
+static void accel_one(int64_t n, const double *x, const double *m, double G,
+                      double eps, int64_t i, double out[3])
+{
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double dx = x[3 * j] - xi;
+        double dy = x[3 * j + 1] - yi;
+        double dz = x[3 * j + 2] - zi;
+        double s2 = dx * dx + dy * dy + dz * dz + eps * eps;
+        double inv_s3 = 1.0 / (s2 * sqrt(s2));
+        ax += m[j] * dx * inv_s3;
+        ay += m[j] * dy * inv_s3;
+        az += m[j] * dz * inv_s3;
+    }
+    out[0] = G * ax;
+    out[1] = G * ay;
+    out[2] = G * az;
+}
+
+/* a_i for every body. */
+void oracle_accel(int64_t n, const double *x, const double *m, double G,
+                  double eps, double *acc)
+{
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, ORACLE_CHUNK)
+    for (i = 0; i < n; ++i) accel_one(n, x, m, G, eps, i, acc + 3 * i);
+}
+
+/* a_i for the listed bodies only: acc is (nrows,3), row r is body rows[r]. */
+void oracle_accel_rows(int64_t n, const double *x, const double *m, double G,
+                       double eps, int64_t nrows, const int64_t *rows,
+                       double *acc)
+{
+    int64_t r;
+#pragma omp parallel for schedule(dynamic, ORACLE_CHUNK)
+    for (r = 0; r < nrows; ++r) accel_one(n, x, m, G, eps, rows[r], acc + 3 * r);
+}
+
+/*
+ * Diagnostics: out = {E_kin, E_pot, E_tot, P_x, P_y, P_z, F_x, F_y, F_z}
+ * with E_kin = 1/2 sum m|v|^2, E_pot = -G sum_{i<j} m_i m_j / s_ij,
+ * P = sum m v and F = sum m a (zero by Newton's third law).
+ */
+void oracle_energy(int64_t n, const double *x, const double *v,
+                   const double *m, double G, double eps, double *out)
+{
+    double *phi = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *acc = (double *)calloc((size_t)(n > 0 ? 3 * n : 1), sizeof(double));
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, ORACLE_CHUNK)
+    for (i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx = x[3 * j] - x[3 * i];
+            double dy = x[3 * j + 1] - x[3 * i + 1];
+            double dz = x[3 * j + 2] - x[3 * i + 2];
+            s += m[j] / sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
+        }
+        phi[i] = s;
+    }
+    oracle_accel(n, x, m, G, eps, acc);
+    double ek = 0.0, ep = 0.0, p[3] = {0, 0, 0}, f[3] = {0, 0, 0};
+    for (i = 0; i < n; ++i) {
+        ek += 0.5 * m[i] * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] +
+                            v[3 * i + 2] * v[3 * i + 2]);
+        ep += -G * m[i] * phi[i];
+        for (int c = 0; c < 3; ++c) {
+            p[c] += m[i] * v[3 * i + c];
+            f[c] += m[i] * acc[3 * i + c];
+        }
+    }
+    out[0] = ek;
+    out[1] = ep;
+    out[2] = ek + ep;
+    for (int c = 0; c < 3; ++c) {
+        out[3 + c] = p[c];
+        out[6 + c] = f[c];
+    }
+    free(phi);
+    free(acc);
+}
+
+/*
+ * Kick-drift-kick leapfrog, nsteps steps of dt, in place on x and v.
+ * The force at the initial positions is computed here, then each step is
+ *   v += dt/2 a;  x += dt v;  a = F(x);  v += dt/2 a,
+ * so nsteps steps take nsteps + 1 force evaluations.  On return acc holds
+ * F at the final positions.
+ */
+void oracle_kdk(int64_t n, double *x, double *v, const double *m, double G,
+                double eps, double dt, int64_t nsteps, double *acc)
+{
+    oracle_accel(n, x, m, G, eps, acc);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * acc[k];
+        for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt * v[k];
+        oracle_accel(n, x, m, G, eps, acc);
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * acc[k];
+    }
+}
+
+/*
+ * Vector-Jacobian product of the force map a = F(x, m) with cotangent
+ * lam = dL/da (n,3).  With d_kj = x_j - x_k, s = sqrt(|d|^2 + eps^2) and the
+ * symmetric tensor K(d) = I/s^3 - 3 d d^T / s^5 (the derivative of d/s^3):
+ *   gx_k = G sum_{j != k} K(d_kj) (m_k lam_j - m_j lam_k)
+ *   gm_k = G sum_{i != k} lam_i . (x_k - x_i) / s_ik^3
+ * gx and gm are overwritten.
+ */
+void oracle_force_vjp(int64_t n, const double *x, const double *m, double G,
+                      double eps, const double *lam, double *gx, double *gm)
+{
+    int64_t k;
+#pragma omp parallel for schedule(dynamic, ORACLE_CHUNK)
+    for (k = 0; k < n; ++k) {
+        double g[3] = {0, 0, 0}, gmk = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == k) continue;
+            double d[3], w[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = x[3 * j + c] - x[3 * k + c];
+                w[c] = m[k] * lam[3 * j + c] - m[j] * lam[3 * k + c];
+            }
+            double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps * eps;
+            double s = sqrt(s2);
+            double inv_s3 = 1.0 / (s2 * s);
+            double inv_s5 = inv_s3 / s2;
+            double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+            for (int c = 0; c < 3; ++c)
+                g[c] += w[c] * inv_s3 - 3.0 * d[c] * dw * inv_s5;
+            /* x_k - x_j = -d */
+            double ld = lam[3 * j] * d[0] + lam[3 * j + 1] * d[1] +
+                        lam[3 * j + 2] * d[2];
+            gmk += -ld * inv_s3;
+        }
+        for (int c = 0; c < 3; ++c) gx[3 * k + c] = G * g[c];
+        gm[k] = G * gmk;
+    }
+}
+
+/*
+ * Gradient of a loss L(x_K, v_K) through nsteps leapfrog steps, from the
+ * cotangents gxT = dL/dx_K and gvT = dL/dv_K.  The forward run stores every
+ * position; the reverse sweep undoes each step in the opposite order:
+ *   second half-kick  v_K = v_h + dt/2 F(x_K):  lx += VJP_F(x_K, dt/2 lv)
+ *   drift             x_K = x + dt v_h:         lv += dt lx
+ *   first half-kick   v_h = v + dt/2 F(x):      lx += VJP_F(x, dt/2 lv)
+ * with the mass cotangent accumulated from every VJP.  Outputs
+ * gx0 = dL/dx_0, gv0 = dL/dv_0, gm = dL/dm (overwritten).
+ */
+int oracle_kdk_grad(int64_t n, const double *x0, const double *v0,
+                    const double *m, double G, double eps, double dt,
+                    int64_t nsteps, const double *gxT, const double *gvT,
+                    double *gx0, double *gv0, double *gm)
+{
+    size_t per = (size_t)(3 * n);
+    double *traj = (double *)malloc(sizeof(double) * per * (size_t)(nsteps + 1) + 8);
+    double *v = (double *)malloc(sizeof(double) * per + 8);
+    double *acc = (double *)malloc(sizeof(double) * per + 8);
+    double *mu = (double *)malloc(sizeof(double) * per + 8);
+    double *dgx = (double *)malloc(sizeof(double) * per + 8);
+    double *dgm = (double *)malloc(sizeof(double) * (size_t)n + 8);
+    if (!traj || !v || !acc || !mu || !dgx || !dgm) {
+        free(traj); free(v); free(acc); free(mu); free(dgx); free(dgm);
+        return -1;
+    }
+    memcpy(traj, x0, sizeof(double) * per);
+    memcpy(v, v0, sizeof(double) * per);
+    oracle_accel(n, traj, m, G, eps, acc);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        double *xs = traj + per * (size_t)s, *xn = traj + per * (size_t)(s + 1);
+        for (size_t k = 0; k < per; ++k) v[k] += 0.5 * dt * acc[k];
+        for (size_t k = 0; k < per; ++k) xn[k] = xs[k] + dt * v[k];
+        oracle_accel(n, xn, m, G, eps, acc);
+        for (size_t k = 0; k < per; ++k) v[k] += 0.5 * dt * acc[k];
+    }
+    double *lx = gx0, *lv = gv0;
+    memcpy(lx, gxT, sizeof(double) * per);
+    memcpy(lv, gvT, sizeof(double) * per);
+    for (int64_t k = 0; k < n; ++k) gm[k] = 0.0;
+    for (int64_t s = nsteps - 1; s >= 0; --s) {
+        double *xs = traj + per * (size_t)s, *xn = traj + per * (size_t)(s + 1);
+        for (size_t k = 0; k < per; ++k) mu[k] = 0.5 * dt * lv[k];
+        oracle_force_vjp(n, xn, m, G, eps, mu, dgx, dgm);
+        for (size_t k = 0; k < per; ++k) lx[k] += dgx[k];
+        for (int64_t k = 0; k < n; ++k) gm[k] += dgm[k];
+        for (size_t k = 0; k < per; ++k) lv[k] += dt * lx[k];
+        for (size_t k = 0; k < per; ++k) mu[k] = 0.5 * dt * lv[k];
+        oracle_force_vjp(n, xs, m, G, eps, mu, dgx, dgm);
+        for (size_t k = 0; k < per; ++k) lx[k] += dgx[k];
+        for (int64_t k = 0; k < n; ++k) gm[k] += dgm[k];
+    }
+    free(traj); free(v); free(acc); free(mu); free(dgx); free(dgm);
+    return 0;
+}
