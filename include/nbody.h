@@ -1,0 +1,248 @@
+/*
+ * nbody.h -- C ABI of libnbody.so, the GB300 (sm_103a) softened direct-sum
+ * n-body force path.
+ *
+ * The operation (paper Sec. IV, "the n-body problem"; Sec. IV-B: the force
+ * calculation takes upwards of 90% of the cycles):
+ *
+ *   a_i = G * sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2}
+ *
+ * summed exactly over all pairs (the paper's tree code, Sec. IV-A,
+ * approximates this sum), plus the position/velocity update that consumes it
+ * ("Move_bodies", Sec. IV-B pseudo-code) as a kick-drift-kick leapfrog.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are caller-owned DEVICE pointers on the context's device,
+ *     contiguous, float64, 8-byte aligned: positions, velocities and
+ *     accelerations are row-major (n,3) ("[n][3]"), masses (n).
+ *   - Work is enqueued on the context's stream; no call synchronises unless
+ *     its comment says so.  Inputs must stay valid until the stream reaches
+ *     the work.
+ *   - Arguments are checked on the host before anything is enqueued; a
+ *     rejected call enqueues nothing and returns NB_EINVAL.
+ *   - Errors are status codes; nb_last_error() gives the message.  No C++
+ *     exception crosses this boundary.
+ *   - Outputs are overwritten unless stated as accumulated.
+ *   - G, eps and dt are float64 in every precision mode; eps >= 0.
+ *     With eps == 0 the self pair is skipped explicitly; with eps > 0 it
+ *     contributes exactly zero.
+ *   - The library owns only scratch memory inside the context.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx; /* opaque, created and freed by the library */
+
+typedef enum {
+    NB_OK = 0,
+    NB_EINVAL = 1,      /* bad argument (null/misaligned pointer, n out of range, NaN G ...) */
+    NB_ECUDA = 2,       /* a CUDA runtime call failed (message holds its name and text) */
+    NB_ENOMEM = 3,      /* device allocation failed or scratch too small */
+    NB_ENONFINITE = 4,  /* a kernel produced a non-finite result (reported by nb_sync/nb_energy) */
+    NB_ETIMEOUT = 5     /* reserved: no entry point waits on a device flag */
+} nb_status;
+
+typedef enum {
+    NB_FP64 = 0,      /* every pair term and sum in float64 */
+    NB_FP32 = 1,      /* float32 pair terms, one float32 running sum per body */
+    NB_FP32_COMP = 2  /* float32 pair terms, float32 sums per j-tile added into
+                         per-body Kahan-compensated (sum, carry) pairs */
+} nb_precision;
+
+/* Flags for nb_step / nb_rollout / nb_step_batched. */
+#define NB_ACC_VALID 1u   /* acc already holds F(pos): skip the initial force evaluation */
+#define NB_USE_GRAPH 2u   /* run the step loop as one captured CUDA graph */
+
+/* Flags for nb_step_backward. */
+#define NB_BWD_AT_END   1u  /* traj[nsteps] is the last state of the run */
+#define NB_BWD_AT_START 2u  /* traj[0] is the first state of the run */
+
+/*
+ * Create a context on `device` for systems of up to n_max bodies in
+ * precision `p`.  Work is enqueued on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  Allocates the scratch (packed bodies, split
+ * partials, reduction buffers) up front.  *out is NULL on failure.
+ */
+nb_status nb_create(nb_ctx **out, int64_t n_max, nb_precision p, int device,
+                    void *cuda_stream);
+
+/* Free the context and its scratch (synchronises its stream first).  NULL is a no-op. */
+nb_status nb_destroy(nb_ctx *ctx);
+
+/* Change the stream later work is enqueued on. */
+nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
+
+/* Message of the last failed call on this context (or of the last failed
+ * nb_create when ctx is NULL).  Owned by the library; valid until the next call. */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Wait for the context's stream; NB_ENONFINITE if any kernel flagged a
+ * non-finite output since the last check (the flag is then cleared). */
+nb_status nb_sync(nb_ctx *ctx);
+
+/*
+ * Accelerations a = F(pos, mass) (paper Sec. IV-A/IV-B force calculation,
+ * as the exact all-pairs sum).  pos [n][3], mass [n], acc [n][3] (out).
+ * 0 <= n <= n_max; n == 0 is a no-op.
+ */
+nb_status nb_forces(nb_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                    double G, double eps, double *acc);
+
+/*
+ * nsteps kick-drift-kick leapfrog steps of dt, in place on pos and vel (the
+ * reading of "Move_bodies", paper Sec. IV-B):
+ *   v += dt/2 a;  x += dt v;  a = F(x);  v += dt/2 a.
+ * acc [n][3] is the force cache: on entry it must hold F(pos) if flags has
+ * NB_ACC_VALID, otherwise it is computed first (nsteps + 1 force
+ * evaluations); on return it holds F at the final positions.  The state
+ * update is float64 in every precision mode.  nsteps >= 0.
+ */
+nb_status nb_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                  double G, double eps, double dt, int64_t nsteps, double *acc,
+                  unsigned flags);
+
+/*
+ * nb_step that also records the state every `record_every` steps (before
+ * step 0, after step record_every, ...; the final state is recorded when
+ * nsteps is a multiple of record_every): record r goes to rec_pos[r][n][3]
+ * and, if rec_vel is not NULL, rec_vel[r][n][3].  The caller sizes them for
+ * nsteps / record_every + 1 records.  record_every <= 0 records nothing.
+ * Used for adjoint checkpoints and for recomputing a segment's trajectory.
+ */
+nb_status nb_rollout(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                     double G, double eps, double dt, int64_t nsteps, double *acc,
+                     unsigned flags, int64_t record_every, double *rec_pos,
+                     double *rec_vel);
+
+/*
+ * Diagnostics in float64 (pair terms too, in every precision mode):
+ * out_host[9] = {E_kin, E_pot, E_tot, P_x, P_y, P_z, F_x, F_y, F_z} with
+ * E_kin = 1/2 sum m|v|^2, E_pot = -G sum_{i<j} m_i m_j / sqrt(r_ij^2+eps^2),
+ * P = sum m v and F = sum m a (zero by Newton's third law).  out_host is
+ * HOST memory; this call synchronises the stream and also reports
+ * NB_ENONFINITE.  The paper reports no diagnostics; these are the standard
+ * conserved quantities of the softened problem.
+ */
+nb_status nb_energy(nb_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                    const double *mass, double G, double eps, double *out_host);
+
+/*
+ * Vector-Jacobian product of the force map (no counterpart in the paper;
+ * derived from the force formula).  With d_kj = x_j - x_k,
+ * s = sqrt(|d|^2+eps^2) and K(d) = I/s^3 - 3 d d^T/s^5:
+ *   grad_pos_k  = G sum_{j != k} K(d_kj) (m_k lam_j - m_j lam_k)
+ *   grad_mass_k = G sum_{i != k} lam_i . (x_k - x_i) / s_ik^3
+ * for lam = grad_acc [n][3] = dL/da.  grad_pos [n][3] and grad_mass [n] are
+ * overwritten.  FP32 modes: float32 pair terms, float64 accumulation.
+ */
+nb_status nb_forces_backward(nb_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                             double G, double eps, const double *grad_acc,
+                             double *grad_pos, double *grad_mass);
+
+/*
+ * Reverse sweep of nsteps leapfrog steps (no counterpart in the paper).
+ * traj [nsteps+1][n][3] holds the positions x_0..x_nsteps of the segment
+ * (from nb_rollout with record_every = 1).  lam_x, lam_v [n][3] hold on entry
+ * the adjoints of the segment's final position and velocity, lam_m [n] the
+ * mass adjoint so far; on return lam_x, lam_v hold the adjoints of the
+ * segment's initial state and lam_m has the segment's contribution ADDED.
+ * Per step, last to first: lam_v += dt lam_x (drift); the two half-kicks
+ * that meet at a position x_s add VJP_F(x_s, dt lam_v) to (lam_x, lam_m).
+ * Flags: NB_BWD_AT_END: traj[nsteps] is the end of the whole run, so its
+ * closing half-kick VJP_F(x, dt/2 lam_v) is applied first; otherwise the
+ * later segment already applied it.  NB_BWD_AT_START: traj[0] is the start
+ * of the run, so the VJP there uses dt/2 instead of dt.  nsteps == 0 is a
+ * no-op.
+ */
+nb_status nb_step_backward(nb_ctx *ctx, int64_t n, const double *traj, const double *mass,
+                           double G, double eps, double dt, int64_t nsteps,
+                           double *lam_x, double *lam_v, double *lam_m, unsigned flags);
+
+/*
+ * Batched independent systems (the paper's dynamic-chunk load balancing,
+ * Sec. V-C / Table VI, applied to (system, i-tile) work items).
+ * nb_batch_plan builds the work queue for nsys systems whose bodies are
+ * concatenated, system k owning bodies [offsets[k], offsets[k+1]); offsets
+ * is HOST memory with nsys + 1 entries, offsets[0] = 0, non-decreasing,
+ * offsets[nsys] <= n_max.  Items are ordered largest cost first.  The plan
+ * stays in the context until the next nb_batch_plan.
+ */
+nb_status nb_batch_plan(nb_ctx *ctx, int64_t nsys, const int64_t *offsets);
+
+/* Forces of every planned system in one persistent launch.  Arrays cover all
+ * offsets[nsys] bodies; bodies of different systems do not interact. */
+nb_status nb_forces_batched(nb_ctx *ctx, const double *pos, const double *mass,
+                            double G, double eps, double *acc);
+
+/* nb_step over every planned system: one persistent force launch per step;
+ * with NB_USE_GRAPH the whole loop is one CUDA graph launch (captured on
+ * first use and cached per argument set). */
+nb_status nb_step_batched(nb_ctx *ctx, double *pos, double *vel, const double *mass,
+                          double G, double eps, double dt, int64_t nsteps, double *acc,
+                          unsigned flags);
+
+/*
+ * Kernel variants and tuning (used by the autotuner).  kind: 0 = force,
+ * 1 = batched force, 2 = force VJP; the variant tables depend on precision.
+ * nb_variant_count -> number of compiled variants (0 if none);
+ * nb_variant_info fills threads per CTA, bodies per thread and j-tile size.
+ * nb_tune_set makes calls with lo <= n < hi use `variant`, with `split`
+ * j-splits across CTAs (0 = chosen by the scheduler); later entries win.
+ * variant < 0 clears the kind's table.  nb_tune_get reports the variant and
+ * split a call with n bodies would use.
+ */
+int nb_variant_count(int kind, nb_precision p);
+nb_status nb_variant_info(int kind, nb_precision p, int variant, int *threads,
+                          int *bodies_per_thread, int *jtile);
+nb_status nb_tune_set(nb_ctx *ctx, int kind, int64_t lo, int64_t hi, int variant, int split);
+nb_status nb_tune_get(nb_ctx *ctx, int kind, int64_t n, int *variant, int *split);
+
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t nb_launch_count(const nb_ctx *ctx);
+
+/*
+ * Kernel timing with CUDA events recorded on the context's stream around
+ * each pair-kernel launch (not inside captured graphs).  nb_profile(ctx, 1)
+ * clears the record and starts recording, nb_profile(ctx, 0) stops.
+ * nb_profile_read synchronises the stream and returns, for `kind`
+ * (0 force, 1 batched force, 2 force VJP, 3 energy), the launches recorded
+ * and their summed duration in milliseconds.
+ */
+nb_status nb_profile(nb_ctx *ctx, int enable);
+nb_status nb_profile_read(nb_ctx *ctx, int kind, int64_t *launches, double *total_ms);
+
+/* Device properties the scheduler uses: SM count, and resident CTAs per SM
+ * of the force kernel a call with n bodies would use. */
+nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm);
+
+/*
+ * Host-only scheduling helpers (no GPU needed; exported for tests).
+ *
+ * nb_choose_split: number of j-splits for n_itiles i-tiles of tile_bodies
+ * bodies over n_jtiles j-tiles on `slots` resident CTAs, maximising
+ * (items / slots) / ceil(items / slots) times a per-item overhead factor,
+ * with nsplit * n_itiles * tile_bodies <= max_split_bodies.
+ *
+ * nb_plan_batch_host: the work items of the batched kernel for CTAs of
+ * `threads` x `bodies_per_thread` bodies and j-tiles of `jtile`, largest
+ * cost first.  items_out holds 8 int32 per item {i0, i_end, j0, j1, lanes,
+ * sys, 0, 0}; returns the item count (items_out may be NULL to count), or -1
+ * for invalid offsets or when more than max_items are needed.
+ */
+int nb_choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots,
+                    int64_t max_split_bodies, int64_t tile_bodies);
+int64_t nb_plan_batch_host(int64_t nsys, const int64_t *offsets, int threads,
+                           int bodies_per_thread, int jtile, int32_t *items_out,
+                           int64_t max_items);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

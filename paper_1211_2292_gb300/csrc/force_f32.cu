@@ -1,0 +1,414 @@
+// float32 softened direct-sum force kernels (paper Sec. IV-A/IV-B: the force
+// calculation, here the exact all-pairs sum):
+//
+//   a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^{3/2},   d_ij = x_j - x_i.
+//
+// Design (sm_103a):
+//  * An i-tile of T*I bodies per CTA; each thread keeps I bodies in
+//    registers, paired into float32x2 lanes so that every pair operation is
+//    one issue slot for two bodies.
+//  * j-bodies stream through a double-buffered shared-memory tile of J
+//    bodies, stored with each component duplicated ((x,x,y,y),(z,z,m,m)) so a
+//    broadcast 128-bit shared load yields the float32x2 operands directly.
+//    The next tile's global loads are issued before the current tile is
+//    consumed.  Out-of-range j slots are zero-mass bodies at the origin.
+//  * Per pair: 3 add, 3 fma (r^2), 1 MUFU rsqrt per body, 3 mul, 3 fma;
+//    12 float32 operations, i.e. 6 float32x2 issues per body.
+//  * NB_FP32_COMP: each tile's float32 partial sum is added into a per-body
+//    Kahan (sum, carry) pair, so rounding grows with the tile count, not
+//    with N.  NB_FP32: one running float32 sum.
+//  * j-split: the grid is (i-tiles x nsplit).  With nsplit > 1, each CTA
+//    stores its float64 partial; the last CTA of an i-tile (arrival counter)
+//    adds the partials in split order (deterministic) and runs the epilogue.
+//    No CTA ever waits for another.
+//  * Epilogue: acc = G*sum in float64, optional fused half-kick
+//    vel += dt/2 * acc, non-finite outputs flagged in the error word.
+#include <cuda_runtime.h>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nb {
+namespace {
+
+constexpr int UNROLL_F32 = 8;
+
+// Final write of one body's acceleration (float64, G applied).
+__device__ __forceinline__ void write_acc(const ForceParams &p, int i, double ax, double ay,
+                                          double az)
+{
+    double *a = p.acc + 3 * (size_t)i;
+    a[0] = ax;
+    a[1] = ay;
+    a[2] = az;
+    if (p.vel) {
+        double *v = p.vel + 3 * (size_t)i;
+        v[0] += p.half_dt * ax;
+        v[1] += p.half_dt * ay;
+        v[2] += p.half_dt * az;
+    }
+    if (!finite3(ax, ay, az)) atomicOr(p.err, ERR_NONFINITE);
+}
+
+// Interaction of one body pair-lane set with j-body (xj,yj,zj,mj) given as
+// duplicated float32x2 values.  nx/ny/nz hold the NEGATED i positions.
+template <bool ZEPS>
+__device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float2 mj, float2 e2,
+                                          float2 nx, float2 ny, float2 nz, float2 &ax, float2 &ay,
+                                          float2 &az)
+{
+    float2 dx = add2(xj, nx);
+    float2 dy = add2(yj, ny);
+    float2 dz = add2(zj, nz);
+    float2 r2 = fma2(dx, dx, e2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float2 ri;
+    ri.x = rsqrt_mufu(r2.x);
+    ri.y = rsqrt_mufu(r2.y);
+    if (ZEPS) {  // eps == 0: the self pair (r^2 == 0) must contribute nothing
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    float2 ri2 = mul2(ri, ri);
+    float2 mri = mul2(mj, ri);
+    float2 s = mul2(ri2, mri);
+    ax = fma2(dx, s, ax);
+    ay = fma2(dy, s, ay);
+    az = fma2(dz, s, az);
+}
+
+// Stage J float4 bodies (this thread's share held in `buf`) into a
+// duplicated shared tile.
+template <int T, int J>
+__device__ __forceinline__ void stage_store(float4 *tile, const float4 (&buf)[J / T])
+{
+#pragma unroll
+    for (int l = 0; l < J / T; ++l) {
+        const int jj = l * T + threadIdx.x;
+        const float4 b = buf[l];
+        tile[2 * jj] = make_float4(b.x, b.x, b.y, b.y);
+        tile[2 * jj + 1] = make_float4(b.z, b.z, b.w, b.w);
+    }
+}
+
+template <int T, int J>
+__device__ __forceinline__ void stage_load(float4 (&buf)[J / T], const float4 *__restrict__ P,
+                                           int jbase, int jend)
+{
+#pragma unroll
+    for (int l = 0; l < J / T; ++l) {
+        const int j = jbase + l * T + threadIdx.x;
+        buf[l] = j < jend ? __ldg(P + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Accumulator state for the I bodies of one thread.
+template <int I, bool COMP>
+struct Acc {
+    static constexpr int NP = I / 2;
+    float2 ax[NP], ay[NP], az[NP];
+    float sx[COMP ? I : 1], sy[COMP ? I : 1], sz[COMP ? I : 1];
+    float cx[COMP ? I : 1], cy[COMP ? I : 1], cz[COMP ? I : 1];
+
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
+        if (COMP) {
+#pragma unroll
+            for (int k = 0; k < I; ++k) sx[k] = sy[k] = sz[k] = cx[k] = cy[k] = cz[k] = 0.f;
+        }
+    }
+    // End of a j-tile: fold the tile partial into the compensated sums.
+    __device__ __forceinline__ void end_tile()
+    {
+        if (COMP) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                kahan_add(sx[2 * p], cx[2 * p], ax[p].x);
+                kahan_add(sx[2 * p + 1], cx[2 * p + 1], ax[p].y);
+                kahan_add(sy[2 * p], cy[2 * p], ay[p].x);
+                kahan_add(sy[2 * p + 1], cy[2 * p + 1], ay[p].y);
+                kahan_add(sz[2 * p], cz[2 * p], az[p].x);
+                kahan_add(sz[2 * p + 1], cz[2 * p + 1], az[p].y);
+                ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    // Value of body k's sum, component c, in float64.
+    __device__ __forceinline__ void get(int k, double &x, double &y, double &z) const
+    {
+        if (COMP) {
+            x = (double)sx[k] - (double)cx[k];
+            y = (double)sy[k] - (double)cy[k];
+            z = (double)sz[k] - (double)cz[k];
+        } else {
+            const int p = k >> 1;
+            x = (k & 1) ? ax[p].y : ax[p].x;
+            y = (k & 1) ? ay[p].y : ay[p].x;
+            z = (k & 1) ? az[p].y : az[p].x;
+        }
+    }
+};
+
+// Sweep the j-tiles [t0, t1) of bodies [jlo, jhi) (tile t starts at
+// jlo + t*J) for this thread's bodies.  Threads split each tile's j loop in
+// `lanes` interleaved parts (lanes == 1 for the solo kernel).
+template <int T, int I, int J, bool COMP, bool ZEPS, bool LANES>
+__device__ __forceinline__ void sweep(const float4 *__restrict__ P, int jlo, int jhi, int t0,
+                                      int t1, int lane, int lanes, float2 e2,
+                                      const float2 (&nx)[I / 2], const float2 (&ny)[I / 2],
+                                      const float2 (&nz)[I / 2], Acc<I, COMP> &acc,
+                                      float4 (*tile)[2 * J])
+{
+    constexpr int NP = I / 2;
+    float4 buf[J / T];
+    if (t0 < t1) {
+        stage_load<T, J>(buf, P, jlo + t0 * J, jhi);
+        stage_store<T, J>(tile[0], buf);
+    }
+    __syncthreads();
+    for (int t = t0; t < t1; ++t) {
+        const int b = (t - t0) & 1;
+        if (t + 1 < t1) stage_load<T, J>(buf, P, jlo + (t + 1) * J, jhi);
+        const float4 *s = tile[b];
+        if (LANES) {
+#pragma unroll 4
+            for (int jj = lane; jj < J; jj += lanes) {
+                const float4 q0 = s[2 * jj], q1 = s[2 * jj + 1];
+                const float2 xj = make_float2(q0.x, q0.y), yj = make_float2(q0.z, q0.w);
+                const float2 zj = make_float2(q1.x, q1.y), mj = make_float2(q1.z, q1.w);
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    interact2<ZEPS>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p], acc.ay[p],
+                                    acc.az[p]);
+            }
+        } else {
+#pragma unroll UNROLL_F32
+            for (int jj = 0; jj < J; ++jj) {
+                const float4 q0 = s[2 * jj], q1 = s[2 * jj + 1];
+                const float2 xj = make_float2(q0.x, q0.y), yj = make_float2(q0.z, q0.w);
+                const float2 zj = make_float2(q1.x, q1.y), mj = make_float2(q1.z, q1.w);
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    interact2<ZEPS>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p], acc.ay[p],
+                                    acc.az[p]);
+            }
+        }
+        acc.end_tile();
+        if (t + 1 < t1) stage_store<T, J>(tile[b ^ 1], buf);
+        __syncthreads();
+    }
+}
+
+// Load this thread's i-bodies (negated positions, paired).  Body k of the
+// thread is `first + k*stride`; bodies at or past `end` read as the origin.
+template <int I>
+__device__ __forceinline__ void load_i(const float4 *__restrict__ P, int first, int stride, int end,
+                                       float2 (&nx)[I / 2], float2 (&ny)[I / 2],
+                                       float2 (&nz)[I / 2])
+{
+#pragma unroll
+    for (int p = 0; p < I / 2; ++p) {
+        const int ia = first + (2 * p) * stride, ib = first + (2 * p + 1) * stride;
+        const float4 a = ia < end ? __ldg(P + ia) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = ib < end ? __ldg(P + ib) : make_float4(0.f, 0.f, 0.f, 0.f);
+        nx[p] = make_float2(-a.x, -b.x);
+        ny[p] = make_float2(-a.y, -b.y);
+        nz[p] = make_float2(-a.z, -b.z);
+    }
+}
+
+// -------------------------------------------------------------- solo kernel
+template <int T, int I, int J, bool COMP, bool ZEPS>
+__global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
+{
+    static_assert(I % 2 == 0 && J % T == 0, "bad tile shape");
+    constexpr int TILE_I = T * I;
+    __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ int s_last;
+
+    const float4 *P = static_cast<const float4 *>(p.P);
+    const int n = p.n;
+    const int n_itiles = (n + TILE_I - 1) / TILE_I;
+    const int it = blockIdx.x % n_itiles;
+    const int js = blockIdx.x / n_itiles;
+    const int i0 = it * TILE_I;
+    int t0, t1;
+    split_range((n + J - 1) / J, p.nsplit, js, t0, t1);
+
+    float2 nx[I / 2], ny[I / 2], nz[I / 2];
+    load_i<I>(P, i0 + threadIdx.x, T, n, nx, ny, nz);
+    Acc<I, COMP> acc;
+    acc.init();
+    const float2 e2 = make_float2(p.eps2f, p.eps2f);
+    sweep<T, I, J, COMP, ZEPS, false>(P, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
+
+    if (p.nsplit == 1) {
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int i = i0 + threadIdx.x + k * T;
+            if (i < n) {
+                double x, y, z;
+                acc.get(k, x, y, z);
+                write_acc(p, i, p.G * x, p.G * y, p.G * z);
+            }
+        }
+        return;
+    }
+    // Split: publish this CTA's partial, the last arriving CTA combines.
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        const int i = i0 + threadIdx.x + k * T;
+        if (i < n) {
+            double x, y, z;
+            acc.get(k, x, y, z);
+            double *q = p.partial + ((size_t)js * n + i) * 3;
+            q[0] = x;
+            q[1] = y;
+            q[2] = z;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(p.counters + it, 1u) == (unsigned)(p.nsplit - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        const int i = i0 + threadIdx.x + k * T;
+        if (i < n) {
+            double x = 0.0, y = 0.0, z = 0.0;
+            for (int q = 0; q < p.nsplit; ++q) {
+                const double *r = p.partial + ((size_t)q * n + i) * 3;
+                x += __ldcg(r);
+                y += __ldcg(r + 1);
+                z += __ldcg(r + 2);
+            }
+            write_acc(p, i, p.G * x, p.G * y, p.G * z);
+        }
+    }
+    if (threadIdx.x == 0) p.counters[it] = 0u;
+}
+
+// ----------------------------------------------------------- batched kernel
+// Persistent: each CTA pops items (largest cost first) from an atomic
+// counter until the queue is empty, the GPU analogue of the paper's dynamic
+// loop schedule (Sec. V-C, Table VI).  The last CTA to finish resets the
+// counters for the next launch; nothing waits.
+template <int T, int I, int J, bool COMP, bool ZEPS>
+__global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams p)
+{
+    __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ BatchItem s_item;
+    __shared__ int s_idx;
+    const float2 e2 = make_float2(p.eps2f, p.eps2f);
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int q = (int)atomicAdd(p.queue, 1u);
+            s_idx = q;
+            if (q < p.n_items) s_item = p.items[q];
+        }
+        __syncthreads();
+        if (s_idx >= p.n_items) break;
+        const BatchItem it = s_item;
+        __syncthreads();  // everyone has read s_item before thread 0 may overwrite it
+
+        const int lanes = it.lanes;
+        const int lane = threadIdx.x & (lanes - 1);
+        const int group = threadIdx.x / lanes;
+        const int groups = T / lanes;
+        float2 nx[I / 2], ny[I / 2], nz[I / 2];
+        load_i<I>(p.P, it.i0 + group, groups, it.i_end, nx, ny, nz);
+        Acc<I, COMP> acc;
+        acc.init();
+        const int ntiles = (it.j1 - it.j0 + J - 1) / J;
+        if (lanes == 1)
+            sweep<T, I, J, COMP, ZEPS, false>(p.P, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx, ny, nz,
+                                              acc, tile);
+        else
+            sweep<T, I, J, COMP, ZEPS, true>(p.P, it.j0, it.j1, 0, ntiles, lane, lanes, e2, nx, ny,
+                                             nz, acc, tile);
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            double x, y, z;
+            acc.get(k, x, y, z);
+            // lanes of a group are adjacent in one warp: butterfly sum
+            for (int off = lanes >> 1; off > 0; off >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, off);
+                y += __shfl_xor_sync(0xffffffffu, y, off);
+                z += __shfl_xor_sync(0xffffffffu, z, off);
+            }
+            const int i = it.i0 + group + k * groups;
+            if (lane == 0 && i < it.i_end) {
+                double *a = p.acc + 3 * (size_t)i;
+                const double gx = p.G * x, gy = p.G * y, gz = p.G * z;
+                a[0] = gx;
+                a[1] = gy;
+                a[2] = gz;
+                if (p.vel) {
+                    double *v = p.vel + 3 * (size_t)i;
+                    v[0] += p.half_dt * gx;
+                    v[1] += p.half_dt * gy;
+                    v[2] += p.half_dt * gz;
+                }
+                if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(p.queue + 1, 1u) == gridDim.x - 1) {
+            p.queue[0] = 0u;
+            p.queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+#define NB_F32_ENTRY(T, I, J)                                                           \
+    {{{T, I, J, (const void *)force_f32_kernel<T, I, J, false, false>},                 \
+      {T, I, J, (const void *)force_f32_kernel<T, I, J, false, true>}},                 \
+     {{T, I, J, (const void *)force_f32_kernel<T, I, J, true, false>},                  \
+      {T, I, J, (const void *)force_f32_kernel<T, I, J, true, true>}}}
+
+#define NB_F32B_ENTRY(T, I, J)                                                          \
+    {{{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, false>},         \
+      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, true>}},         \
+     {{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, false>},          \
+      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, true>}}}
+
+typedef KernelEntry Quad[2][2];
+
+const Quad kForce[] = {
+    NB_F32_ENTRY(128, 4, 128),
+    NB_F32_ENTRY(256, 4, 256),
+    NB_F32_ENTRY(128, 8, 128),
+    NB_F32_ENTRY(256, 2, 256),
+    NB_F32_ENTRY(64, 8, 128),
+    NB_F32_ENTRY(128, 6, 256),
+    NB_F32_ENTRY(256, 8, 256),
+    NB_F32_ENTRY(128, 2, 256),
+};
+
+const Quad kBatched[] = {
+    NB_F32B_ENTRY(128, 2, 128),
+    NB_F32B_ENTRY(128, 4, 128),
+    NB_F32B_ENTRY(256, 2, 256),
+    NB_F32B_ENTRY(64, 4, 128),
+};
+
+}  // namespace
+
+int f32_force_variants() { return (int)(sizeof(kForce) / sizeof(kForce[0])); }
+const KernelEntry &f32_force_kernel(int v, bool comp, bool zeps) { return kForce[v][comp][zeps]; }
+int f32_batched_variants() { return (int)(sizeof(kBatched) / sizeof(kBatched[0])); }
+const KernelEntry &f32_batched_kernel(int v, bool comp, bool zeps)
+{
+    return kBatched[v][comp][zeps];
+}
+
+}  // namespace nb

@@ -1,0 +1,180 @@
+// Internal declarations shared by the CUDA translation units and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "nbody.h"
+
+namespace nb {
+
+// Kernel families with autotuned variants (the `kind` of nb_variant_*).
+enum Kind : int { KIND_FORCE = 0, KIND_BATCHED = 1, KIND_VJP = 2, KIND_COUNT = 3 };
+
+// One compiled kernel: CTA shape plus the function to launch.  Every kernel
+// of a family takes a single by-value parameter struct.
+struct KernelEntry {
+    int T;   // threads per CTA
+    int I;   // i-bodies per thread
+    int J;   // j-bodies per shared-memory tile
+    const void *fn;
+};
+
+// -------------------------------------------------------------- parameters
+struct ForceParams {
+    const void *P;        // packed bodies: float4 (x,y,z,m) or double4
+    int n;                // bodies
+    int nsplit;           // j-splits across CTAs (grid = i-tiles * nsplit)
+    float eps2f;          // eps^2 in float32
+    double eps2;          // eps^2 in float64
+    double G;
+    double *acc;          // out [n][3]
+    double *vel;          // optional fused half-kick: vel += half_dt * acc
+    double half_dt;
+    double *partial;      // [nsplit][n][3] split partial sums (nsplit > 1)
+    unsigned *counters;   // per-i-tile arrival counters, zero between launches
+    int *err;             // error word
+};
+
+// One work item of the batched kernel: bodies [i0, i_end) of one system
+// (i_end clipped to the item), interacting with bodies [j0, j1) of the same
+// system, `lanes` threads splitting the j loop of each body.
+struct BatchItem {
+    int i0, i_end, j0, j1;
+    int lanes, sys, pad0, pad1;
+};
+
+struct BatchParams {
+    const float4 *P;
+    const BatchItem *items;
+    int n_items;
+    unsigned *queue;      // [0] next item, [1] CTAs done; both zero between launches
+    float eps2f;
+    double G;
+    double *acc;
+    double *vel;
+    double half_dt;
+    int *err;
+};
+
+struct VjpParams {
+    const void *PV;       // packed (x,y,z,m),(mu_x,mu_y,mu_z,0) per body, float or double
+    int n;
+    int nsplit;
+    float eps2f;
+    double eps2;
+    double G;
+    double *gx;           // [n][3]
+    double *gm;           // [n]
+    int accumulate;       // 0: overwrite gx/gm with G*sum; 1: add G*sum
+    double *partial;      // [nsplit][n][4]
+    unsigned *counters;
+    int *err;
+};
+
+struct EnergyParams {
+    const double4 *P;     // packed float64 bodies
+    const double *vel;    // [n][3]
+    int n;
+    int nsplit;
+    double eps2;
+    double *red;          // [grid][8] per-CTA partial sums
+    int *err;
+};
+
+// ----------------------------------------------------------- kernel tables
+// Defined in force_f32.cu / force_f64.cu / adjoint.cu.  Index [variant][comp][zero_eps].
+int f32_force_variants();
+const KernelEntry &f32_force_kernel(int variant, bool comp, bool zeps);
+int f32_batched_variants();
+const KernelEntry &f32_batched_kernel(int variant, bool comp, bool zeps);
+int f64_force_variants();
+const KernelEntry &f64_force_kernel(int variant, bool zeps);
+const KernelEntry &f64_energy_kernel(bool zeps);
+int f32_vjp_variants();
+const KernelEntry &f32_vjp_kernel(int variant, bool zeps);
+int f64_vjp_variants();
+const KernelEntry &f64_vjp_kernel(int variant, bool zeps);
+
+// ------------------------------------------------- O(n) kernels (integrate.cu)
+cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
+cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const double *mass, double4 *P);
+// v += half_dt a; x += dt v; repack.  Records (x, v) before the update when rec_* is set.
+cudaError_t launch_kdp(cudaStream_t s, bool f64, int n, double *pos, double *vel, const double *acc,
+                       const double *mass, double half_dt, double dt, void *P, double *rec_pos,
+                       double *rec_vel);
+// Adjoint packing: lam_v += drift * lam_x (if lam_x), mu = coef * lam_v, pack (x, m, mu).
+cudaError_t launch_pack_vjp(cudaStream_t s, bool f64, int n, const double *pos, const double *mass,
+                            const double *lam, double *lam_v, const double *lam_x, double drift,
+                            double coef, void *PV);
+cudaError_t launch_energy_final(cudaStream_t s, const double *red, int nparts, double G, double *out);
+
+// Host-side scheduling helpers (nbody_abi.cpp; exported for tests).
+int choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots, int64_t max_split_bodies,
+                 int64_t tile_bodies);
+
+}  // namespace nb
+
+// ------------------------------------------------------------------ context
+struct nb_ctx {
+    int device = 0;
+    int num_sms = 0;
+    nb_precision prec = NB_FP64;
+    int64_t n_max = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t cap_stream = nullptr;  // library stream used for graph capture/launch
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+    // scratch
+    void *pack = nullptr;        // packed bodies (force/energy/VJP)
+    size_t pack_bytes = 0;
+    double *partial = nullptr;   // split partials
+    int64_t partial_bodies = 0;  // capacity in body-splits (4 doubles each)
+    unsigned *counters = nullptr;
+    int64_t n_counters = 0;
+    double *red = nullptr;       // energy per-CTA partials
+    int64_t n_red = 0;           // capacity in CTAs
+    double *dev_out = nullptr;   // 16 doubles
+    double *host_out = nullptr;  // pinned, 16 doubles
+    int *err = nullptr;
+    unsigned *queue = nullptr;   // batched queue counters [2]
+
+    // batched plan
+    nb::BatchItem *items = nullptr;
+    int64_t n_items = 0, items_cap = 0;
+    int batch_variant = 0;
+    int64_t batch_n = 0;         // bodies covered by the plan
+    int64_t batch_nsys = 0;
+    uint64_t plan_gen = 0;
+
+    // tuning: per kind, list of (lo, hi, variant, split)
+    struct TuneEntry { int64_t lo, hi; int variant, split; };
+    std::vector<TuneEntry> tune[nb::KIND_COUNT];
+
+    // graph cache for nb_step_batched
+    struct GraphKey {
+        int kind;  // 0: nb_rollout, 1: nb_step_batched
+        const void *pos, *vel, *mass, *acc, *rec_pos, *rec_vel;
+        double G, eps, dt;
+        int64_t n, nsteps, every;
+        unsigned flags;
+        uint64_t plan_gen;
+        bool operator<(const GraphKey &o) const;
+    };
+    struct GraphVal { cudaGraphExec_t exec; int64_t kernels; };
+    std::map<GraphKey, GraphVal> graphs;
+
+    std::map<const void *, int> occ;  // resident CTAs per SM, per kernel
+
+    // event timing of pair-kernel launches (nb_profile)
+    bool prof_on = false;
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof;          // recorded launches
+    std::vector<cudaEvent_t> ev_pool;   // free events
+    int64_t launches = 0;
+    std::string last_error;
+};

@@ -1,0 +1,994 @@
+// C ABI of libnbody.so (declared in include/nbody.h): argument checking,
+// scratch ownership, kernel selection and split scheduling, the leapfrog
+// loop, graph capture and the batched work queue.  Host code only; the
+// arithmetic lives in the .cu files.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "nb_internal.h"
+
+using nb::BatchItem;
+using nb::KernelEntry;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+nb_status failf(nb_ctx *c, nb_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->last_error = buf;
+    else
+        g_create_error = buf;
+    return s;
+}
+
+#define NB_CUDA(ctx, call)                                                                     \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return failf(ctx, NB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+#define NB_TRY(expr)                       \
+    do {                                   \
+        nb_status s_ = (expr);             \
+        if (s_ != NB_OK) return s_;        \
+    } while (0)
+
+// Makes ctx->device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// ----------------------------------------------------------- pointer checks
+typedef CUresult (*PfnGetAddressRange)(CUdeviceptr *, size_t *, CUdeviceptr);
+
+PfnGetAddressRange address_range_fn()
+{
+    static PfnGetAddressRange fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 3020, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PfnGetAddressRange)p;
+    }();
+    return fn;
+}
+
+// A device array of `bytes` bytes: non-null, 8-byte aligned, device (or
+// managed) memory of the context's device, lying inside one allocation.
+nb_status check_dev(nb_ctx *c, const void *p, size_t bytes, const char *name)
+{
+    if (bytes == 0) return NB_OK;
+    if (!p) return failf(c, NB_EINVAL, "%s is NULL", name);
+    if ((uintptr_t)p % 8) return failf(c, NB_EINVAL, "%s is not 8-byte aligned", name);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return failf(c, NB_EINVAL, "%s is not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return failf(c, NB_EINVAL, "%s is not device memory", name);
+    if (a.type == cudaMemoryTypeDevice && a.device != c->device)
+        return failf(c, NB_EINVAL, "%s is on device %d, context on %d", name, a.device, c->device);
+    if (PfnGetAddressRange f = address_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (f(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
+            if ((uintptr_t)p + bytes > (uintptr_t)base + size)
+                return failf(c, NB_EINVAL, "%s: %zu bytes do not fit in its allocation", name,
+                             bytes);
+        }
+    }
+    return NB_OK;
+}
+
+nb_status check_scalars(nb_ctx *c, double G, double eps)
+{
+    if (!std::isfinite(G)) return failf(c, NB_EINVAL, "G is not finite");
+    if (!std::isfinite(eps) || eps < 0) return failf(c, NB_EINVAL, "eps must be finite and >= 0");
+    return NB_OK;
+}
+
+nb_status check_n(nb_ctx *c, int64_t n)
+{
+    if (n < 0 || n > c->n_max)
+        return failf(c, NB_EINVAL, "n = %lld outside [0, n_max = %lld]", (long long)n,
+                     (long long)c->n_max);
+    return NB_OK;
+}
+
+// ----------------------------------------------------------- kernel choice
+bool is_f64(const nb_ctx *c) { return c->prec == NB_FP64; }
+
+int variant_count(int kind, nb_precision p)
+{
+    switch (kind) {
+    case nb::KIND_FORCE: return p == NB_FP64 ? nb::f64_force_variants() : nb::f32_force_variants();
+    case nb::KIND_BATCHED: return p == NB_FP64 ? 0 : nb::f32_batched_variants();
+    case nb::KIND_VJP: return p == NB_FP64 ? nb::f64_vjp_variants() : nb::f32_vjp_variants();
+    default: return 0;
+    }
+}
+
+const KernelEntry &kernel_for(int kind, nb_precision p, int v, bool zeps)
+{
+    const bool comp = p == NB_FP32_COMP;
+    switch (kind) {
+    case nb::KIND_FORCE:
+        return p == NB_FP64 ? nb::f64_force_kernel(v, zeps) : nb::f32_force_kernel(v, comp, zeps);
+    case nb::KIND_BATCHED: return nb::f32_batched_kernel(v, comp, zeps);
+    default: return p == NB_FP64 ? nb::f64_vjp_kernel(v, zeps) : nb::f32_vjp_kernel(v, zeps);
+    }
+}
+
+// Untuned defaults.
+int default_variant(int kind, nb_precision p, int64_t n)
+{
+    (void)n;
+    if (kind == nb::KIND_FORCE) return p == NB_FP64 ? 0 : 0;
+    return 0;
+}
+
+void pick(nb_ctx *c, int kind, int64_t n, int &variant, int &split)
+{
+    variant = default_variant(kind, c->prec, n);
+    split = 0;
+    for (const auto &e : c->tune[kind])
+        if (n >= e.lo && n < e.hi) {
+            variant = e.variant;
+            split = e.split;
+        }
+}
+
+int occupancy(nb_ctx *c, const KernelEntry &k)
+{
+    auto it = c->occ.find(k.fn);
+    if (it != c->occ.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, k.T, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    nb = nb < 1 ? 1 : nb;
+    c->occ[k.fn] = nb;
+    return nb;
+}
+
+cudaEvent_t pooled_event(nb_ctx *c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Launch a pair kernel; `kind` tags its event timing (nb_profile).
+nb_status launch(nb_ctx *c, const KernelEntry &k, int64_t grid, void *params, cudaStream_t s,
+                 int kind)
+{
+    if (grid <= 0) return NB_OK;
+    if (grid > 0x7fffffffLL) return failf(c, NB_EINVAL, "grid of %lld CTAs too large", (long long)grid);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    const bool timed = c->prof_on && cs == cudaStreamCaptureStatusNone;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (timed) {
+        ea = pooled_event(c);
+        eb = pooled_event(c);
+        if (ea && eb) NB_CUDA(c, cudaEventRecord(ea, s));
+    }
+    void *args[] = {params};
+    NB_CUDA(c, cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(k.T), args, 0, s));
+    c->launches++;
+    if (timed && ea && eb) {
+        NB_CUDA(c, cudaEventRecord(eb, s));
+        c->prof.push_back({kind, ea, eb});
+    }
+    return NB_OK;
+}
+
+#define NB_LAUNCHED(ctx, expr)     \
+    do {                           \
+        NB_CUDA(ctx, (expr));      \
+        (ctx)->launches++;         \
+    } while (0)
+
+// Number of j-splits for a pair kernel over n bodies (see nb_choose_split).
+int splits_for(nb_ctx *c, const KernelEntry &k, int64_t n, int forced, int64_t per_split_doubles)
+{
+    const int64_t tile = (int64_t)k.T * k.I;
+    const int64_t n_itiles = (n + tile - 1) / tile;
+    const int64_t n_jtiles = (n + k.J - 1) / k.J;
+    const int64_t cap = c->partial_bodies * 4 / per_split_doubles;  // body-splits that fit
+    int s;
+    if (forced > 0)
+        s = (int)std::min<int64_t>(forced, n_jtiles);
+    else
+        s = nb::choose_split(n_itiles, n_jtiles, (int64_t)c->num_sms * occupancy(c, k), cap, tile);
+    while (s > 1 && (int64_t)s * n > cap) --s;
+    if (s > 1 && n_itiles > c->n_counters) s = 1;
+    return s < 1 ? 1 : s;
+}
+
+// ------------------------------------------------------------- force paths
+// Force on the already packed bodies; optional fused half-kick of vel.
+nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double eps, double *acc,
+                       double *vel, double half_dt)
+{
+    if (n == 0) return NB_OK;
+    const bool zeps = eps == 0.0;
+    int v, forced;
+    pick(c, nb::KIND_FORCE, n, v, forced);
+    const KernelEntry &k = kernel_for(nb::KIND_FORCE, c->prec, v, zeps);
+    const int S = splits_for(c, k, n, forced, 3);
+    nb::ForceParams p;
+    p.P = c->pack;
+    p.n = (int)n;
+    p.nsplit = S;
+    p.eps2f = (float)(eps * eps);
+    p.eps2 = eps * eps;
+    p.G = G;
+    p.acc = acc;
+    p.vel = vel;
+    p.half_dt = half_dt;
+    p.partial = c->partial;
+    p.counters = c->counters;
+    p.err = c->err;
+    const int64_t tile = (int64_t)k.T * k.I;
+    return launch(c, k, (n + tile - 1) / tile * S, &p, s, 0);
+}
+
+nb_status pack(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos, const double *mass)
+{
+    if (n == 0) return NB_OK;
+    if (is_f64(c))
+        NB_LAUNCHED(c, nb::launch_pack_f64(s, (int)n, pos, mass, (double4 *)c->pack));
+    else
+        NB_LAUNCHED(c, nb::launch_pack_f32(s, (int)n, pos, mass, (float4 *)c->pack));
+    return NB_OK;
+}
+
+// Forward leapfrog loop (shared by nb_step, nb_rollout and the graph body).
+nb_status rollout_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, double *vel,
+                          const double *mass, double G, double eps, double dt, int64_t nsteps,
+                          double *acc, unsigned flags, int64_t every, double *rec_pos,
+                          double *rec_vel)
+{
+    if (n == 0) return NB_OK;
+    if (!(flags & NB_ACC_VALID)) {
+        NB_TRY(pack(c, s, n, pos, mass));
+        NB_TRY(force_packed(c, s, n, G, eps, acc, nullptr, 0.0));
+    }
+    const size_t rec = (size_t)n * 3;
+    for (int64_t st = 0; st < nsteps; ++st) {
+        double *rp = nullptr, *rv = nullptr;
+        if (every > 0 && st % every == 0) {
+            rp = rec_pos + rec * (size_t)(st / every);
+            rv = rec_vel ? rec_vel + rec * (size_t)(st / every) : nullptr;
+        }
+        NB_LAUNCHED(c, nb::launch_kdp(s, is_f64(c), (int)n, pos, vel, acc, mass, 0.5 * dt, dt,
+                                      c->pack, rp, rv));
+        NB_TRY(force_packed(c, s, n, G, eps, acc, vel, 0.5 * dt));
+    }
+    if (every > 0 && nsteps % every == 0) {
+        const size_t r = (size_t)(nsteps / every);
+        NB_CUDA(c, cudaMemcpyAsync(rec_pos + rec * r, pos, rec * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
+        if (rec_vel)
+            NB_CUDA(c, cudaMemcpyAsync(rec_vel + rec * r, vel, rec * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+    }
+    return NB_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+nb_status vjp_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double eps, double *gx,
+                     double *gm, int accumulate)
+{
+    if (n == 0) return NB_OK;
+    const bool zeps = eps == 0.0;
+    int v, forced;
+    pick(c, nb::KIND_VJP, n, v, forced);
+    const KernelEntry &k = kernel_for(nb::KIND_VJP, c->prec, v, zeps);
+    const int S = splits_for(c, k, n, forced, 4);
+    nb::VjpParams p;
+    p.PV = c->pack;
+    p.n = (int)n;
+    p.nsplit = S;
+    p.eps2f = (float)(eps * eps);
+    p.eps2 = eps * eps;
+    p.G = G;
+    p.gx = gx;
+    p.gm = gm;
+    p.accumulate = accumulate;
+    p.partial = c->partial;
+    p.counters = c->counters;
+    p.err = c->err;
+    const int64_t tile = (int64_t)k.T * k.I;
+    return launch(c, k, (n + tile - 1) / tile * S, &p, s, 2);
+}
+
+// ------------------------------------------------------------------ batched
+nb_status batched_force(nb_ctx *c, cudaStream_t s, double G, double eps, double *acc, double *vel,
+                        double half_dt)
+{
+    if (c->n_items == 0) return NB_OK;
+    const KernelEntry &k = kernel_for(nb::KIND_BATCHED, c->prec, c->batch_variant, eps == 0.0);
+    const int64_t slots = (int64_t)c->num_sms * occupancy(c, k);
+    nb::BatchParams p;
+    p.P = (const float4 *)c->pack;
+    p.items = c->items;
+    p.n_items = (int)c->n_items;
+    p.queue = c->queue;
+    p.eps2f = (float)(eps * eps);
+    p.G = G;
+    p.acc = acc;
+    p.vel = vel;
+    p.half_dt = half_dt;
+    p.err = c->err;
+    return launch(c, k, std::min<int64_t>(slots, c->n_items), &p, s, 1);
+}
+
+nb_status batched_enqueue(nb_ctx *c, cudaStream_t s, double *pos, double *vel, const double *mass,
+                          double G, double eps, double dt, int64_t nsteps, double *acc,
+                          unsigned flags)
+{
+    const int64_t n = c->batch_n;
+    if (n == 0) return NB_OK;
+    if (!(flags & NB_ACC_VALID)) {
+        NB_TRY(pack(c, s, n, pos, mass));
+        NB_TRY(batched_force(c, s, G, eps, acc, nullptr, 0.0));
+    }
+    for (int64_t st = 0; st < nsteps; ++st) {
+        NB_LAUNCHED(c, nb::launch_kdp(s, false, (int)n, pos, vel, acc, mass, 0.5 * dt, dt, c->pack,
+                                      nullptr, nullptr));
+        NB_TRY(batched_force(c, s, G, eps, acc, vel, 0.5 * dt));
+    }
+    return NB_OK;
+}
+
+// ------------------------------------------------------------ graph capture
+// Runs `body` captured once as a CUDA graph on the library's capture stream,
+// ordered after prior work on the caller's stream (events both ways).
+nb_status run_graph(nb_ctx *c, const nb_ctx::GraphKey &key,
+                    const std::function<nb_status(cudaStream_t)> &body)
+{
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        const int64_t saved = c->launches;
+        NB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        nb_status st = body(c->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        const int64_t kernels = c->launches - saved;
+        c->launches = saved;
+        if (st != NB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return failf(c, NB_ECUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess)
+            return failf(c, NB_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+        it = c->graphs.emplace(key, nb_ctx::GraphVal{ex, kernels}).first;
+    }
+    NB_CUDA(c, cudaEventRecord(c->ev_in, c->stream));
+    NB_CUDA(c, cudaStreamWaitEvent(c->cap_stream, c->ev_in, 0));
+    NB_CUDA(c, cudaGraphLaunch(it->second.exec, c->cap_stream));
+    NB_CUDA(c, cudaEventRecord(c->ev_out, c->cap_stream));
+    NB_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+    c->launches += it->second.kernels;
+    return NB_OK;
+}
+
+void drop_graphs(nb_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+}
+
+template <typename T>
+T *dev_alloc(nb_ctx *c, size_t count, nb_status &st)
+{
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        st = failf(c, NB_ENOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+        return nullptr;
+    }
+    return (T *)p;
+}
+
+void free_ctx(nb_ctx *c)
+{
+    drop_graphs(c);
+    for (auto &r : c->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    cudaFree(c->pack);
+    cudaFree(c->partial);
+    cudaFree(c->counters);
+    cudaFree(c->red);
+    cudaFree(c->dev_out);
+    cudaFree(c->err);
+    cudaFree(c->queue);
+    cudaFree(c->items);
+    if (c->host_out) cudaFreeHost(c->host_out);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    delete c;
+}
+
+int min_tile_bodies()
+{
+    int m = 1 << 30;
+    const nb_precision ps[] = {NB_FP64, NB_FP32, NB_FP32_COMP};
+    for (nb_precision p : ps)
+        for (int kind = 0; kind < nb::KIND_COUNT; ++kind)
+            for (int v = 0; v < variant_count(kind, p); ++v) {
+                const KernelEntry &k = kernel_for(kind, p, v, false);
+                m = std::min(m, k.T * k.I);
+            }
+    return std::max(m, 1);
+}
+
+}  // namespace
+
+bool nb_ctx::GraphKey::operator<(const GraphKey &o) const
+{
+    return std::tie(kind, pos, vel, mass, acc, rec_pos, rec_vel, G, eps, dt, n, nsteps, every,
+                    flags, plan_gen) <
+           std::tie(o.kind, o.pos, o.vel, o.mass, o.acc, o.rec_pos, o.rec_vel, o.G, o.eps, o.dt,
+                    o.n, o.nsteps, o.every, o.flags, o.plan_gen);
+}
+
+namespace nb {
+
+int choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots, int64_t max_split_bodies,
+                 int64_t tile_bodies)
+{
+    if (n_itiles <= 0 || n_jtiles <= 0 || slots <= 0) return 1;
+    auto score = [&](int64_t s) {
+        const double items = (double)(n_itiles * s);
+        const double waves = items / (double)slots;
+        const double q = waves / std::ceil(waves);
+        const double per_item = (double)n_jtiles / (double)s;  // j-tiles per item
+        return q * per_item / (per_item + 1.0);
+    };
+    int64_t best_s = 1;
+    double best = score(1);
+    const int64_t smax = std::min<int64_t>(n_jtiles, 256);
+    for (int64_t s = 2; s <= smax; ++s) {
+        if (s * n_itiles * tile_bodies > max_split_bodies) break;
+        const double sc = score(s);
+        if (sc > best * 1.002) {
+            best = sc;
+            best_s = s;
+        }
+    }
+    return (int)best_s;
+}
+
+}  // namespace nb
+
+// ====================================================================== ABI
+extern "C" {
+
+int nb_choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots, int64_t max_split_bodies,
+                    int64_t tile_bodies)
+{
+    return nb::choose_split(n_itiles, n_jtiles, slots, max_split_bodies, tile_bodies);
+}
+
+int64_t nb_plan_batch_host(int64_t nsys, const int64_t *off, int T, int I, int J,
+                           int32_t *items_out, int64_t max_items)
+{
+    if (nsys < 0 || !off || T <= 0 || I <= 0 || J <= 0 || (T & (T - 1))) return -1;
+    if (off[0] != 0) return -1;
+    for (int64_t k = 0; k < nsys; ++k)
+        if (off[k + 1] < off[k] || off[k + 1] > 0x7fffffffLL) return -1;
+    struct Cand { BatchItem it; int64_t cost; };
+    std::vector<Cand> v;
+    for (int64_t k = 0; k < nsys; ++k) {
+        const int64_t nk = off[k + 1] - off[k];
+        if (nk == 0) continue;
+        int lanes = 1;
+        while (lanes < 32 && lanes * 2 <= T && (int64_t)T * I / (lanes * 2) >= nk) lanes *= 2;
+        const int64_t per = (int64_t)T * I / lanes;
+        const int64_t cost = (nk + J - 1) / J * J / lanes;  // j-pairs per thread
+        for (int64_t i0 = off[k]; i0 < off[k + 1]; i0 += per) {
+            BatchItem b;
+            b.i0 = (int)i0;
+            b.i_end = (int)std::min(i0 + per, off[k + 1]);
+            b.j0 = (int)off[k];
+            b.j1 = (int)off[k + 1];
+            b.lanes = lanes;
+            b.sys = (int)k;
+            b.pad0 = b.pad1 = 0;
+            v.push_back({b, cost});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const Cand &a, const Cand &b) { return a.cost > b.cost; });
+    const int64_t cnt = (int64_t)v.size();
+    if (items_out) {
+        if (cnt > max_items) return -1;
+        for (int64_t q = 0; q < cnt; ++q) std::memcpy(items_out + 8 * q, &v[q].it, sizeof(BatchItem));
+    }
+    return cnt;
+}
+
+const char *nb_last_error(const nb_ctx *ctx)
+{
+    return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+int nb_variant_count(int kind, nb_precision p)
+{
+    if (kind < 0 || kind >= nb::KIND_COUNT || p < NB_FP64 || p > NB_FP32_COMP) return 0;
+    return variant_count(kind, p);
+}
+
+nb_status nb_variant_info(int kind, nb_precision p, int variant, int *T, int *I, int *J)
+{
+    if (variant < 0 || variant >= nb_variant_count(kind, p)) return NB_EINVAL;
+    const KernelEntry &k = kernel_for(kind, p, variant, false);
+    if (T) *T = k.T;
+    if (I) *I = k.I;
+    if (J) *J = k.J;
+    return NB_OK;
+}
+
+nb_status nb_create(nb_ctx **out, int64_t n_max, nb_precision p, int device, void *stream)
+{
+    if (!out) return failf(nullptr, NB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_max < 0 || n_max > (int64_t)0x7fffffff / 4)
+        return failf(nullptr, NB_EINVAL, "n_max = %lld out of range", (long long)n_max);
+    if (p < NB_FP64 || p > NB_FP32_COMP) return failf(nullptr, NB_EINVAL, "bad precision %d", (int)p);
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return failf(nullptr, NB_ECUDA, "cudaGetDeviceCount failed: %s", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= count)
+        return failf(nullptr, NB_EINVAL, "device %d not in [0, %d)", device, count);
+    DeviceGuard guard(device);
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != device)
+        return failf(nullptr, NB_ECUDA, "cannot make device %d current", device);
+
+    nb_ctx *c = new nb_ctx();
+    c->device = device;
+    c->prec = p;
+    c->n_max = n_max;
+    c->stream = (cudaStream_t)stream;
+    nb_status st = NB_OK;
+    auto bail = [&](nb_status s) {
+        g_create_error = c->last_error;
+        free_ctx(c);
+        return s;
+    };
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(failf(c, NB_ECUDA, "cannot read the SM count"));
+    const int64_t ncap = std::max<int64_t>(n_max, 1);
+    c->pack_bytes = (size_t)ncap * 64;
+    c->pack = dev_alloc<char>(c, c->pack_bytes, st);
+    c->partial_bodies = std::max<int64_t>(4 * ncap, (int64_t)1 << 22);
+    if (st == NB_OK) c->partial = dev_alloc<double>(c, (size_t)c->partial_bodies * 4, st);
+    c->n_counters = ncap / min_tile_bodies() + 2;
+    if (st == NB_OK) c->counters = dev_alloc<unsigned>(c, (size_t)c->n_counters, st);
+    c->n_red = c->partial_bodies / 64 + 4096;
+    if (st == NB_OK) c->red = dev_alloc<double>(c, (size_t)c->n_red * 8, st);
+    if (st == NB_OK) c->dev_out = dev_alloc<double>(c, 16, st);
+    if (st == NB_OK) c->err = dev_alloc<int>(c, 4, st);
+    if (st == NB_OK) c->queue = dev_alloc<unsigned>(c, 4, st);
+    if (st != NB_OK) return bail(st);
+    if (cudaMallocHost(&c->host_out, 16 * sizeof(double)) != cudaSuccess)
+        return bail(failf(c, NB_ENOMEM, "cudaMallocHost failed"));
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return bail(failf(c, NB_ECUDA, "stream/event creation failed"));
+    if (cudaMemset(c->counters, 0, (size_t)c->n_counters * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->err, 0, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->queue, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        return bail(failf(c, NB_ECUDA, "scratch initialisation failed"));
+    *out = c;
+    return NB_OK;
+}
+
+nb_status nb_destroy(nb_ctx *c)
+{
+    if (!c) return NB_OK;
+    DeviceGuard guard(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->cap_stream);
+    free_ctx(c);
+    return NB_OK;
+}
+
+nb_status nb_set_stream(nb_ctx *c, void *stream)
+{
+    if (!c) return NB_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return NB_OK;
+}
+
+nb_status nb_sync(nb_ctx *c)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    int h = 0;
+    NB_CUDA(c, cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h) {
+        NB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        return failf(c, NB_ENONFINITE, "a kernel produced a non-finite result");
+    }
+    return NB_OK;
+}
+
+nb_status nb_forces(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
+                    double eps, double *acc)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (n == 0) return NB_OK;
+    NB_TRY(pack(c, c->stream, n, pos, mass));
+    return force_packed(c, c->stream, n, G, eps, acc, nullptr, 0.0);
+}
+
+nb_status nb_rollout(nb_ctx *c, int64_t n, double *pos, double *vel, const double *mass, double G,
+                     double eps, double dt, int64_t nsteps, double *acc, unsigned flags,
+                     int64_t every, double *rec_pos, double *rec_vel)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
+    if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
+    if (flags & ~(NB_ACC_VALID | NB_USE_GRAPH)) return failf(c, NB_EINVAL, "unknown flags");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (every > 0) {
+        const size_t nrec = (size_t)(nsteps / every) + 1;
+        NB_TRY(check_dev(c, rec_pos, v3 * nrec, "rec_pos"));
+        if (rec_vel) NB_TRY(check_dev(c, rec_vel, v3 * nrec, "rec_vel"));
+    } else {
+        every = 0;
+    }
+    if (n == 0) return NB_OK;
+    if (flags & NB_USE_GRAPH) {
+        nb_ctx::GraphKey key{0,  pos,   vel, mass, acc,    rec_pos, rec_vel, G,
+                             eps, dt,   n,   nsteps, every, flags,  0};
+        return run_graph(c, key, [&](cudaStream_t s) {
+            return rollout_enqueue(c, s, n, pos, vel, mass, G, eps, dt, nsteps, acc, flags, every,
+                                   rec_pos, rec_vel);
+        });
+    }
+    return rollout_enqueue(c, c->stream, n, pos, vel, mass, G, eps, dt, nsteps, acc, flags, every,
+                           rec_pos, rec_vel);
+}
+
+nb_status nb_step(nb_ctx *c, int64_t n, double *pos, double *vel, const double *mass, double G,
+                  double eps, double dt, int64_t nsteps, double *acc, unsigned flags)
+{
+    return nb_rollout(c, n, pos, vel, mass, G, eps, dt, nsteps, acc, flags, 0, nullptr, nullptr);
+}
+
+nb_status nb_energy(nb_ctx *c, int64_t n, const double *pos, const double *vel, const double *mass,
+                    double G, double eps, double *out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    if (!out) return failf(c, NB_EINVAL, "out_host is NULL");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    if (n == 0) {
+        for (int q = 0; q < 9; ++q) out[q] = 0.0;
+        return NB_OK;
+    }
+    cudaStream_t s = c->stream;
+    NB_LAUNCHED(c, nb::launch_pack_f64(s, (int)n, pos, mass, (double4 *)c->pack));
+    const KernelEntry &k = nb::f64_energy_kernel(eps == 0.0);
+    int S = splits_for(c, k, n, 0, 3);
+    const int64_t tile = (int64_t)k.T * k.I;
+    const int64_t n_itiles = (n + tile - 1) / tile;
+    while (S > 1 && n_itiles * S > c->n_red) --S;
+    if (n_itiles * S > c->n_red) return failf(c, NB_ENOMEM, "energy reduction scratch too small");
+    nb::EnergyParams p;
+    p.P = (const double4 *)c->pack;
+    p.vel = vel;
+    p.n = (int)n;
+    p.nsplit = S;
+    p.eps2 = eps * eps;
+    p.red = c->red;
+    p.err = c->err;
+    NB_TRY(launch(c, k, n_itiles * S, &p, s, 3));
+    NB_LAUNCHED(c, nb::launch_energy_final(s, c->red, (int)(n_itiles * S), G, c->dev_out));
+    NB_CUDA(c, cudaMemcpyAsync(c->host_out, c->dev_out, 9 * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    for (int q = 0; q < 9; ++q) out[q] = c->host_out[q];
+    for (int q = 0; q < 9; ++q)
+        if (!std::isfinite(out[q])) return failf(c, NB_ENONFINITE, "non-finite diagnostic");
+    return nb_sync(c);
+}
+
+nb_status nb_forces_backward(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
+                             double eps, const double *grad_acc, double *grad_pos,
+                             double *grad_mass)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, grad_acc, v3, "grad_acc"));
+    NB_TRY(check_dev(c, grad_pos, v3, "grad_pos"));
+    NB_TRY(check_dev(c, grad_mass, v1, "grad_mass"));
+    if (n == 0) return NB_OK;
+    cudaStream_t s = c->stream;
+    NB_LAUNCHED(c, nb::launch_pack_vjp(s, is_f64(c), (int)n, pos, mass, grad_acc, nullptr, nullptr,
+                                       0.0, 1.0, c->pack));
+    return vjp_packed(c, s, n, G, eps, grad_pos, grad_mass, 0);
+}
+
+nb_status nb_step_backward(nb_ctx *c, int64_t n, const double *traj, const double *mass, double G,
+                           double eps, double dt, int64_t nsteps, double *lam_x, double *lam_v,
+                           double *lam_m, unsigned flags)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
+    if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
+    if (flags & ~(NB_BWD_AT_END | NB_BWD_AT_START)) return failf(c, NB_EINVAL, "unknown flags");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, traj, v3 * (size_t)(nsteps + 1), "traj"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, lam_x, v3, "lam_x"));
+    NB_TRY(check_dev(c, lam_v, v3, "lam_v"));
+    NB_TRY(check_dev(c, lam_m, v1, "lam_m"));
+    if (n == 0 || nsteps == 0) return NB_OK;  // no step: nothing to reverse
+    cudaStream_t s = c->stream;
+    const size_t per = (size_t)n * 3;
+    const bool f64 = is_f64(c);
+    if (flags & NB_BWD_AT_END) {
+        // closing half-kick of the run's last step: VJP at x_K with dt/2 lam_v
+        NB_LAUNCHED(c, nb::launch_pack_vjp(s, f64, (int)n, traj + per * (size_t)nsteps, mass,
+                                           nullptr, lam_v, nullptr, 0.0, 0.5 * dt, c->pack));
+        NB_TRY(vjp_packed(c, s, n, G, eps, lam_x, lam_m, 1));
+    }
+    for (int64_t st = nsteps - 1; st >= 0; --st) {
+        const double coef = (st == 0 && (flags & NB_BWD_AT_START)) ? 0.5 * dt : dt;
+        NB_LAUNCHED(c, nb::launch_pack_vjp(s, f64, (int)n, traj + per * (size_t)st, mass, nullptr,
+                                           lam_v, lam_x, dt, coef, c->pack));
+        NB_TRY(vjp_packed(c, s, n, G, eps, lam_x, lam_m, 1));
+    }
+    return NB_OK;
+}
+
+nb_status nb_batch_plan(nb_ctx *c, int64_t nsys, const int64_t *offsets)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    if (nsys < 0 || !offsets) return failf(c, NB_EINVAL, "bad nsys/offsets");
+    if (offsets[0] != 0) return failf(c, NB_EINVAL, "offsets[0] must be 0");
+    for (int64_t k = 0; k < nsys; ++k)
+        if (offsets[k + 1] < offsets[k]) return failf(c, NB_EINVAL, "offsets must be non-decreasing");
+    if (offsets[nsys] > c->n_max) return failf(c, NB_EINVAL, "offsets[nsys] > n_max");
+    int v, forced;
+    pick(c, nb::KIND_BATCHED, offsets[nsys], v, forced);
+    const KernelEntry &k = nb::f32_batched_kernel(v, false, false);
+    const int64_t cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, nullptr, 0);
+    if (cnt < 0) return failf(c, NB_EINVAL, "cannot plan these offsets");
+    std::vector<int32_t> host((size_t)std::max<int64_t>(cnt, 1) * 8);
+    nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, host.data(), cnt);
+    if (cnt > c->items_cap) {
+        cudaFree(c->items);
+        c->items = nullptr;
+        c->items_cap = 0;
+        nb_status st = NB_OK;
+        c->items = dev_alloc<BatchItem>(c, (size_t)cnt, st);
+        if (st != NB_OK) return st;
+        c->items_cap = cnt;
+    }
+    if (cnt > 0)
+        NB_CUDA(c, cudaMemcpyAsync(c->items, host.data(), (size_t)cnt * sizeof(BatchItem),
+                                   cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(c->queue, 0, 4 * sizeof(unsigned), c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->n_items = cnt;
+    c->batch_variant = v;
+    c->batch_n = offsets[nsys];
+    c->batch_nsys = nsys;
+    c->plan_gen++;
+    drop_graphs(c);
+    return NB_OK;
+}
+
+nb_status nb_forces_batched(nb_ctx *c, const double *pos, const double *mass, double G, double eps,
+                            double *acc)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    NB_TRY(check_scalars(c, G, eps));
+    const int64_t n = c->batch_n;
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (n == 0) return NB_OK;
+    NB_TRY(pack(c, c->stream, n, pos, mass));
+    return batched_force(c, c->stream, G, eps, acc, nullptr, 0.0);
+}
+
+nb_status nb_step_batched(nb_ctx *c, double *pos, double *vel, const double *mass, double G,
+                          double eps, double dt, int64_t nsteps, double *acc, unsigned flags)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    NB_TRY(check_scalars(c, G, eps));
+    if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
+    if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
+    if (flags & ~(NB_ACC_VALID | NB_USE_GRAPH)) return failf(c, NB_EINVAL, "unknown flags");
+    const int64_t n = c->batch_n;
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (n == 0) return NB_OK;
+    if (flags & NB_USE_GRAPH) {
+        nb_ctx::GraphKey key{1,   pos, vel,           mass, acc,   nullptr,     nullptr, G,
+                             eps, dt,  c->batch_n,    nsteps, 0,   flags,       c->plan_gen};
+        return run_graph(c, key, [&](cudaStream_t s) {
+            return batched_enqueue(c, s, pos, vel, mass, G, eps, dt, nsteps, acc, flags);
+        });
+    }
+    return batched_enqueue(c, c->stream, pos, vel, mass, G, eps, dt, nsteps, acc, flags);
+}
+
+nb_status nb_tune_set(nb_ctx *c, int kind, int64_t lo, int64_t hi, int variant, int split)
+{
+    if (!c) return NB_EINVAL;
+    if (kind < 0 || kind >= nb::KIND_COUNT) return failf(c, NB_EINVAL, "bad kind %d", kind);
+    if (variant < 0) {
+        c->tune[kind].clear();
+        drop_graphs(c);
+        return NB_OK;
+    }
+    if (variant >= variant_count(kind, c->prec))
+        return failf(c, NB_EINVAL, "variant %d out of range for kind %d", variant, kind);
+    if (lo < 0 || hi <= lo || split < 0) return failf(c, NB_EINVAL, "bad range or split");
+    c->tune[kind].push_back({lo, hi, variant, split});
+    drop_graphs(c);
+    return NB_OK;
+}
+
+nb_status nb_tune_get(nb_ctx *c, int kind, int64_t n, int *variant, int *split)
+{
+    if (!c || kind < 0 || kind >= nb::KIND_COUNT) return NB_EINVAL;
+    int v, s;
+    pick(c, kind, n, v, s);
+    if (variant) *variant = v;
+    if (split) *split = s;
+    return NB_OK;
+}
+
+int64_t nb_launch_count(const nb_ctx *c) { return c ? c->launches : 0; }
+
+nb_status nb_profile(nb_ctx *c, int enable)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (enable) {
+        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (auto &r : c->prof) {
+            c->ev_pool.push_back(r.a);
+            c->ev_pool.push_back(r.b);
+        }
+        c->prof.clear();
+    }
+    c->prof_on = enable != 0;
+    return NB_OK;
+}
+
+nb_status nb_profile_read(nb_ctx *c, int kind, int64_t *launches, double *total_ms)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    int64_t cnt = 0;
+    double ms = 0.0;
+    for (const auto &r : c->prof) {
+        if (r.kind != kind) continue;
+        float t = 0.f;
+        NB_CUDA(c, cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        ++cnt;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    return NB_OK;
+}
+
+nb_status nb_device_info(nb_ctx *c, int64_t n, int *num_sms, int *ctas_per_sm)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    int v, s;
+    pick(c, nb::KIND_FORCE, n, v, s);
+    if (num_sms) *num_sms = c->num_sms;
+    if (ctas_per_sm) *ctas_per_sm = occupancy(c, kernel_for(nb::KIND_FORCE, c->prec, v, false));
+    return NB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+"""GPU force kernels against the FP64 oracle, through the C ABI.
+
+Tolerances (per-body relative error e_i = |a_i - a_i^ref| / |a_i^ref|):
+  FP64 form:        max e_i <= 1e-12
+  FP32 compensated: RMS e_i <= 1e-5, max e_i <= 1e-4
+  FP32 plain:       RMS e_i <= 1e-4 at N <= 4097 (one float32 running sum)
+Sizes span one and several tiles with ragged tails; every compiled variant
+and forced j-splits are exercised.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_2292_gb300 import inputs, nbody
+from helpers import host, relerr_per_body, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 3, 31, 32, 33, 127, 1000, 1024, 4097]
+
+
+def _forces(cuda, prec, b, G, eps, variant=None, split=0):
+    with nbody.NBody(max(b.n, 1), prec) as nb:
+        if variant is not None:
+            nb.tune_set(nbody.KIND_FORCE, 0, 1 << 40, variant, split)
+        a = nb.forces(to_dev(b.pos, cuda), to_dev(b.mass, cuda), G, eps)
+        nb.sync()
+        return host(a)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fp64_matches_oracle(cuda, n):
+    b = inputs.plummer(n, seed=n)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
+    a = _forces(cuda, "fp64", b, 1.0, 0.01)
+    if n == 1:
+        assert np.all(a == 0)
+        return
+    assert relerr_per_body(a, ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fp32_comp_matches_oracle(cuda, n):
+    b = inputs.plummer(n, seed=100 + n)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.005)
+    a = _forces(cuda, "fp32_comp", b, 1.0, 0.005)
+    if n == 1:
+        assert np.all(a == 0)
+        return
+    e = relerr_per_body(a, ref)
+    assert np.sqrt((e ** 2).mean()) <= 1e-5 and e.max() <= 1e-4
+
+
+@pytest.mark.parametrize("n", [33, 1000, 4097])
+def test_fp32_plain_matches_oracle(cuda, n):
+    b = inputs.plummer(n, seed=200 + n)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
+    e = relerr_per_body(_forces(cuda, "fp32", b, 1.0, 0.01), ref)
+    assert np.sqrt((e ** 2).mean()) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp"])
+def test_every_variant_and_forced_splits(cuda, prec):
+    b = inputs.plummer(3001, seed=7)
+    ref = oracle.accel(b.pos, b.mass, 1.3, 0.02)
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    nvar = len(nbody.variants(nbody.KIND_FORCE, prec))
+    for v in range(nvar):
+        for split in (1, 3, 7):
+            a = _forces(cuda, prec, b, 1.3, 0.02, variant=v, split=split)
+            e = relerr_per_body(a, ref)
+            assert e.max() <= tol, (v, split, e.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp"])
+def test_zero_softening_skips_self_pair(cuda, prec):
+    x = np.array([[0.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    m = np.array([1.0, 3.0])
+    b = inputs.Bodies(x, np.zeros_like(x), m)
+    a = _forces(cuda, prec, b, 1.0, 0.0)
+    np.testing.assert_allclose(a, [[0, 0.75, 0], [0, -0.25, 0]], rtol=1e-6 if prec != "fp64" else 1e-15)
+    b = inputs.random_system(33, seed=3)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.0)
+    e = relerr_per_body(_forces(cuda, prec, b, 1.0, 0.0), ref)
+    assert np.isfinite(e).all() and e.max() <= (1e-12 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_comp"])
+def test_deterministic_across_calls(cuda, prec):
+    b = inputs.plummer(5000, seed=9)
+    with nbody.NBody(b.n, prec) as nb:
+        nb.tune_set(nbody.KIND_FORCE, 0, 1 << 40, 0, 5)
+        x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+        a1 = host(nb.forces(x, m, 1.0, 0.01))
+        a2 = host(nb.forces(x, m, 1.0, 0.01))
+    assert np.array_equal(a1, a2)
+
+
+def test_scaling_laws_fp64(cuda):
+    # Power-of-two scalings: G and mass linear, lengths (x and eps) as
+    # length^-2.  A wrong power of s or a dropped factor breaks these.
+    b = inputs.plummer(700, seed=10)
+    a = _forces(cuda, "fp64", b, 1.0, 0.05)
+    a2 = _forces(cuda, "fp64", inputs.Bodies(2 * b.pos, b.vel, b.mass), 1.0, 0.1)
+    np.testing.assert_allclose(a2, a / 4, rtol=1e-14, atol=0)
+    a3 = _forces(cuda, "fp64", b, 2.0, 0.05)
+    np.testing.assert_array_equal(a3, 2 * a)
+
+
+def test_empty_and_n_max(cuda):
+    import torch
+    with nbody.NBody(16, "fp32_comp") as nb:
+        z = torch.zeros((0, 3), dtype=torch.float64, device=cuda)
+        nb.forces(z, torch.zeros(0, dtype=torch.float64, device=cuda), 1.0, 0.1, out=z)
+        b = inputs.plummer(16, seed=1)
+        a = host(nb.forces(to_dev(b.pos, cuda), to_dev(b.mass, cuda), 1.0, 0.1))
+        ref = oracle.accel(b.pos, b.mass, 1.0, 0.1)
+        assert relerr_per_body(a, ref).max() < 1e-4
+        b17 = inputs.plummer(17, seed=1)
+        with pytest.raises(nbody.NBodyError) as ei:
+            nb.forces(to_dev(b17.pos, cuda), to_dev(b17.mass, cuda), 1.0, 0.1)
+        assert ei.value.status == 1
+
+
+def test_argument_checks_reject_before_launch(cuda):
+    import ctypes
+    import torch
+    lib = nbody.load()
+    with nbody.NBody(64, "fp32_comp") as nb:
+        x = torch.zeros((64, 3), dtype=torch.float64, device=cuda)
+        m = torch.ones(64, dtype=torch.float64, device=cuda)
+        a = torch.zeros((64, 3), dtype=torch.float64, device=cuda)
+        before = nb.launches
+        # host memory instead of device memory
+        hx = np.zeros((64, 3))
+        st = lib.nb_forces(nb.h, 64, hx.ctypes.data, m.data_ptr(), 1.0, 0.1, a.data_ptr())
+        assert st == 1
+        # misaligned pointer
+        st = lib.nb_forces(nb.h, 63, x.data_ptr() + 4, m.data_ptr(), 1.0, 0.1, a.data_ptr())
+        assert st == 1
+        # NULL, NaN G, negative eps, n out of range
+        assert lib.nb_forces(nb.h, 64, None, m.data_ptr(), 1.0, 0.1, a.data_ptr()) == 1
+        assert lib.nb_forces(nb.h, 64, x.data_ptr(), m.data_ptr(), float("nan"), 0.1, a.data_ptr()) == 1
+        assert lib.nb_forces(nb.h, 64, x.data_ptr(), m.data_ptr(), 1.0, -0.1, a.data_ptr()) == 1
+        assert lib.nb_forces(nb.h, 65, x.data_ptr(), m.data_ptr(), 1.0, 0.1, a.data_ptr()) == 1
+        assert lib.nb_forces(nb.h, -1, x.data_ptr(), m.data_ptr(), 1.0, 0.1, a.data_ptr()) == 1
+        torch.cuda.synchronize()
+        assert nb.launches == before
+        nb.sync()
+
+
+def test_nonfinite_flag_reported(cuda):
+    b = inputs.plummer(100, seed=2)
+    pos = b.pos.copy()
+    pos[5, 0] = np.inf
+    with nbody.NBody(100, "fp64") as nb:
+        nb.forces(to_dev(pos, cuda), to_dev(b.mass, cuda), 1.0, 0.01)
+        with pytest.raises(nbody.NBodyError) as ei:
+            nb.sync()
+        assert ei.value.status == 4
+        nb.sync()  # flag cleared
