@@ -203,6 +203,17 @@ nb_status nb_variant_info(int kind, nb_precision p, int variant, int *threads,
 nb_status nb_tune_set(nb_ctx *ctx, int kind, int64_t lo, int64_t hi, int variant, int split);
 nb_status nb_tune_get(nb_ctx *ctx, int kind, int64_t n, int *variant, int *split);
 
+/*
+ * Body order of the float32 force kernels.  Each CTA forms pair differences
+ * relative to the centre of its i-tile; with spatially compact i-tiles this
+ * keeps close pairs accurate far from the origin.  mode 0: bodies in input
+ * order; 1: always in Morton (Z-curve) order; 2 (default): Morton order when
+ * n >= min_n (default 131072).  The order is recomputed (deterministically)
+ * for every force evaluation; results are returned in input order.  No
+ * effect on NB_FP64 contexts or on the batched kernel.
+ */
+nb_status nb_set_order(nb_ctx *ctx, int mode, int64_t min_n);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t nb_launch_count(const nb_ctx *ctx);
 

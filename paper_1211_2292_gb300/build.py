@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
-SOURCES = ["force_f32.cu", "force_f64.cu", "adjoint.cu", "integrate.cu", "nbody_abi.cpp"]
+SOURCES = ["force_f32.cu", "force_f64.cu", "adjoint.cu", "integrate.cu", "order.cu",
+           "nbody_abi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

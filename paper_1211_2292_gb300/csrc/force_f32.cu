@@ -11,7 +11,14 @@
 //    bodies, stored with each component duplicated ((x,x,y,y),(z,z,m,m)) so a
 //    broadcast 128-bit shared load yields the float32x2 operands directly.
 //    The next tile's global loads are issued before the current tile is
-//    consumed.  Out-of-range j slots are zero-mass bodies at the origin.
+//    consumed.  Out-of-range j slots are zero-mass bodies.
+//  * Tile-local origin: positions arrive as float32 hi/lo pairs
+//    (x = x_hi + x_lo).  Each CTA takes the centre c of its i-tile's bounding
+//    box as origin and forms every coordinate as (x_hi - c) + x_lo, once per
+//    body per CTA when staging.  The pair differences then carry the
+//    rounding of |x - c| instead of |x|, which for spatially ordered i-tiles
+//    (order.cu) keeps close pairs accurate far from the global origin.  The
+//    per-pair arithmetic is unchanged.
 //  * Per pair: 3 add, 3 fma (r^2), 1 MUFU rsqrt per body, 3 mul, 3 fma;
 //    12 float32 operations, i.e. 6 float32x2 issues per body.
 //  * NB_FP32_COMP: each tile's float32 partial sum is added into a per-body
@@ -78,28 +85,38 @@ __device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float
     az = fma2(dz, s, az);
 }
 
-// Stage J float4 bodies (this thread's share held in `buf`) into a
-// duplicated shared tile.
+// Tile-local coordinate of a hi/lo packed component.
+__device__ __forceinline__ float rel(float hi, float lo, float c) { return (hi - c) + lo; }
+
+// Stage this thread's share of a j-tile into the duplicated shared layout,
+// in coordinates relative to the tile origin c.
 template <int T, int J>
-__device__ __forceinline__ void stage_store(float4 *tile, const float4 (&buf)[J / T])
+__device__ __forceinline__ void stage_store(float4 *tile, const float4 (&bh)[J / T],
+                                            const float4 (&bl)[J / T], float3 c)
 {
 #pragma unroll
     for (int l = 0; l < J / T; ++l) {
         const int jj = l * T + threadIdx.x;
-        const float4 b = buf[l];
-        tile[2 * jj] = make_float4(b.x, b.x, b.y, b.y);
-        tile[2 * jj + 1] = make_float4(b.z, b.z, b.w, b.w);
+        const float x = rel(bh[l].x, bl[l].x, c.x);
+        const float y = rel(bh[l].y, bl[l].y, c.y);
+        const float z = rel(bh[l].z, bl[l].z, c.z);
+        const float m = bh[l].w;
+        tile[2 * jj] = make_float4(x, x, y, y);
+        tile[2 * jj + 1] = make_float4(z, z, m, m);
     }
 }
 
 template <int T, int J>
-__device__ __forceinline__ void stage_load(float4 (&buf)[J / T], const float4 *__restrict__ P,
-                                           int jbase, int jend)
+__device__ __forceinline__ void stage_load(float4 (&bh)[J / T], float4 (&bl)[J / T],
+                                           const float4 *__restrict__ P,
+                                           const float4 *__restrict__ Plo, int jbase, int jend)
 {
 #pragma unroll
     for (int l = 0; l < J / T; ++l) {
         const int j = jbase + l * T + threadIdx.x;
-        buf[l] = j < jend ? __ldg(P + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = j < jend;
+        bh[l] = ok ? __ldg(P + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        bl[l] = ok ? __ldg(Plo + j) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -156,22 +173,22 @@ struct Acc {
 // jlo + t*J) for this thread's bodies.  Threads split each tile's j loop in
 // `lanes` interleaved parts (lanes == 1 for the solo kernel).
 template <int T, int I, int J, bool COMP, bool ZEPS, bool LANES>
-__device__ __forceinline__ void sweep(const float4 *__restrict__ P, int jlo, int jhi, int t0,
-                                      int t1, int lane, int lanes, float2 e2,
-                                      const float2 (&nx)[I / 2], const float2 (&ny)[I / 2],
-                                      const float2 (&nz)[I / 2], Acc<I, COMP> &acc,
-                                      float4 (*tile)[2 * J])
+__device__ __forceinline__ void sweep(const float4 *__restrict__ P, const float4 *__restrict__ Plo,
+                                      float3 c, int jlo, int jhi, int t0, int t1, int lane,
+                                      int lanes, float2 e2, const float2 (&nx)[I / 2],
+                                      const float2 (&ny)[I / 2], const float2 (&nz)[I / 2],
+                                      Acc<I, COMP> &acc, float4 (*tile)[2 * J])
 {
     constexpr int NP = I / 2;
-    float4 buf[J / T];
+    float4 bh[J / T], bl[J / T];
     if (t0 < t1) {
-        stage_load<T, J>(buf, P, jlo + t0 * J, jhi);
-        stage_store<T, J>(tile[0], buf);
+        stage_load<T, J>(bh, bl, P, Plo, jlo + t0 * J, jhi);
+        stage_store<T, J>(tile[0], bh, bl, c);
     }
     __syncthreads();
     for (int t = t0; t < t1; ++t) {
         const int b = (t - t0) & 1;
-        if (t + 1 < t1) stage_load<T, J>(buf, P, jlo + (t + 1) * J, jhi);
+        if (t + 1 < t1) stage_load<T, J>(bh, bl, P, Plo, jlo + (t + 1) * J, jhi);
         const float4 *s = tile[b];
         if (LANES) {
 #pragma unroll 4
@@ -197,27 +214,84 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ P, int jlo, int
             }
         }
         acc.end_tile();
-        if (t + 1 < t1) stage_store<T, J>(tile[b ^ 1], buf);
+        if (t + 1 < t1) stage_store<T, J>(tile[b ^ 1], bh, bl, c);
         __syncthreads();
     }
 }
 
-// Load this thread's i-bodies (negated positions, paired).  Body k of the
-// thread is `first + k*stride`; bodies at or past `end` read as the origin.
-template <int I>
-__device__ __forceinline__ void load_i(const float4 *__restrict__ P, int first, int stride, int end,
-                                       float2 (&nx)[I / 2], float2 (&ny)[I / 2],
-                                       float2 (&nz)[I / 2])
+// Centre of the bounding box of the CTA's valid i-bodies (every thread gets
+// the same value).  red: shared scratch of 6 x (T/32) floats.
+template <int T>
+__device__ __forceinline__ float3 block_center(float (&mn)[3], float (&mx)[3], float (*red)[T / 32])
 {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            red[c][warp] = mn[c];
+            red[3 + c][warp] = mx[c];
+        }
+    }
+    __syncthreads();
+    float a[3], b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = red[c][0];
+        b[c] = red[3 + c][0];
+#pragma unroll
+        for (int w = 1; w < T / 32; ++w) {
+            a[c] = fminf(a[c], red[c][w]);
+            b[c] = fmaxf(b[c], red[3 + c][w]);
+        }
+    }
+    __syncthreads();  // red may be reused by the caller afterwards
+    float3 o;
+    o.x = a[0] <= b[0] ? 0.5f * (a[0] + b[0]) : 0.f;
+    o.y = a[1] <= b[1] ? 0.5f * (a[1] + b[1]) : 0.f;
+    o.z = a[2] <= b[2] ? 0.5f * (a[2] + b[2]) : 0.f;
+    return o;
+}
+
+// Load this thread's i-bodies.  Body k of the thread is at packed slot
+// `first + k*stride`; slots at or past `end` read as zero.  Returns the tile
+// origin; nx/ny/nz receive the NEGATED tile-local positions, paired.
+template <int T, int I>
+__device__ __forceinline__ float3 load_i(const float4 *__restrict__ P, const float4 *__restrict__ Plo,
+                                         int first, int stride, int end, float2 (&nx)[I / 2],
+                                         float2 (&ny)[I / 2], float2 (&nz)[I / 2],
+                                         float (*red)[T / 32])
+{
+    float4 h[I], l[I];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        const int i = first + k * stride;
+        const bool ok = i < end;
+        h[k] = ok ? __ldg(P + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = ok ? __ldg(Plo + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+            mn[0] = fminf(mn[0], h[k].x); mx[0] = fmaxf(mx[0], h[k].x);
+            mn[1] = fminf(mn[1], h[k].y); mx[1] = fmaxf(mx[1], h[k].y);
+            mn[2] = fminf(mn[2], h[k].z); mx[2] = fmaxf(mx[2], h[k].z);
+        }
+    }
+    const float3 c = block_center<T>(mn, mx, red);
 #pragma unroll
     for (int p = 0; p < I / 2; ++p) {
-        const int ia = first + (2 * p) * stride, ib = first + (2 * p + 1) * stride;
-        const float4 a = ia < end ? __ldg(P + ia) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = ib < end ? __ldg(P + ib) : make_float4(0.f, 0.f, 0.f, 0.f);
-        nx[p] = make_float2(-a.x, -b.x);
-        ny[p] = make_float2(-a.y, -b.y);
-        nz[p] = make_float2(-a.z, -b.z);
+        const float4 a = h[2 * p], b = h[2 * p + 1], al = l[2 * p], bl = l[2 * p + 1];
+        nx[p] = make_float2(-rel(a.x, al.x, c.x), -rel(b.x, bl.x, c.x));
+        ny[p] = make_float2(-rel(a.y, al.y, c.y), -rel(b.y, bl.y, c.y));
+        nz[p] = make_float2(-rel(a.z, al.z, c.z), -rel(b.z, bl.z, c.z));
     }
+    return c;
 }
 
 // -------------------------------------------------------------- solo kernel
@@ -227,6 +301,7 @@ __global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
     static_assert(I % 2 == 0 && J % T == 0, "bad tile shape");
     constexpr int TILE_I = T * I;
     __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ float red[6][T / 32];
     __shared__ int s_last;
 
     const float4 *P = static_cast<const float4 *>(p.P);
@@ -239,11 +314,11 @@ __global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
     split_range((n + J - 1) / J, p.nsplit, js, t0, t1);
 
     float2 nx[I / 2], ny[I / 2], nz[I / 2];
-    load_i<I>(P, i0 + threadIdx.x, T, n, nx, ny, nz);
+    const float3 c = load_i<T, I>(P, p.Plo, i0 + threadIdx.x, T, n, nx, ny, nz, red);
     Acc<I, COMP> acc;
     acc.init();
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
-    sweep<T, I, J, COMP, ZEPS, false>(P, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
+    sweep<T, I, J, COMP, ZEPS, false>(P, p.Plo, c, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
 
     if (p.nsplit == 1) {
 #pragma unroll
@@ -252,7 +327,7 @@ __global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
             if (i < n) {
                 double x, y, z;
                 acc.get(k, x, y, z);
-                write_acc(p, i, p.G * x, p.G * y, p.G * z);
+                write_acc(p, p.perm ? p.perm[i] : i, p.G * x, p.G * y, p.G * z);
             }
         }
         return;
@@ -287,7 +362,7 @@ __global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
                 y += __ldcg(r + 1);
                 z += __ldcg(r + 2);
             }
-            write_acc(p, i, p.G * x, p.G * y, p.G * z);
+            write_acc(p, p.perm ? p.perm[i] : i, p.G * x, p.G * y, p.G * z);
         }
     }
     if (threadIdx.x == 0) p.counters[it] = 0u;
@@ -302,6 +377,7 @@ template <int T, int I, int J, bool COMP, bool ZEPS>
 __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams p)
 {
     __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ float red[6][T / 32];
     __shared__ BatchItem s_item;
     __shared__ int s_idx;
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
@@ -322,16 +398,16 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
         const int group = threadIdx.x / lanes;
         const int groups = T / lanes;
         float2 nx[I / 2], ny[I / 2], nz[I / 2];
-        load_i<I>(p.P, it.i0 + group, groups, it.i_end, nx, ny, nz);
+        const float3 c = load_i<T, I>(p.P, p.Plo, it.i0 + group, groups, it.i_end, nx, ny, nz, red);
         Acc<I, COMP> acc;
         acc.init();
         const int ntiles = (it.j1 - it.j0 + J - 1) / J;
         if (lanes == 1)
-            sweep<T, I, J, COMP, ZEPS, false>(p.P, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx, ny, nz,
-                                              acc, tile);
+            sweep<T, I, J, COMP, ZEPS, false>(p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx,
+                                              ny, nz, acc, tile);
         else
-            sweep<T, I, J, COMP, ZEPS, true>(p.P, it.j0, it.j1, 0, ntiles, lane, lanes, e2, nx, ny,
-                                             nz, acc, tile);
+            sweep<T, I, J, COMP, ZEPS, true>(p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, lane, lanes,
+                                             e2, nx, ny, nz, acc, tile);
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             double x, y, z;

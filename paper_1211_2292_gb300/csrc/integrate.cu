@@ -28,6 +28,15 @@ __device__ __forceinline__ void put(double4 *P, int i, double x, double y, doubl
 {
     P[i] = make_double4(x, y, z, m);
 }
+// float32 hi/lo pair: x = hi + lo with hi = fl(x), lo = fl(x - hi).
+__device__ __forceinline__ void put_hilo(float4 *P, float4 *Plo, int i, double x, double y,
+                                         double z, double m)
+{
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    P[i] = make_float4(hx, hy, hz, (float)m);
+    Plo[i] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz),
+                         0.f);
+}
 
 template <typename V>
 __global__ void pack_kernel(int n, const double *__restrict__ pos, const double *__restrict__ mass,
@@ -45,7 +54,7 @@ __global__ void pack_kernel(int n, const double *__restrict__ pos, const double 
 template <typename V>
 __global__ void kdp_kernel(int n, double *__restrict__ pos, double *__restrict__ vel,
                            const double *__restrict__ acc, const double *__restrict__ mass,
-                           double half_dt, double dt, V *__restrict__ P,
+                           double half_dt, double dt, V *__restrict__ P, float4 *__restrict__ Plo,
                            double *__restrict__ rec_pos, double *__restrict__ rec_vel)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -70,7 +79,10 @@ __global__ void kdp_kernel(int n, double *__restrict__ pos, double *__restrict__
         xz += dt * vz;
         v[0] = vx; v[1] = vy; v[2] = vz;
         x[0] = xx; x[1] = xy; x[2] = xz;
-        put(P, i, xx, xy, xz, mass[i]);
+        if (Plo)
+            put_hilo((float4 *)P, Plo, i, xx, xy, xz, mass[i]);
+        else if (P)
+            put(P, i, xx, xy, xz, mass[i]);
     }
 }
 
@@ -158,14 +170,15 @@ cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const doub
 
 cudaError_t launch_kdp(cudaStream_t s, bool f64, int n, double *pos, double *vel,
                        const double *acc, const double *mass, double half_dt, double dt, void *P,
-                       double *rec_pos, double *rec_vel)
+                       float4 *Plo, double *rec_pos, double *rec_vel)
 {
     if (f64)
         kdp_kernel<double4><<<grid_for(n), TPB, 0, s>>>(n, pos, vel, acc, mass, half_dt, dt,
-                                                         (double4 *)P, rec_pos, rec_vel);
+                                                         (double4 *)P, nullptr, rec_pos, rec_vel);
     else
         kdp_kernel<float4><<<grid_for(n), TPB, 0, s>>>(n, pos, vel, acc, mass, half_dt, dt,
-                                                        (float4 *)P, rec_pos, rec_vel);
+                                                        (float4 *)P, P ? Plo : nullptr, rec_pos,
+                                                        rec_vel);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,9 @@ struct KernelEntry {
 
 // -------------------------------------------------------------- parameters
 struct ForceParams {
-    const void *P;        // packed bodies: float4 (x,y,z,m) or double4
+    const void *P;        // packed bodies: float4 (x_hi,y_hi,z_hi,m) or double4 (x,y,z,m)
+    const float4 *Plo;    // float32 modes: (x_lo,y_lo,z_lo,0), x = x_hi + x_lo
+    const int *perm;      // float32 modes: body stored at packed slot k (NULL = identity)
     int n;                // bodies
     int nsplit;           // j-splits across CTAs (grid = i-tiles * nsplit)
     float eps2f;          // eps^2 in float32
@@ -49,7 +51,8 @@ struct BatchItem {
 };
 
 struct BatchParams {
-    const float4 *P;
+    const float4 *P;      // (x_hi,y_hi,z_hi,m)
+    const float4 *Plo;    // (x_lo,y_lo,z_lo,0)
     const BatchItem *items;
     int n_items;
     unsigned *queue;      // [0] next item, [1] CTAs done; both zero between launches
@@ -100,13 +103,31 @@ const KernelEntry &f32_vjp_kernel(int variant, bool zeps);
 int f64_vjp_variants();
 const KernelEntry &f64_vjp_kernel(int variant, bool zeps);
 
+// -------------------------------------------------- spatial order (order.cu)
+constexpr int SORT_CHUNK = 1024;  // keys per warp-chunk of the radix sort
+struct OrderScratch {
+    double *box;        // [1024][6] bounding-box partials
+    unsigned *keys[2];  // [n] Morton keys (ping-pong)
+    int *vals[2];       // [n] body indices (ping-pong)
+    unsigned *hist;     // [256][chunks] digit counts / offsets
+};
+int sort_chunks(int n);
+// perm_out[k] = body at Morton rank k (stable in body index); `kernels` = launches made.
+cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
+                               int *perm_out, int &kernels);
+// Phi[k], Plo[k] = float32 hi/lo packing of body perm[k] (perm NULL = identity).
+cudaError_t launch_pack_hilo(cudaStream_t s, int n, const double *pos, const double *mass,
+                             const int *perm, float4 *Phi, float4 *Plo);
+
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
 cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const double *mass, double4 *P);
-// v += half_dt a; x += dt v; repack.  Records (x, v) before the update when rec_* is set.
+// v += half_dt a; x += dt v; then repack into P (double4) when f64, into the
+// float32 hi/lo pair (P, Plo) otherwise; P == NULL skips the packing.  Records
+// (x, v) before the update when rec_* is set.
 cudaError_t launch_kdp(cudaStream_t s, bool f64, int n, double *pos, double *vel, const double *acc,
-                       const double *mass, double half_dt, double dt, void *P, double *rec_pos,
-                       double *rec_vel);
+                       const double *mass, double half_dt, double dt, void *P, float4 *Plo,
+                       double *rec_pos, double *rec_vel);
 // Adjoint packing: lam_v += drift * lam_x (if lam_x), mu = coef * lam_v, pack (x, m, mu).
 cudaError_t launch_pack_vjp(cudaStream_t s, bool f64, int n, const double *pos, const double *mass,
                             const double *lam, double *lam_v, const double *lam_x, double drift,
@@ -138,6 +159,11 @@ struct nb_ctx {
     int64_t n_counters = 0;
     double *red = nullptr;       // energy per-CTA partials
     int64_t n_red = 0;           // capacity in CTAs
+    int *perm = nullptr;         // spatial order of the last float32 force call
+    bool perm_active = false;    // the packed bodies are in perm order
+    nb::OrderScratch order{};
+    int order_mode = 2;          // 0 never, 1 always, 2 when n >= order_min_n
+    int64_t order_min_n = 131072;
     double *dev_out = nullptr;   // 16 doubles
     double *host_out = nullptr;  // pinned, 16 doubles
     int *err = nullptr;

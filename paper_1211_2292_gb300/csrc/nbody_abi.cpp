@@ -247,6 +247,9 @@ int splits_for(nb_ctx *c, const KernelEntry &k, int64_t n, int forced, int64_t p
     return s < 1 ? 1 : s;
 }
 
+// Second half of the float32 pack buffer: the lo parts of the hi/lo pairs.
+float4 *lo_half(nb_ctx *c) { return (float4 *)c->pack + std::max<int64_t>(c->n_max, 1); }
+
 // ------------------------------------------------------------- force paths
 // Force on the already packed bodies; optional fused half-kick of vel.
 nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double eps, double *acc,
@@ -260,6 +263,8 @@ nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double ep
     const int S = splits_for(c, k, n, forced, 3);
     nb::ForceParams p;
     p.P = c->pack;
+    p.Plo = is_f64(c) ? nullptr : lo_half(c);
+    p.perm = (!is_f64(c) && c->perm_active) ? c->perm : nullptr;
     p.n = (int)n;
     p.nsplit = S;
     p.eps2f = (float)(eps * eps);
@@ -275,13 +280,31 @@ nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double ep
     return launch(c, k, (n + tile - 1) / tile * S, &p, s, 0);
 }
 
-nb_status pack(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos, const double *mass)
+// Whether float32 force calls with n bodies process them in Morton order.
+bool use_order(const nb_ctx *c, int64_t n)
+{
+    if (c->prec == NB_FP64 || !c->perm) return false;
+    return c->order_mode == 1 || (c->order_mode == 2 && n >= c->order_min_n);
+}
+
+// Pack bodies for a force call: float64 (x,y,z,m) in FP64 mode; float32
+// hi/lo pairs otherwise, in Morton order when use_order() holds.
+nb_status pack(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos, const double *mass,
+               bool allow_order = true)
 {
     if (n == 0) return NB_OK;
-    if (is_f64(c))
+    if (is_f64(c)) {
         NB_LAUNCHED(c, nb::launch_pack_f64(s, (int)n, pos, mass, (double4 *)c->pack));
-    else
-        NB_LAUNCHED(c, nb::launch_pack_f32(s, (int)n, pos, mass, (float4 *)c->pack));
+        return NB_OK;
+    }
+    c->perm_active = allow_order && use_order(c, n);
+    if (c->perm_active) {
+        int k = 0;
+        NB_CUDA(c, nb::launch_morton_sort(s, (int)n, pos, c->order, c->perm, k));
+        c->launches += k;
+    }
+    NB_LAUNCHED(c, nb::launch_pack_hilo(s, (int)n, pos, mass, c->perm_active ? c->perm : nullptr,
+                                        (float4 *)c->pack, lo_half(c)));
     return NB_OK;
 }
 
@@ -297,14 +320,21 @@ nb_status rollout_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, dou
         NB_TRY(force_packed(c, s, n, G, eps, acc, nullptr, 0.0));
     }
     const size_t rec = (size_t)n * 3;
+    const bool order = use_order(c, n);
     for (int64_t st = 0; st < nsteps; ++st) {
         double *rp = nullptr, *rv = nullptr;
         if (every > 0 && st % every == 0) {
             rp = rec_pos + rec * (size_t)(st / every);
             rv = rec_vel ? rec_vel + rec * (size_t)(st / every) : nullptr;
         }
+        // kick + drift; it also repacks unless the bodies are re-ordered first
         NB_LAUNCHED(c, nb::launch_kdp(s, is_f64(c), (int)n, pos, vel, acc, mass, 0.5 * dt, dt,
-                                      c->pack, rp, rv));
+                                      order ? nullptr : c->pack, lo_half(c), rp, rv));
+        if (order) {
+            NB_TRY(pack(c, s, n, pos, mass));
+        } else {
+            c->perm_active = false;
+        }
         NB_TRY(force_packed(c, s, n, G, eps, acc, vel, 0.5 * dt));
     }
     if (every > 0 && nsteps % every == 0) {
@@ -354,6 +384,7 @@ nb_status batched_force(nb_ctx *c, cudaStream_t s, double G, double eps, double 
     const int64_t slots = (int64_t)c->num_sms * occupancy(c, k);
     nb::BatchParams p;
     p.P = (const float4 *)c->pack;
+    p.Plo = lo_half(c);
     p.items = c->items;
     p.n_items = (int)c->n_items;
     p.queue = c->queue;
@@ -373,12 +404,12 @@ nb_status batched_enqueue(nb_ctx *c, cudaStream_t s, double *pos, double *vel, c
     const int64_t n = c->batch_n;
     if (n == 0) return NB_OK;
     if (!(flags & NB_ACC_VALID)) {
-        NB_TRY(pack(c, s, n, pos, mass));
+        NB_TRY(pack(c, s, n, pos, mass, false));
         NB_TRY(batched_force(c, s, G, eps, acc, nullptr, 0.0));
     }
     for (int64_t st = 0; st < nsteps; ++st) {
         NB_LAUNCHED(c, nb::launch_kdp(s, false, (int)n, pos, vel, acc, mass, 0.5 * dt, dt, c->pack,
-                                      nullptr, nullptr));
+                                      lo_half(c), nullptr, nullptr));
         NB_TRY(batched_force(c, s, G, eps, acc, vel, 0.5 * dt));
     }
     return NB_OK;
@@ -455,6 +486,13 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->err);
     cudaFree(c->queue);
     cudaFree(c->items);
+    cudaFree(c->perm);
+    cudaFree(c->order.box);
+    cudaFree(c->order.keys[0]);
+    cudaFree(c->order.keys[1]);
+    cudaFree(c->order.vals[0]);
+    cudaFree(c->order.vals[1]);
+    cudaFree(c->order.hist);
     if (c->host_out) cudaFreeHost(c->host_out);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -626,6 +664,17 @@ nb_status nb_create(nb_ctx **out, int64_t n_max, nb_precision p, int device, voi
     if (st == NB_OK) c->dev_out = dev_alloc<double>(c, 16, st);
     if (st == NB_OK) c->err = dev_alloc<int>(c, 4, st);
     if (st == NB_OK) c->queue = dev_alloc<unsigned>(c, 4, st);
+    if (p != NB_FP64) {  // Morton-order scratch for the float32 kernels
+        const size_t nc = (size_t)ncap;
+        if (st == NB_OK) c->perm = dev_alloc<int>(c, nc, st);
+        if (st == NB_OK) c->order.box = dev_alloc<double>(c, 1024 * 6, st);
+        for (int q = 0; q < 2 && st == NB_OK; ++q) {
+            c->order.keys[q] = dev_alloc<unsigned>(c, nc, st);
+            if (st == NB_OK) c->order.vals[q] = dev_alloc<int>(c, nc, st);
+        }
+        if (st == NB_OK)
+            c->order.hist = dev_alloc<unsigned>(c, (size_t)256 * nb::sort_chunks((int)ncap), st);
+    }
     if (st != NB_OK) return bail(st);
     if (cudaMallocHost(&c->host_out, 16 * sizeof(double)) != cudaSuccess)
         return bail(failf(c, NB_ENOMEM, "cudaMallocHost failed"));
@@ -885,7 +934,7 @@ nb_status nb_forces_batched(nb_ctx *c, const double *pos, const double *mass, do
     NB_TRY(check_dev(c, mass, v1, "mass"));
     NB_TRY(check_dev(c, acc, v3, "acc"));
     if (n == 0) return NB_OK;
-    NB_TRY(pack(c, c->stream, n, pos, mass));
+    NB_TRY(pack(c, c->stream, n, pos, mass, false));
     return batched_force(c, c->stream, G, eps, acc, nullptr, 0.0);
 }
 
@@ -944,6 +993,16 @@ nb_status nb_tune_get(nb_ctx *c, int kind, int64_t n, int *variant, int *split)
 }
 
 int64_t nb_launch_count(const nb_ctx *c) { return c ? c->launches : 0; }
+
+nb_status nb_set_order(nb_ctx *c, int mode, int64_t min_n)
+{
+    if (!c) return NB_EINVAL;
+    if (mode < 0 || mode > 2 || min_n < 0) return failf(c, NB_EINVAL, "bad order mode");
+    c->order_mode = mode;
+    c->order_min_n = min_n;
+    drop_graphs(c);
+    return NB_OK;
+}
 
 nb_status nb_profile(nb_ctx *c, int enable)
 {

@@ -1,0 +1,244 @@
+// Spatial ordering of bodies for the float32 force kernels.
+//
+// The float32 pair differences d = x_j - x_i are formed in coordinates
+// relative to an origin at the centre of the i-tile (see force_f32.cu).  This
+// only helps close pairs when an i-tile is spatially compact, so for large N
+// the bodies are processed in Morton (Z-curve) order:
+//   1. bounding box of all positions (per-block partials, re-reduced by every
+//      block of the next kernel: no atomics, deterministic);
+//   2. 24-bit Morton key per body (8 bits per axis over the cube that holds
+//      the box);
+//   3. stable LSD radix sort of (key, body index), three 8-bit passes: per
+//      warp-chunk digit histograms, one exclusive scan in (digit, chunk)
+//      order, then a stable scatter that ranks equal digits within a warp
+//      with __match_any_sync, chunk keys taken strictly in order;
+//   4. packing in sorted order as float32 hi/lo pairs:
+//      P_hi = (fl(x), fl(y), fl(z), fl(m)), P_lo = (fl(x - fl(x)), ..., 0).
+// Every step is deterministic, so the order and the forces are reproducible.
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nb {
+namespace {
+
+constexpr int OTPB = 256;
+constexpr int MAX_BOX_PARTS = 1024;
+
+__device__ __forceinline__ unsigned spread8(unsigned v)
+{
+    v &= 0xffu;
+    v = (v | (v << 8)) & 0x00f00fu;
+    v = (v | (v << 4)) & 0x0c30c3u;
+    v = (v | (v << 2)) & 0x249249u;
+    return v;
+}
+
+// Per-block min/max of the positions: parts[b] = {minx,miny,minz,maxx,maxy,maxz}.
+__global__ void __launch_bounds__(OTPB) bbox_kernel(int n, const double *__restrict__ pos,
+                                                     double *__restrict__ parts)
+{
+    __shared__ double sh[6][OTPB];
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double v = pos[3 * (size_t)i + c];
+            mn[c] = fmin(mn[c], v);
+            mx[c] = fmax(mx[c], v);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        sh[c][threadIdx.x] = mn[c];
+        sh[3 + c][threadIdx.x] = mx[c];
+    }
+    __syncthreads();
+    for (int w = OTPB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sh[c][threadIdx.x] = fmin(sh[c][threadIdx.x], sh[c][threadIdx.x + w]);
+                sh[3 + c][threadIdx.x] = fmax(sh[3 + c][threadIdx.x], sh[3 + c][threadIdx.x + w]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) parts[6 * (size_t)blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Morton keys; every block first folds the box partials.
+__global__ void __launch_bounds__(OTPB) morton_kernel(int n, const double *__restrict__ pos,
+                                                       const double *__restrict__ parts,
+                                                       int nparts, unsigned *__restrict__ keys,
+                                                       int *__restrict__ vals)
+{
+    __shared__ double box[6];
+    if (threadIdx.x < 6) {
+        const bool is_min = threadIdx.x < 3;
+        double v = is_min ? DBL_MAX : -DBL_MAX;
+        for (int b = 0; b < nparts; ++b) {
+            const double p = parts[6 * (size_t)b + threadIdx.x];
+            v = is_min ? fmin(v, p) : fmax(v, p);
+        }
+        box[threadIdx.x] = v;
+    }
+    __syncthreads();
+    const double ext = fmax(fmax(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
+    const double scale = ext > 0.0 ? 256.0 / ext : 0.0;
+    for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
+        unsigned q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double t = (pos[3 * (size_t)i + c] - box[c]) * scale;
+            t = fmin(fmax(t, 0.0), 255.0);
+            q[c] = (unsigned)t;
+        }
+        keys[i] = spread8(q[0]) | (spread8(q[1]) << 1) | (spread8(q[2]) << 2);
+        vals[i] = i;
+    }
+}
+
+// Digit histogram per warp-chunk of SORT_CHUNK keys: hist[d * nchunks + chunk].
+__global__ void __launch_bounds__(OTPB) radix_hist_kernel(int n, const unsigned *__restrict__ keys,
+                                                           int shift, int nchunks,
+                                                           unsigned *__restrict__ hist)
+{
+    __shared__ unsigned cnt[OTPB / 32][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0u;
+    __syncwarp();
+    const int chunk = blockIdx.x * (OTPB / 32) + warp;
+    if (chunk < nchunks) {
+        const int base = chunk * SORT_CHUNK;
+        const int end = min(base + SORT_CHUNK, n);
+        for (int i = base + lane; i < end; i += 32) atomicAdd(&cnt[warp][(keys[i] >> shift) & 255u], 1u);
+        __syncwarp();
+        for (int d = lane; d < 256; d += 32) hist[(size_t)d * nchunks + chunk] = cnt[warp][d];
+    }
+}
+
+// In-place exclusive scan of hist[0..total) by one block, in index order.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(unsigned *__restrict__ hist, int total)
+{
+    __shared__ unsigned part[1024];
+    const int seg = (total + 1023) / 1024;
+    const int b = threadIdx.x * seg, e = min(b + seg, total);
+    unsigned s = 0u;
+    for (int i = b; i < e; ++i) s += hist[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = part[threadIdx.x] - s;  // exclusive prefix of this segment
+    for (int i = b; i < e; ++i) {
+        const unsigned h = hist[i];
+        hist[i] = run;
+        run += h;
+    }
+}
+
+// Stable scatter: one warp per chunk, keys taken 32 at a time in order.
+__global__ void __launch_bounds__(OTPB) radix_scatter_kernel(int n,
+                                                              const unsigned *__restrict__ kin,
+                                                              const int *__restrict__ vin,
+                                                              unsigned *__restrict__ kout,
+                                                              int *__restrict__ vout, int shift,
+                                                              int nchunks,
+                                                              const unsigned *__restrict__ offs)
+{
+    __shared__ unsigned run[OTPB / 32][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int chunk = blockIdx.x * (OTPB / 32) + warp;
+    if (chunk >= nchunks) return;  // whole warp leaves together
+    for (int d = lane; d < 256; d += 32) run[warp][d] = offs[(size_t)d * nchunks + chunk];
+    __syncwarp();
+    const int base = chunk * SORT_CHUNK;
+    const int end = min(base + SORT_CHUNK, n);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = base; r < end; r += 32) {
+        const int i = r + lane;
+        const bool valid = i < end;
+        const unsigned k = valid ? kin[i] : 0u;
+        const unsigned d = valid ? ((k >> shift) & 255u) : 256u + (unsigned)lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned off = 0u;
+        if (valid) off = run[warp][d] + (unsigned)__popc(peers & lt);
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) run[warp][d] += (unsigned)__popc(peers);
+        __syncwarp();
+        if (valid) {
+            kout[off] = k;
+            vout[off] = vin[i];
+        }
+    }
+}
+
+// Pack body perm[k] at slot k as float32 hi/lo pairs.
+__global__ void __launch_bounds__(OTPB) pack_hilo_kernel(int n, const double *__restrict__ pos,
+                                                          const double *__restrict__ mass,
+                                                          const int *__restrict__ perm,
+                                                          float4 *__restrict__ Phi,
+                                                          float4 *__restrict__ Plo)
+{
+    for (int k = blockIdx.x * OTPB + threadIdx.x; k < n; k += gridDim.x * OTPB) {
+        const int i = perm ? perm[k] : k;
+        const double *x = pos + 3 * (size_t)i;
+        const float hx = (float)x[0], hy = (float)x[1], hz = (float)x[2];
+        Phi[k] = make_float4(hx, hy, hz, (float)mass[i]);
+        Plo[k] = make_float4((float)(x[0] - (double)hx), (float)(x[1] - (double)hy),
+                             (float)(x[2] - (double)hz), 0.f);
+    }
+}
+
+inline int grid_for(int n)
+{
+    int g = (n + OTPB - 1) / OTPB;
+    return g < 1 ? 1 : (g > 4096 ? 4096 : g);
+}
+
+}  // namespace
+
+int sort_chunks(int n) { return (n + SORT_CHUNK - 1) / SORT_CHUNK; }
+
+cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
+                               int *perm_out, int &kernels)
+{
+    kernels = 0;
+    if (n <= 0) return cudaSuccess;
+    const int nparts = grid_for(n) < MAX_BOX_PARTS ? grid_for(n) : MAX_BOX_PARTS;
+    bbox_kernel<<<nparts, OTPB, 0, s>>>(n, pos, o.box);
+    ++kernels;
+    morton_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, nparts, o.keys[0], o.vals[0]);
+    ++kernels;
+    const int nchunks = sort_chunks(n);
+    const int blocks = (nchunks + OTPB / 32 - 1) / (OTPB / 32);
+    int cur = 0;
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = 8 * pass;
+        radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
+        radix_scan_kernel<<<1, 1024, 0, s>>>(o.hist, 256 * nchunks);
+        int *vout = pass == 2 ? perm_out : o.vals[cur ^ 1];
+        radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
+                                                     vout, shift, nchunks, o.hist);
+        kernels += 3;
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_hilo(cudaStream_t s, int n, const double *pos, const double *mass,
+                             const int *perm, float4 *Phi, float4 *Plo)
+{
+    if (n <= 0) return cudaSuccess;
+    pack_hilo_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, mass, perm, Phi, Plo);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

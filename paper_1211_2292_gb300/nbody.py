@@ -59,6 +59,7 @@ SIGNATURES = {
     "nb_tune_get": (_c_int, [_c_vp, _c_int, _c_i64, ctypes.POINTER(_c_int),
                              ctypes.POINTER(_c_int)]),
     "nb_launch_count": (_c_i64, [_c_vp]),
+    "nb_set_order": (_c_int, [_c_vp, _c_int, _c_i64]),
     "nb_profile": (_c_int, [_c_vp, _c_int]),
     "nb_profile_read": (_c_int, [_c_vp, _c_int, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_dbl)]),
     "nb_device_info": (_c_int, [_c_vp, _c_i64, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
@@ -265,6 +266,10 @@ class NBody:
         v, s = ctypes.c_int(), ctypes.c_int()
         self._call("nb_tune_get", int(kind), int(n), ctypes.byref(v), ctypes.byref(s))
         return v.value, s.value
+
+    def set_order(self, mode: int, min_n: int = 131072):
+        """Float32 body order: 0 input order, 1 Morton, 2 Morton when n >= min_n."""
+        self._call("nb_set_order", int(mode), int(min_n))
 
     def profile(self, enable: bool):
         """Start (clearing earlier records) or stop event timing of pair kernels."""

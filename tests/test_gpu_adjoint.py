@@ -63,7 +63,7 @@ def _grads(cuda, prec, b, G, eps, dt, K, every, tgt):
         xT, vT = rollout(nb, x0, v0, m, G, eps, dt, K, every)
         loss = ((xT - to_dev(tgt, cuda)) ** 2).sum(-1).mean()
         loss.backward()
-        return host(x0.grad), host(v0.grad), host(m.grad), float(loss)
+        return host(x0.grad), host(v0.grad), host(m.grad), float(loss.detach())
 
 
 @pytest.mark.parametrize("K,every", [(30, 7), (30, 30), (1, 1)])
