@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-per", type=int, default=WORKLOAD["n_per"],
+                    help="bodies per sphere (smaller cases for profiling)")
+    ap.add_argument("--tuning", default="default",
+                    help="kernel tuning table (JSON from paper_1211_2292_gb300.tune), "
+                         "'default' for the packaged GB300 table, 'none' for built-in defaults")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -224,9 +229,10 @@ def main():
         print("bench: --warmup raised to 3", file=sys.stderr)
         args.warmup = 3
     w = WORKLOAD
-    b = inputs.two_plummer(w["n_per"], seed=w["seed"])
+    b = inputs.two_plummer(args.n_per, seed=w["seed"])
     n = b.n
     G, eps, dt, nk = w["G"], w["eps"], w["dt"], w["steps"]
+    wname = w["name"] if n == 2 * WORKLOAD["n_per"] else w["name"].replace("1048576", str(n))
 
     # CPU baseline (oracle) before any GPU work; its rows also give the
     # reference forces for the float32 error.
@@ -258,7 +264,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    from paper_1211_2292_gb300 import tune
+    table = None if args.tuning == "none" else (None if args.tuning == "default" else args.tuning)
     nb = nbody.NBody(n, "fp32_comp", device=dev.index)
+    tuned = 0 if args.tuning == "none" else tune.apply(nb, table)
     pos = torch.as_tensor(b.pos, device=dev).contiguous()
     vel = torch.as_tensor(b.vel, device=dev).contiguous()
     mass = torch.as_tensor(b.mass, device=dev).contiguous()
@@ -333,6 +342,8 @@ def main():
     n64 = min(args.fp64_n, n)
     if n64 > 0:
         nb64 = nbody.NBody(n64, "fp64", device=dev.index)
+        if args.tuning != "none":
+            tune.apply(nb64, table)
         p64, m64 = pos[:n64].contiguous(), mass[:n64].contiguous()
         a64 = torch.empty_like(p64)
         nb64.forces(p64, m64, G, eps, out=a64)
@@ -392,10 +403,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Plummer spheres)",
-            "config": {"workload": WORKLOAD["name"], "n": n, "G": G, "eps": eps, "dt": dt,
+            "config": {"workload": wname, "n": n, "G": G, "eps": eps, "dt": dt,
                        "force_evals_per_step": evals, "precision": "fp32_comp",
                        "state": "f64", "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "tuning_entries": tuned,
+                       "variant": nb.tune_get(0, n)},
             "fp32_peak_frac": roofline["frac"],
             "force_error": force_err,
             "fp64_form": fp64,
