@@ -233,6 +233,38 @@ nb_status nb_profile_read(nb_ctx *ctx, int kind, int64_t *launches, double *tota
 nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm);
 
 /*
+ * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form
+ * (float32 pair terms, Kahan-compensated per-tile sums, float64 output), for
+ * callers that cannot allocate device memory: code running inside a CUDA
+ * stream capture that must not record allocations, code whose device memory
+ * is owned by another allocator or capped, and latency-critical loops where
+ * cudaMalloc could block.  The paper has no counterpart; this is a service of
+ * the library.
+ *
+ * It allocates nothing: no context, no cudaMalloc/cudaFree.  Its scratch
+ * (packed bodies, split partials, counters; about 8 MiB) is one fixed
+ * __device__ array that every GPU loading the library holds until the
+ * process exits, which bounds n to NB_NOALLOC_MAX_BODIES.  Work runs on the
+ * calling thread's current device, enqueued on `cuda_stream` (NULL = legacy
+ * default stream); pos [n][3], mass [n] and acc [n][3] are device arrays of
+ * that device, acc is overwritten.  Bodies are processed in input order (no
+ * spatial sort).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array: calls whose work
+ * overlaps on the GPU (different streams without ordering, several threads)
+ * race and give wrong results; order them on one stream.  Each call clears
+ * the counters it uses before its kernels run.  Returns NB_EINVAL (n < 0,
+ * n > NB_NOALLOC_MAX_BODIES, NULL/misaligned/non-device arrays, non-finite G,
+ * eps < 0) before enqueuing anything, NB_ECUDA if the runtime fails; there is
+ * no message text.  n == 0 is a no-op.
+ */
+#define NB_NOALLOC_MAX_BODIES 65536
+nb_status nb_forces_noalloc(int64_t n, const double *pos, const double *mass, double G,
+                            double eps, double *acc, void *cuda_stream);
+
+/*
  * Host-only scheduling helpers (no GPU needed; exported for tests).
  *
  * nb_choose_split: number of j-splits for n_itiles i-tiles of tile_bodies

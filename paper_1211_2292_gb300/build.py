@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
 SOURCES = ["force_f32.cu", "force_f64.cu", "adjoint.cu", "integrate.cu", "order.cu",
-           "nbody_abi.cpp"]
+           "noalloc.cu", "nbody_abi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

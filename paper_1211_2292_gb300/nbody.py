@@ -63,6 +63,7 @@ SIGNATURES = {
     "nb_profile": (_c_int, [_c_vp, _c_int]),
     "nb_profile_read": (_c_int, [_c_vp, _c_int, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_dbl)]),
     "nb_device_info": (_c_int, [_c_vp, _c_i64, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
                                     ctypes.POINTER(ctypes.c_int32), _c_i64]),
