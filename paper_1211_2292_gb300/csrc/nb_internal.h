@@ -104,7 +104,7 @@ int f64_vjp_variants();
 const KernelEntry &f64_vjp_kernel(int variant, bool zeps);
 
 // -------------------------------------------------- spatial order (order.cu)
-constexpr int SORT_CHUNK = 1024;  // keys per warp-chunk of the radix sort
+constexpr int SORT_CHUNK = 4096;  // keys per warp-chunk of the radix sort
 struct OrderScratch {
     double *box;        // [1024][6] bounding-box partials
     unsigned *keys[2];  // [n] Morton keys (ping-pong)

@@ -76,14 +76,21 @@ __global__ void __launch_bounds__(OTPB) morton_kernel(int n, const double *__res
                                                        int *__restrict__ vals)
 {
     __shared__ double box[6];
-    if (threadIdx.x < 6) {
-        const bool is_min = threadIdx.x < 3;
+    // warp c (c < 6) folds component c of the partials, lanes striding
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 6) {
+        const bool is_min = warp < 3;
         double v = is_min ? DBL_MAX : -DBL_MAX;
-        for (int b = 0; b < nparts; ++b) {
-            const double p = parts[6 * (size_t)b + threadIdx.x];
+        for (int b = lane; b < nparts; b += 32) {
+            const double p = parts[6 * (size_t)b + warp];
             v = is_min ? fmin(v, p) : fmax(v, p);
         }
-        box[threadIdx.x] = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, v, off);
+            v = is_min ? fmin(v, o) : fmax(v, o);
+        }
+        if (lane == 0) box[warp] = v;
     }
     __syncthreads();
     const double ext = fmax(fmax(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
