@@ -1,24 +1,26 @@
 #!/usr/bin/env python
 """Throughput benchmark of the softened direct-sum n-body path on GB300.
 
-Default workload: two Plummer spheres of 524,288 bodies each (N = 1,048,576),
-centres at (+-5, 0, 0) approaching at relative velocity 0.5, lognormal
-(sigma 0.5) masses normalised to 1, eps = 0.002, seed 2.  One bench step is
-one force evaluation plus 10 kick-drift-kick steps (11 force evaluations) in
-the float32 Kahan-compensated form with float64 state.  Metric: pairwise
-interactions per second, N^2 per force evaluation.
+Default workload ("throughput"): two Plummer spheres of 524,288 bodies each
+(N = 1,048,576), centres at (+-5, 0, 0) approaching at relative velocity
+0.5, lognormal (sigma 0.5) masses normalised to 1, eps = 0.002, seed 2.  One
+bench step is one force evaluation plus 10 kick-drift-kick steps (11 force
+evaluations) in the float32 Kahan-compensated form with float64 state.
+Metric: pairwise interactions per second, N^2 per force evaluation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload throughput|batched]
 
-Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
-the workload (the single-system path is not sharded); value is the sum over
-ranks divided by the slowest rank's time.
+Multi-GPU (torchrun, one rank per GPU): for "throughput" every rank runs its
+own replica (the single-system path is not sharded); for "batched" the 512
+independent systems are dealt to ranks largest first, with no collective on
+the data path.  value = interactions of all ranks / slowest rank's time.
 
-The JSON line also carries: the float64 form's rate, the float32 force error
-against the FP64 oracle on 4096 sampled bodies, the force kernel's roofline
-(event-timed inside the timed region), the oracle's CPU rate, an end-to-end
-rate with host buffers, the SM clocks sampled during the timed region and
-the number of library kernels launched.
+The JSON line also carries the float32 force error against the FP64 oracle on
+4096 sampled bodies, the force kernel's roofline (event-timed inside the timed
+region), the float64 form's rate, the batched and adjoint forms, the oracle's
+CPU rate, an end-to-end rate with host buffers, the SM clocks sampled during
+the timed region and the number of library kernels launched.
 """
 from __future__ import annotations
 
@@ -43,6 +45,12 @@ WORKLOAD = {
     "name": "two-plummer N=1048576, 1 force eval + 10 KDK steps, fp32 Kahan-compensated",
     "n_per": 524_288, "seed": 2, "G": 1.0, "eps": 0.002, "dt": 1e-3, "steps": 10,
 }
+BATCHED = {
+    "name": "512 Plummer systems, N log-uniform in [64, 8192], 100 KDK steps per graph launch, "
+            "fp32 Kahan-compensated",
+    "nsys": 512, "lo": 64, "hi": 8192, "seed": 3, "G": 1.0, "eps": 0.01, "dt": 1e-3, "steps": 100,
+}
+ADJOINT = {"n": 16384, "seed": 4, "eps": 0.01, "dt": 1e-3, "steps": 200, "every": 20}
 METRIC = "pairwise interactions/s (G/s)"
 UNIT = "Ginteractions/s"
 
@@ -53,31 +61,33 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["throughput", "batched"], default="throughput")
     ap.add_argument("--fp64-n", type=int, default=262_144,
                     help="bodies for the float64-form rate (first bodies of the workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched/adjoint form measurements")
     ap.add_argument("--n-per", type=int, default=WORKLOAD["n_per"],
                     help="bodies per sphere (smaller cases for profiling)")
+    ap.add_argument("--force-variant", type=int, default=-1,
+                    help="run the force kernel variant with this index (profiling)")
     ap.add_argument("--tuning", default="default",
                     help="kernel tuning table (JSON from paper_1211_2292_gb300.tune), "
                          "'default' for the packaged GB300 table, 'none' for built-in defaults")
-    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def dist_setup(args):
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+def dist_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def load_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(p) as f:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
@@ -111,7 +121,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -120,6 +130,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
+                power.append(float(f[3]))
             except ValueError:
                 continue
             for nm, val in zip(names, f[5:9]):
@@ -128,7 +139,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
 
 
 def traffic_from_profile():
@@ -154,140 +166,256 @@ def traffic_from_profile():
         return None
 
 
-def cpu_oracle_rate(pos, mass, G, eps, target_s, rows_idx=None):
-    """Oracle interactions/s on host cores over a bounded sample of rows."""
-    import numpy as np
+def oracle_rate(pos, mass, G, eps, target_s, seed=8):
+    """Oracle interactions/s on host cores over a bounded sample of force rows."""
     import oracle
     from paper_1211_2292_gb300 import inputs
     n = mass.shape[0]
     probe = inputs.sample_rows(n, 64, seed=7)
     t0 = time.perf_counter()
     oracle.accel_rows(pos, mass, probe, G, eps)
-    dt0 = max(time.perf_counter() - t0, 1e-6)
-    rate = probe.size * n / dt0
+    rate = probe.size * n / max(time.perf_counter() - t0, 1e-6)
     rows = int(min(n, max(256, rate * target_s / n)))
-    idx = inputs.sample_rows(n, rows, seed=8) if rows_idx is None else rows_idx
+    idx = inputs.sample_rows(n, rows, seed=seed)
     t0 = time.perf_counter()
-    ref = oracle.accel_rows(pos, mass, idx, G, eps)
+    oracle.accel_rows(pos, mass, idx, G, eps)
     el = time.perf_counter() - t0
-    return idx.size * n / el, el, idx, ref, oracle.threads()
+    return idx.size * n / el, el, rows
 
 
 def reference_arm(args, ws, rank):
-    """Oracle (FP64 CPU) timed on the host cores, same metric and workload."""
+    """The FP64 CPU oracle timed on the host cores, same metric and workload;
+    each step is a bounded sample of force rows of that workload."""
     if rank != 0:
         return 0
-    import numpy as np
     import oracle
     from paper_1211_2292_gb300 import inputs
-    w = WORKLOAD
-    b = inputs.two_plummer(w["n_per"], seed=w["seed"])
-    n = b.n
-    # rows per step so that one step is ~ a few seconds of CPU work
-    probe = inputs.sample_rows(n, 64, seed=7)
+    if args.workload == "batched":
+        w = BATCHED
+        bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
+        k = int(max(range(len(off) - 1), key=lambda q: off[q + 1] - off[q]))
+        pos, mass = bodies.pos[off[k]:off[k + 1]], bodies.mass[off[k]:off[k + 1]]
+        name, sample_of = w["name"], f"system {k} (N={off[k + 1] - off[k]})"
+    else:
+        w = WORKLOAD
+        b = inputs.two_plummer(w["n_per"], seed=w["seed"])
+        pos, mass = b.pos, b.mass
+        name, sample_of = w["name"], f"N={b.n}"
+    n = mass.shape[0]
+    probe = inputs.sample_rows(n, min(64, n), seed=7)
     t0 = time.perf_counter()
-    oracle.accel_rows(b.pos, b.mass, probe, w["G"], w["eps"])
+    oracle.accel_rows(pos, mass, probe, w["G"], w["eps"])
     rate = probe.size * n / max(time.perf_counter() - t0, 1e-6)
     rows = int(min(n, max(128, rate * 6.0 / n)))
     idx = inputs.sample_rows(n, rows, seed=9)
     for _ in range(args.warmup):
-        oracle.accel_rows(b.pos, b.mass, idx, w["G"], w["eps"])
+        oracle.accel_rows(pos, mass, idx, w["G"], w["eps"])
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.accel_rows(b.pos, b.mass, idx, w["G"], w["eps"])
+        oracle.accel_rows(pos, mass, idx, w["G"], w["eps"])
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = rows * n * args.steps / tot / 1e9
+    sample = f"{rows} force rows x {n} bodies of {sample_of} per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Plummer spheres)",
-        "config": {"workload": w["name"], "n": n, "eps": w["eps"],
-                   "sample": f"{rows} of {n} force rows per step"},
+        "config": {"workload": name, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
-                         "kind": "oracle",
-                         "sample": f"{rows} rows x {n} bodies of one force evaluation per step"},
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+class Timer:
+    """CUDA-event timing on one stream, bracketed by barrier + synchronize."""
+
+    def __init__(self, torch, dev, stream, barrier):
+        self.torch, self.dev, self.stream, self.barrier = torch, dev, stream, barrier
+
+    def __enter__(self):
+        self.barrier()
+        self.torch.cuda.synchronize(self.dev)
+        self.e0 = self.torch.cuda.Event(enable_timing=True)
+        self.e1 = self.torch.cuda.Event(enable_timing=True)
+        self.e0.record(self.stream)
+        return self
+
+    def __exit__(self, *exc):
+        self.e1.record(self.stream)
+        self.torch.cuda.synchronize(self.dev)
+        self.barrier()
+        self.ms = self.e0.elapsed_time(self.e1)
+
+
+def measure_forms(torch, dev, tune, table, peak_tflops):
+    """Rates of the batched and adjoint forms (rank-local, after the timed region)."""
+    from paper_1211_2292_gb300 import inputs, nbody
+    from paper_1211_2292_gb300.autograd import rollout
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    w = BATCHED
+    bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
+    pairs = float(sum(int(off[k + 1] - off[k]) ** 2 for k in range(len(off) - 1)))
+    with nbody.NBody(bodies.n, "fp32_comp", device=dev.index) as nb:
+        tune.apply(nb, table)
+        nb.batch_plan(off)
+        x, v, m = (torch.as_tensor(a, device=dev).contiguous()
+                   for a in (bodies.pos, bodies.vel, bodies.mass))
+        a = nb.forces_batched(x, m, w["G"], w["eps"])
+        nb.step_batched(x, v, m, w["G"], w["eps"], w["dt"], w["steps"], a, acc_valid=True,
+                        graph=True)
+        with Timer(torch, dev, stream, lambda: None) as t:
+            nb.step_batched(x, v, m, w["G"], w["eps"], w["dt"], w["steps"], a, acc_valid=True,
+                            graph=True)
+        nb.profile(True)
+        nb.forces_batched(x, m, w["G"], w["eps"], out=a)
+        kn, kms = nb.profile_read(1)
+        nb.profile(False)
+        out["batched"] = {"value": pairs * w["steps"] / (t.ms / 1e3) / 1e9, "unit": UNIT,
+                          "systems": w["nsys"], "bodies": bodies.n, "pairs_per_eval": pairs,
+                          "ms_per_100_steps_graph": t.ms, "kernel_ms": kms / max(kn, 1),
+                          "kernel_frac_of_fp32_peak": FLOPS_PER_INTERACTION * pairs
+                          / (kms / max(kn, 1) / 1e3) / 1e12 / peak_tflops}
+    a_ = ADJOINT
+    b, dx = inputs.plummer_with_perturbation(a_["n"], seed=a_["seed"])
+    with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+        tune.apply(nb, table)
+        x = torch.as_tensor(b.pos, device=dev).contiguous()
+        v = torch.as_tensor(b.vel, device=dev).contiguous()
+        m = torch.as_tensor(b.mass, device=dev).contiguous()
+        lam = torch.ones_like(x)
+        nb.forces_backward(x, m, 1.0, a_["eps"], lam)
+        nb.profile(True)
+        for _ in range(5):
+            nb.forces_backward(x, m, 1.0, a_["eps"], lam)
+        vn, vms = nb.profile_read(2)
+        nb.profile(False)
+        tgt = x + torch.as_tensor(dx, device=dev)
+
+        def grad():
+            x0 = x.clone().requires_grad_()
+            v0 = v.clone().requires_grad_()
+            mm = m.clone().requires_grad_()
+            xT, _ = rollout(nb, x0, v0, mm, 1.0, a_["eps"], a_["dt"], a_["steps"], a_["every"])
+            ((xT - tgt) ** 2).sum(-1).mean().backward()
+
+        grad()
+        with Timer(torch, dev, stream, lambda: None) as t:
+            grad()
+        n = float(b.n)
+        out["adjoint"] = {"vjp_value": n * n / (vms / vn / 1e3) / 1e9, "unit": UNIT,
+                          "vjp_ms": vms / vn, "n": b.n,
+                          "gradient_ms": t.ms,
+                          "gradient": f"{a_['steps']} steps, checkpoints every {a_['every']}, "
+                                      "forward + recompute + reverse sweep"}
+    return out
+
+
 def main():
     args = parse()
-    ws, rank, local = dist_setup(args)
+    ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
 
     import numpy as np
     import torch
-    from paper_1211_2292_gb300 import inputs, nbody
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody, shard, tune
 
     if args.warmup < 3:
         print("bench: --warmup raised to 3", file=sys.stderr)
         args.warmup = 3
-    w = WORKLOAD
-    b = inputs.two_plummer(args.n_per, seed=w["seed"])
-    n = b.n
-    G, eps, dt, nk = w["G"], w["eps"], w["dt"], w["steps"]
-    wname = w["name"] if n == 2 * WORKLOAD["n_per"] else w["name"].replace("1048576", str(n))
 
-    # CPU baseline (oracle) before any GPU work; its rows also give the
-    # reference forces for the float32 error.
-    cpu = None
-    err_idx = inputs.sample_rows(n, 4096, seed=1)
-    import oracle
-    t0 = time.perf_counter()
-    ref_rows = oracle.accel_rows(b.pos, b.mass, err_idx, G, eps)
-    t_err = time.perf_counter() - t0
-    if rank == 0 and not args.no_cpu_baseline:
-        rate = err_idx.size * n / t_err
-        el = t_err
-        rows = err_idx.size
-        if t_err < 0.5 * args.cpu_seconds:
-            rate, el, idx2, _, _ = cpu_oracle_rate(b.pos, b.mass, G, eps, args.cpu_seconds)
-            rows = idx2.size
+    # ---------------------------------------------------------------- inputs
+    if args.workload == "batched":
+        w = BATCHED
+        bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
+        mine = shard.shard_systems(np.diff(off), ws, rank)
+        idx, loc = shard.gather_rows(off, mine)
+        b = inputs.Bodies(bodies.pos[idx], bodies.vel[idx], bodies.mass[idx])
+        pairs_per_eval = float(sum(int(loc[k + 1] - loc[k]) ** 2 for k in range(len(loc) - 1)))
+        G, eps, dt, nk = w["G"], w["eps"], w["dt"], w["steps"]
+        wname, evals = w["name"], nk
+        prec_desc = "fp32_comp (batched persistent kernel, graph)"
+    else:
+        w = WORKLOAD
+        b = inputs.two_plummer(args.n_per, seed=w["seed"])
+        G, eps, dt, nk = w["G"], w["eps"], w["dt"], w["steps"]
+        wname = w["name"] if b.n == 2 * w["n_per"] else w["name"].replace("1048576", str(b.n))
+        pairs_per_eval = float(b.n) ** 2
+        evals = nk + 1
+        prec_desc = "fp32_comp"
+    n = b.n
+
+    # CPU baseline (oracle, before any GPU work) and float32 error reference
+    cpu, err_idx, ref_rows = None, None, None
+    if args.workload == "throughput":
+        err_idx = inputs.sample_rows(n, 4096, seed=1)
+        t0 = time.perf_counter()
+        ref_rows = oracle.accel_rows(b.pos, b.mass, err_idx, G, eps)
+        t_err = time.perf_counter() - t0
+        if rank == 0 and not args.no_cpu_baseline:
+            rate, el, rows = err_idx.size * n / t_err, t_err, err_idx.size
+            if t_err < 0.5 * args.cpu_seconds:
+                rate, el, rows = oracle_rate(b.pos, b.mass, G, eps, args.cpu_seconds)
+            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                   "sample": f"{rows} of {n} rows of one force evaluation ({el:.1f} s, FP64 C)"}
+    elif rank == 0 and not args.no_cpu_baseline:
+        k = int(np.argmax(np.diff(off)))
+        s, e = off[k], off[k + 1]
+        rate, el, rows = oracle_rate(bodies.pos[s:e], bodies.mass[s:e], G, eps, args.cpu_seconds)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-               "sample": f"{rows} of {n} rows of one force evaluation ({el:.1f} s, FP64 C)"}
+               "sample": f"{rows} force rows of the largest system (N={e - s}) ({el:.1f} s)"}
 
     dist = None
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
+    barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
+    stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    from paper_1211_2292_gb300 import tune
-    table = None if args.tuning == "none" else (None if args.tuning == "default" else args.tuning)
-    nb = nbody.NBody(n, "fp32_comp", device=dev.index)
+    table = None if args.tuning in ("none", "default") else args.tuning
+    nb = nbody.NBody(max(n, 1), "fp32_comp", device=dev.index)
     tuned = 0 if args.tuning == "none" else tune.apply(nb, table)
+    if args.force_variant >= 0:
+        nb.tune_set(0, 0, 1 << 40, args.force_variant, 0)
     pos = torch.as_tensor(b.pos, device=dev).contiguous()
     vel = torch.as_tensor(b.vel, device=dev).contiguous()
     mass = torch.as_tensor(b.mass, device=dev).contiguous()
     acc = torch.empty_like(pos)
 
-    # float32 force error on the sampled bodies at t = 0
-    a0 = nb.forces(pos, mass, G, eps).cpu().numpy()[err_idx]
-    e = np.linalg.norm(a0 - ref_rows, axis=1) / np.linalg.norm(ref_rows, axis=1)
-    force_err = {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
-                 "sample": "4096 bodies (seeded), vs FP64 oracle"}
+    force_err = None
+    if args.workload == "throughput":
+        a0 = nb.forces(pos, mass, G, eps).cpu().numpy()[err_idx]
+        e = np.linalg.norm(a0 - ref_rows, axis=1) / np.linalg.norm(ref_rows, axis=1)
+        force_err = {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
+                     "sample": "4096 bodies (seeded), vs FP64 oracle"}
+
+    if args.workload == "batched":
+        nb.batch_plan(loc)
+        nb.forces_batched(pos, mass, G, eps, out=acc)
+
+        def step():
+            nb.step_batched(pos, vel, mass, G, eps, dt, nk, acc, acc_valid=True, graph=True)
+    else:
+        def step():
+            nb.step(pos, vel, mass, G, eps, dt, nk, acc)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
     for _ in range(args.warmup):
-        nb.step(pos, vel, mass, G, eps, dt, nk, acc)
+        step()
         flush.fill_(1.0)
     torch.cuda.synchronize(dev)
 
-    gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -296,66 +424,72 @@ def main():
     time.sleep(0.3)
     nb.profile(True)
     l0 = nb.launches
-    barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        nb.step(pos, vel, mass, G, eps, dt, nk, acc)
-        flush.fill_(1.0)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
+    with Timer(torch, dev, stream, barrier) as t:
+        for _ in range(args.steps):
+            step()
+            flush.fill_(1.0)
     launches = nb.launches - l0
-    nf, force_ms = nb.profile_read(0)
+    kind = 1 if args.workload == "batched" else 0
+    nf, force_ms = nb.profile_read(kind)
     nb.profile(False)
     clk = clocks.stop()
-
-    evals = nk + 1
-    t_max = ms
+    if nf == 0:  # kernels ran inside a captured graph: time eager launches
+        nb.profile(True)
+        for _ in range(3):
+            nb.forces_batched(pos, mass, G, eps, out=acc)
+        nf, force_ms = nb.profile_read(kind)
+        nb.profile(False)
+    t_max = shard.max_over_ranks(t.ms, dist)
+    # every rank processes the same amount in "throughput"; in "batched" each
+    # rank's share is summed
+    pairs_total = pairs_per_eval * evals * args.steps
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    inter = float(n) * n * evals * args.steps * ws
-    value = inter / (t_max / 1e3) / 1e9
+        pt = torch.tensor([pairs_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(pt)
+        pairs_total = float(pt.item())
+    value = pairs_total / (t_max / 1e3) / 1e9
 
-    # roofline of the force kernel (plain FP32 ALU work)
+    # roofline of the dominant kernel (plain FP32 ALU work)
     props = torch.cuda.get_device_properties(dev)
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", NOMINAL_SM_MAX_MHZ))
+    sm_max = float(load_peaks().get("sm_max_mhz", NOMINAL_SM_MAX_MHZ))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    avg_force_ms = force_ms / max(nf, 1)
-    achieved = FLOPS_PER_INTERACTION * float(n) * n / (avg_force_ms / 1e3) / 1e12
+    avg_ms = force_ms / max(nf, 1)
+    achieved = FLOPS_PER_INTERACTION * pairs_per_eval / (avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic_from_profile(),
-                "kernel": "force_f32_kernel (Kahan)", "launches_timed": nf,
-                "avg_launch_ms": avg_force_ms,
-                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes"
-                              f" x 2 x {sm_max:.0f} MHz (sm_max_mhz)"}
+                "frac": achieved / peak_tflops,
+                "traffic": traffic_from_profile() if args.workload == "throughput" else None,
+                "kernel": ("force_f32_batched_kernel (Kahan)" if kind else
+                           "force_f32_kernel (Kahan)"),
+                "launches_timed": nf, "avg_launch_ms": avg_ms,
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                              f"lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz); "
+                              f"{FLOPS_PER_INTERACTION} flops per interaction"}
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak_tflops * clk["sm_mhz"] / sm_max)
 
-    # float64 form on the first fp64_n bodies
+    # float64 form (first fp64_n bodies of the workload)
     fp64 = None
-    n64 = min(args.fp64_n, n)
+    n64 = min(args.fp64_n, n) if args.workload == "throughput" else 0
     if n64 > 0:
-        nb64 = nbody.NBody(n64, "fp64", device=dev.index)
-        if args.tuning != "none":
-            tune.apply(nb64, table)
-        p64, m64 = pos[:n64].contiguous(), mass[:n64].contiguous()
-        a64 = torch.empty_like(p64)
-        nb64.forces(p64, m64, G, eps, out=a64)
-        nb64.profile(True)
-        nb64.forces(p64, m64, G, eps, out=a64)
-        k64, ms64 = nb64.profile_read(0)
-        nb64.profile(False)
-        fp64 = {"value": float(n64) ** 2 / (ms64 / 1e3) / 1e9, "unit": UNIT, "n": n64,
-                "kernel_ms": ms64, "note": "one FP64 force evaluation of the first n bodies "
-                                           "(the rate does not depend on N once the GPU is full)"}
-        fp64["fp32_over_fp64"] = (float(n) * n / (avg_force_ms / 1e3) / 1e9) / fp64["value"]
-        nb64.close()
+        with nbody.NBody(n64, "fp64", device=dev.index) as nb64:
+            if args.tuning != "none":
+                tune.apply(nb64, table)
+            p64, m64 = pos[:n64].contiguous(), mass[:n64].contiguous()
+            a64 = torch.empty_like(p64)
+            nb64.forces(p64, m64, G, eps, out=a64)
+            nb64.profile(True)
+            nb64.forces(p64, m64, G, eps, out=a64)
+            k64, ms64 = nb64.profile_read(0)
+            nb64.profile(False)
+        v64 = float(n64) ** 2 / (ms64 / 1e3) / 1e9
+        fp64 = {"value": v64, "unit": UNIT, "n": n64, "kernel_ms": ms64,
+                "fp32_over_fp64": (pairs_per_eval / (avg_ms / 1e3) / 1e9) / v64,
+                "note": "one FP64 force evaluation of the first n bodies (the rate does not "
+                        "depend on N once the GPU is full); FP64 error <= 1e-12 in the tests"}
+
+    forms = None
+    if not args.no_forms and rank == 0 and args.workload == "throughput":
+        forms = measure_forms(torch, dev, tune, table, peak_tflops)
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -365,53 +499,50 @@ def main():
         hm = torch.as_tensor(b.mass).pin_memory()
         op = torch.empty_like(hp).pin_memory()
         ov = torch.empty_like(hv).pin_memory()
-        dp, dv, dm = torch.empty_like(pos), torch.empty_like(vel), torch.empty_like(mass)
         e2e_steps = max(1, min(args.steps, 3))
 
         def e2e_step():
-            dp.copy_(hp, non_blocking=True)
-            dv.copy_(hv, non_blocking=True)
-            dm.copy_(hm, non_blocking=True)
-            nb.step(dp, dv, dm, G, eps, dt, nk, acc)
-            op.copy_(dp, non_blocking=True)
-            ov.copy_(dv, non_blocking=True)
+            pos.copy_(hp, non_blocking=True)
+            vel.copy_(hv, non_blocking=True)
+            mass.copy_(hm, non_blocking=True)
+            if args.workload == "batched":
+                nb.step_batched(pos, vel, mass, G, eps, dt, nk, acc, graph=True)
+            else:
+                nb.step(pos, vel, mass, G, eps, dt, nk, acc)
+            op.copy_(pos, non_blocking=True)
+            ov.copy_(vel, non_blocking=True)
             flush.fill_(1.0)
 
         e2e_step()
-        torch.cuda.synchronize(dev)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": float(n) * n * evals * e2e_steps * ws / (ems / 1e3) / 1e9, "unit": UNIT,
+        with Timer(torch, dev, stream, barrier) as te:
+            for _ in range(e2e_steps):
+                e2e_step()
+        ems = shard.max_over_ranks(te.ms, dist)
+        e_evals = evals + (1 if args.workload == "batched" else 0)
+        e2e = {"value": pairs_total / (args.steps * evals) * e_evals * e2e_steps / (ems / 1e3) / 1e9,
+               "unit": UNIT,
                "h2d_bytes_per_step": int(hp.numel() + hv.numel() + hm.numel()) * 8,
-               "d2h_bytes_per_step": int(op.numel() + ov.numel()) * 8,
-               "steps": e2e_steps}
+               "d2h_bytes_per_step": int(op.numel() + ov.numel()) * 8, "steps": e2e_steps}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak" if args.workload == "throughput" else "strong",
+            "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Plummer spheres)",
-            "config": {"workload": wname, "n": n, "G": G, "eps": eps, "dt": dt,
-                       "force_evals_per_step": evals, "precision": "fp32_comp",
-                       "state": "f64", "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "tuning_entries": tuned,
-                       "variant": nb.tune_get(0, n)},
+            "config": {"workload": wname, "n": n if ws == 1 or args.workload == "throughput"
+                       else int(BATCHED["nsys"]), "G": G, "eps": eps, "dt": dt,
+                       "force_evals_per_step": evals, "precision": prec_desc, "state": "f64",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": ("single GPU" if ws == 1 else
+                                       "replicas" if args.workload == "throughput" else
+                                       "systems sharded across ranks (LPT), no collective"),
+                       "tuning_entries": tuned, "variant": nb.tune_get(kind, n)},
             "fp32_peak_frac": roofline["frac"],
             "force_error": force_err,
             "fp64_form": fp64,
+            "forms": forms,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -50,7 +50,9 @@ typedef enum {
 
 typedef enum {
     NB_FP64 = 0,      /* every pair term and sum in float64 */
-    NB_FP32 = 1,      /* float32 pair terms, one float32 running sum per body */
+    NB_FP32 = 1,      /* float32 pair terms, one float32 running sum per body;
+                         float32 modes need masses >= 0 (a negative mass can give
+                         NB_ENONFINITE with the log-domain kernel variants) */
     NB_FP32_COMP = 2  /* float32 pair terms, float32 sums per j-tile added into
                          per-body Kahan-compensated (sum, carry) pairs */
 } nb_precision;

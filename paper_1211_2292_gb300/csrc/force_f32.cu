@@ -57,10 +57,21 @@ __device__ __forceinline__ void write_acc(const ForceParams &p, int i, double ax
     if (!finite3(ax, ay, az)) atomicOr(p.err, ERR_NONFINITE);
 }
 
-// Interaction of one body pair-lane set with j-body (xj,yj,zj,mj) given as
+// Interaction of one body pair-lane set with j-body (xj,yj,zj,wj) given as
 // duplicated float32x2 values.  nx/ny/nz hold the NEGATED i positions.
-template <bool ZEPS>
-__device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float2 mj, float2 e2,
+//
+// Two forms of the pair factor s = m_j / (r^2 + eps^2)^{3/2}:
+//  * rsqrt (LOGM = false, wj = m_j): r = rsqrt(r^2) on the MUFU pipe, then
+//    s = (r*r)*(m_j*r): 12 float32 operations per pair in total.
+//  * log domain (LOGM = true, wj = log2 m_j): s = 2^(log2 m_j - 1.5 log2 r^2)
+//    with lg2 and ex2 on the MUFU pipe and one fma: 10 float32 operations and
+//    2 MUFU per pair.  Measured on GB300: FFMA2 241 flop/clk/SM, rsqrt and
+//    lg2 16/clk/SM, ex2 32/clk/SM.  The rsqrt form is FMA-bound and the log
+//    form MUFU-bound at the same 10.7 pairs/clk/SM; a thread that runs 2/3 of
+//    its body pairs in the log form balances both pipes at 12 pairs/clk/SM.
+//    Needs m_j >= 0 (m_j = 0 gives log2 = -inf, s = 0).
+template <bool ZEPS, bool LOGM>
+__device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float2 wj, float2 e2,
                                           float2 nx, float2 ny, float2 nz, float2 &ax, float2 &ay,
                                           float2 &az)
 {
@@ -70,16 +81,30 @@ __device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float
     float2 r2 = fma2(dx, dx, e2);
     r2 = fma2(dy, dy, r2);
     r2 = fma2(dz, dz, r2);
-    float2 ri;
-    ri.x = rsqrt_mufu(r2.x);
-    ri.y = rsqrt_mufu(r2.y);
-    if (ZEPS) {  // eps == 0: the self pair (r^2 == 0) must contribute nothing
-        ri.x = r2.x > 0.f ? ri.x : 0.f;
-        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    float2 s;
+    if (LOGM) {
+        float2 l;
+        l.x = lg2_mufu(r2.x);
+        l.y = lg2_mufu(r2.y);
+        const float2 t = fma2(l, make_float2(-1.5f, -1.5f), wj);
+        s.x = ex2_mufu(t.x);
+        s.y = ex2_mufu(t.y);
+        if (ZEPS) {  // eps == 0: the self pair (r^2 == 0) must contribute nothing
+            s.x = r2.x > 0.f ? s.x : 0.f;
+            s.y = r2.y > 0.f ? s.y : 0.f;
+        }
+    } else {
+        float2 ri;
+        ri.x = rsqrt_mufu(r2.x);
+        ri.y = rsqrt_mufu(r2.y);
+        if (ZEPS) {
+            ri.x = r2.x > 0.f ? ri.x : 0.f;
+            ri.y = r2.y > 0.f ? ri.y : 0.f;
+        }
+        const float2 ri2 = mul2(ri, ri);
+        const float2 mri = mul2(wj, ri);
+        s = mul2(ri2, mri);
     }
-    float2 ri2 = mul2(ri, ri);
-    float2 mri = mul2(mj, ri);
-    float2 s = mul2(ri2, mri);
     ax = fma2(dx, s, ax);
     ay = fma2(dy, s, ay);
     az = fma2(dz, s, az);
@@ -88,12 +113,20 @@ __device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float
 // Tile-local coordinate of a hi/lo packed component.
 __device__ __forceinline__ float rel(float hi, float lo, float c) { return (hi - c) + lo; }
 
+// Shared-tile slots per j-body: (x,x,y,y), (z,z,m,m) and, for kernels with
+// log-domain pairs, (log2 m, log2 m, ., .).
+template <int LP>
+struct Slots {
+    static constexpr int W = LP > 0 ? 3 : 2;
+};
+
 // Stage this thread's share of a j-tile into the duplicated shared layout,
 // in coordinates relative to the tile origin c.
-template <int T, int J>
+template <int T, int J, int LP>
 __device__ __forceinline__ void stage_store(float4 *tile, const float4 (&bh)[J / T],
                                             const float4 (&bl)[J / T], float3 c)
 {
+    constexpr int W = Slots<LP>::W;
 #pragma unroll
     for (int l = 0; l < J / T; ++l) {
         const int jj = l * T + threadIdx.x;
@@ -101,11 +134,13 @@ __device__ __forceinline__ void stage_store(float4 *tile, const float4 (&bh)[J /
         const float y = rel(bh[l].y, bl[l].y, c.y);
         const float z = rel(bh[l].z, bl[l].z, c.z);
         const float m = bh[l].w;
-        tile[2 * jj] = make_float4(x, x, y, y);
-        tile[2 * jj + 1] = make_float4(z, z, m, m);
+        tile[W * jj] = make_float4(x, x, y, y);
+        tile[W * jj + 1] = make_float4(z, z, m, m);
+        if (W == 3) tile[W * jj + 2] = make_float4(bl[l].w, bl[l].w, 0.f, 0.f);
     }
 }
 
+// Out-of-range j slots become massless bodies (m = 0, log2 m = -inf).
 template <int T, int J>
 __device__ __forceinline__ void stage_load(float4 (&bh)[J / T], float4 (&bl)[J / T],
                                            const float4 *__restrict__ P,
@@ -116,31 +151,52 @@ __device__ __forceinline__ void stage_load(float4 (&bh)[J / T], float4 (&bl)[J /
         const int j = jbase + l * T + threadIdx.x;
         const bool ok = j < jend;
         bh[l] = ok ? __ldg(P + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        bl[l] = ok ? __ldg(Plo + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        bl[l] = ok ? __ldg(Plo + j) : make_float4(0.f, 0.f, 0.f, -INFINITY);
     }
 }
 
-// Accumulator state for the I bodies of one thread.
-template <int I, bool COMP>
+// Accumulator state for the I bodies of one thread.  The per-tile partials
+// live in registers; with KSM the Kahan (sum, carry) pairs live in shared
+// memory instead (touched once per j-tile), which frees 6*I registers for
+// occupancy.  ks: this CTA's [6][I][T] float array (KSM only).
+template <int T, int I, bool COMP, bool KSM>
 struct Acc {
     static constexpr int NP = I / 2;
+    static constexpr bool REG = COMP && !KSM;
     float2 ax[NP], ay[NP], az[NP];
-    float sx[COMP ? I : 1], sy[COMP ? I : 1], sz[COMP ? I : 1];
-    float cx[COMP ? I : 1], cy[COMP ? I : 1], cz[COMP ? I : 1];
+    float sx[REG ? I : 1], sy[REG ? I : 1], sz[REG ? I : 1];
+    float cx[REG ? I : 1], cy[REG ? I : 1], cz[REG ? I : 1];
+    float *ks;
 
-    __device__ __forceinline__ void init()
+    __device__ __forceinline__ float &ksm(int q, int k) const { return ks[(q * I + k) * T + threadIdx.x]; }
+
+    __device__ __forceinline__ void init(float *ks_)
     {
+        ks = ks_;
 #pragma unroll
         for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
-        if (COMP) {
+        if (REG) {
 #pragma unroll
             for (int k = 0; k < I; ++k) sx[k] = sy[k] = sz[k] = cx[k] = cy[k] = cz[k] = 0.f;
         }
+        if (COMP && KSM) {
+#pragma unroll
+            for (int k = 0; k < I; ++k)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) ksm(q, k) = 0.f;
+        }
+    }
+    __device__ __forceinline__ void fold(int q, int k, float part)
+    {
+        float sv = ksm(q, k), cv = ksm(q + 3, k);
+        kahan_add(sv, cv, part);
+        ksm(q, k) = sv;
+        ksm(q + 3, k) = cv;
     }
     // End of a j-tile: fold the tile partial into the compensated sums.
     __device__ __forceinline__ void end_tile()
     {
-        if (COMP) {
+        if (REG) {
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 kahan_add(sx[2 * p], cx[2 * p], ax[p].x);
@@ -151,15 +207,30 @@ struct Acc {
                 kahan_add(sz[2 * p + 1], cz[2 * p + 1], az[p].y);
                 ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
             }
+        } else if (COMP && KSM) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                fold(0, 2 * p, ax[p].x);
+                fold(0, 2 * p + 1, ax[p].y);
+                fold(1, 2 * p, ay[p].x);
+                fold(1, 2 * p + 1, ay[p].y);
+                fold(2, 2 * p, az[p].x);
+                fold(2, 2 * p + 1, az[p].y);
+                ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
+            }
         }
     }
-    // Value of body k's sum, component c, in float64.
+    // Value of body k's sum in float64.
     __device__ __forceinline__ void get(int k, double &x, double &y, double &z) const
     {
-        if (COMP) {
+        if (REG) {
             x = (double)sx[k] - (double)cx[k];
             y = (double)sy[k] - (double)cy[k];
             z = (double)sz[k] - (double)cz[k];
+        } else if (COMP && KSM) {
+            x = (double)ksm(0, k) - (double)ksm(3, k);
+            y = (double)ksm(1, k) - (double)ksm(4, k);
+            z = (double)ksm(2, k) - (double)ksm(5, k);
         } else {
             const int p = k >> 1;
             x = (k & 1) ? ax[p].y : ax[p].x;
@@ -171,19 +242,21 @@ struct Acc {
 
 // Sweep the j-tiles [t0, t1) of bodies [jlo, jhi) (tile t starts at
 // jlo + t*J) for this thread's bodies.  Threads split each tile's j loop in
-// `lanes` interleaved parts (lanes == 1 for the solo kernel).
-template <int T, int I, int J, bool COMP, bool ZEPS, bool LANES>
+// `lanes` interleaved parts (lanes == 1 for the solo kernel).  Body pairs
+// p < LP use the log-domain pair factor, the others rsqrt.
+template <int T, int I, int J, bool COMP, bool ZEPS, int LP, bool LANES, bool KSM, int UNR>
 __device__ __forceinline__ void sweep(const float4 *__restrict__ P, const float4 *__restrict__ Plo,
                                       float3 c, int jlo, int jhi, int t0, int t1, int lane,
                                       int lanes, float2 e2, const float2 (&nx)[I / 2],
                                       const float2 (&ny)[I / 2], const float2 (&nz)[I / 2],
-                                      Acc<I, COMP> &acc, float4 (*tile)[2 * J])
+                                      Acc<T, I, COMP, KSM> &acc, float4 (*tile)[Slots<LP>::W * J])
 {
     constexpr int NP = I / 2;
+    constexpr int W = Slots<LP>::W;
     float4 bh[J / T], bl[J / T];
     if (t0 < t1) {
         stage_load<T, J>(bh, bl, P, Plo, jlo + t0 * J, jhi);
-        stage_store<T, J>(tile[0], bh, bl, c);
+        stage_store<T, J, LP>(tile[0], bh, bl, c);
     }
     __syncthreads();
     for (int t = t0; t < t1; ++t) {
@@ -193,28 +266,38 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ P, const float4
         if (LANES) {
 #pragma unroll 4
             for (int jj = lane; jj < J; jj += lanes) {
-                const float4 q0 = s[2 * jj], q1 = s[2 * jj + 1];
+                const float4 q0 = s[W * jj], q1 = s[W * jj + 1];
                 const float2 xj = make_float2(q0.x, q0.y), yj = make_float2(q0.z, q0.w);
                 const float2 zj = make_float2(q1.x, q1.y), mj = make_float2(q1.z, q1.w);
 #pragma unroll
                 for (int p = 0; p < NP; ++p)
-                    interact2<ZEPS>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p], acc.ay[p],
-                                    acc.az[p]);
+                    interact2<ZEPS, false>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p],
+                                           acc.ay[p], acc.az[p]);
             }
         } else {
-#pragma unroll UNROLL_F32
+#pragma unroll UNR
             for (int jj = 0; jj < J; ++jj) {
-                const float4 q0 = s[2 * jj], q1 = s[2 * jj + 1];
+                const float4 q0 = s[W * jj], q1 = s[W * jj + 1];
                 const float2 xj = make_float2(q0.x, q0.y), yj = make_float2(q0.z, q0.w);
                 const float2 zj = make_float2(q1.x, q1.y), mj = make_float2(q1.z, q1.w);
+                float2 lj = mj;
+                if (LP > 0) {
+                    const float4 q2 = s[W * jj + 2];
+                    lj = make_float2(q2.x, q2.y);
+                }
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
-                    interact2<ZEPS>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p], acc.ay[p],
-                                    acc.az[p]);
+                for (int p = 0; p < NP; ++p) {
+                    if (p < LP)
+                        interact2<ZEPS, true>(xj, yj, zj, lj, e2, nx[p], ny[p], nz[p], acc.ax[p],
+                                              acc.ay[p], acc.az[p]);
+                    else
+                        interact2<ZEPS, false>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p],
+                                               acc.ay[p], acc.az[p]);
+                }
             }
         }
         acc.end_tile();
-        if (t + 1 < t1) stage_store<T, J>(tile[b ^ 1], bh, bl, c);
+        if (t + 1 < t1) stage_store<T, J, LP>(tile[b ^ 1], bh, bl, c);
         __syncthreads();
     }
 }
@@ -295,13 +378,16 @@ __device__ __forceinline__ float3 load_i(const float4 *__restrict__ P, const flo
 }
 
 // -------------------------------------------------------------- solo kernel
-template <int T, int I, int J, bool COMP, bool ZEPS>
-__global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
+// MINB > 0 caps registers so that MINB CTAs fit per SM; 0 leaves the choice
+// to the compiler.
+template <int T, int I, int J, bool COMP, bool ZEPS, int LP, bool KSM, int MINB>
+__global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceParams p)
 {
-    static_assert(I % 2 == 0 && J % T == 0, "bad tile shape");
+    static_assert(I % 2 == 0 && J % T == 0 && LP <= I / 2, "bad tile shape");
     constexpr int TILE_I = T * I;
-    __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ __align__(16) float4 tile[2][Slots<LP>::W * J];
     __shared__ float red[6][T / 32];
+    __shared__ float ks[(COMP && KSM) ? 6 * I * T : 1];
     __shared__ int s_last;
 
     const float4 *P = static_cast<const float4 *>(p.P);
@@ -315,10 +401,11 @@ __global__ void __launch_bounds__(T) force_f32_kernel(const ForceParams p)
 
     float2 nx[I / 2], ny[I / 2], nz[I / 2];
     const float3 c = load_i<T, I>(P, p.Plo, i0 + threadIdx.x, T, n, nx, ny, nz, red);
-    Acc<I, COMP> acc;
-    acc.init();
+    Acc<T, I, COMP, KSM> acc;
+    acc.init(ks);
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
-    sweep<T, I, J, COMP, ZEPS, false>(P, p.Plo, c, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
+    sweep<T, I, J, COMP, ZEPS, LP, false, KSM, (MINB > 0 ? 4 : UNROLL_F32)>(
+        P, p.Plo, c, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
 
     if (p.nsplit == 1) {
 #pragma unroll
@@ -399,15 +486,15 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
         const int groups = T / lanes;
         float2 nx[I / 2], ny[I / 2], nz[I / 2];
         const float3 c = load_i<T, I>(p.P, p.Plo, it.i0 + group, groups, it.i_end, nx, ny, nz, red);
-        Acc<I, COMP> acc;
-        acc.init();
+        Acc<T, I, COMP, false> acc;
+        acc.init(nullptr);
         const int ntiles = (it.j1 - it.j0 + J - 1) / J;
         if (lanes == 1)
-            sweep<T, I, J, COMP, ZEPS, false>(p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx,
-                                              ny, nz, acc, tile);
+            sweep<T, I, J, COMP, ZEPS, 0, false, false, UNROLL_F32>(
+                p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx, ny, nz, acc, tile);
         else
-            sweep<T, I, J, COMP, ZEPS, true>(p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, lane, lanes,
-                                             e2, nx, ny, nz, acc, tile);
+            sweep<T, I, J, COMP, ZEPS, 0, true, false, UNROLL_F32>(
+                p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, lane, lanes, e2, nx, ny, nz, acc, tile);
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             double x, y, z;
@@ -445,29 +532,49 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
     }
 }
 
-#define NB_F32_ENTRY(T, I, J)                                                           \
-    {{{T, I, J, (const void *)force_f32_kernel<T, I, J, false, false>},                 \
-      {T, I, J, (const void *)force_f32_kernel<T, I, J, false, true>}},                 \
-     {{T, I, J, (const void *)force_f32_kernel<T, I, J, true, false>},                  \
-      {T, I, J, (const void *)force_f32_kernel<T, I, J, true, true>}}}
+#define NB_F32_KERNEL(T, I, J, C, Z, L, K, M) \
+    {T, I, J, (const void *)force_f32_kernel<T, I, J, C, Z, L, K, M>, (L) > 0}
+// [comp][zero_eps]; L = body pairs per thread in the log-domain form;
+// K (Kahan state in shared memory) and M (register cap for M CTAs/SM) only
+// change the compensated kernels.
+#define NB_F32_ENTRY_X(T, I, J, L, K, M)                                                   \
+    {{NB_F32_KERNEL(T, I, J, false, false, L, false, 0),                                   \
+      NB_F32_KERNEL(T, I, J, false, true, L, false, 0)},                                   \
+     {NB_F32_KERNEL(T, I, J, true, false, L, K, M), NB_F32_KERNEL(T, I, J, true, true, L, K, M)}}
+#define NB_F32_ENTRY(T, I, J, L) NB_F32_ENTRY_X(T, I, J, L, false, 0)
 
 #define NB_F32B_ENTRY(T, I, J)                                                          \
-    {{{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, false>},         \
-      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, true>}},         \
-     {{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, false>},          \
-      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, true>}}}
+    {{{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, false>, false},  \
+      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, true>, false}},  \
+     {{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, false>, false},   \
+      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, true>, false}}}
 
 typedef KernelEntry Quad[2][2];
 
 const Quad kForce[] = {
-    NB_F32_ENTRY(128, 4, 128),
-    NB_F32_ENTRY(256, 4, 256),
-    NB_F32_ENTRY(128, 8, 128),
-    NB_F32_ENTRY(256, 2, 256),
-    NB_F32_ENTRY(64, 8, 128),
-    NB_F32_ENTRY(128, 6, 256),
-    NB_F32_ENTRY(256, 8, 256),
-    NB_F32_ENTRY(128, 2, 256),
+    // rsqrt form (variants 0..7)
+    NB_F32_ENTRY(128, 4, 128, 0),
+    NB_F32_ENTRY(256, 4, 256, 0),
+    NB_F32_ENTRY(128, 8, 128, 0),
+    NB_F32_ENTRY(256, 2, 256, 0),
+    NB_F32_ENTRY(64, 8, 128, 0),
+    NB_F32_ENTRY(128, 6, 256, 0),
+    NB_F32_ENTRY(256, 8, 256, 0),
+    NB_F32_ENTRY(128, 2, 256, 0),
+    // log-domain form for every pair (8..9)
+    NB_F32_ENTRY(256, 8, 256, 4),
+    NB_F32_ENTRY(64, 8, 128, 4),
+    // mixed: LP of the I/2 body pairs in the log-domain form (10..15)
+    NB_F32_ENTRY(256, 8, 256, 2),
+    NB_F32_ENTRY(256, 8, 256, 3),
+    NB_F32_ENTRY(128, 6, 256, 2),
+    NB_F32_ENTRY(256, 6, 256, 2),
+    NB_F32_ENTRY(64, 8, 128, 2),
+    NB_F32_ENTRY(128, 8, 128, 3),
+    // Kahan state in shared memory, registers capped at 128 for 4 CTAs of
+    // 128 threads per SM (16..17)
+    NB_F32_ENTRY_X(128, 8, 128, 0, true, 4),
+    NB_F32_ENTRY_X(128, 6, 128, 2, true, 4),
 };
 
 const Quad kBatched[] = {

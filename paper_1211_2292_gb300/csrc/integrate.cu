@@ -28,14 +28,15 @@ __device__ __forceinline__ void put(double4 *P, int i, double x, double y, doubl
 {
     P[i] = make_double4(x, y, z, m);
 }
-// float32 hi/lo pair: x = hi + lo with hi = fl(x), lo = fl(x - hi).
+// float32 hi/lo pair: x = hi + lo with hi = fl(x), lo = fl(x - hi); the lo
+// slot's w carries log2 m for the log-domain pair factor.
 __device__ __forceinline__ void put_hilo(float4 *P, float4 *Plo, int i, double x, double y,
                                          double z, double m)
 {
     const float hx = (float)x, hy = (float)y, hz = (float)z;
     P[i] = make_float4(hx, hy, hz, (float)m);
     Plo[i] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz),
-                         0.f);
+                         (float)log2(m));
 }
 
 template <typename V>

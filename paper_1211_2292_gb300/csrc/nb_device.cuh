@@ -27,6 +27,22 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     return y;
 }
 
+// Hardware base-2 logarithm and exponential (MUFU), subnormals flushed.
+// lg2: absolute error below 2^-22 on [0.5, 2) (relative elsewhere through the
+// exact exponent); ex2: relative error below 2^-22.
+__device__ __forceinline__ float lg2_mufu(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_mufu(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // float64 reciprocal square root: a float32 MUFU seed y0 (relative error
 // e0 < 2^-22) refined by one second-order Householder step for
 // f(y) = 1/y^2 - x.  With e = 1 - x*y0^2 the exact answer is

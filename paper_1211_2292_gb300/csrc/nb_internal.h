@@ -22,6 +22,7 @@ struct KernelEntry {
     int I;   // i-bodies per thread
     int J;   // j-bodies per shared-memory tile
     const void *fn;
+    bool logm = false;  // float32 kernels with log-domain pairs (read log2 m from P_lo.w)
 };
 
 // -------------------------------------------------------------- parameters
@@ -115,7 +116,8 @@ int sort_chunks(int n);
 // perm_out[k] = body at Morton rank k (stable in body index); `kernels` = launches made.
 cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
                                int *perm_out, int &kernels);
-// Phi[k], Plo[k] = float32 hi/lo packing of body perm[k] (perm NULL = identity).
+// Phi[k], Plo[k] = float32 hi/lo packing of body perm[k] (perm NULL = identity);
+// Phi.w = m, Plo.w = log2(m).
 cudaError_t launch_pack_hilo(cudaStream_t s, int n, const double *pos, const double *mass,
                              const int *perm, float4 *Phi, float4 *Plo);
 

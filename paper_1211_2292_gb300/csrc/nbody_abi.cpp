@@ -288,7 +288,8 @@ bool use_order(const nb_ctx *c, int64_t n)
 }
 
 // Pack bodies for a force call: float64 (x,y,z,m) in FP64 mode; float32
-// hi/lo pairs otherwise, in Morton order when use_order() holds.
+// hi/lo pairs otherwise, in Morton order when use_order() holds (never for
+// the batched kernel, allow_order = false).
 nb_status pack(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos, const double *mass,
                bool allow_order = true)
 {

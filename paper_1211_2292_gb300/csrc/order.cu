@@ -13,7 +13,8 @@
 //      order, then a stable scatter that ranks equal digits within a warp
 //      with __match_any_sync, chunk keys taken strictly in order;
 //   4. packing in sorted order as float32 hi/lo pairs:
-//      P_hi = (fl(x), fl(y), fl(z), fl(m)), P_lo = (fl(x - fl(x)), ..., 0).
+//      P_hi = (fl(x), fl(y), fl(z), fl(m)),
+//      P_lo = (fl(x - fl(x)), ..., fl(log2 m)) (log2 m for the log-domain pairs).
 // Every step is deterministic, so the order and the forces are reproducible.
 #include <cuda_runtime.h>
 #include <float.h>
@@ -198,9 +199,10 @@ __global__ void __launch_bounds__(OTPB) pack_hilo_kernel(int n, const double *__
         const int i = perm ? perm[k] : k;
         const double *x = pos + 3 * (size_t)i;
         const float hx = (float)x[0], hy = (float)x[1], hz = (float)x[2];
-        Phi[k] = make_float4(hx, hy, hz, (float)mass[i]);
+        const double m = mass[i];
+        Phi[k] = make_float4(hx, hy, hz, (float)m);
         Plo[k] = make_float4((float)(x[0] - (double)hx), (float)(x[1] - (double)hy),
-                             (float)(x[2] - (double)hz), 0.f);
+                             (float)(x[2] - (double)hz), (float)log2(m));
     }
 }
 

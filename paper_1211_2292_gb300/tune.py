@@ -152,13 +152,20 @@ def main():
     ap.add_argument("--sizes", default="", help="force sizes, comma separated")
     ap.add_argument("--splits", default="0")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--merge", default="",
+                    help="existing table whose entries for other precisions are kept")
     a = ap.parse_args()
     sizes = None
     if a.sizes:
         sizes = {nbody.KIND_FORCE: [int(x) for x in a.sizes.split(",")],
                  nbody.KIND_VJP: DEFAULT_SIZES[nbody.KIND_VJP]}
-    t = autotune(tuple(a.precisions.split(",")), sizes=sizes,
-                 splits=tuple(int(s) for s in a.splits.split(",")), reps=a.reps)
+    precs = tuple(a.precisions.split(","))
+    t = autotune(precs, sizes=sizes, splits=tuple(int(s) for s in a.splits.split(",")),
+                 reps=a.reps)
+    if a.merge and os.path.exists(a.merge):
+        old = load(a.merge)
+        t["entries"] = [e for e in old.get("entries", []) if e["precision"] not in precs] + \
+            t["entries"]
     with open(a.out, "w") as f:
         json.dump(t, f, indent=1)
     print(f"wrote {len(t['entries'])} entries to {a.out}")
