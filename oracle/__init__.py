@@ -46,27 +46,30 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    i64, dbl = ctypes.c_int64, ctypes.c_double
+    lib.oracle_threads.restype = ctypes.c_int
+    lib.oracle_accel.argtypes = [i64, _D, _D, dbl, dbl, _D]
+    lib.oracle_accel_rows.argtypes = [i64, _D, _D, dbl, dbl, i64, _I, _D]
+    lib.oracle_energy.argtypes = [i64, _D, _D, _D, dbl, dbl, _D]
+    lib.oracle_kdk.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64, _D]
+    lib.oracle_force_vjp.argtypes = [i64, _D, _D, dbl, dbl, _D, _D, _D]
+    lib.oracle_kdk_grad.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64,
+                                    _D, _D, _D, _D, _D]
+    lib.oracle_kdk_grad.restype = ctypes.c_int
+    for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
+              lib.oracle_kdk, lib.oracle_force_vjp):
+        f.restype = None
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        i64, dbl = ctypes.c_int64, ctypes.c_double
-        lib.oracle_threads.restype = ctypes.c_int
-        lib.oracle_accel.argtypes = [i64, _D, _D, dbl, dbl, _D]
-        lib.oracle_accel_rows.argtypes = [i64, _D, _D, dbl, dbl, i64, _I, _D]
-        lib.oracle_energy.argtypes = [i64, _D, _D, _D, dbl, dbl, _D]
-        lib.oracle_kdk.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64, _D]
-        lib.oracle_force_vjp.argtypes = [i64, _D, _D, dbl, dbl, _D, _D, _D]
-        lib.oracle_kdk_grad.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64,
-                                        _D, _D, _D, _D, _D]
-        lib.oracle_kdk_grad.restype = ctypes.c_int
-        for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
-                  lib.oracle_kdk, lib.oracle_force_vjp):
-            f.restype = None
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
 
 
 def _f64(a, shape=None):

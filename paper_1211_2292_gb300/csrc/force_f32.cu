@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceParams p)
     Acc<T, I, COMP, KSM> acc;
     acc.init(ks);
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
-    sweep<T, I, J, COMP, ZEPS, LP, false, KSM, (MINB > 0 ? 4 : UNROLL_F32)>(
+    sweep<T, I, J, COMP, ZEPS, LP, false, KSM, (MINB >= 4 ? 4 : UNROLL_F32)>(
         P, p.Plo, c, 0, n, t0, t1, 0, 1, e2, nx, ny, nz, acc, tile);
 
     if (p.nsplit == 1) {
@@ -575,6 +575,10 @@ const Quad kForce[] = {
     // 128 threads per SM (16..17)
     NB_F32_ENTRY_X(128, 8, 128, 0, true, 4),
     NB_F32_ENTRY_X(128, 6, 128, 2, true, 4),
+    // mixed, registers capped for 3 CTAs of 128 threads per SM (18..20)
+    NB_F32_ENTRY_X(128, 6, 256, 2, false, 3),
+    NB_F32_ENTRY_X(128, 6, 256, 2, true, 3),
+    NB_F32_ENTRY_X(128, 6, 128, 2, true, 3),
 };
 
 const Quad kBatched[] = {

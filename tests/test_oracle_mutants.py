@@ -1,0 +1,97 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a flipped
+sign, a wrong power of s, a dropped softening term, a swapped index, a wrong
+kick factor, a wrong adjoint term), builds it, swaps it in for the real
+oracle, and runs the pins of test_oracle_pins.py against it: at least one pin
+must fail.  The real oracle is restored afterwards.  Only the oracle (CPU)
+is mutated.
+"""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "nbody_oracle.c")
+
+MUTANTS = {
+    "sign of d": ("double dx = x[3 * j] - xi;", "double dx = xi - x[3 * j];"),
+    "power of s": ("double inv_s3 = 1.0 / (s2 * sqrt(s2));\n        ax",
+                   "double inv_s3 = 1.0 / s2;\n        ax"),
+    "softening dropped": ("dz * dz + eps * eps;\n        double inv_s3",
+                          "dz * dz;\n        double inv_s3"),
+    "mass index": ("ax += m[j] * dx * inv_s3;", "ax += m[i] * dx * inv_s3;"),
+    "self pair kept": ("        if (j == i) continue;\n        double dx",
+                       "        double dx"),
+    "G dropped": ("out[0] = G * ax;", "out[0] = ax;"),
+    "potential power": ("s += m[j] / sqrt(dx * dx + dy * dy + dz * dz + eps * eps);",
+                        "s += m[j] / (dx * dx + dy * dy + dz * dz + eps * eps);"),
+    "kinetic factor": ("ek += 0.5 * m[i] *", "ek += m[i] *"),
+    "first kick": ("for (int64_t k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * acc[k];\n"
+                   "        for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt * v[k];",
+                   "for (int64_t k = 0; k < 3 * n; ++k) v[k] += dt * acc[k];\n"
+                   "        for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt * v[k];"),
+    "vjp dyadic sign": ("g[c] += w[c] * inv_s3 - 3.0 * d[c] * dw * inv_s5;",
+                        "g[c] += w[c] * inv_s3 + 3.0 * d[c] * dw * inv_s5;"),
+    "vjp w swapped": ("w[c] = m[k] * lam[3 * j + c] - m[j] * lam[3 * k + c];",
+                      "w[c] = m[j] * lam[3 * j + c] - m[k] * lam[3 * k + c];"),
+    "vjp mass sign": ("gmk += -ld * inv_s3;", "gmk += ld * inv_s3;"),
+    "adjoint drift": ("for (size_t k = 0; k < per; ++k) lv[k] += dt * lx[k];",
+                      "for (size_t k = 0; k < per; ++k) lv[k] += 0.5 * dt * lx[k];"),
+}
+
+PINS = [
+    pins.test_two_body_closed_form, pins.test_two_body_zero_softening,
+    pins.test_equilateral_triangle, pins.test_newton_third_law,
+    pins.test_power_of_two_scaling_is_exact, pins.test_monopole_far_field,
+    pins.test_force_is_minus_gradient_of_potential, pins.test_energy_closed_forms,
+    pins.test_circular_orbit_phase_error_is_second_order,
+    pins.test_kepler_orbit_zero_softening, pins.test_time_reversibility,
+    pins.test_force_vjp_central_differences, pins.test_kdk_grad_central_differences,
+]
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+                    "-shared", str(path), "-o", str(so), "-lm"], check=True)
+    return oracle._bind(ctypes.CDLL(str(so)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    mutant = _build_mutant(tmp_path, old, new)
+    real = oracle._load()
+    caught = []
+    try:
+        oracle._lib = mutant
+        for pin in PINS:
+            try:
+                with __import__("warnings").catch_warnings():
+                    __import__("warnings").simplefilter("ignore")
+                    pin()
+            except (AssertionError, FloatingPointError, ValueError):
+                caught.append(pin.__name__)
+    finally:
+        oracle._lib = real
+    assert caught, f"no pin caught the mutant '{name}'"
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    real = oracle._load()
+    copy = _build_mutant(tmp_path, "int oracle_threads(void)", "int oracle_threads(void)")
+    try:
+        oracle._lib = copy
+        for pin in PINS:
+            pin()
+    finally:
+        oracle._lib = real
