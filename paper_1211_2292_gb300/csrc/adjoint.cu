@@ -6,11 +6,24 @@
 //        = G sum_j [ w/s^3 - 3 d (d.w)/s^5 ],      w = m_k mu_j - m_j mu_k
 //   gm_k = G sum_j mu_j . (x_k - x_j) / s^3  =  -G sum_j (mu_j . d_kj)/s^3
 //
-// The self pair contributes zero (d = 0 and w = 0).  Schedule as in the
-// force kernels: i-tile in registers, j-tiles (x,y,z,m),(mu,0) through
+// Schedule as in the force kernels: i-tile in registers, j-tiles through
 // double-buffered shared memory, j-split across CTAs with an ordered
-// last-CTA combine.  float32 variant: pair terms in float32, each tile's
-// partial added into float64 accumulators.  float64 variant: all float64.
+// last-CTA combine.
+//
+// float32 kernel (vjp_f32_kernel): float32x2 lanes over pairs of i-bodies,
+// positions as hi/lo pairs in coordinates relative to the i-tile's centre
+// (as in the force kernel), the direct w form accumulated as
+//   P_k = sum_j w/s^3,  Q_k = sum_j d (d.w)/s^5,  gx_k = G (P_k - 3 Q_k),
+//   M_k = sum_j (mu_j . d)/s^3,  gm_k = -G M_k,
+// 29 float32 operations (14.5 float32x2 issues) and one rsqrt per pair.
+// (Splitting w into m_k sum mu_j/s^3 - mu_k sum m_j/s^3 would save three
+// operations but rounds against large coherent sums when w is small, as for
+// smooth cotangent fields.)  The self pair is masked out exactly in the
+// j-tiles that overlap the CTA's own bodies, since fl(m_k mu_k) - fl(m_k mu_k)
+// through an fma leaves a rounding residue that 1/eps^3 would magnify.
+// Each tile's float32 partials are added into float64 totals.
+//
+// float64 kernel (vjp_kernel<double>): the direct form above, all float64.
 #include <cuda_runtime.h>
 
 #include "nb_device.cuh"
@@ -179,15 +192,301 @@ __global__ void __launch_bounds__(T) vjp_kernel(const VjpParams p)
     if (threadIdx.x == 0) p.counters[it] = 0u;
 }
 
+
+// ------------------------------------------------------ float32x2 kernel
+template <int T, int J>
+__device__ __forceinline__ void vjp_stage_load(float4 (&bh)[J / T], float4 (&bl)[J / T],
+                                               float4 (&bu)[J / T], const float4 *__restrict__ Ph,
+                                               const float4 *__restrict__ Pl,
+                                               const float4 *__restrict__ Pu, int jbase, int jend)
+{
+#pragma unroll
+    for (int l = 0; l < J / T; ++l) {
+        const int j = jbase + l * T + threadIdx.x;
+        const bool ok = j < jend;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        bh[l] = ok ? __ldg(Ph + j) : z;
+        bl[l] = ok ? __ldg(Pl + j) : z;
+        bu[l] = ok ? __ldg(Pu + j) : z;
+    }
+}
+
+// Shared layout per j: (x,x,y,y), (z,z,m,m), (ux,ux,uy,uy), (uz,uz,0,0).
+template <int T, int J>
+__device__ __forceinline__ void vjp_stage_store(float4 *tile, const float4 (&bh)[J / T],
+                                                const float4 (&bl)[J / T],
+                                                const float4 (&bu)[J / T], float3 c)
+{
+#pragma unroll
+    for (int l = 0; l < J / T; ++l) {
+        const int jj = l * T + threadIdx.x;
+        const float x = rel(bh[l].x, bl[l].x, c.x);
+        const float y = rel(bh[l].y, bl[l].y, c.y);
+        const float z = rel(bh[l].z, bl[l].z, c.z);
+        tile[4 * jj] = make_float4(x, x, y, y);
+        tile[4 * jj + 1] = make_float4(z, z, bh[l].w, bh[l].w);
+        tile[4 * jj + 2] = make_float4(bu[l].x, bu[l].x, bu[l].y, bu[l].y);
+        tile[4 * jj + 3] = make_float4(bu[l].z, bu[l].z, 0.f, 0.f);
+    }
+}
+
+// Per-pair-lane state of the float32 VJP.
+template <int NP>
+struct VjpAcc {
+    float2 px[NP], py[NP], pz[NP], qx[NP], qy[NP], qz[NP], gm[NP];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+            px[p] = py[p] = pz[p] = qx[p] = qy[p] = qz[p] = gm[p] = make_float2(0.f, 0.f);
+    }
+};
+
+template <bool ZEPS, bool MASK>
+__device__ __forceinline__ void vjp_pair(float2 xj, float2 yj, float2 zj, float2 mj, float2 ujx,
+                                         float2 ujy, float2 ujz, float2 e2, float2 nx, float2 ny,
+                                         float2 nz, float2 mk, float2 nukx, float2 nuky,
+                                         float2 nukz, bool self_a, bool self_b, float2 &px,
+                                         float2 &py, float2 &pz, float2 &qx, float2 &qy,
+                                         float2 &qz, float2 &gm)
+{
+    const float2 dx = add2(xj, nx), dy = add2(yj, ny), dz = add2(zj, nz);
+    float2 r2 = fma2(dx, dx, e2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float2 ri;
+    ri.x = rsqrt_mufu(r2.x);
+    ri.y = rsqrt_mufu(r2.y);
+    if (ZEPS) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    if (MASK) {  // the self pair j == k contributes nothing
+        ri.x = self_a ? 0.f : ri.x;
+        ri.y = self_b ? 0.f : ri.y;
+    }
+    const float2 ri2 = mul2(ri, ri);
+    const float2 ri3 = mul2(ri2, ri);
+    const float2 q5 = mul2(ri3, ri2);
+    // w = m_k mu_j - m_j mu_k
+    const float2 wx = fma2(mk, ujx, mul2(mj, nukx));
+    const float2 wy = fma2(mk, ujy, mul2(mj, nuky));
+    const float2 wz = fma2(mk, ujz, mul2(mj, nukz));
+    float2 dw = mul2(dx, wx);
+    dw = fma2(dy, wy, dw);
+    dw = fma2(dz, wz, dw);
+    const float2 c = mul2(dw, q5);
+    px = fma2(wx, ri3, px);
+    py = fma2(wy, ri3, py);
+    pz = fma2(wz, ri3, pz);
+    qx = fma2(dx, c, qx);
+    qy = fma2(dy, c, qy);
+    qz = fma2(dz, c, qz);
+    float2 dlj = mul2(dx, ujx);
+    dlj = fma2(dy, ujy, dlj);
+    dlj = fma2(dz, ujz, dlj);
+    gm = fma2(dlj, ri3, gm);
+}
+
+template <int T, int I, int J, bool ZEPS>
+__global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
+{
+    static_assert(I % 2 == 0 && J % T == 0, "bad tile shape");
+    constexpr int NP = I / 2;
+    constexpr int TILE_I = T * I;
+    constexpr int LPT = J / T;
+    __shared__ __align__(16) float4 tile[2][4 * J];
+    __shared__ float red[6][T / 32];
+    __shared__ int s_last;
+
+    const float4 *Ph = static_cast<const float4 *>(p.PV);
+    const float4 *Pl = p.Plo, *Pu = p.Plam;
+    const int n = p.n;
+    const int n_itiles = (n + TILE_I - 1) / TILE_I;
+    const int it = blockIdx.x % n_itiles;
+    const int js = blockIdx.x / n_itiles;
+    const int i0 = it * TILE_I;
+    int t0, t1;
+    split_range((n + J - 1) / J, p.nsplit, js, t0, t1);
+
+    // i-bodies: k-th body of the thread is i0 + tid + k*T; pair p = (2p, 2p+1)
+    float2 nx[NP], ny[NP], nz[NP], mk[NP], nukx[NP], nuky[NP], nukz[NP];
+    int ia[NP], ib[NP];
+    float3 c;
+    {
+        float4 h[I], l[I], u[I];
+        float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int i = i0 + threadIdx.x + k * T;
+            const bool ok = i < n;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            h[k] = ok ? __ldg(Ph + i) : z;
+            l[k] = ok ? __ldg(Pl + i) : z;
+            u[k] = ok ? __ldg(Pu + i) : z;
+            if (ok) {
+                mn[0] = fminf(mn[0], h[k].x); mx[0] = fmaxf(mx[0], h[k].x);
+                mn[1] = fminf(mn[1], h[k].y); mx[1] = fmaxf(mx[1], h[k].y);
+                mn[2] = fminf(mn[2], h[k].z); mx[2] = fmaxf(mx[2], h[k].z);
+            }
+        }
+        c = block_center<T>(mn, mx, red);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int a = 2 * q, b = 2 * q + 1;
+            nx[q] = make_float2(-rel(h[a].x, l[a].x, c.x), -rel(h[b].x, l[b].x, c.x));
+            ny[q] = make_float2(-rel(h[a].y, l[a].y, c.y), -rel(h[b].y, l[b].y, c.y));
+            nz[q] = make_float2(-rel(h[a].z, l[a].z, c.z), -rel(h[b].z, l[b].z, c.z));
+            mk[q] = make_float2(h[a].w, h[b].w);
+            nukx[q] = make_float2(-u[a].x, -u[b].x);
+            nuky[q] = make_float2(-u[a].y, -u[b].y);
+            nukz[q] = make_float2(-u[a].z, -u[b].z);
+            ia[q] = i0 + threadIdx.x + a * T;
+            ib[q] = i0 + threadIdx.x + b * T;
+        }
+    }
+    const float2 e2 = make_float2(p.eps2f, p.eps2f);
+    VjpAcc<NP> acc;
+    double tot[7][I];
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int k = 0; k < I; ++k) tot[q][k] = 0.0;
+
+    float4 bh[LPT], bl[LPT], bu[LPT];
+    if (t0 < t1) {
+        vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, t0 * J, n);
+        vjp_stage_store<T, J>(tile[0], bh, bl, bu, c);
+    }
+    __syncthreads();
+    for (int t = t0; t < t1; ++t) {
+        const int bsel = (t - t0) & 1;
+        if (t + 1 < t1) vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, (t + 1) * J, n);
+        acc.zero();
+        const float4 *s = tile[bsel];
+        const int jb = t * J;
+        const bool self_tile = jb < i0 + TILE_I && i0 < jb + J;
+        if (self_tile) {
+#pragma unroll 2
+            for (int jj = 0; jj < J; ++jj) {
+                const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
+                             q3 = s[4 * jj + 3];
+                const int jg = jb + jj;
+#pragma unroll
+                for (int q = 0; q < NP; ++q)
+                    vjp_pair<ZEPS, true>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                                         make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
+                                         make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                                         make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q], mk[q],
+                                         nukx[q], nuky[q], nukz[q], jg == ia[q], jg == ib[q],
+                                         acc.px[q], acc.py[q], acc.pz[q], acc.qx[q], acc.qy[q],
+                                         acc.qz[q], acc.gm[q]);
+            }
+        } else {
+#pragma unroll 4
+            for (int jj = 0; jj < J; ++jj) {
+                const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
+                             q3 = s[4 * jj + 3];
+#pragma unroll
+                for (int q = 0; q < NP; ++q)
+                    vjp_pair<ZEPS, false>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                                          make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
+                                          make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                                          make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q],
+                                          mk[q], nukx[q], nuky[q], nukz[q], false, false,
+                                          acc.px[q], acc.py[q], acc.pz[q], acc.qx[q], acc.qy[q],
+                                          acc.qz[q], acc.gm[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float2 *v[7] = {&acc.px[q], &acc.py[q], &acc.pz[q], &acc.qx[q],
+                                  &acc.qy[q], &acc.qz[q], &acc.gm[q]};
+#pragma unroll
+            for (int r = 0; r < 7; ++r) {
+                tot[r][2 * q] += (double)v[r]->x;
+                tot[r][2 * q + 1] += (double)v[r]->y;
+            }
+        }
+        if (t + 1 < t1) vjp_stage_store<T, J>(tile[bsel ^ 1], bh, bl, bu, c);
+        __syncthreads();
+    }
+
+    // gx = G (P - 3 Q), gm = -G M
+    auto emit = [&](int i, const double *sums) {
+        const double x = p.G * (sums[0] - 3.0 * sums[3]);
+        const double y = p.G * (sums[1] - 3.0 * sums[4]);
+        const double z = p.G * (sums[2] - 3.0 * sums[5]);
+        const double g = -p.G * sums[6];
+        double *o = p.gx + 3 * (size_t)i;
+        if (p.accumulate) {
+            o[0] += x; o[1] += y; o[2] += z;
+            p.gm[i] += g;
+        } else {
+            o[0] = x; o[1] = y; o[2] = z;
+            p.gm[i] = g;
+        }
+        if (!(finite3(x, y, z) && isfinite(g))) atomicOr(p.err, ERR_NONFINITE);
+    };
+    if (p.nsplit == 1) {
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int i = i0 + threadIdx.x + k * T;
+            if (i < n) {
+                double sums[7];
+#pragma unroll
+                for (int r = 0; r < 7; ++r) sums[r] = tot[r][k];
+                emit(i, sums);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        const int i = i0 + threadIdx.x + k * T;
+        if (i < n) {
+            double *q = p.partial + ((size_t)js * n + i) * 7;
+#pragma unroll
+            for (int r = 0; r < 7; ++r) q[r] = tot[r][k];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(p.counters + it, 1u) == (unsigned)(p.nsplit - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+        const int i = i0 + threadIdx.x + k * T;
+        if (i < n) {
+            double sums[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < p.nsplit; ++q) {
+                const double *r = p.partial + ((size_t)q * n + i) * 7;
+#pragma unroll
+                for (int u = 0; u < 7; ++u) sums[u] += __ldcg(r + u);
+            }
+            emit(i, sums);
+        }
+    }
+    if (threadIdx.x == 0) p.counters[it] = 0u;
+}
+
 #define NB_VJP_ENTRY(R, T, I, J)                                       \
     {{T, I, J, (const void *)vjp_kernel<R, T, I, J, false>},           \
      {T, I, J, (const void *)vjp_kernel<R, T, I, J, true>}}
 
 typedef KernelEntry Pair[2];
+#define NB_VJP32_ENTRY(T, I, J)                                   \
+    {{T, I, J, (const void *)vjp_f32_kernel<T, I, J, false>},     \
+     {T, I, J, (const void *)vjp_f32_kernel<T, I, J, true>}}
+
 const Pair kVjp32[] = {
-    NB_VJP_ENTRY(float, 128, 2, 128),
-    NB_VJP_ENTRY(float, 128, 4, 128),
-    NB_VJP_ENTRY(float, 256, 2, 256),
+    NB_VJP32_ENTRY(128, 2, 128),
+    NB_VJP32_ENTRY(128, 4, 128),
+    NB_VJP32_ENTRY(256, 2, 256),
+    NB_VJP32_ENTRY(64, 4, 128),
+    NB_VJP32_ENTRY(128, 4, 256),
 };
 const Pair kVjp64[] = {
     NB_VJP_ENTRY(double, 128, 1, 128),

@@ -89,12 +89,13 @@ __global__ void kdp_kernel(int n, double *__restrict__ pos, double *__restrict__
 
 // Adjoint packing: optional drift adjoint lam_v += drift * lam_x, then
 // cotangent mu = coef * lam (lam = lam_v when given, else `lam`), packed as
-// (x,y,z,m),(mu_x,mu_y,mu_z,0).
+// (x,y,z,m),(mu_x,mu_y,mu_z,0) in float64, or as hi/lo float32 positions plus
+// mu in three arrays `stride` float4 apart.
 template <typename V>
 __global__ void pack_vjp_kernel(int n, const double *__restrict__ pos,
                                 const double *__restrict__ mass, const double *__restrict__ lam,
                                 double *__restrict__ lam_v, const double *__restrict__ lam_x,
-                                double drift, double coef, V *__restrict__ PV)
+                                double drift, double coef, V *__restrict__ PV, size_t stride)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double *x = pos + 3 * (size_t)i;
@@ -113,8 +114,14 @@ __global__ void pack_vjp_kernel(int n, const double *__restrict__ pos,
             const double *l = lam + 3 * (size_t)i;
             l0 = l[0]; l1 = l[1]; l2 = l[2];
         }
-        put(PV, 2 * i, x[0], x[1], x[2], mass[i]);
-        put(PV, 2 * i + 1, coef * l0, coef * l1, coef * l2, 0.0);
+        if (sizeof(V) == sizeof(double4)) {
+            put(PV, 2 * i, x[0], x[1], x[2], mass[i]);
+            put(PV, 2 * i + 1, coef * l0, coef * l1, coef * l2, 0.0);
+        } else {
+            float4 *F = reinterpret_cast<float4 *>(PV);
+            put_hilo(F, F + stride, i, x[0], x[1], x[2], mass[i]);
+            put(F + 2 * stride, i, coef * l0, coef * l1, coef * l2, 0.0);
+        }
     }
 }
 
@@ -185,14 +192,14 @@ cudaError_t launch_kdp(cudaStream_t s, bool f64, int n, double *pos, double *vel
 
 cudaError_t launch_pack_vjp(cudaStream_t s, bool f64, int n, const double *pos, const double *mass,
                             const double *lam, double *lam_v, const double *lam_x, double drift,
-                            double coef, void *PV)
+                            double coef, void *PV, size_t stride)
 {
     if (f64)
         pack_vjp_kernel<double4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, lam, lam_v, lam_x,
-                                                              drift, coef, (double4 *)PV);
+                                                              drift, coef, (double4 *)PV, stride);
     else
         pack_vjp_kernel<float4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, lam, lam_v, lam_x,
-                                                             drift, coef, (float4 *)PV);
+                                                             drift, coef, (float4 *)PV, stride);
     return cudaGetLastError();
 }
 

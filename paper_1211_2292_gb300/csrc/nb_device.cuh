@@ -80,6 +80,50 @@ __device__ __forceinline__ bool finite3(double a, double b, double c)
     return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
+// Tile-local coordinate of a hi/lo packed component.
+__device__ __forceinline__ float rel(float hi, float lo, float c) { return (hi - c) + lo; }
+
+// Centre of the bounding box of the CTA's valid i-bodies (every thread gets
+// the same value).  red: shared scratch of 6 x (T/32) floats.
+template <int T>
+__device__ __forceinline__ float3 block_center(float (&mn)[3], float (&mx)[3], float (*red)[T / 32])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            red[c][warp] = mn[c];
+            red[3 + c][warp] = mx[c];
+        }
+    }
+    __syncthreads();
+    float a[3], b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = red[c][0];
+        b[c] = red[3 + c][0];
+#pragma unroll
+        for (int w = 1; w < T / 32; ++w) {
+            a[c] = fminf(a[c], red[c][w]);
+            b[c] = fmaxf(b[c], red[3 + c][w]);
+        }
+    }
+    __syncthreads();  // red may be reused by the caller afterwards
+    float3 o;
+    o.x = a[0] <= b[0] ? 0.5f * (a[0] + b[0]) : 0.f;
+    o.y = a[1] <= b[1] ? 0.5f * (a[1] + b[1]) : 0.f;
+    o.z = a[2] <= b[2] ? 0.5f * (a[2] + b[2]) : 0.f;
+    return o;
+}
+
 // Error-word bits (ctx scratch, read by nb_sync / nb_energy).
 enum : int { ERR_NONFINITE = 1 };
 

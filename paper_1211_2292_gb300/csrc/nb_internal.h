@@ -66,7 +66,10 @@ struct BatchParams {
 };
 
 struct VjpParams {
-    const void *PV;       // packed (x,y,z,m),(mu_x,mu_y,mu_z,0) per body, float or double
+    const void *PV;       // float64: (x,y,z,m),(mu_x,mu_y,mu_z,0) per body (double4 pairs);
+                          // float32: (x_hi,y_hi,z_hi,m) per body
+    const float4 *Plo;    // float32: (x_lo,y_lo,z_lo,.)
+    const float4 *Plam;   // float32: (mu_x,mu_y,mu_z,0)
     int n;
     int nsplit;
     float eps2f;
@@ -75,7 +78,7 @@ struct VjpParams {
     double *gx;           // [n][3]
     double *gm;           // [n]
     int accumulate;       // 0: overwrite gx/gm with G*sum; 1: add G*sum
-    double *partial;      // [nsplit][n][4]
+    double *partial;      // [nsplit][n][4] (float64 kernel) or [nsplit][n][7] (float32)
     unsigned *counters;
     int *err;
 };
@@ -130,10 +133,12 @@ cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const doub
 cudaError_t launch_kdp(cudaStream_t s, bool f64, int n, double *pos, double *vel, const double *acc,
                        const double *mass, double half_dt, double dt, void *P, float4 *Plo,
                        double *rec_pos, double *rec_vel);
-// Adjoint packing: lam_v += drift * lam_x (if lam_x), mu = coef * lam_v, pack (x, m, mu).
+// Adjoint packing: lam_v += drift * lam_x (if lam_x), mu = coef * lam_v, pack (x, m, mu):
+// float64 as double4 pairs at PV[2i], PV[2i+1]; float32 as three float4 arrays
+// PV[i] = (x_hi,y_hi,z_hi,m), PV[stride + i] = (x_lo,..,0), PV[2 stride + i] = (mu,0).
 cudaError_t launch_pack_vjp(cudaStream_t s, bool f64, int n, const double *pos, const double *mass,
                             const double *lam, double *lam_v, const double *lam_x, double drift,
-                            double coef, void *PV);
+                            double coef, void *PV, size_t stride);
 cudaError_t launch_energy_final(cudaStream_t s, const double *red, int nparts, double G, double *out);
 
 // Host-side scheduling helpers (nbody_abi.cpp; exported for tests).

@@ -247,8 +247,11 @@ int splits_for(nb_ctx *c, const KernelEntry &k, int64_t n, int forced, int64_t p
     return s < 1 ? 1 : s;
 }
 
-// Second half of the float32 pack buffer: the lo parts of the hi/lo pairs.
-float4 *lo_half(nb_ctx *c) { return (float4 *)c->pack + std::max<int64_t>(c->n_max, 1); }
+// float4 slots between the arrays of the float32 pack (hi, lo, cotangent).
+size_t pack_stride(const nb_ctx *c) { return (size_t)std::max<int64_t>(c->n_max, 1); }
+
+// Second array of the float32 pack buffer: the lo parts of the hi/lo pairs.
+float4 *lo_half(nb_ctx *c) { return (float4 *)c->pack + pack_stride(c); }
 
 // ------------------------------------------------------------- force paths
 // Force on the already packed bodies; optional fused half-kick of vel.
@@ -358,9 +361,11 @@ nb_status vjp_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double eps,
     int v, forced;
     pick(c, nb::KIND_VJP, n, v, forced);
     const KernelEntry &k = kernel_for(nb::KIND_VJP, c->prec, v, zeps);
-    const int S = splits_for(c, k, n, forced, 4);
+    const int S = splits_for(c, k, n, forced, is_f64(c) ? 4 : 7);
     nb::VjpParams p;
     p.PV = c->pack;
+    p.Plo = is_f64(c) ? nullptr : lo_half(c);
+    p.Plam = is_f64(c) ? nullptr : lo_half(c) + std::max<int64_t>(c->n_max, 1);
     p.n = (int)n;
     p.nsplit = S;
     p.eps2f = (float)(eps * eps);
@@ -842,7 +847,7 @@ nb_status nb_forces_backward(nb_ctx *c, int64_t n, const double *pos, const doub
     if (n == 0) return NB_OK;
     cudaStream_t s = c->stream;
     NB_LAUNCHED(c, nb::launch_pack_vjp(s, is_f64(c), (int)n, pos, mass, grad_acc, nullptr, nullptr,
-                                       0.0, 1.0, c->pack));
+                                       0.0, 1.0, c->pack, pack_stride(c)));
     return vjp_packed(c, s, n, G, eps, grad_pos, grad_mass, 0);
 }
 
@@ -870,13 +875,14 @@ nb_status nb_step_backward(nb_ctx *c, int64_t n, const double *traj, const doubl
     if (flags & NB_BWD_AT_END) {
         // closing half-kick of the run's last step: VJP at x_K with dt/2 lam_v
         NB_LAUNCHED(c, nb::launch_pack_vjp(s, f64, (int)n, traj + per * (size_t)nsteps, mass,
-                                           nullptr, lam_v, nullptr, 0.0, 0.5 * dt, c->pack));
+                                           nullptr, lam_v, nullptr, 0.0, 0.5 * dt, c->pack,
+                                           pack_stride(c)));
         NB_TRY(vjp_packed(c, s, n, G, eps, lam_x, lam_m, 1));
     }
     for (int64_t st = nsteps - 1; st >= 0; --st) {
         const double coef = (st == 0 && (flags & NB_BWD_AT_START)) ? 0.5 * dt : dt;
         NB_LAUNCHED(c, nb::launch_pack_vjp(s, f64, (int)n, traj + per * (size_t)st, mass, nullptr,
-                                           lam_v, lam_x, dt, coef, c->pack));
+                                           lam_v, lam_x, dt, coef, c->pack, pack_stride(c)));
         NB_TRY(vjp_packed(c, s, n, G, eps, lam_x, lam_m, 1));
     }
     return NB_OK;

@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--sizes", default="", help="force sizes, comma separated")
     ap.add_argument("--splits", default="0")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--kinds", default="force,vjp,batched",
+                    help="which kernel families to tune")
     ap.add_argument("--merge", default="",
                     help="existing table whose entries for other precisions are kept")
     a = ap.parse_args()
@@ -160,12 +162,15 @@ def main():
         sizes = {nbody.KIND_FORCE: [int(x) for x in a.sizes.split(",")],
                  nbody.KIND_VJP: DEFAULT_SIZES[nbody.KIND_VJP]}
     precs = tuple(a.precisions.split(","))
-    t = autotune(precs, sizes=sizes, splits=tuple(int(s) for s in a.splits.split(",")),
-                 reps=a.reps)
+    names = {"force": nbody.KIND_FORCE, "vjp": nbody.KIND_VJP, "batched": nbody.KIND_BATCHED}
+    kinds = [names[k] for k in a.kinds.split(",") if k]
+    t = autotune(precs, kinds=tuple(k for k in kinds if k != nbody.KIND_BATCHED), sizes=sizes,
+                 splits=tuple(int(s) for s in a.splits.split(",")), reps=a.reps,
+                 batch=nbody.KIND_BATCHED in kinds)
     if a.merge and os.path.exists(a.merge):
         old = load(a.merge)
-        t["entries"] = [e for e in old.get("entries", []) if e["precision"] not in precs] + \
-            t["entries"]
+        t["entries"] = [e for e in old.get("entries", [])
+                        if not (e["precision"] in precs and e["kind"] in kinds)] + t["entries"]
     with open(a.out, "w") as f:
         json.dump(t, f, indent=1)
     print(f"wrote {len(t['entries'])} entries to {a.out}")

@@ -15,9 +15,13 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_comp", 2e-5), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_comp", 5e-5), ("fp32", 5e-5)])
 @pytest.mark.parametrize("n", [2, 33, 1000, 2049])
 def test_force_vjp_matches_oracle(cuda, prec, tol, n):
+    # FP32 tolerance: the float32 rounding of the positions perturbs each
+    # close-pair term by about ulp(|x - c|)/|d| relative (c the tile origin),
+    # and the VJP sums cancel (random-sign cotangents), so 5e-5 relative in
+    # norm; the direct float32 arithmetic itself contributes ~1e-6.
     b = inputs.plummer(n, seed=40 + n)
     lam = np.random.default_rng(n).normal(size=(n, 3))
     rgx, rgm = oracle.force_vjp(b.pos, b.mass, lam, 1.2, 0.01)
@@ -34,7 +38,7 @@ def test_vjp_variants_and_splits(cuda, prec):
     b = inputs.plummer(1500, seed=41)
     lam = np.random.default_rng(1).normal(size=(1500, 3))
     rgx, rgm = oracle.force_vjp(b.pos, b.mass, lam, 1.0, 0.02)
-    tol = 1e-12 if prec == "fp64" else 2e-5
+    tol = 1e-12 if prec == "fp64" else 5e-5
     for v in range(len(nbody.variants(nbody.KIND_VJP, prec))):
         for split in (1, 4):
             with nbody.NBody(1500, prec) as nb:
@@ -43,6 +47,19 @@ def test_vjp_variants_and_splits(cuda, prec):
                                             to_dev(lam, cuda))
                 nb.sync()
             assert _rel(host(gx), rgx) <= tol and _rel(host(gm), rgm) <= tol, (v, split)
+
+
+def test_vjp_smooth_cotangent_fp32(cuda):
+    # A smooth cotangent field (as the adjoint's dt*lam_v is) makes
+    # w = m_k mu_j - m_j mu_k small for close pairs: the direct w form keeps
+    # the float32 VJP accurate there.
+    b = inputs.plummer(3000, seed=48)
+    lam = np.stack([np.sin(b.pos[:, 0]), np.cos(b.pos[:, 1]), b.pos[:, 2] * 0.5], axis=1) + 1.0
+    rgx, rgm = oracle.force_vjp(b.pos, b.mass, lam, 1.0, 0.01)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        gx, gm = nb.forces_backward(to_dev(b.pos, cuda), to_dev(b.mass, cuda), 1.0, 0.01,
+                                    to_dev(lam, cuda))
+    assert _rel(host(gx), rgx) <= 5e-5 and _rel(host(gm), rgm) <= 5e-5
 
 
 def test_vjp_zero_softening(cuda):
