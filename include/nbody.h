@@ -276,15 +276,17 @@ nb_status nb_forces_noalloc(int64_t n, const double *pos, const double *mass, do
  *
  * nb_plan_batch_host: the work items of the batched kernel for CTAs of
  * `threads` x `bodies_per_thread` bodies and j-tiles of `jtile`, largest
- * cost first.  items_out holds 8 int32 per item {i0, i_end, j0, j1, lanes,
- * sys, 0, 0}; returns the item count (items_out may be NULL to count), or -1
- * for invalid offsets or when more than max_items are needed.
+ * cost first.  Each system gets the most lanes per body that still cover it
+ * with one item, and more while an item would exceed max_item_pairs
+ * (0 = no cap).  items_out holds 8 int32 per item {i0, i_end, j0, j1,
+ * lanes, sys, 0, 0}; returns the item count (items_out may be NULL to
+ * count), or -1 for invalid offsets or when more than max_items are needed.
  */
 int nb_choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots,
                     int64_t max_split_bodies, int64_t tile_bodies);
 int64_t nb_plan_batch_host(int64_t nsys, const int64_t *offsets, int threads,
-                           int bodies_per_thread, int jtile, int32_t *items_out,
-                           int64_t max_items);
+                           int bodies_per_thread, int jtile, int64_t max_item_pairs,
+                           int32_t *items_out, int64_t max_items);
 
 #ifdef __cplusplus
 }

@@ -267,10 +267,20 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ P, const float4
                 const float4 q0 = s[W * jj], q1 = s[W * jj + 1];
                 const float2 xj = make_float2(q0.x, q0.y), yj = make_float2(q0.z, q0.w);
                 const float2 zj = make_float2(q1.x, q1.y), mj = make_float2(q1.z, q1.w);
+                float2 lj = mj;
+                if (LP > 0) {
+                    const float4 q2 = s[W * jj + 2];
+                    lj = make_float2(q2.x, q2.y);
+                }
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
-                    interact2<ZEPS, false>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p],
-                                           acc.ay[p], acc.az[p]);
+                for (int p = 0; p < NP; ++p) {
+                    if (p < LP)
+                        interact2<ZEPS, true>(xj, yj, zj, lj, e2, nx[p], ny[p], nz[p], acc.ax[p],
+                                              acc.ay[p], acc.az[p]);
+                    else
+                        interact2<ZEPS, false>(xj, yj, zj, mj, e2, nx[p], ny[p], nz[p], acc.ax[p],
+                                               acc.ay[p], acc.az[p]);
+                }
             }
         } else {
 #pragma unroll UNR
@@ -417,10 +427,10 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceParams p)
 // counter until the queue is empty, the GPU analogue of the paper's dynamic
 // loop schedule (Sec. V-C, Table VI).  The last CTA to finish resets the
 // counters for the next launch; nothing waits.
-template <int T, int I, int J, bool COMP, bool ZEPS>
+template <int T, int I, int J, bool COMP, bool ZEPS, int LP>
 __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams p)
 {
-    __shared__ __align__(16) float4 tile[2][2 * J];
+    __shared__ __align__(16) float4 tile[2][Slots<LP>::W * J];
     __shared__ float red[6][T / 32];
     __shared__ BatchItem s_item;
     __shared__ int s_idx;
@@ -447,10 +457,10 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
         acc.init(nullptr);
         const int ntiles = (it.j1 - it.j0 + J - 1) / J;
         if (lanes == 1)
-            sweep<T, I, J, COMP, ZEPS, 0, false, false, UNROLL_F32>(
+            sweep<T, I, J, COMP, ZEPS, LP, false, false, UNROLL_F32>(
                 p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, 0, 1, e2, nx, ny, nz, acc, tile);
         else
-            sweep<T, I, J, COMP, ZEPS, 0, true, false, UNROLL_F32>(
+            sweep<T, I, J, COMP, ZEPS, LP, true, false, UNROLL_F32>(
                 p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, lane, lanes, e2, nx, ny, nz, acc, tile);
 #pragma unroll
         for (int k = 0; k < I; ++k) {
@@ -500,11 +510,11 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
      {NB_F32_KERNEL(T, I, J, true, false, L, K, M), NB_F32_KERNEL(T, I, J, true, true, L, K, M)}}
 #define NB_F32_ENTRY(T, I, J, L) NB_F32_ENTRY_X(T, I, J, L, false, 0)
 
-#define NB_F32B_ENTRY(T, I, J)                                                          \
-    {{{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, false>, false},  \
-      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, false, true>, false}},  \
-     {{T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, false>, false},   \
-      {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, true, true>, false}}}
+#define NB_F32B_KERNEL(T, I, J, C, Z, L) \
+    {T, I, J, (const void *)force_f32_batched_kernel<T, I, J, C, Z, L>, (L) > 0}
+#define NB_F32B_ENTRY(T, I, J, L)                                                          \
+    {{NB_F32B_KERNEL(T, I, J, false, false, L), NB_F32B_KERNEL(T, I, J, false, true, L)},   \
+     {NB_F32B_KERNEL(T, I, J, true, false, L), NB_F32B_KERNEL(T, I, J, true, true, L)}}
 
 typedef KernelEntry Quad[2][2];
 
@@ -539,10 +549,15 @@ const Quad kForce[] = {
 };
 
 const Quad kBatched[] = {
-    NB_F32B_ENTRY(128, 2, 128),
-    NB_F32B_ENTRY(128, 4, 128),
-    NB_F32B_ENTRY(256, 2, 256),
-    NB_F32B_ENTRY(64, 4, 128),
+    NB_F32B_ENTRY(128, 2, 128, 0),
+    NB_F32B_ENTRY(128, 4, 128, 0),
+    NB_F32B_ENTRY(256, 2, 256, 0),
+    NB_F32B_ENTRY(64, 4, 128, 0),
+    // wider tiles, mixed rsqrt / log-domain pairs (4..7)
+    NB_F32B_ENTRY(128, 6, 256, 2),
+    NB_F32B_ENTRY(64, 6, 128, 2),
+    NB_F32B_ENTRY(128, 8, 128, 0),
+    NB_F32B_ENTRY(128, 4, 128, 1),
 };
 
 }  // namespace

@@ -568,7 +568,7 @@ int nb_choose_split(int64_t n_itiles, int64_t n_jtiles, int64_t slots, int64_t m
 }
 
 int64_t nb_plan_batch_host(int64_t nsys, const int64_t *off, int T, int I, int J,
-                           int32_t *items_out, int64_t max_items)
+                           int64_t max_item_pairs, int32_t *items_out, int64_t max_items)
 {
     if (nsys < 0 || !off || T <= 0 || I <= 0 || J <= 0 || (T & (T - 1))) return -1;
     if (off[0] != 0) return -1;
@@ -579,8 +579,14 @@ int64_t nb_plan_batch_host(int64_t nsys, const int64_t *off, int T, int I, int J
     for (int64_t k = 0; k < nsys; ++k) {
         const int64_t nk = off[k + 1] - off[k];
         if (nk == 0) continue;
+        // lanes: as many as still cover the system with one item, and more
+        // while an item would cost more than max_item_pairs (shorter items
+        // leave a shorter tail when the queue runs dry)
         int lanes = 1;
-        while (lanes < 32 && lanes * 2 <= T && (int64_t)T * I / (lanes * 2) >= nk) lanes *= 2;
+        while (lanes < 32 && lanes * 2 <= T && lanes * 2 <= J &&
+               ((int64_t)T * I / (lanes * 2) >= nk ||
+                (max_item_pairs > 0 && (int64_t)T * I / lanes * nk > max_item_pairs)))
+            lanes *= 2;
         const int64_t per = (int64_t)T * I / lanes;
         const int64_t cost = (nk + J - 1) / J * J / lanes;  // j-pairs per thread
         for (int64_t i0 = off[k]; i0 < off[k + 1]; i0 += per) {
@@ -900,11 +906,20 @@ nb_status nb_batch_plan(nb_ctx *c, int64_t nsys, const int64_t *offsets)
     if (offsets[nsys] > c->n_max) return failf(c, NB_EINVAL, "offsets[nsys] > n_max");
     int v, forced;
     pick(c, nb::KIND_BATCHED, offsets[nsys], v, forced);
-    const KernelEntry &k = nb::f32_batched_kernel(v, false, false);
-    const int64_t cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, nullptr, 0);
+    const KernelEntry &k = nb::f32_batched_kernel(v, c->prec == NB_FP32_COMP, false);
+    // When the batch already has more items than resident CTAs, cap an item
+    // at 1/4 of an even share of the pairs per CTA to shorten the tail.
+    double pairs = 0.0;
+    for (int64_t q = 0; q < nsys; ++q)
+        pairs += (double)(offsets[q + 1] - offsets[q]) * (double)(offsets[q + 1] - offsets[q]);
+    const int64_t slots = (int64_t)c->num_sms * occupancy(c, k);
+    int64_t cap = 0;
+    if (nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, 0, nullptr, 0) >= slots)
+        cap = (int64_t)(pairs / (double)(4 * std::max<int64_t>(slots, 1))) + 1;
+    const int64_t cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, nullptr, 0);
     if (cnt < 0) return failf(c, NB_EINVAL, "cannot plan these offsets");
     std::vector<int32_t> host((size_t)std::max<int64_t>(cnt, 1) * 8);
-    nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, host.data(), cnt);
+    nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, host.data(), cnt);
     if (cnt > c->items_cap) {
         cudaFree(c->items);
         c->items = nullptr;

@@ -66,7 +66,7 @@ SIGNATURES = {
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
-                                    ctypes.POINTER(ctypes.c_int32), _c_i64]),
+                                    _c_i64, ctypes.POINTER(ctypes.c_int32), _c_i64]),
 }
 
 
@@ -305,14 +305,16 @@ def choose_split(n_itiles, n_jtiles, slots, max_split_bodies, tile_bodies) -> in
     return int(load().nb_choose_split(n_itiles, n_jtiles, slots, max_split_bodies, tile_bodies))
 
 
-def plan_batch_host(offsets, threads, bodies_per_thread, jtile):
+def plan_batch_host(offsets, threads, bodies_per_thread, jtile, max_item_pairs=0):
     """Work items [(i0, i_end, j0, j1, lanes, sys)] the batched kernel would run."""
     lib = load()
     offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
     nsys = len(offsets) - 1
-    cnt = lib.nb_plan_batch_host(nsys, offs, threads, bodies_per_thread, jtile, None, 0)
+    cnt = lib.nb_plan_batch_host(nsys, offs, threads, bodies_per_thread, jtile,
+                                 int(max_item_pairs), None, 0)
     if cnt < 0:
         raise ValueError("invalid offsets")
     buf = (ctypes.c_int32 * (8 * max(cnt, 1)))()
-    lib.nb_plan_batch_host(nsys, offs, threads, bodies_per_thread, jtile, buf, cnt)
+    lib.nb_plan_batch_host(nsys, offs, threads, bodies_per_thread, jtile, int(max_item_pairs),
+                           buf, cnt)
     return [tuple(buf[8 * q: 8 * q + 6]) for q in range(cnt)]

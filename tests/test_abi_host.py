@@ -88,12 +88,18 @@ def test_choose_split_degenerate():
     assert nbody.choose_split(4, 1000, 608, 1024, 256) == 1  # no room for partials
 
 
-@pytest.mark.parametrize("T,I,J", [(128, 2, 128), (128, 4, 128), (256, 2, 256), (64, 4, 128)])
-def test_plan_batch_covers_every_body_once(T, I, J):
+@pytest.mark.parametrize("cap", [0, 200_000])
+@pytest.mark.parametrize("T,I,J", [(128, 2, 128), (128, 4, 128), (256, 2, 256), (64, 4, 128),
+                                   (128, 6, 256)])
+def test_plan_batch_covers_every_body_once(T, I, J, cap):
     from paper_1211_2292_gb300 import inputs
     sizes = [0, 1, 2, 64, 100, 255, 256, 257, 8192] + list(inputs.batch_sizes(60, seed=3))
     off = np.concatenate([[0], np.cumsum(sizes)])
-    items = nbody.plan_batch_host(off, T, I, J)
+    items = nbody.plan_batch_host(off, T, I, J, cap)
+    if cap:
+        # an item's bodies x j-range stay under the cap unless lanes ran out
+        for i0, i_end, j0, j1, lanes, sys in items:
+            assert (T * I // lanes) * (j1 - j0) <= cap or lanes == min(32, T, J)
     cover = np.zeros(off[-1], dtype=int)
     costs = []
     for i0, i_end, j0, j1, lanes, sys in items:
