@@ -156,7 +156,7 @@ def traffic_from_profile():
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+            k, v = line.strip()[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("force_f32.cu sha256[:16]") != sha:
         return None
