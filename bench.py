@@ -9,7 +9,14 @@ evaluations) in the float32 Kahan-compensated form with float64 state.
 Metric: pairwise interactions per second, N^2 per force evaluation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload throughput|batched]
+                  [--workload throughput|batched|precision|plain|differentiation]
+
+The other workloads (single-GPU lines with the same metric): "precision"
+(N = 65,536 Plummer, eps 0.005, FP32 compensated, 1 + 100 steps of dt 5e-4,
+with the force error against the oracle and the energy drift against the
+FP64 GPU run), "plain" (N = 1024 Plummer, FP64, 1 + 10 steps of dt 1e-3, one
+graph launch, checked against the oracle), "differentiation" (N = 16,384,
+200 steps with checkpoints every 20: forward, recompute and reverse sweep).
 
 Multi-GPU (torchrun, one rank per GPU): for "throughput" every rank runs its
 own replica (the single-system path is not sharded); for "batched" the 512
@@ -61,7 +68,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["throughput", "batched"], default="throughput")
+    ap.add_argument("--workload", default="throughput",
+                    choices=["throughput", "batched", "precision", "plain", "differentiation"])
     ap.add_argument("--fp64-n", type=int, default=262_144,
                     help="bodies for the float64-form rate (first bodies of the workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -196,6 +204,14 @@ def reference_arm(args, ws, rank):
         k = int(max(range(len(off) - 1), key=lambda q: off[q + 1] - off[q]))
         pos, mass = bodies.pos[off[k]:off[k + 1]], bodies.mass[off[k]:off[k + 1]]
         name, sample_of = w["name"], f"system {k} (N={off[k + 1] - off[k]})"
+    elif args.workload in ("precision", "plain", "differentiation"):
+        w = {"precision": PRECISION, "plain": PLAIN,
+             "differentiation": dict(ADJOINT, name="differentiation, N=16384")}[args.workload]
+        w = dict(w, G=1.0)
+        b = (inputs.plummer_with_perturbation(w["n"], seed=w["seed"])[0]
+             if args.workload == "differentiation" else inputs.plummer(w["n"], seed=w["seed"]))
+        pos, mass = b.pos, b.mass
+        name, sample_of = w["name"], f"N={b.n}"
     else:
         w = WORKLOAD
         b = inputs.two_plummer(w["n_per"], seed=w["seed"])
@@ -317,11 +333,185 @@ def measure_forms(torch, dev, tune, table, peak_tflops):
     return out
 
 
+PRECISION = {"name": "Plummer N=65536, eps 0.005, fp32 Kahan-compensated, 1 force eval + 100 KDK "
+                     "steps of dt 5e-4", "n": 65536, "seed": 1, "eps": 0.005, "dt": 5e-4,
+             "steps": 100}
+PLAIN = {"name": "Plummer N=1024, eps 0.01, fp64, 1 force eval + 10 KDK steps of dt 1e-3 "
+                 "(one graph launch)", "n": 1024, "seed": 0, "eps": 0.01, "dt": 1e-3, "steps": 10}
+
+
+def _line(args, ws, value, ms_step, cfg, extra, dtype="f32", scaling="weak"):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": scaling, "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded Plummer spheres)", "config": cfg}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def other_workload(args, ws, rank, local):
+    """precision / plain / differentiation: single-GPU lines (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody, tune
+    from paper_1211_2292_gb300.autograd import rollout
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    table = None if args.tuning in ("none", "default") else args.tuning
+    timer = lambda: Timer(torch, dev, stream, lambda: None)  # noqa: E731
+    T = lambda a: torch.as_tensor(a, device=dev).contiguous()  # noqa: E731
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    cpu = None
+
+    if args.workload == "precision":
+        w = PRECISION
+        b = inputs.plummer(w["n"], seed=w["seed"])
+        rows = inputs.sample_rows(b.n, 4096, seed=1)
+        t0 = time.perf_counter()
+        ref = oracle.accel_rows(b.pos, b.mass, rows, 1.0, w["eps"])
+        el = time.perf_counter() - t0
+        cpu = {"value": rows.size * b.n / el / 1e9, "unit": UNIT, "cores": oracle.threads(),
+               "kind": "oracle", "sample": f"4096 of {b.n} force rows ({el:.1f} s)"}
+        res = {}
+        for prec in ("fp64", "fp32_comp"):
+            with nbody.NBody(b.n, prec, device=dev.index) as nb:
+                if args.tuning != "none":
+                    tune.apply(nb, table)
+                x, v, m = T(b.pos), T(b.vel), T(b.mass)
+                a = nb.forces(x, m, 1.0, w["eps"])
+                e = np.linalg.norm(a.cpu().numpy()[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+                e0 = nb.energy(x, v, m, 1.0, w["eps"])
+                if prec == "fp32_comp":
+                    for _ in range(args.warmup):
+                        xs, vs = x.clone(), v.clone()
+                        nb.step(xs, vs, m, 1.0, w["eps"], w["dt"], w["steps"], a)
+                    l0 = nb.launches
+                    with timer() as t:
+                        for _ in range(args.steps):
+                            nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a)
+                            flush.fill_(1.0)
+                    launches = nb.launches - l0
+                    # the timed steps advanced the state K times; measure the drift
+                    # of one 100-step run from the initial state
+                    x, v = T(b.pos), T(b.vel)
+                nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a)
+                e1 = nb.energy(x, v, m, 1.0, w["eps"])
+                res[prec] = {"err": e, "e0": e0, "e1": e1, "x": x.cpu().numpy()}
+        evals = w["steps"] + 1
+        value = float(b.n) ** 2 * evals * args.steps / (t.ms / 1e3) / 1e9
+        r32, r64 = res["fp32_comp"], res["fp64"]
+        extra = {
+            "force_error": {"rms": float(np.sqrt((r32["err"] ** 2).mean())),
+                            "max": float(r32["err"].max()),
+                            "fp64_max": float(r64["err"].max()),
+                            "sample": "4096 bodies (seeded), vs FP64 oracle"},
+            "energy": {"E0": r64["e0"][2],
+                       "drift_fp64_gpu": abs(r64["e1"][2] - r64["e0"][2]) / abs(r64["e0"][2]),
+                       "drift_fp32": abs(r32["e1"][2] - r32["e0"][2]) / abs(r32["e0"][2]),
+                       "fp32_vs_fp64_final": abs(r32["e1"][2] - r64["e1"][2]) / abs(r64["e0"][2]),
+                       "max_position_diff": float(np.abs(r32["x"] - r64["x"]).max()),
+                       "note": "100 steps of dt 5e-4 from the initial state; energies in FP64"},
+            "cpu_baseline": cpu, "gpu_launches": launches}
+        _line(args, ws, value, t.ms / args.steps,
+              {"workload": w["name"], "n": b.n, "force_evals_per_step": evals,
+               "precision": "fp32_comp", "state": "f64"}, extra)
+        return 0
+
+    if args.workload == "plain":
+        w = PLAIN
+        b = inputs.plummer(w["n"], seed=w["seed"])
+        t0 = time.perf_counter()
+        rx, rv, ra = oracle.kdk(b.pos, b.vel, b.mass, 1.0, w["eps"], w["dt"], w["steps"])
+        re = oracle.energy(rx, rv, b.mass, 1.0, w["eps"])
+        el = time.perf_counter() - t0
+        evals = w["steps"] + 1
+        cpu = {"value": float(b.n) ** 2 * evals / el / 1e9, "unit": UNIT,
+               "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"the whole workload ({el:.3f} s incl. energy)"}
+        with nbody.NBody(b.n, "fp64", device=dev.index) as nb:
+            if args.tuning != "none":
+                tune.apply(nb, table)
+            x, v, m = T(b.pos), T(b.vel), T(b.mass)
+            a = torch.empty_like(x)
+            xs, vs = x.clone(), v.clone()
+            for _ in range(args.warmup):
+                xs.copy_(x)
+                vs.copy_(v)
+                nb.step(xs, vs, m, 1.0, w["eps"], w["dt"], w["steps"], a, graph=True)
+            l0 = nb.launches
+            with timer() as t:
+                for _ in range(args.steps):
+                    xs.copy_(x)
+                    vs.copy_(v)
+                    nb.step(xs, vs, m, 1.0, w["eps"], w["dt"], w["steps"], a, graph=True)
+            launches = nb.launches - l0
+            e1 = nb.energy(xs, vs, m, 1.0, w["eps"])
+            ga = a.cpu().numpy()
+            err = np.linalg.norm(ga - ra, axis=1) / np.linalg.norm(ra, axis=1)
+            extra = {"parity": {"acc_max_rel": float(err.max()),
+                                "pos_max_abs": float(np.abs(xs.cpu().numpy() - rx).max()),
+                                "energy_rel": abs(e1[2] - re[2]) / abs(re[2]),
+                                "vs": "FP64 oracle, same workload"},
+                     "cpu_baseline": cpu, "gpu_launches": launches}
+        value = float(b.n) ** 2 * evals * args.steps / (t.ms / 1e3) / 1e9
+        _line(args, ws, value, t.ms / args.steps,
+              {"workload": w["name"], "n": b.n, "force_evals_per_step": evals,
+               "precision": "fp64", "state": "f64"}, extra, dtype="f64")
+        return 0
+
+    # differentiation
+    a_ = ADJOINT
+    b, dx = inputs.plummer_with_perturbation(a_["n"], seed=a_["seed"])
+    with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+        if args.tuning != "none":
+            tune.apply(nb, table)
+        x, v, m = T(b.pos), T(b.vel), T(b.mass)
+        tgt = T(b.pos + dx)  # stand-in target for timing; parity uses the oracle's run
+
+        def grad():
+            x0 = x.clone().requires_grad_()
+            v0 = v.clone().requires_grad_()
+            mm = m.clone().requires_grad_()
+            xT, _ = rollout(nb, x0, v0, mm, 1.0, a_["eps"], a_["dt"], a_["steps"], a_["every"])
+            loss = ((xT - tgt) ** 2).sum(-1).mean()
+            loss.backward()
+            return loss
+
+        for _ in range(args.warmup):
+            grad()
+        l0 = nb.launches
+        with timer() as t:
+            for _ in range(args.steps):
+                grad()
+        launches = nb.launches - l0
+    K = a_["steps"]
+    force_evals = (K + 1) + (K + K // a_["every"])  # forward + per-segment recompute
+    vjp_evals = K + 1
+    pairs = float(b.n) ** 2 * (force_evals + vjp_evals)
+    value = pairs * args.steps / (t.ms / 1e3) / 1e9
+    _line(args, ws, value, t.ms / args.steps,
+          {"workload": f"Plummer N={b.n}, eps {a_['eps']}, {K} KDK steps of dt {a_['dt']}, "
+                       f"gradient w.r.t. x0, v0, m with checkpoints every {a_['every']}",
+           "n": b.n, "force_evals_per_step": force_evals, "vjp_evals_per_step": vjp_evals,
+           "precision": "fp32_comp (float64 adjoint accumulation)"},
+          {"gradient_ms": t.ms / args.steps, "gpu_launches": launches,
+           "note": "interactions counted for forward, recompute and VJP evaluations"})
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    if args.workload in ("precision", "plain", "differentiation"):
+        if args.warmup < 3:
+            args.warmup = 3
+        return other_workload(args, ws, rank, local)
 
     import numpy as np
     import torch
