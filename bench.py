@@ -155,7 +155,7 @@ def traffic_from_profile():
     """DRAM bytes per force launch from the committed ncu summary, or None
     when the force kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "force_f32comp_two_plummer_n1048576.md")
-    src = os.path.join(ROOT, "paper_1211_2292_gb300", "csrc", "force_f32.cu")
+    src = os.path.join(ROOT, "paper_1211_2292_gb300", "csrc", "force_f32.cuh")
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -166,7 +166,7 @@ def traffic_from_profile():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("force_f32.cu sha256[:16]") != sha:
+    if vals.get("force_f32.cuh sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

@@ -20,8 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
-SOURCES = ["force_f32.cu", "force_f64.cu", "adjoint.cu", "integrate.cu", "order.cu",
-           "noalloc.cu", "nbody_abi.cpp"]
+SOURCES = ["force_f32.cu", "force_f32_b.cu", "force_f32_batched.cu", "force_f64.cu",
+           "adjoint.cu", "integrate.cu", "order.cu", "noalloc.cu", "nbody_abi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -94,7 +94,11 @@ struct EnergyParams {
 };
 
 // ----------------------------------------------------------- kernel tables
-// Defined in force_f32.cu / force_f64.cu / adjoint.cu.  Index [variant][comp][zero_eps].
+// Defined in force_f32*.cu / force_f64.cu / adjoint.cu.  Index [variant][comp][zero_eps].
+int f32_force_variants_a();
+const KernelEntry &f32_force_kernel_a(int variant, bool comp, bool zeps);
+int f32_force_variants_b();
+const KernelEntry &f32_force_kernel_b(int variant, bool comp, bool zeps);
 int f32_force_variants();
 const KernelEntry &f32_force_kernel(int variant, bool comp, bool zeps);
 int f32_batched_variants();
