@@ -58,6 +58,9 @@ def _bind(lib):
     lib.oracle_kdk_grad.argtypes = [i64, _D, _D, _D, dbl, dbl, dbl, i64,
                                     _D, _D, _D, _D, _D]
     lib.oracle_kdk_grad.restype = ctypes.c_int
+    lib.oracle_bh_forces.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                     _D, _I, _I]
+    lib.oracle_bh_forces.restype = ctypes.c_int
     for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
               lib.oracle_kdk, lib.oracle_force_vjp):
         f.restype = None
@@ -163,3 +166,26 @@ def kdk_grad(pos, vel, mass, G, eps, dt, nsteps, gxT, gvT):
     if rc != 0:
         raise MemoryError("oracle_kdk_grad: allocation failed")
     return ox, ov, om
+
+
+def bh_forces(pos, mass, G=1.0, eps=0.0, theta=0.5, leaf_cap=16, group=32, counts=False):
+    """Barnes-Hut accelerations (paper Sec. IV-A, readings in nbody_oracle.c).
+
+    Returns acc (n, 3), stats {nodes, leaves, cell_interactions,
+    body_interactions} and, with counts=True, per-body (cells, bodies) list
+    sizes (n, 2).
+    """
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    out = np.zeros((n, 3))
+    st = np.zeros(4, dtype=np.int64)
+    cnt = np.zeros((n, 2), dtype=np.int64) if counts else None
+    rc = _load().oracle_bh_forces(n, _p(x), _p(m), float(G), float(eps), float(theta),
+                                  int(leaf_cap), int(group), _p(out), st.ctypes.data_as(_I),
+                                  cnt.ctypes.data_as(_I) if counts else None)
+    if rc != 0:
+        raise ValueError("oracle_bh_forces: bad leaf_cap/group")
+    stats = dict(zip(("nodes", "leaves", "cell_interactions", "body_interactions"),
+                     (int(v) for v in st)))
+    return (out, stats, cnt) if counts else (out, stats)

@@ -248,3 +248,264 @@ int oracle_kdk_grad(int64_t n, const double *x0, const double *v0,
     free(traj); free(v); free(acc); free(mu); free(dgx); free(dgm);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/*
+ * Barnes-Hut tree code (paper Sec. IV-A): the bodies are distributed in an
+ * octree by recursively dividing space into 8 subspaces until a subspace
+ * holds few enough bodies; the force on a body is evaluated by traversing
+ * the tree from the root, adding a cell to the interaction list when it is
+ * distant enough and otherwise continuing with its children; the list is
+ * then looped through to compute the force.
+ *
+ * Readings where the paper is silent (no opening criterion, threshold or
+ * grouping is given):
+ *  - space: the cube at the bodies' bounding-box minimum with edge equal to
+ *    the longest box side; a body's cell at level L is given by the top 3L
+ *    bits of its 30-bit Morton key, q_c = floor((x_c - lo_c) * (1024 / ext))
+ *    clamped to [0, 1023];
+ *  - a cell is a leaf when it holds at most `leaf_cap` bodies or is at
+ *    level 10;
+ *  - cells interact as their total mass at their centre of mass (monopole),
+ *    softened like a body;
+ *  - "distant enough": the distance from the body to the cell's cube is at
+ *    least (cell edge) / theta, evaluated in float32 from float32 inputs;
+ *  - bodies are taken in groups of `group` consecutive bodies in key order,
+ *    and a group walks the tree together: a cell goes on the group's list
+ *    only when it is distant enough from every body of the group.  group = 1
+ *    is the per-body traversal the paper describes.
+ * stats (optional) receives {nodes, leaves, cell interactions, body
+ * interactions}; cnt (optional, [n][2]) receives per body the number of
+ * cells and bodies on its list (the self pair included).
+ */
+typedef struct {
+    int64_t start, end;
+    int level;
+    uint32_t prefix;
+    int64_t child[8];
+    double M, com[3];
+    float lo[3], hi[3];
+} bh_node;
+
+typedef struct {
+    bh_node *nodes;
+    int64_t nnodes, cap;
+    const uint32_t *key;
+    int leaf_cap;
+} bh_tree;
+
+static uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+static const uint32_t *g_sort_key;
+static int cmp_key_index(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    if (g_sort_key[i] != g_sort_key[j]) return g_sort_key[i] < g_sort_key[j] ? -1 : 1;
+    return i < j ? -1 : (i > j);
+}
+
+static int64_t bh_build(bh_tree *t, int level, uint32_t prefix, int64_t start, int64_t end)
+{
+    if (t->nnodes == t->cap) {
+        t->cap *= 2;
+        t->nodes = (bh_node *)realloc(t->nodes, sizeof(bh_node) * (size_t)t->cap);
+    }
+    int64_t id = t->nnodes++;
+    bh_node *nd = &t->nodes[id];
+    nd->start = start;
+    nd->end = end;
+    nd->level = level;
+    nd->prefix = prefix;
+    for (int o = 0; o < 8; ++o) nd->child[o] = -1;
+    if (end - start <= t->leaf_cap || level == 10) return id;
+    int shift = 3 * (10 - (level + 1));
+    int64_t s = start;
+    for (int o = 0; o < 8; ++o) {
+        uint32_t cp = prefix * 8u + (uint32_t)o;
+        int64_t e = s;
+        while (e < end && (t->key[e] >> shift) == cp) ++e;
+        if (e > s) {
+            int64_t c = bh_build(t, level + 1, cp, s, e);
+            t->nodes[id].child[o] = c;
+        }
+        s = e;
+    }
+    return id;
+}
+
+int oracle_bh_forces(int64_t n, const double *x, const double *m, double G, double eps,
+                     double theta, int leaf_cap, int group, double *acc, int64_t *stats,
+                     int64_t *cnt)
+{
+    if (n <= 0) return 0;
+    if (leaf_cap < 1 || group < 1) return -1;
+    double lo[3], hi[3];
+    for (int c = 0; c < 3; ++c) lo[c] = hi[c] = x[c];
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            if (x[3 * i + c] < lo[c]) lo[c] = x[3 * i + c];
+            if (x[3 * i + c] > hi[c]) hi[c] = x[3 * i + c];
+        }
+    double ext = hi[0] - lo[0];
+    if (hi[1] - lo[1] > ext) ext = hi[1] - lo[1];
+    if (hi[2] - lo[2] > ext) ext = hi[2] - lo[2];
+    if (!(ext > 0.0)) ext = 1.0;
+    const double scale = 1024.0 / ext;
+
+    uint32_t *key0 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    uint32_t *key = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t q[3];
+        for (int c = 0; c < 3; ++c) {
+            double tq = (x[3 * i + c] - lo[c]) * scale;
+            q[c] = tq >= 1023.0 ? 1023u : (tq <= 0.0 ? 0u : (uint32_t)tq);
+        }
+        key0[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+        perm[i] = i;
+    }
+    g_sort_key = key0;
+    qsort(perm, (size_t)n, sizeof(int64_t), cmp_key_index);
+    for (int64_t k = 0; k < n; ++k) key[k] = key0[perm[k]];
+
+    bh_tree t;
+    t.cap = 1024;
+    t.nnodes = 0;
+    t.nodes = (bh_node *)malloc(sizeof(bh_node) * (size_t)t.cap);
+    t.key = key;
+    t.leaf_cap = leaf_cap;
+    bh_build(&t, 0, 0u, 0, n);
+
+    /* monopole moments and float32 cell cubes */
+    int64_t leaves = 0;
+    for (int64_t id = 0; id < t.nnodes; ++id) {
+        bh_node *nd = &t.nodes[id];
+        double M = 0.0, s[3] = {0, 0, 0};
+        for (int64_t k = nd->start; k < nd->end; ++k) {
+            int64_t j = perm[k];
+            M += m[j];
+            for (int c = 0; c < 3; ++c) s[c] += m[j] * x[3 * j + c];
+        }
+        nd->M = M;
+        for (int c = 0; c < 3; ++c) nd->com[c] = M > 0.0 ? s[c] / M : 0.0;
+        uint32_t ic[3] = {0, 0, 0};
+        for (int b = 0; b < nd->level; ++b) {  /* de-interleave the prefix */
+            uint32_t trip = (nd->prefix >> (3 * b)) & 7u;
+            for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << b;
+        }
+        double cell = ext / (double)(1u << nd->level);
+        for (int c = 0; c < 3; ++c) {
+            nd->lo[c] = (float)(lo[c] + cell * (double)ic[c]);
+            nd->hi[c] = (float)(lo[c] + cell * (double)(ic[c] + 1u));
+        }
+        int leaf = 1;
+        for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
+        leaves += leaf;
+    }
+    /* squared opening distance per level, in float32 */
+    float crit2[11];
+    const float th = (float)theta;
+    for (int L = 0; L <= 10; ++L) {
+        float edge = (float)(ext / (double)(1u << L));
+        float d = edge / th;
+        crit2[L] = d * d;
+    }
+
+    int64_t ncell = 0, nbody = 0;
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(8 * 11 + 8));
+    int64_t lcap = 1024, *lst = (int64_t *)malloc(sizeof(int64_t) * (size_t)lcap);
+    float *xf = (float *)malloc(sizeof(float) * 3 * (size_t)group);
+    for (int64_t g0 = 0; g0 < n; g0 += group) {
+        int64_t g1 = g0 + group < n ? g0 + group : n;
+        for (int64_t k = g0; k < g1; ++k)
+            for (int c = 0; c < 3; ++c) xf[3 * (k - g0) + c] = (float)x[3 * perm[k] + c];
+        /* walk: list entries >= 0 are cells, < 0 encode leaf nodes as ~id */
+        int64_t nl = 0, sp = 0;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            int64_t id = stack[--sp];
+            const bh_node *nd = &t.nodes[id];
+            int all = 1;
+            for (int64_t k = g0; k < g1 && all; ++k) {
+                const float *p = xf + 3 * (k - g0);
+                float d2 = 0.0f;
+                for (int c = 0; c < 3; ++c) {
+                    float a = nd->lo[c] - p[c];
+                    float b = p[c] - nd->hi[c];
+                    float dd = a > b ? a : b;
+                    dd = dd > 0.0f ? dd : 0.0f;
+                    float sq = dd * dd;
+                    d2 = d2 + sq;
+                }
+                if (!(d2 >= crit2[nd->level])) all = 0;
+            }
+            int leaf = 1;
+            for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
+            if (all || leaf) {
+                if (nl == lcap) {
+                    lcap *= 2;
+                    lst = (int64_t *)realloc(lst, sizeof(int64_t) * (size_t)lcap);
+                }
+                lst[nl++] = all ? id : ~id;
+            } else {
+                for (int o = 7; o >= 0; --o)
+                    if (nd->child[o] >= 0) stack[sp++] = nd->child[o];
+            }
+        }
+        for (int64_t k = g0; k < g1; ++k) {
+            int64_t i = perm[k];
+            double a[3] = {0, 0, 0};
+            int64_t nc = 0, nb = 0;
+            for (int64_t q = 0; q < nl; ++q) {
+                if (lst[q] >= 0) {
+                    const bh_node *nd = &t.nodes[lst[q]];
+                    double d[3], s2 = eps * eps;
+                    for (int c = 0; c < 3; ++c) {
+                        d[c] = nd->com[c] - x[3 * i + c];
+                        s2 += d[c] * d[c];
+                    }
+                    double w = nd->M / (s2 * sqrt(s2));
+                    for (int c = 0; c < 3; ++c) a[c] += w * d[c];
+                    ++nc;
+                } else {
+                    const bh_node *nd = &t.nodes[~lst[q]];
+                    for (int64_t kk = nd->start; kk < nd->end; ++kk) {
+                        int64_t j = perm[kk];
+                        ++nb;
+                        if (j == i) continue;
+                        double d[3], s2 = eps * eps;
+                        for (int c = 0; c < 3; ++c) {
+                            d[c] = x[3 * j + c] - x[3 * i + c];
+                            s2 += d[c] * d[c];
+                        }
+                        double w = m[j] / (s2 * sqrt(s2));
+                        for (int c = 0; c < 3; ++c) a[c] += w * d[c];
+                    }
+                }
+            }
+            for (int c = 0; c < 3; ++c) acc[3 * i + c] = G * a[c];
+            if (cnt) {
+                cnt[2 * i] = nc;
+                cnt[2 * i + 1] = nb;
+            }
+            ncell += nc;
+            nbody += nb;
+        }
+    }
+    if (stats) {
+        stats[0] = t.nnodes;
+        stats[1] = leaves;
+        stats[2] = ncell;
+        stats[3] = nbody;
+    }
+    free(key0); free(perm); free(key); free(t.nodes); free(stack); free(lst); free(xf);
+    return 0;
+}

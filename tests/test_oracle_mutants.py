@@ -14,6 +14,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_bh as bhpins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "nbody_oracle.c")
@@ -42,6 +43,14 @@ MUTANTS = {
     "vjp mass sign": ("gmk += -ld * inv_s3;", "gmk += ld * inv_s3;"),
     "adjoint drift": ("for (size_t k = 0; k < per; ++k) lv[k] += dt * lx[k];",
                       "for (size_t k = 0; k < per; ++k) lv[k] += 0.5 * dt * lx[k];"),
+    "bh acceptance inverted": ("if (!(d2 >= crit2[nd->level])) all = 0;",
+                               "if (!(d2 <= crit2[nd->level])) all = 0;"),
+    "bh centre of mass": ("nd->com[c] = M > 0.0 ? s[c] / M : 0.0;", "nd->com[c] = s[c];"),
+    "bh cell mass": ("double w = nd->M / (s2 * sqrt(s2));", "double w = 1.0 / (s2 * sqrt(s2));"),
+    "bh octant shift": ("while (e < end && (t->key[e] >> shift) == cp) ++e;",
+                        "while (e < end && (t->key[e] >> (shift + 3)) == cp) ++e;"),
+    "bh key axis": ("key0[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);",
+                    "key0[i] = spread10(q[0]) | (spread10(q[0]) << 1) | (spread10(q[2]) << 2);"),
 }
 
 PINS = [
@@ -52,6 +61,8 @@ PINS = [
     pins.test_circular_orbit_phase_error_is_second_order,
     pins.test_kepler_orbit_zero_softening, pins.test_time_reversibility,
     pins.test_force_vjp_central_differences, pins.test_kdk_grad_central_differences,
+    lambda: bhpins.test_theta_zero_is_the_direct_sum(8, 32), bhpins.test_error_falls_with_theta,
+    bhpins.test_far_cluster_is_its_monopole, bhpins.test_tree_counts_and_cost,
 ]
 
 
@@ -80,7 +91,7 @@ def test_pins_catch_mutant(tmp_path, name):
                     __import__("warnings").simplefilter("ignore")
                     pin()
             except (AssertionError, FloatingPointError, ValueError):
-                caught.append(pin.__name__)
+                caught.append(getattr(pin, "__name__", "pin"))
     finally:
         oracle._lib = real
     assert caught, f"no pin caught the mutant '{name}'"
