@@ -224,8 +224,9 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * each pair-kernel launch (not inside captured graphs).  nb_profile(ctx, 1)
  * clears the record and starts recording, nb_profile(ctx, 0) stops.
  * nb_profile_read synchronises the stream and returns, for `kind`
- * (0 force, 1 batched force, 2 force VJP, 3 energy), the launches recorded
- * and their summed duration in milliseconds.
+ * (0 force, 1 batched force, 2 force VJP, 3 energy, 4 tree walk, 5 tree
+ * build: sort, pack, levels, moments), the launches (sequences, for 5)
+ * recorded and their summed duration in milliseconds.
  */
 nb_status nb_profile(nb_ctx *ctx, int enable);
 nb_status nb_profile_read(nb_ctx *ctx, int kind, int64_t *launches, double *total_ms);
@@ -233,6 +234,57 @@ nb_status nb_profile_read(nb_ctx *ctx, int kind, int64_t *launches, double *tota
 /* Device properties the scheduler uses: SM count, and resident CTAs per SM
  * of the force kernel a call with n bodies would use. */
 nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm);
+
+/*
+ * Barnes-Hut tree code (paper Sec. IV-A): the bodies are put in an octree by
+ * dividing space 8 ways until a cell holds few enough bodies; a body meets a
+ * cell that is distant enough as one particle of the cell's total mass at its
+ * centre of mass, and otherwise the cell's children, down to the bodies of
+ * nearby leaves.  The paper names neither an opening rule nor a threshold;
+ * this library's reading:
+ *   - space is the cube at the bodies' box minimum with edge `ext`, the
+ *     longest box side; a body's cell at level L (edge ext / 2^L) is given by
+ *     the top 3L bits of its 30-bit Morton key, q = floor((x - lo) 1024/ext)
+ *     clamped to [0, 1023] per axis;
+ *   - a cell is a leaf when it holds at most leaf_cap bodies or is at level 10;
+ *   - bodies are taken 32 at a time in key order, and the 32 walk the tree
+ *     together: a cell acts as its monopole only when, for every one of the
+ *     32, the float32 distance from the body to the cell's cube is at least
+ *     edge / theta (theta = 0 opens every cell: the direct sum through the
+ *     tree);
+ *   - cell masses and centres of mass are float64; pair terms are float32 in
+ *     coordinates relative to the 32 bodies' centre, summed per cell and
+ *     leaf, and folded into Kahan-compensated sums; acc is float64.
+ * The tree is rebuilt on every call, fully on the device (no host
+ * synchronisation, so nb_tree_step can run as one captured graph).
+ *
+ * nb_tree_forces: acc [n][3] (out).  theta >= 0 and finite; 1 <= leaf_cap <=
+ * NB_TREE_MAX_LEAF; counts (optional, int32 [n][2], 8-byte aligned) receives
+ * per body the number of cells and of bodies (itself included) it met.
+ * Any precision mode (the walk is float32 in each).  The first call (and a
+ * call whose leaf_cap needs more nodes than any before) allocates the tree
+ * scratch: 124 bytes per node for 1 + sum_{L=1..10} min(8^L, n_max,
+ * 8 floor(n_max / (leaf_cap + 1))) nodes, a bound no tree exceeds (about
+ * 2.3e6 nodes for n_max = 2^20, leaf_cap = 16), plus 40 bytes per body; this
+ * synchronises the device and drops the context's captured graphs.  nb_sync
+ * returns NB_ENOMEM if a tree ever outgrew its arrays (the build then stops a
+ * level early; the bound rules it out).
+ *
+ * nb_tree_step: nb_step with tree forces (nsteps + 1 tree builds and walks,
+ * the first skipped with NB_ACC_VALID); NB_USE_GRAPH runs the steps as one
+ * captured graph.
+ *
+ * nb_tree_stats: {nodes, leaves, cell interactions, body interactions} of
+ * the last tree force evaluation on the context (synchronises its stream).
+ */
+#define NB_TREE_MAX_LEAF 65536
+nb_status nb_tree_forces(nb_ctx *ctx, int64_t n, const double *pos, const double *mass,
+                         double G, double eps, double theta, int leaf_cap, double *acc,
+                         int32_t *counts);
+nb_status nb_tree_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                       double G, double eps, double theta, int leaf_cap, double dt,
+                       int64_t nsteps, double *acc, unsigned flags);
+nb_status nb_tree_stats(nb_ctx *ctx, int64_t *out);
 
 /*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form

@@ -124,7 +124,4 @@ __device__ __forceinline__ float3 block_center(float (&mn)[3], float (&mx)[3], f
     return o;
 }
 
-// Error-word bits (ctx scratch, read by nb_sync / nb_energy).
-enum : int { ERR_NONFINITE = 1 };
-
 }  // namespace nb

@@ -12,8 +12,13 @@
 
 namespace nb {
 
+// Error-word bits (ctx scratch, read by nb_sync / nb_energy): a non-finite
+// result; a tree that outgrew its node arrays.
+enum : int { ERR_NONFINITE = 1, ERR_TREE = 2 };
 // Kernel families with autotuned variants (the `kind` of nb_variant_*).
 enum Kind : int { KIND_FORCE = 0, KIND_BATCHED = 1, KIND_VJP = 2, KIND_COUNT = 3 };
+// Event-timing tags of nb_profile_read: 0-2 the kinds above, then these.
+enum ProfKind : int { PROF_ENERGY = 3, PROF_TREE_WALK = 4, PROF_TREE_BUILD = 5 };
 
 // One compiled kernel: CTA shape plus the function to launch.  Every kernel
 // of a family takes a single by-value parameter struct.
@@ -123,10 +128,52 @@ int sort_chunks(int n);
 // perm_out[k] = body at Morton rank k (stable in body index); `kernels` = launches made.
 cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
                                int *perm_out, int &kernels);
+// Tree-code order: 30-bit Morton keys (float64 quantisation), stable radix
+// sort; sorted keys end in o.keys[0], box_out = {lo_x, lo_y, lo_z, ext}.
+cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
+                             int *perm_out, double *box_out, int &kernels);
 // Phi[k], Plo[k] = float32 hi/lo packing of body perm[k] (perm NULL = identity);
 // Phi.w = m, Plo.w = log2(m).
 cudaError_t launch_pack_hilo(cudaStream_t s, int n, const double *pos, const double *mass,
                              const int *perm, float4 *Phi, float4 *Plo);
+
+// ------------------------------------------------------ tree code (tree.cu)
+// Octree over bodies in 30-bit Morton order.  Node arrays hold `cap` entries;
+// a node covers sorted bodies [start, end), sits at `level` with key prefix
+// `prefix` (3 * level bits), and has `nchild` children stored contiguously
+// from `first` in octant order (nchild == 0: leaf).
+struct TreeView {
+    int cap;
+    int *meta;            // [tree_meta_ints()] per-level node counts and bases, overflow flag
+    int *start, *end, *level, *nchild, *first, *offs;
+    unsigned *prefix;
+    double *M, *com;      // float64 monopoles: mass, centre of mass [cap][3]
+    float4 *box_lo, *box_hi;  // float32 cell cube corners (.w unused)
+    float4 *chi, *clo;    // centre of mass hi/lo float32 pair; chi.w = mass
+    unsigned long long *stats;  // [4] nodes, leaves, cell and body interactions
+};
+struct TreeWalkParams {
+    TreeView tree;
+    const float4 *P, *Plo;  // bodies in tree order, float32 hi/lo
+    const int *perm;        // tree rank -> body index
+    const double *box;      // {lo_x, lo_y, lo_z, ext}
+    int n;
+    float theta, eps2f;
+    double G;
+    double *acc, *vel;      // vel != NULL: vel += half_dt * acc
+    double half_dt;
+    int *counts;            // optional [n][2]: cells, bodies met per body
+    int *err;
+};
+int tree_meta_ints();
+// Upper bound on the node count of a tree over n bodies with leaves of at
+// most leaf_cap bodies (no build can exceed it).
+int64_t tree_node_bound(int64_t n, int leaf_cap);
+// Build over sorted keys (launch_tree_sort), float64 moments, float32 walk data.
+cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const unsigned *keys,
+                              const double *box, const double *pos, const double *mass,
+                              const int *perm, int leaf_cap, int *err, int &kernels);
+cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps, int &kernels);
 
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
@@ -200,10 +247,18 @@ struct nb_ctx {
         int64_t n, nsteps, every;
         unsigned flags;
         uint64_t plan_gen;
+        double theta = 0.0;  // tree code only
+        int leaf_cap = 0;
         bool operator<(const GraphKey &o) const;
     };
     struct GraphVal { cudaGraphExec_t exec; int64_t kernels; };
     std::map<GraphKey, GraphVal> graphs;
+
+    // tree code scratch (allocated on first use; bodies sized for n_max)
+    nb::TreeView tree{};
+    float4 *tree_P = nullptr, *tree_Plo = nullptr;
+    int *tree_perm = nullptr;
+    double *tree_box = nullptr;
 
     std::map<const void *, int> occ;  // resident CTAs per SM, per kernel
 

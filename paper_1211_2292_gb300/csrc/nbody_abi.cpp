@@ -476,6 +476,19 @@ T *dev_alloc(nb_ctx *c, size_t count, nb_status &st)
     return (T *)p;
 }
 
+void free_tree_nodes(nb_ctx *c)
+{
+    nb::TreeView &t = c->tree;
+    void *arrays[] = {t.start, t.end,   t.level,  t.nchild, t.first, t.offs, t.prefix,
+                      t.M,     t.com,   t.box_lo, t.box_hi, t.chi,   t.clo};
+    for (void *a : arrays) cudaFree(a);
+    t.start = t.end = t.level = t.nchild = t.first = t.offs = nullptr;
+    t.prefix = nullptr;
+    t.M = t.com = nullptr;
+    t.box_lo = t.box_hi = t.chi = t.clo = nullptr;
+    t.cap = 0;
+}
+
 void free_ctx(nb_ctx *c)
 {
     drop_graphs(c);
@@ -499,11 +512,173 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->order.vals[0]);
     cudaFree(c->order.vals[1]);
     cudaFree(c->order.hist);
+    free_tree_nodes(c);
+    cudaFree(c->tree.meta);
+    cudaFree(c->tree.stats);
+    cudaFree(c->tree_P);
+    cudaFree(c->tree_Plo);
+    cudaFree(c->tree_perm);
+    cudaFree(c->tree_box);
     if (c->host_out) cudaFreeHost(c->host_out);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     delete c;
+}
+
+// ---------------------------------------------------------------- tree code
+// Morton-sort scratch (float64 contexts allocate it on first tree call).
+nb_status ensure_order(nb_ctx *c)
+{
+    if (c->order.hist) return NB_OK;
+    nb_status st = NB_OK;
+    const size_t nc = (size_t)std::max<int64_t>(c->n_max, 1);
+    if (!c->order.box) c->order.box = dev_alloc<double>(c, 1024 * 6, st);
+    for (int q = 0; q < 2 && st == NB_OK; ++q) {
+        if (!c->order.keys[q]) c->order.keys[q] = dev_alloc<unsigned>(c, nc, st);
+        if (st == NB_OK && !c->order.vals[q]) c->order.vals[q] = dev_alloc<int>(c, nc, st);
+    }
+    if (st == NB_OK)
+        c->order.hist = dev_alloc<unsigned>(c, (size_t)256 * nb::sort_chunks((int)nc), st);
+    return st;
+}
+
+// Tree scratch for leaves of up to leaf_cap bodies: body arrays for n_max
+// bodies and node arrays for tree_node_bound(n_max, leaf_cap) nodes.  Growing
+// the node arrays frees the old ones (cudaFree synchronises the device) and
+// drops captured graphs, which hold the old addresses.
+nb_status ensure_tree(nb_ctx *c, int leaf_cap)
+{
+    NB_TRY(ensure_order(c));
+    nb_status st = NB_OK;
+    const size_t nc = (size_t)std::max<int64_t>(c->n_max, 1);
+    if (!c->tree_box) {
+        c->tree_P = dev_alloc<float4>(c, nc, st);
+        if (st == NB_OK) c->tree_Plo = dev_alloc<float4>(c, nc, st);
+        if (st == NB_OK) c->tree_perm = dev_alloc<int>(c, nc, st);
+        if (st == NB_OK) c->tree.meta = dev_alloc<int>(c, (size_t)nb::tree_meta_ints(), st);
+        if (st == NB_OK) c->tree.stats = dev_alloc<unsigned long long>(c, 4, st);
+        if (st == NB_OK) c->tree_box = dev_alloc<double>(c, 4, st);
+        if (st != NB_OK) return st;
+    }
+    const int64_t need = nb::tree_node_bound((int64_t)nc, leaf_cap);
+    if (need <= c->tree.cap) return NB_OK;
+    if (need > 0x7fffffffLL)
+        return failf(c, NB_ENOMEM, "tree of %lld nodes too large", (long long)need);
+    drop_graphs(c);
+    free_tree_nodes(c);
+    nb::TreeView &t = c->tree;
+    const size_t m = (size_t)need;
+    int **ints[] = {&t.start, &t.end, &t.level, &t.nchild, &t.first, &t.offs};
+    for (int **a : ints)
+        if (st == NB_OK) *a = dev_alloc<int>(c, m, st);
+    if (st == NB_OK) t.prefix = dev_alloc<unsigned>(c, m, st);
+    if (st == NB_OK) t.M = dev_alloc<double>(c, m, st);
+    if (st == NB_OK) t.com = dev_alloc<double>(c, 3 * m, st);
+    float4 **f4[] = {&t.box_lo, &t.box_hi, &t.chi, &t.clo};
+    for (float4 **a : f4)
+        if (st == NB_OK) *a = dev_alloc<float4>(c, m, st);
+    if (st != NB_OK) {
+        free_tree_nodes(c);
+        return st;
+    }
+    t.cap = (int)need;
+    return NB_OK;
+}
+
+nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap)
+{
+    if (!std::isfinite(theta) || theta < 0)
+        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
+    if (leaf_cap < 1 || leaf_cap > NB_TREE_MAX_LEAF)
+        return failf(c, NB_EINVAL, "leaf_cap = %d outside [1, %d]", leaf_cap, NB_TREE_MAX_LEAF);
+    return NB_OK;
+}
+
+// Events around a tree-code launch sequence (nb_profile), outside captures.
+struct TreeTimer {
+    nb_ctx *c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    TreeTimer(nb_ctx *c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_)
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (!c->prof_on || cs != cudaStreamCaptureStatusNone) return;
+        a = pooled_event(c);
+        b = pooled_event(c);
+        if (a && b) cudaEventRecord(a, s);
+    }
+    void done()
+    {
+        if (a && b && cudaEventRecord(b, s) == cudaSuccess) {
+            c->prof.push_back({kind, a, b});
+            a = b = nullptr;
+        }
+    }
+    ~TreeTimer()
+    {
+        if (a) c->ev_pool.push_back(a);
+        if (b) c->ev_pool.push_back(b);
+    }
+};
+
+// Sort, pack, build and walk: acc = G * (tree sum); vel += half_dt * acc when vel.
+nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos,
+                              const double *mass, double G, double eps, double theta,
+                              int leaf_cap, double *acc, double *vel, double half_dt, int *counts)
+{
+    if (n == 0) return NB_OK;
+    int k = 0;
+    {
+        TreeTimer tm(c, nb::PROF_TREE_BUILD, s);
+        NB_CUDA(c, nb::launch_tree_sort(s, (int)n, pos, c->order, c->tree_perm, c->tree_box, k));
+        c->launches += k;
+        NB_LAUNCHED(c, nb::launch_pack_hilo(s, (int)n, pos, mass, c->tree_perm, c->tree_P,
+                                            c->tree_Plo));
+        NB_CUDA(c, nb::launch_tree_build(s, c->tree, (int)n, c->order.keys[0], c->tree_box, pos,
+                                         mass, c->tree_perm, leaf_cap, c->err, k));
+        c->launches += k;
+        tm.done();
+    }
+    nb::TreeWalkParams p;
+    p.tree = c->tree;
+    p.P = c->tree_P;
+    p.Plo = c->tree_Plo;
+    p.perm = c->tree_perm;
+    p.box = c->tree_box;
+    p.n = (int)n;
+    p.theta = (float)theta;
+    p.eps2f = (float)(eps * eps);
+    p.G = G;
+    p.acc = acc;
+    p.vel = vel;
+    p.half_dt = half_dt;
+    p.counts = counts;
+    p.err = c->err;
+    TreeTimer tm(c, nb::PROF_TREE_WALK, s);
+    NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
+    c->launches += k;
+    tm.done();
+    return NB_OK;
+}
+
+nb_status tree_step_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, double *vel,
+                            const double *mass, double G, double eps, double theta, int leaf_cap,
+                            double dt, int64_t nsteps, double *acc, unsigned flags)
+{
+    if (n == 0) return NB_OK;
+    if (!(flags & NB_ACC_VALID))
+        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, acc, nullptr, 0.0,
+                                   nullptr));
+    for (int64_t st = 0; st < nsteps; ++st) {
+        NB_LAUNCHED(c, nb::launch_kdp(s, is_f64(c), (int)n, pos, vel, acc, mass, 0.5 * dt, dt,
+                                      nullptr, nullptr, nullptr, nullptr));
+        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, acc, vel, 0.5 * dt,
+                                   nullptr));
+    }
+    return NB_OK;
 }
 
 int min_tile_bodies()
@@ -524,9 +699,9 @@ int min_tile_bodies()
 bool nb_ctx::GraphKey::operator<(const GraphKey &o) const
 {
     return std::tie(kind, pos, vel, mass, acc, rec_pos, rec_vel, G, eps, dt, n, nsteps, every,
-                    flags, plan_gen) <
+                    flags, plan_gen, theta, leaf_cap) <
            std::tie(o.kind, o.pos, o.vel, o.mass, o.acc, o.rec_pos, o.rec_vel, o.G, o.eps, o.dt,
-                    o.n, o.nsteps, o.every, o.flags, o.plan_gen);
+                    o.n, o.nsteps, o.every, o.flags, o.plan_gen, o.theta, o.leaf_cap);
 }
 
 namespace nb {
@@ -730,6 +905,8 @@ nb_status nb_sync(nb_ctx *c)
     if (h) {
         NB_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
         NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (h & nb::ERR_TREE)
+            return failf(c, NB_ENOMEM, "a tree outgrew its node arrays (it stopped a level early)");
         return failf(c, NB_ENONFINITE, "a kernel produced a non-finite result");
     }
     return NB_OK;
@@ -1058,6 +1235,70 @@ nb_status nb_profile_read(nb_ctx *c, int kind, int64_t *launches, double *total_
     }
     if (launches) *launches = cnt;
     if (total_ms) *total_ms = ms;
+    return NB_OK;
+}
+
+nb_status nb_tree_forces(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
+                         double eps, double theta, int leaf_cap, double *acc, int32_t *counts)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    NB_TRY(check_tree_args(c, theta, leaf_cap));
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 2 * sizeof(int32_t), "counts"));
+    if (n == 0) return NB_OK;
+    NB_TRY(ensure_tree(c, leaf_cap));
+    return tree_forces_enqueue(c, c->stream, n, pos, mass, G, eps, theta, leaf_cap, acc, nullptr,
+                               0.0, counts);
+}
+
+nb_status nb_tree_step(nb_ctx *c, int64_t n, double *pos, double *vel, const double *mass,
+                       double G, double eps, double theta, int leaf_cap, double dt,
+                       int64_t nsteps, double *acc, unsigned flags)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    NB_TRY(check_tree_args(c, theta, leaf_cap));
+    if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
+    if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
+    if (flags & ~(NB_ACC_VALID | NB_USE_GRAPH)) return failf(c, NB_EINVAL, "unknown flags");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (n == 0) return NB_OK;
+    NB_TRY(ensure_tree(c, leaf_cap));
+    if (flags & NB_USE_GRAPH) {
+        nb_ctx::GraphKey key{2,   pos, vel, mass,   acc, nullptr, nullptr, G,
+                             eps, dt,  n,   nsteps, 0,   flags,   0};
+        key.theta = theta;
+        key.leaf_cap = leaf_cap;
+        return run_graph(c, key, [&](cudaStream_t s) {
+            return tree_step_enqueue(c, s, n, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps,
+                                     acc, flags);
+        });
+    }
+    return tree_step_enqueue(c, c->stream, n, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps,
+                             acc, flags);
+}
+
+nb_status nb_tree_stats(nb_ctx *c, int64_t *out)
+{
+    if (!c || !out) return failf(c, NB_EINVAL, "ctx or out is NULL");
+    DeviceGuard guard(c->device);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (c->tree.stats)
+        NB_CUDA(c, cudaMemcpyAsync(h, c->tree.stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < 4; ++q) out[q] = (int64_t)h[q];
     return NB_OK;
 }
 

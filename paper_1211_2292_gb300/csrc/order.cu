@@ -109,6 +109,62 @@ __global__ void __launch_bounds__(OTPB) morton_kernel(int n, const double *__res
     }
 }
 
+__device__ __forceinline__ unsigned spread10(unsigned v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// 30-bit Morton keys for the tree code: q = floor((x - lo) * (1024 / ext)),
+// clamped to [0, 1023], with lo the box minimum and ext its longest side, all
+// in float64 (the same operations as the tree's cell geometry, so a body's
+// key and its cells agree exactly).  Block 0 also stores {lo_x, lo_y, lo_z,
+// ext} for the tree kernels.
+__global__ void __launch_bounds__(OTPB) morton30_kernel(int n, const double *__restrict__ pos,
+                                                         const double *__restrict__ parts,
+                                                         int nparts, unsigned *__restrict__ keys,
+                                                         int *__restrict__ vals,
+                                                         double *__restrict__ box_out)
+{
+    __shared__ double box[6];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 6) {
+        const bool is_min = warp < 3;
+        double v = is_min ? DBL_MAX : -DBL_MAX;
+        for (int b = lane; b < nparts; b += 32) {
+            const double p = parts[6 * (size_t)b + warp];
+            v = is_min ? fmin(v, p) : fmax(v, p);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, v, off);
+            v = is_min ? fmin(v, o) : fmax(v, o);
+        }
+        if (lane == 0) box[warp] = v;
+    }
+    __syncthreads();
+    double ext = box[3] - box[0];
+    if (box[4] - box[1] > ext) ext = box[4] - box[1];
+    if (box[5] - box[2] > ext) ext = box[5] - box[2];
+    if (!(ext > 0.0)) ext = 1.0;
+    const double scale = 1024.0 / ext;
+    if (blockIdx.x == 0 && threadIdx.x < 4) box_out[threadIdx.x] = threadIdx.x < 3 ? box[threadIdx.x] : ext;
+    for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
+        unsigned q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double t = __dmul_rn(__dsub_rn(pos[3 * (size_t)i + c], box[c]), scale);
+            q[c] = t >= 1023.0 ? 1023u : (t <= 0.0 ? 0u : (unsigned)t);
+        }
+        keys[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+        vals[i] = i;
+    }
+}
+
 // Digit histogram per warp-chunk of SORT_CHUNK keys: hist[d * nchunks + chunk].
 __global__ void __launch_bounds__(OTPB) radix_hist_kernel(int n, const unsigned *__restrict__ keys,
                                                            int shift, int nchunks,
@@ -234,6 +290,32 @@ cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderSc
         radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
         radix_scan_kernel<<<1, 1024, 0, s>>>(o.hist, 256 * nchunks);
         int *vout = pass == 2 ? perm_out : o.vals[cur ^ 1];
+        radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
+                                                     vout, shift, nchunks, o.hist);
+        kernels += 3;
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
+                             int *perm_out, double *box_out, int &kernels)
+{
+    kernels = 0;
+    if (n <= 0) return cudaSuccess;
+    const int nparts = grid_for(n) < MAX_BOX_PARTS ? grid_for(n) : MAX_BOX_PARTS;
+    bbox_kernel<<<nparts, OTPB, 0, s>>>(n, pos, o.box);
+    morton30_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, nparts, o.keys[0], o.vals[0],
+                                                 box_out);
+    kernels += 2;
+    const int nchunks = sort_chunks(n);
+    const int blocks = (nchunks + OTPB / 32 - 1) / (OTPB / 32);
+    int cur = 0;
+    for (int pass = 0; pass < 4; ++pass) {  // 30-bit keys: 4 passes, sorted keys end in keys[0]
+        const int shift = 8 * pass;
+        radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
+        radix_scan_kernel<<<1, 1024, 0, s>>>(o.hist, 256 * nchunks);
+        int *vout = pass == 3 ? perm_out : o.vals[cur ^ 1];
         radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
                                                      vout, shift, nchunks, o.hist);
         kernels += 3;

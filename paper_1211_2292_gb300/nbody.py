@@ -63,6 +63,11 @@ SIGNATURES = {
     "nb_profile": (_c_int, [_c_vp, _c_int]),
     "nb_profile_read": (_c_int, [_c_vp, _c_int, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_dbl)]),
     "nb_device_info": (_c_int, [_c_vp, _c_i64, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "nb_tree_forces": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_vp,
+                                _c_vp]),
+    "nb_tree_step": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
+                              _c_dbl, _c_i64, _c_vp, _c_uint]),
+    "nb_tree_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
@@ -115,6 +120,17 @@ def _ptr(t, name, n3=None):
         raise ValueError(f"{name} must be contiguous")
     if n3 is not None and t.numel() < n3:
         raise ValueError(f"{name} has {t.numel()} elements, needs {n3}")
+    return t.data_ptr() if t.numel() else None
+
+
+def _ptr_i32(t, name, numel):
+    """Device pointer of a contiguous int32 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32
+            and t.is_contiguous() and t.numel() >= numel):
+        raise ValueError(f"{name} must be a contiguous int32 CUDA tensor of {numel} elements")
     return t.data_ptr() if t.numel() else None
 
 
@@ -278,10 +294,39 @@ class NBody:
 
     def profile_read(self, kind: int):
         """(launches, total milliseconds) recorded for kind 0 force, 1 batched,
-        2 VJP, 3 energy."""
+        2 VJP, 3 energy, 4 tree walk, 5 tree build."""
         cnt, ms = ctypes.c_int64(), ctypes.c_double()
         self._call("nb_profile_read", int(kind), ctypes.byref(cnt), ctypes.byref(ms))
         return cnt.value, ms.value
+
+    def tree_forces(self, pos, mass, G, eps, theta, leaf_cap=16, out=None, counts=False):
+        """Barnes-Hut accelerations (paper Sec. IV-A); with counts=True also
+        the int32 [n, 2] cells and bodies each body met."""
+        import torch
+        n = mass.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+        cnt = None
+        if counts:
+            cnt = torch.empty((n, 2), dtype=torch.int32, device=pos.device)
+        self._call("nb_tree_forces", n, _ptr(pos, "pos", 3 * n), _ptr(mass, "mass", n), float(G),
+                   float(eps), float(theta), int(leaf_cap), _ptr(out, "acc", 3 * n),
+                   _ptr_i32(cnt, "counts", 2 * n))
+        return (out, cnt) if counts else out
+
+    def tree_step(self, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps, acc,
+                  acc_valid=False, graph=False):
+        n = mass.shape[0]
+        flags = (NB_ACC_VALID if acc_valid else 0) | (NB_USE_GRAPH if graph else 0)
+        self._call("nb_tree_step", n, _ptr(pos, "pos", 3 * n), _ptr(vel, "vel", 3 * n),
+                   _ptr(mass, "mass", n), float(G), float(eps), float(theta), int(leaf_cap),
+                   float(dt), int(nsteps), _ptr(acc, "acc", 3 * n), flags)
+
+    def tree_stats(self):
+        """{nodes, leaves, cell_interactions, body_interactions} of the last tree call."""
+        out = (ctypes.c_int64 * 4)()
+        self._call("nb_tree_stats", out)
+        return dict(zip(("nodes", "leaves", "cell_interactions", "body_interactions"), out))
 
     def device_info(self, n):
         sms, occ = ctypes.c_int(), ctypes.c_int()

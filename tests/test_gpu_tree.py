@@ -1,0 +1,147 @@
+"""GPU Barnes-Hut tree code (paper Sec. IV-A) against the oracle's tree code.
+
+Both sides build the same octree and take the same opening decisions (the
+acceptance test is float32 arithmetic written out identically), so the cells
+and bodies each body meets must agree exactly; the accelerations agree to
+the float32 walk's rounding.  With theta = 0 the tree walk is the direct sum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import host, relerr_per_body, to_dev
+from paper_1211_2292_gb300 import inputs, nbody
+
+pytestmark = pytest.mark.gpu
+
+RMS_TOL, MAX_TOL = 1e-5, 1e-4  # float32 pair terms, as the direct-sum float32 forms
+
+
+def _gpu_tree(cuda, b, G, eps, theta, leaf_cap, prec="fp32_comp"):
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    with nbody.NBody(b.n, prec) as nb:
+        a, cnt = nb.tree_forces(x, m, G, eps, theta, leaf_cap, counts=True)
+        nb.sync()
+        st = nb.tree_stats()
+    return host(a), host(cnt).astype(np.int64), st
+
+
+@pytest.mark.parametrize("n,theta,leaf_cap", [(1000, 0.5, 16), (4099, 0.7, 8), (20000, 0.5, 16),
+                                              (20000, 0.3, 32), (777, 1.0, 1)])
+def test_matches_oracle_tree(cuda, n, theta, leaf_cap):
+    b = inputs.plummer(n, seed=61)
+    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, theta, leaf_cap)
+    ref, rst, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.01, theta, leaf_cap, 32, counts=True)
+    assert np.array_equal(cnt, rcnt)
+    assert st == rst
+    e = relerr_per_body(a, ref)
+    assert np.sqrt((e ** 2).mean()) <= RMS_TOL and e.max() <= MAX_TOL
+
+
+def test_theta_zero_is_the_direct_sum(cuda):
+    b = inputs.plummer(3000, seed=62)
+    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, 0.0, 16)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
+    assert np.all(cnt[:, 0] == 0) and np.all(cnt[:, 1] == b.n)
+    assert st["cell_interactions"] == 0 and st["body_interactions"] == b.n * b.n
+    e = relerr_per_body(a, ref)
+    assert np.sqrt((e ** 2).mean()) <= RMS_TOL and e.max() <= MAX_TOL
+
+
+def test_two_clusters_and_every_precision_mode(cuda):
+    # Two distant clusters: whole subtrees are accepted as monopoles.
+    b = inputs.two_plummer(2500, seed=63)
+    ref, _, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.005, 0.6, 16, 32, counts=True)
+    for prec in ("fp64", "fp32", "fp32_comp"):
+        a, cnt, _ = _gpu_tree(cuda, b, 1.0, 0.005, 0.6, 16, prec)
+        assert np.array_equal(cnt, rcnt), prec
+        e = relerr_per_body(a, ref)
+        assert np.sqrt((e ** 2).mean()) <= RMS_TOL and e.max() <= MAX_TOL, prec
+
+
+def test_error_against_direct_sum_falls_with_theta(cuda):
+    b = inputs.plummer(30000, seed=64)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
+    rms = []
+    for th in (0.8, 0.4, 0.2):
+        a, _, _ = _gpu_tree(cuda, b, 1.0, 0.01, th, 16)
+        e = relerr_per_body(a, ref)
+        rms.append(np.sqrt((e ** 2).mean()))
+    assert rms[0] > rms[1] > rms[2] and rms[1] < 1e-3
+
+
+def test_degenerate_inputs(cuda):
+    # all bodies at one point: ext = 0 is read as 1, keys all 0, one chain of
+    # single-child cells down to a level-10 leaf holding every body
+    pos = np.zeros((100, 3)) + 0.25
+    m = np.full(100, 0.01)
+    b = inputs.Bodies(pos, np.zeros_like(pos), m)
+    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.1, 0.5, 4)
+    _, rst, rcnt = oracle.bh_forces(pos, m, 1.0, 0.1, 0.5, 4, 32, counts=True)
+    assert np.all(a == 0) and np.array_equal(cnt, rcnt) and st == rst and st["nodes"] == 11
+    # one body; a pair with zero softening (self pair skipped); ragged 33
+    for n, eps in ((1, 0.1), (2, 0.0), (33, 0.0)):
+        bb = inputs.random_system(n, seed=65 + n)
+        a, cnt, _ = _gpu_tree(cuda, bb, 1.3, eps, 0.5, 1)
+        ref, _, rcnt = oracle.bh_forces(bb.pos, bb.mass, 1.3, eps, 0.5, 1, 32, counts=True)
+        assert np.array_equal(cnt, rcnt) and np.isfinite(a).all()
+        if n == 1:
+            assert np.all(a == 0)
+        else:
+            assert relerr_per_body(a, ref).max() <= MAX_TOL
+
+
+def test_deterministic_and_empty(cuda):
+    b = inputs.plummer(5000, seed=66)
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        a1 = host(nb.tree_forces(x, m, 1.0, 0.01, 0.5, 16))
+        a2 = host(nb.tree_forces(x, m, 1.0, 0.01, 0.5, 16))
+        e = nb.tree_forces(x[:0], m[:0], 1.0, 0.01, 0.5, 16)
+        nb.sync()
+    assert np.array_equal(a1, a2) and e.shape == (0, 3)
+
+
+def test_argument_checks(cuda):
+    import torch
+    b = inputs.plummer(64, seed=67)
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    a = torch.empty((64, 3), dtype=torch.float64, device=cuda)
+    with nbody.NBody(64, "fp32_comp") as nb:
+        lib, before = nb.lib, nb.launches
+        args = (nb.h, 64, x.data_ptr(), m.data_ptr(), 1.0, 0.01)
+        assert lib.nb_tree_forces(*args, -0.1, 16, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, float("inf"), 16, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, 0.5, 0, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, 0.5, 65537, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(nb.h, 65, x.data_ptr(), m.data_ptr(), 1.0, 0.01, 0.5, 16,
+                                  a.data_ptr(), None) == 1
+        assert nb.launches == before
+
+
+def test_tree_step_matches_oracle_kdk_at_theta_zero(cuda):
+    b = inputs.plummer(2000, seed=68)
+    xr, vr, _ = oracle.kdk(b.pos, b.vel, b.mass, 1.0, 0.01, 1e-3, 10)
+    x, v, m = (to_dev(t, cuda) for t in (b.pos, b.vel, b.mass))
+    acc = to_dev(np.zeros((b.n, 3)), cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        nb.tree_step(x, v, m, 1.0, 0.01, 0.0, 16, 1e-3, 10, acc)
+        nb.sync()
+    assert np.abs(host(x) - xr).max() <= 1e-9
+    assert np.abs(host(v) - vr).max() <= 1e-6
+
+
+def test_tree_step_graph_equals_eager(cuda):
+    b = inputs.plummer(6000, seed=69)
+    outs = []
+    for graph in (False, True, True):
+        x, v, m = (to_dev(t, cuda) for t in (b.pos, b.vel, b.mass))
+        acc = to_dev(np.zeros((b.n, 3)), cuda)
+        with nbody.NBody(b.n, "fp32_comp") as nb:
+            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, graph=graph)
+            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, acc_valid=True, graph=graph)
+            nb.sync()
+        outs.append((host(x), host(v), host(acc)))
+    for o in outs[1:]:
+        for p, q in zip(outs[0], o):
+            assert np.array_equal(p, q)
