@@ -148,7 +148,7 @@ struct TreeView {
     int *start, *end, *level, *nchild, *first, *offs;
     unsigned *prefix;
     double *M, *com;      // float64 monopoles: mass, centre of mass [cap][3]
-    float4 *box_lo, *box_hi;  // float32 cell cube corners (.w unused)
+    float4 *box_lo, *box_hi;  // float32 cell cube corners; .w = nchild, first (int bits)
     float4 *chi, *clo;    // centre of mass hi/lo float32 pair; chi.w = mass
     unsigned long long *stats;  // [4] nodes, leaves, cell and body interactions
 };

@@ -39,7 +39,6 @@ namespace {
 
 constexpr int TTPB = 256;
 constexpr int WALK_WARPS = 4;
-constexpr int STACK_CAP = 96;  // >= 1 + 7 * 10 entries of a depth-first walk
 
 enum { META_COUNT = 0, META_BASE = 12, META_OVERFLOW = 24, META_INTS = 32 };
 
@@ -239,8 +238,9 @@ __global__ void __launch_bounds__(TTPB) tree_walkdata_kernel(TreeView t, const d
             blo[c] = (float)__dadd_rn(lo[c], __dmul_rn(cell, (double)ic[c]));
             bhi[c] = (float)__dadd_rn(lo[c], __dmul_rn(cell, (double)(ic[c] + 1u)));
         }
-        t.box_lo[node] = make_float4(blo[0], blo[1], blo[2], 0.f);
-        t.box_hi[node] = make_float4(bhi[0], bhi[1], bhi[2], 0.f);
+        // .w carries the child count and first child for the walk
+        t.box_lo[node] = make_float4(blo[0], blo[1], blo[2], __int_as_float(t.nchild[node]));
+        t.box_hi[node] = make_float4(bhi[0], bhi[1], bhi[2], __int_as_float(t.first[node]));
         const double cx = t.com[3 * (size_t)node], cy = t.com[3 * (size_t)node + 1],
                      cz = t.com[3 * (size_t)node + 2];
         const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
@@ -277,96 +277,247 @@ __device__ __forceinline__ float cube_dist2(float4 lo, float4 hi, float px, floa
     return d2;
 }
 
-template <bool ZEPS>
-__device__ __forceinline__ void pair1(float dx, float dy, float dz, float m, float e2, float &ax,
-                                      float &ay, float &az)
+// Squared distance from the cube [lo, hi] to the box [mn, mx], written as
+// cube_dist2 with the box's far corner in each difference.  Rounding is
+// monotonic, so for every p inside the box this value is <= cube_dist2(p):
+// when it passes the opening test, every body of the box passes it too.
+__device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const float (&mn)[3],
+                                                const float (&mx)[3])
 {
-    float r2 = fmaf(dx, dx, e2);
-    r2 = fmaf(dy, dy, r2);
-    r2 = fmaf(dz, dz, r2);
-    float ri = rsqrt_mufu(r2);
-    if (ZEPS) ri = r2 > 0.f ? ri : 0.f;
-    const float s = (m * ri) * (ri * ri);
-    ax = fmaf(dx, s, ax);
-    ay = fmaf(dy, s, ay);
-    az = fmaf(dz, s, az);
+    float d2 = 0.0f;
+    const float pl[3] = {lo.x, lo.y, lo.z}, ph[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float a = __fsub_rn(pl[c], mx[c]);
+        const float b = __fsub_rn(mn[c], ph[c]);
+        float dd = a > b ? a : b;
+        dd = dd > 0.0f ? dd : 0.0f;
+        d2 = __fadd_rn(d2, __fmul_rn(dd, dd));
+    }
+    return d2;
 }
 
+// Interaction list of a warp: up to LIST_CAP sources (cells or bodies) as
+// (x, y, z, m), coordinates relative to the warp's centre, stored in pairs
+// so that one pair is two float4 loads, already in float32x2 order:
+// {x0, x1, y0, y1}, {z0, z1, m0, m1}.
+constexpr int LIST_CAP = 64;
+constexpr int LEVELS = 11;
+
+__device__ __forceinline__ void list_put(float *L, int q, float x, float y, float z, float m)
+{
+    float *b = L + 8 * (q >> 1) + (q & 1);
+    b[0] = x;
+    b[2] = y;
+    b[4] = z;
+    b[6] = m;
+}
+
+// Accumulate the first 2 * npairs sources of the list onto this lane's body
+// (float32x2 over source pairs: one instruction covers two sources).
+template <bool ZEPS>
+__device__ __forceinline__ void list_eval(const float4 *L4, int npairs, float2 nx, float2 ny,
+                                          float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az)
+{
+#pragma unroll 4
+    for (int q = 0; q < npairs; ++q) {
+        const float4 A = L4[2 * q], B = L4[2 * q + 1];
+        const float2 dx = add2(make_float2(A.x, A.y), nx);
+        const float2 dy = add2(make_float2(A.z, A.w), ny);
+        const float2 dz = add2(make_float2(B.x, B.y), nz);
+        float2 r2 = fma2(dx, dx, e2);
+        r2 = fma2(dy, dy, r2);
+        r2 = fma2(dz, dz, r2);
+        float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        if (ZEPS) {
+            ri.x = r2.x > 0.f ? ri.x : 0.f;
+            ri.y = r2.y > 0.f ? ri.y : 0.f;
+        }
+        const float2 s = mul2(mul2(make_float2(B.z, B.w), ri), mul2(ri, ri));
+        ax = fma2(dx, s, ax);
+        ay = fma2(dy, s, ay);
+        az = fma2(dz, s, az);
+    }
+}
+
+// One warp per 32 consecutive bodies in key order.  The warp walks the tree
+// level by level, deepest level first, 32 nodes per round (one per lane):
+// the opening test against the 32 bodies decides, per node, between the
+// interaction list (accepted cell: its monopole; leaf: its bodies) and
+// descending (its children, a contiguous range, go on the next level's
+// stack).  Each level's stack holds at most 32 ranges, the children of one
+// round's nodes, since a level is refilled only once every deeper level is
+// empty.  Whenever 32 sources are listed, every lane adds them to its body.
 template <bool ZEPS>
 __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWalkParams p)
 {
-    __shared__ int stack[WALK_WARPS][STACK_CAP];
-    __shared__ float crit2[11];
+    __shared__ float4 list_s[WALK_WARPS][LIST_CAP];
+    __shared__ int2 ranges_s[WALK_WARPS][LEVELS][32];
+    __shared__ int slot_s[WALK_WARPS][32];
+    __shared__ float crit2[LEVELS];
     const TreeView t = p.tree;
-    if (threadIdx.x < 11) crit2[threadIdx.x] = open_dist2(p.box[3], threadIdx.x, p.theta);
+    if (threadIdx.x < LEVELS) crit2[threadIdx.x] = open_dist2(p.box[3], threadIdx.x, p.theta);
     __syncthreads();
 
+    const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n;
-    const int k = (blockIdx.x * WALK_WARPS + warp) * 32 + lane;
-    if ((blockIdx.x * WALK_WARPS + warp) * 32 >= n) return;  // whole warp past the end
+    const int base = (blockIdx.x * WALK_WARPS + warp) * 32;
+    if (base >= n) return;  // whole warp past the end
+    const int k = base + lane;
+    const int nvalid = min(32, n - base);
     const bool valid = k < n;
     const float4 h = valid ? __ldg(p.P + k) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 l = valid ? __ldg(p.Plo + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // warp centre (box midpoint of the valid bodies) as the coordinate origin
     float mn[3] = {valid ? h.x : INFINITY, valid ? h.y : INFINITY, valid ? h.z : INFINITY};
     float mx[3] = {valid ? h.x : -INFINITY, valid ? h.y : -INFINITY, valid ? h.z : -INFINITY};
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
-            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+            mn[c] = fminf(mn[c], __shfl_xor_sync(FULL, mn[c], off));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(FULL, mx[c], off));
         }
     }
     const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]),
                 cz = 0.5f * (mn[2] + mx[2]);
     const float xi = rel(h.x, l.x, cx), yi = rel(h.y, l.y, cy), zi = rel(h.z, l.z, cz);
-    const float e2 = p.eps2f;
+    const float2 nx = make_float2(-xi, -xi), ny = make_float2(-yi, -yi), nz = make_float2(-zi, -zi);
+    const float2 e2 = make_float2(p.eps2f, p.eps2f);
 
-    float ax = 0.f, ay = 0.f, az = 0.f;
+    float *L = reinterpret_cast<float *>(list_s[warp]);
+    const float4 *L4 = list_s[warp];
+    int2(*rs)[32] = ranges_s[warp];
+    int *slot = slot_s[warp];
+    const unsigned lt = (1u << lane) - 1u;
+
+    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
     float sx = 0.f, sy = 0.f, sz = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
-    int nc = 0, nb = 0;
-    int *st = stack[warp];
-    if (lane == 0) st[0] = 0;
-    int sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        const int node = st[--sp];
+    auto fold = [&]() {
+        kahan_add(sx, qx, ax.x);
+        kahan_add(sx, qx, ax.y);
+        kahan_add(sy, qy, ay.x);
+        kahan_add(sy, qy, ay.y);
+        kahan_add(sz, qz, az.x);
+        kahan_add(sz, qz, az.y);
+        ax = ay = az = make_float2(0.f, 0.f);
+    };
+    int cnt = 0;  // listed sources (warp-uniform)
+    // 32 sources listed: add them, move the rest (< 32) to the front
+    auto flush32 = [&]() {
         __syncwarp();
-        const float4 blo = __ldg(t.box_lo + node), bhi = __ldg(t.box_hi + node);
-        const int L = t.level[node];
-        const int nch = t.nchild[node];
-        const bool ok = !valid || cube_dist2(blo, bhi, h.x, h.y, h.z) >= crit2[L];
-        const bool all = __all_sync(0xffffffffu, ok);
-        if (all) {
-            const float4 ch = __ldg(t.chi + node), cl = __ldg(t.clo + node);
-            pair1<ZEPS>(rel(ch.x, cl.x, cx) - xi, rel(ch.y, cl.y, cy) - yi,
-                        rel(ch.z, cl.z, cz) - zi, ch.w, e2, ax, ay, az);
-            ++nc;
-        } else if (nch == 0) {
-            const int s = t.start[node], e = t.end[node];
-            for (int j = s; j < e; ++j) {
-                const float4 bh = __ldg(p.P + j), bl = __ldg(p.Plo + j);
-                pair1<ZEPS>(rel(bh.x, bl.x, cx) - xi, rel(bh.y, bl.y, cy) - yi,
-                            rel(bh.z, bl.z, cz) - zi, bh.w, e2, ax, ay, az);
-            }
-            nb += e - s;
-        } else {
-            const int f = t.first[node];
-            if (lane < nch && sp + lane < STACK_CAP) st[sp + lane] = f + nch - 1 - lane;
-            sp += nch;
-            if (sp > STACK_CAP) {  // cannot happen for 10 levels; keep the walk in bounds
-                if (lane == 0) atomicOr(p.err, ERR_TREE);
-                sp = STACK_CAP;
-            }
-            __syncwarp();
-            continue;
+        list_eval<ZEPS>(L4, 16, nx, ny, nz, e2, ax, ay, az);
+        fold();
+        __syncwarp();
+        list_s[warp][lane] = list_s[warp][LIST_CAP / 2 + lane];
+        cnt -= 32;
+        __syncwarp();
+    };
+
+    int nc = 0, nb = 0;
+    int lsize = lane == 0 ? 1 : 0;  // lane L holds the size of level L's stack
+    if (lane == 0) rs[0][0] = make_int2(0, 1);
+    __syncwarp();
+    for (;;) {
+        const unsigned nonempty = __ballot_sync(FULL, lane < LEVELS && lsize > 0);
+        if (!nonempty) break;
+        const int Lv = 31 - __clz(nonempty);
+        const int size = __shfl_sync(FULL, lsize, Lv);
+        // take up to 32 nodes from the top ranges of level Lv
+        const int R = min(size, 32);
+        const int2 r = lane < R ? rs[Lv][size - 1 - lane] : make_int2(0, 0);
+        int incl = r.y;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += v;
         }
-        kahan_add(sx, qx, ax);
-        kahan_add(sy, qy, ay);
-        kahan_add(sz, qz, az);
-        ax = ay = az = 0.f;
+        const int excl = incl - r.y;
+        const int take = min(__shfl_sync(FULL, incl, 31), 32);
+        if (lane < R)
+            for (int q = excl; q < incl && q < 32; ++q) slot[q] = r.x + (q - excl);
+        const unsigned done = __ballot_sync(FULL, lane < R && incl <= 32);
+        if (lane < R && excl < 32 && incl > 32)
+            rs[Lv][size - 1 - lane] = make_int2(r.x + (32 - excl), incl - 32);
+        __syncwarp();
+        const int node = lane < take ? slot[lane] : -1;
+        if (lane == Lv) lsize -= __popc(done);
+        __syncwarp();
+
+        // opening test: the warp's box first, then body by body
+        const bool has = node >= 0;
+        float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
+        if (has) {
+            blo = __ldg(t.box_lo + node);
+            bhi = __ldg(t.box_hi + node);
+        }
+        const float cr = crit2[Lv];
+        bool accept = has && cube_box_dist2(blo, bhi, mn, mx) >= cr;
+        if (__ballot_sync(FULL, has && !accept)) {
+            bool ok = has && !accept;
+            for (int b = 0; b < nvalid; ++b) {
+                const float px = __shfl_sync(FULL, h.x, b), py = __shfl_sync(FULL, h.y, b),
+                            pz = __shfl_sync(FULL, h.z, b);
+                if (ok) ok = cube_dist2(blo, bhi, px, py, pz) >= cr;
+                if (!__ballot_sync(FULL, ok)) break;
+            }
+            accept = accept || ok;
+        }
+        const int nch = has ? __float_as_int(blo.w) : 0;
+        const bool open = has && !accept && nch > 0;
+        const bool leaf = has && !accept && nch == 0;
+
+        // children ranges onto the next level (Lv < 10 whenever a node opens)
+        const unsigned om = __ballot_sync(FULL, open);
+        if (om) {
+            const int size1 = __shfl_sync(FULL, lsize, Lv + 1);
+            const int slot1 = size1 + __popc(om & lt);
+            if (open && slot1 < 32) rs[Lv + 1][slot1] = make_int2(__float_as_int(bhi.w), nch);
+            if (lane == Lv + 1) lsize = min(size1 + __popc(om), 32);
+            if (lane == 0 && size1 + __popc(om) > 32) atomicOr(p.err, ERR_TREE);  // never: see above
+        }
+        __syncwarp();
+        // accepted cells: their monopoles
+        const unsigned am = __ballot_sync(FULL, accept);
+        if (am) {
+            if (accept) {
+                const float4 ch = __ldg(t.chi + node), cl = __ldg(t.clo + node);
+                list_put(L, cnt + __popc(am & lt), rel(ch.x, cl.x, cx), rel(ch.y, cl.y, cy),
+                         rel(ch.z, cl.z, cz), ch.w);
+            }
+            cnt += __popc(am);
+            nc += __popc(am);
+            if (cnt >= 32) flush32();
+        }
+        // leaves: their bodies, 32 at a time
+        unsigned lm = __ballot_sync(FULL, leaf);
+        int ls = 0, le = 0;
+        if (leaf) {
+            ls = t.start[node];
+            le = t.end[node];
+        }
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int s0 = __shfl_sync(FULL, ls, src), e0 = __shfl_sync(FULL, le, src);
+            nb += e0 - s0;
+            for (int j0 = s0; j0 < e0; j0 += 32) {
+                const int kk = min(32, e0 - j0);
+                if (lane < kk) {
+                    const float4 bh = __ldg(p.P + j0 + lane), bl = __ldg(p.Plo + j0 + lane);
+                    list_put(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
+                             rel(bh.z, bl.z, cz), bh.w);
+                }
+                cnt += kk;
+                if (cnt >= 32) flush32();
+            }
+        }
+    }
+    if (cnt > 0) {  // the rest, padded to a pair with a massless source
+        if (lane == 0 && (cnt & 1)) list_put(L, cnt, 0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        list_eval<ZEPS>(L4, (cnt + 1) >> 1, nx, ny, nz, e2, ax, ay, az);
+        fold();
     }
     if (valid) {
         const int i = p.perm[k];
@@ -389,16 +540,9 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
         }
         if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
     }
-    unsigned long long cnt[2] = {valid ? (unsigned long long)nc : 0ull,
-                                 valid ? (unsigned long long)nb : 0ull};
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        cnt[0] += __shfl_xor_sync(0xffffffffu, cnt[0], off);
-        cnt[1] += __shfl_xor_sync(0xffffffffu, cnt[1], off);
-    }
-    if (lane == 0) {
-        atomicAdd(t.stats + 2, cnt[0]);
-        atomicAdd(t.stats + 3, cnt[1]);
+    if (lane == 0) {  // nc, nb are the same for the group's nvalid bodies
+        atomicAdd(t.stats + 2, (unsigned long long)nc * nvalid);
+        atomicAdd(t.stats + 3, (unsigned long long)nb * nvalid);
     }
 }
 
