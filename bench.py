@@ -9,14 +9,18 @@ evaluations) in the float32 Kahan-compensated form with float64 state.
 Metric: pairwise interactions per second, N^2 per force evaluation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload throughput|batched|precision|plain|differentiation]
+                  [--workload throughput|batched|precision|plain|differentiation|tree]
 
 The other workloads (single-GPU lines with the same metric): "precision"
 (N = 65,536 Plummer, eps 0.005, FP32 compensated, 1 + 100 steps of dt 5e-4,
 with the force error against the oracle and the energy drift against the
 FP64 GPU run), "plain" (N = 1024 Plummer, FP64, 1 + 10 steps of dt 1e-3, one
 graph launch, checked against the oracle), "differentiation" (N = 16,384,
-200 steps with checkpoints every 20: forward, recompute and reverse sweep).
+200 steps with checkpoints every 20: forward, recompute and reverse sweep),
+"tree" (the default workload's bodies through the Barnes-Hut tree code,
+theta 0.5, leaves of at most 16 bodies: 1 + 10 KDK steps with the tree
+rebuilt for every force evaluation; its metric counts the cell and body
+interactions the walk computes).
 
 Multi-GPU (torchrun, one rank per GPU): for "throughput" every rank runs its
 own replica (the single-system path is not sharded); for "batched" the 512
@@ -69,7 +73,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="throughput",
-                    choices=["throughput", "batched", "precision", "plain", "differentiation"])
+                    choices=["throughput", "batched", "precision", "plain", "differentiation",
+                             "tree"])
+    ap.add_argument("--theta", type=float, default=None, help="tree workload: opening angle")
+    ap.add_argument("--leaf-cap", type=int, default=None, help="tree workload: leaf capacity")
     ap.add_argument("--fp64-n", type=int, default=262_144,
                     help="bodies for the float64-form rate (first bodies of the workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -102,14 +109,20 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region.  A reader
+    thread collects the samples; wait_ready() returns once the first one has
+    arrived, so that nvidia-smi's start-up (NVML initialisation) is over
+    before the timed region begins."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_id=None):
+        import threading
         self.proc = None
+        self.lines = []
+        self.ready = threading.Event()
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                "-lms", "200"]
         if gpu_id:
@@ -119,19 +132,35 @@ class ClockSampler:
                                          text=True)
         except OSError:
             self.proc = None
+            self.ready.set()
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
+            self.ready.set()
+        self.ready.set()
+
+    def wait_ready(self, timeout=10.0):
+        self.ready.wait(timeout)
+        self.skip = len(self.lines)  # samples taken before the timed region
 
     def stop(self):
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self.thread.join(timeout=5)
         sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
+        lines = self.lines[getattr(self, "skip", 0):] or self.lines[-1:]
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -198,6 +227,35 @@ def reference_arm(args, ws, rank):
         return 0
     import oracle
     from paper_1211_2292_gb300 import inputs
+    if args.workload == "tree":
+        w = TREE
+        theta = w["theta"] if args.theta is None else args.theta
+        lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+        b = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
+        for _ in range(args.warmup):
+            oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, 32)
+        tot, inter = 0.0, 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            _, st = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, 32)
+            tot += time.perf_counter() - t0
+            inter += st["cell_interactions"] + st["body_interactions"]
+        value = inter / tot / 1e9
+        sample = (f"one tree build + walk of two-plummer N={b.n} (same recipe), theta {theta}, "
+                  f"leaves <= {lc}, groups of 32, per step")
+        line = {
+            "impl": "reference", "metric": TREE_METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer spheres)",
+            "config": {"workload": w["name"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "batched":
         w = BATCHED
         bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
@@ -336,6 +394,11 @@ def measure_forms(torch, dev, tune, table, peak_tflops):
 PRECISION = {"name": "Plummer N=65536, eps 0.005, fp32 Kahan-compensated, 1 force eval + 100 KDK "
                      "steps of dt 5e-4", "n": 65536, "seed": 1, "eps": 0.005, "dt": 5e-4,
              "steps": 100}
+TREE = {"name": "two-plummer N=1048576, Barnes-Hut theta 0.5, leaves <= 16 bodies, groups of 32, "
+                "1 force eval + 10 KDK steps (tree rebuilt per eval), fp32 walk, f64 state",
+        "seed": 2, "eps": 0.002, "dt": 1e-3, "steps": 10, "theta": 0.5, "leaf_cap": 16,
+        "cpu_n_per": 65_536}
+TREE_METRIC = "tree interactions/s (cell + body, G/s)"
 PLAIN = {"name": "Plummer N=1024, eps 0.01, fp64, 1 force eval + 10 KDK steps of dt 1e-3 "
                  "(one graph launch)", "n": 1024, "seed": 0, "eps": 0.01, "dt": 1e-3, "steps": 10}
 
@@ -347,6 +410,126 @@ def _line(args, ws, value, ms_step, cfg, extra, dtype="f32", scaling="weak"):
             "data": "synthetic (seeded Plummer spheres)", "config": cfg}
     line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def tree_oracle_rate(w, theta, leaf_cap):
+    """The oracle's (single-threaded) tree code on the same recipe at 2 x cpu_n_per bodies."""
+    import oracle
+    from paper_1211_2292_gb300 import inputs
+    b = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
+    t0 = time.perf_counter()
+    _, st, cnt = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, leaf_cap, 32, counts=True)
+    el = time.perf_counter() - t0
+    inter = st["cell_interactions"] + st["body_interactions"]
+    sample = (f"two-plummer N={b.n} (same recipe), theta {theta}, leaves <= {leaf_cap}, groups "
+              f"of 32: one tree build + walk, {el:.1f} s")
+    return inter / el / 1e9, sample, b, cnt
+
+
+def tree_workload(args, ws, torch, dev, stream, T, flush, table):
+    """Barnes-Hut line: value = walk interactions / time over 1 + 10 steps."""
+    import numpy as np
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody
+    w = TREE
+    theta = w["theta"] if args.theta is None else args.theta
+    lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+    b = inputs.two_plummer(args.n_per, seed=w["seed"])
+    x0, v0, m = T(b.pos), T(b.vel), T(b.mass)
+    G, eps, dt, K = 1.0, w["eps"], w["dt"], w["steps"]
+    with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+        x, v = x0.clone(), v0.clone()
+        a = torch.empty_like(x)
+
+        def step():
+            x.copy_(x0)
+            v.copy_(v0)
+            nb.tree_step(x, v, m, G, eps, theta, lc, dt, K, a)
+
+        # interactions of one step, eval by eval (the walk is deterministic)
+        inter = []
+        step_evals = []
+        x.copy_(x0)
+        v.copy_(v0)
+        nb.tree_forces(x, m, G, eps, theta, lc, out=a)
+        st = nb.tree_stats()
+        inter.append(st["cell_interactions"] + st["body_interactions"])
+        step_evals.append(st)
+        for _ in range(K):
+            nb.tree_step(x, v, m, G, eps, theta, lc, dt, 1, a, acc_valid=True)
+            st = nb.tree_stats()
+            inter.append(st["cell_interactions"] + st["body_interactions"])
+        per_step = float(sum(inter))
+        for _ in range(args.warmup):
+            step()
+        nb.profile(True)
+        l0 = nb.launches
+        try:
+            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            gpu_id = None
+        clocks = ClockSampler(gpu_id)
+        clocks.wait_ready()
+        with Timer(torch, dev, stream, lambda: None) as t:
+            for _ in range(args.steps):
+                step()
+                flush.fill_(1.0)
+        ck = clocks.stop()
+        launches = nb.launches - l0
+        wn, wms = nb.profile_read(4)
+        bn, bms = nb.profile_read(5)
+        nb.profile(False)
+        # accuracy of the first evaluation: tree vs the exact sum on sampled bodies
+        rows = inputs.sample_rows(b.n, 4096, seed=1)
+        ref = oracle.accel_rows(b.pos, b.mass, rows, G, eps)
+        at = nb.tree_forces(x0, m, G, eps, theta, lc).cpu().numpy()[rows]
+        e = np.linalg.norm(at - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    value = per_step * args.steps / (t.ms / 1e3) / 1e9
+    evals = K + 1
+    walk_ms = wms / max(wn, 1)
+    sm_max = (ck or {}).get("sm_max_mhz") or NOMINAL_SM_MAX_MHZ
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOPS_PER_INTERACTION * per_step / evals / (walk_ms / 1e3) / 1e12
+    cpu = None
+    parity = None
+    if not args.no_cpu_baseline:
+        rate, sample, bs, rcnt = tree_oracle_rate(w, theta, lc)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        with nbody.NBody(bs.n, "fp32_comp", device=dev.index) as nb:
+            _, gcnt = nb.tree_forces(T(bs.pos), T(bs.mass), G, eps, theta, lc, counts=True)
+            nb.sync()
+        parity = {"counts_equal_oracle": bool(np.array_equal(gcnt.cpu().numpy(), rcnt)),
+                  "n": bs.n}
+    n = float(b.n)
+    line = {"metric": TREE_METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t.ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Plummer spheres)",
+            "config": {"workload": w["name"] if args.n_per == WORKLOAD["n_per"] else
+                       f"two-plummer N={b.n} tree", "n": b.n, "theta": theta, "leaf_cap": lc,
+                       "group": 32, "force_evals_per_step": evals,
+                       "l2": "256 MiB buffer written between steps"},
+            "interactions_per_step": per_step,
+            "first_eval": {"nodes": step_evals[0]["nodes"], "leaves": step_evals[0]["leaves"],
+                           "cell_interactions": step_evals[0]["cell_interactions"],
+                           "body_interactions": step_evals[0]["body_interactions"]},
+            "ms_per_force_eval": t.ms / args.steps / evals,
+            "walk_ms": walk_ms, "build_ms": bms / max(bn, 1),
+            "direct_sum_equivalent": {"value": n * n * evals * args.steps / (t.ms / 1e3) / 1e9,
+                                      "unit": UNIT, "note": "N^2 per evaluation / time"},
+            "force_error_vs_direct_sum": {"rms": float(np.sqrt((e ** 2).mean())),
+                                          "max": float(e.max()),
+                                          "sample": "4096 bodies, FP64 oracle direct sum"},
+            "roofline": {"bound": "alu", "kernel": "tree_walk_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "note": f"{FLOPS_PER_INTERACTION} flops per cell or body interaction; "
+                                 "walk kernel event-timed inside the timed region; peak = SMs x "
+                                 "128 FP32 lanes x 2 x max SM clock"},
+            "parity": parity, "cpu_baseline": cpu, "clocks": ck, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def other_workload(args, ws, rank, local):
@@ -463,6 +646,9 @@ def other_workload(args, ws, rank, local):
                "precision": "fp64", "state": "f64"}, extra, dtype="f64")
         return 0
 
+    if args.workload == "tree":
+        return tree_workload(args, ws, torch, dev, stream, T, flush, table)
+
     # differentiation
     a_ = ADJOINT
     b, dx = inputs.plummer_with_perturbation(a_["n"], seed=a_["seed"])
@@ -508,7 +694,7 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
-    if args.workload in ("precision", "plain", "differentiation"):
+    if args.workload in ("precision", "plain", "differentiation", "tree"):
         if args.warmup < 3:
             args.warmup = 3
         return other_workload(args, ws, rank, local)
@@ -611,7 +797,7 @@ def main():
     except Exception:
         gpu_id = None
     clocks = ClockSampler(gpu_id)
-    time.sleep(0.3)
+    clocks.wait_ready()
     nb.profile(True)
     l0 = nb.launches
     with Timer(torch, dev, stream, barrier) as t:

@@ -58,6 +58,63 @@ __device__ __forceinline__ double rsqrt_f64(double x)
     return fma(y * e, p, y);
 }
 
+// Exclusive scan of in[0..total) into out[0..total) (in == out allowed) by
+// one block of 1024 threads, in index order; returns the sum (every thread).
+// Tiles of 8192 entries pass through shared memory (coalesced loads and
+// stores), 8 consecutive entries per thread, a two-level warp scan of the
+// thread sums and a carry from tile to tile.  tile: 8192 + 256 entries,
+// wsum: 32 entries of shared memory.
+constexpr int BSCAN_PER = 8, BSCAN_TILE = 1024 * BSCAN_PER;
+__device__ __forceinline__ int bscan_pad(int i) { return i + (i >> 5); }  // no bank conflicts
+
+template <typename T>
+__device__ T block_scan_exclusive(const T *in, T *out, int total, T *tile, T *wsum)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T carry = 0;
+    for (int base = 0; base < total; base += BSCAN_TILE) {
+        for (int q = threadIdx.x; q < BSCAN_TILE; q += 1024)
+            tile[bscan_pad(q)] = base + q < total ? in[base + q] : T(0);
+        __syncthreads();
+        T v[BSCAN_PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < BSCAN_PER; ++q) {
+            v[q] = tile[bscan_pad(threadIdx.x * BSCAN_PER + q)];
+            sum += v[q];
+        }
+        T incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            T w = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const T t = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        T run = carry + (warp ? wsum[warp - 1] : T(0)) + incl - sum;
+#pragma unroll
+        for (int q = 0; q < BSCAN_PER; ++q) {
+            tile[bscan_pad(threadIdx.x * BSCAN_PER + q)] = run;
+            run += v[q];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < BSCAN_TILE; q += 1024)
+            if (base + q < total) out[base + q] = tile[bscan_pad(q)];
+        carry += wsum[31];
+        __syncthreads();  // tile and wsum are rewritten by the next tile
+    }
+    return carry;
+}
+
 // Kahan-compensated accumulation of a partial sum p into (s, c); the value
 // represented is s - c.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float p)

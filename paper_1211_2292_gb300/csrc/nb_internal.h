@@ -117,9 +117,9 @@ int f64_vjp_variants();
 const KernelEntry &f64_vjp_kernel(int variant, bool zeps);
 
 // -------------------------------------------------- spatial order (order.cu)
-constexpr int SORT_CHUNK = 4096;  // keys per warp-chunk of the radix sort
+constexpr int SORT_CHUNK = 2048;  // keys per warp-chunk of the radix sort
 struct OrderScratch {
-    double *box;        // [1024][6] bounding-box partials
+    double *box;        // [1024][6]: bounding-box partials of up to 1023 blocks, then the folded box
     unsigned *keys[2];  // [n] Morton keys (ping-pong)
     int *vals[2];       // [n] body indices (ping-pong)
     unsigned *hist;     // [256][chunks] digit counts / offsets

@@ -26,7 +26,8 @@ namespace nb {
 namespace {
 
 constexpr int OTPB = 256;
-constexpr int MAX_BOX_PARTS = 1024;
+constexpr int MAX_BOX_PARTS = 1023;            // box partials; the folded box follows them
+constexpr int BOX_FINAL = 6 * MAX_BOX_PARTS;  // {min x,y,z, max x,y,z} in the box scratch
 
 __device__ __forceinline__ unsigned spread8(unsigned v)
 {
@@ -70,30 +71,34 @@ __global__ void __launch_bounds__(OTPB) bbox_kernel(int n, const double *__restr
     if (threadIdx.x < 6) parts[6 * (size_t)blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Morton keys; every block first folds the box partials.
+// One block of 6 warps: warp c folds component c of the box partials into
+// parts[BOX_FINAL + c].
+__global__ void __launch_bounds__(192) box_fold_kernel(double *__restrict__ parts, int nparts)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool is_min = warp < 3;
+    double v = is_min ? DBL_MAX : -DBL_MAX;
+    for (int b = lane; b < nparts; b += 32) {
+        const double p = parts[6 * (size_t)b + warp];
+        v = is_min ? fmin(v, p) : fmax(v, p);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = is_min ? fmin(v, o) : fmax(v, o);
+    }
+    if (lane == 0) parts[BOX_FINAL + warp] = v;
+}
+
+// Morton keys (8 bits per axis) in the folded box.
 __global__ void __launch_bounds__(OTPB) morton_kernel(int n, const double *__restrict__ pos,
                                                        const double *__restrict__ parts,
-                                                       int nparts, unsigned *__restrict__ keys,
+                                                       unsigned *__restrict__ keys,
                                                        int *__restrict__ vals)
 {
-    __shared__ double box[6];
-    // warp c (c < 6) folds component c of the partials, lanes striding
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 6) {
-        const bool is_min = warp < 3;
-        double v = is_min ? DBL_MAX : -DBL_MAX;
-        for (int b = lane; b < nparts; b += 32) {
-            const double p = parts[6 * (size_t)b + warp];
-            v = is_min ? fmin(v, p) : fmax(v, p);
-        }
+    double box[6];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_xor_sync(0xffffffffu, v, off);
-            v = is_min ? fmin(v, o) : fmax(v, o);
-        }
-        if (lane == 0) box[warp] = v;
-    }
-    __syncthreads();
+    for (int c = 0; c < 6; ++c) box[c] = parts[BOX_FINAL + c];
     const double ext = fmax(fmax(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
     const double scale = ext > 0.0 ? 256.0 / ext : 0.0;
     for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
@@ -126,33 +131,24 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
 // ext} for the tree kernels.
 __global__ void __launch_bounds__(OTPB) morton30_kernel(int n, const double *__restrict__ pos,
                                                          const double *__restrict__ parts,
-                                                         int nparts, unsigned *__restrict__ keys,
+                                                         unsigned *__restrict__ keys,
                                                          int *__restrict__ vals,
                                                          double *__restrict__ box_out)
 {
-    __shared__ double box[6];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 6) {
-        const bool is_min = warp < 3;
-        double v = is_min ? DBL_MAX : -DBL_MAX;
-        for (int b = lane; b < nparts; b += 32) {
-            const double p = parts[6 * (size_t)b + warp];
-            v = is_min ? fmin(v, p) : fmax(v, p);
-        }
+    double box[6];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_xor_sync(0xffffffffu, v, off);
-            v = is_min ? fmin(v, o) : fmax(v, o);
-        }
-        if (lane == 0) box[warp] = v;
-    }
-    __syncthreads();
+    for (int c = 0; c < 6; ++c) box[c] = parts[BOX_FINAL + c];
     double ext = box[3] - box[0];
     if (box[4] - box[1] > ext) ext = box[4] - box[1];
     if (box[5] - box[2] > ext) ext = box[5] - box[2];
     if (!(ext > 0.0)) ext = 1.0;
     const double scale = 1024.0 / ext;
-    if (blockIdx.x == 0 && threadIdx.x < 4) box_out[threadIdx.x] = threadIdx.x < 3 ? box[threadIdx.x] : ext;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        box_out[0] = box[0];
+        box_out[1] = box[1];
+        box_out[2] = box[2];
+        box_out[3] = ext;
+    }
     for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
         unsigned q[3];
 #pragma unroll
@@ -187,25 +183,9 @@ __global__ void __launch_bounds__(OTPB) radix_hist_kernel(int n, const unsigned 
 // In-place exclusive scan of hist[0..total) by one block, in index order.
 __global__ void __launch_bounds__(1024) radix_scan_kernel(unsigned *__restrict__ hist, int total)
 {
-    __shared__ unsigned part[1024];
-    const int seg = (total + 1023) / 1024;
-    const int b = threadIdx.x * seg, e = min(b + seg, total);
-    unsigned s = 0u;
-    for (int i = b; i < e; ++i) s += hist[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned run = part[threadIdx.x] - s;  // exclusive prefix of this segment
-    for (int i = b; i < e; ++i) {
-        const unsigned h = hist[i];
-        hist[i] = run;
-        run += h;
-    }
+    __shared__ unsigned tile[BSCAN_TILE + BSCAN_TILE / 32];
+    __shared__ unsigned wsum[32];
+    block_scan_exclusive<unsigned>(hist, hist, total, tile, wsum);
 }
 
 // Stable scatter: one warp per chunk, keys taken 32 at a time in order.
@@ -279,9 +259,9 @@ cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderSc
     if (n <= 0) return cudaSuccess;
     const int nparts = grid_for(n) < MAX_BOX_PARTS ? grid_for(n) : MAX_BOX_PARTS;
     bbox_kernel<<<nparts, OTPB, 0, s>>>(n, pos, o.box);
-    ++kernels;
-    morton_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, nparts, o.keys[0], o.vals[0]);
-    ++kernels;
+    box_fold_kernel<<<1, 192, 0, s>>>(o.box, nparts);
+    morton_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, o.keys[0], o.vals[0]);
+    kernels += 3;
     const int nchunks = sort_chunks(n);
     const int blocks = (nchunks + OTPB / 32 - 1) / (OTPB / 32);
     int cur = 0;
@@ -305,9 +285,9 @@ cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScra
     if (n <= 0) return cudaSuccess;
     const int nparts = grid_for(n) < MAX_BOX_PARTS ? grid_for(n) : MAX_BOX_PARTS;
     bbox_kernel<<<nparts, OTPB, 0, s>>>(n, pos, o.box);
-    morton30_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, nparts, o.keys[0], o.vals[0],
-                                                 box_out);
-    kernels += 2;
+    box_fold_kernel<<<1, 192, 0, s>>>(o.box, nparts);
+    morton30_kernel<<<grid_for(n), OTPB, 0, s>>>(n, pos, o.box, o.keys[0], o.vals[0], box_out);
+    kernels += 3;
     const int nchunks = sort_chunks(n);
     const int blocks = (nchunks + OTPB / 32 - 1) / (OTPB / 32);
     int cur = 0;

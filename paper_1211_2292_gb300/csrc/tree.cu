@@ -77,59 +77,46 @@ __device__ __forceinline__ int lower_bound(const unsigned *__restrict__ keys, in
     return lo;
 }
 
-__device__ __forceinline__ void octant_bounds(const unsigned *__restrict__ keys, int start,
-                                              int end, unsigned prefix, int L, int (&b)[9])
+// One warp per node: lane o (1..7) finds where octant o starts in the
+// node's sorted keys, lane 0 holds start and lane 8 end; lane o < 8 then
+// sees whether child o is non-empty.  Returns the ballot of non-empty
+// children (bit o) and leaves the child's range in [b, nxt) on lane o.
+__device__ __forceinline__ unsigned octants(const unsigned *__restrict__ keys, int s, int e,
+                                            unsigned prefix, int L, int lane, int &b, int &nxt)
 {
     const int shift = 3 * (10 - (L + 1));
-    b[0] = start;
-    b[8] = end;
-#pragma unroll
-    for (int o = 1; o < 8; ++o) b[o] = lower_bound(keys, start, end, (prefix * 8u + o) << shift);
+    b = lane == 0 ? s : (lane <= 7 ? lower_bound(keys, s, e, (prefix * 8u + lane) << shift) : e);
+    nxt = __shfl_down_sync(0xffffffffu, b, 1);
+    return __ballot_sync(0xffffffffu, lane < 8 && nxt > b);
 }
 
 __global__ void __launch_bounds__(TTPB) tree_count_kernel(TreeView t, const unsigned *keys, int L,
                                                           int leaf_cap)
 {
     const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
-    for (int q = blockIdx.x * TTPB + threadIdx.x; q < cnt; q += gridDim.x * TTPB) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (TTPB / 32);
+    for (int q = blockIdx.x * (TTPB / 32) + (threadIdx.x >> 5); q < cnt; q += warps) {
         const int node = base + q;
         const int s = t.start[node], e = t.end[node];
         int nch = 0;
         if (e - s > leaf_cap) {
-            int b[9];
-            octant_bounds(keys, s, e, t.prefix[node], L, b);
-#pragma unroll
-            for (int o = 0; o < 8; ++o) nch += b[o + 1] > b[o];
+            int b, nxt;
+            nch = __popc(octants(keys, s, e, t.prefix[node], L, lane, b, nxt));
         }
-        t.nchild[node] = nch;
+        if (lane == 0) t.nchild[node] = nch;
     }
 }
 
 // One block: exclusive scan of the child counts of level L into t.offs,
-// level L+1's count and base into meta (clipped at the node capacity).
+// level L+1's count and base into meta.
 __global__ void __launch_bounds__(1024) tree_scan_kernel(TreeView t, int L)
 {
-    __shared__ int part[1024];
+    __shared__ int tile[BSCAN_TILE + BSCAN_TILE / 32];
+    __shared__ int wsum[32];
     const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
-    const int seg = (cnt + 1023) / 1024;
-    const int b = threadIdx.x * seg, e = min(b + seg, cnt);
-    int s = 0;
-    for (int q = b; q < e; ++q) s += t.nchild[base + q];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int run = part[threadIdx.x] - s;
-    for (int q = b; q < e; ++q) {
-        t.offs[q] = run;
-        run += t.nchild[base + q];
-    }
-    if (threadIdx.x == 1023) {
-        const int total = part[1023];
+    const int total = block_scan_exclusive<int>(t.nchild + base, t.offs, cnt, tile, wsum);
+    if (threadIdx.x == 0) {
         const int nbase = base + cnt;
         int room = (int)(t.cap - nbase);
         room = room < 0 ? 0 : room;
@@ -146,32 +133,32 @@ __global__ void __launch_bounds__(TTPB) tree_emit_kernel(TreeView t, const unsig
     const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
     const int nbase = t.meta[META_BASE + L + 1];
     const bool stop = t.meta[META_COUNT + L + 1] == 0;
-    for (int q = blockIdx.x * TTPB + threadIdx.x; q < cnt; q += gridDim.x * TTPB) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int warps = gridDim.x * (TTPB / 32);
+    for (int q = blockIdx.x * (TTPB / 32) + (threadIdx.x >> 5); q < cnt; q += warps) {
         const int node = base + q;
         const int nch = t.nchild[node];
         if (nch == 0 || stop) {
-            t.nchild[node] = 0;
-            t.first[node] = -1;
+            if (lane == 0) {
+                t.nchild[node] = 0;
+                t.first[node] = -1;
+            }
             continue;
         }
-        const int s = t.start[node], e = t.end[node];
         const unsigned pre = t.prefix[node];
-        int b[9];
-        octant_bounds(keys, s, e, pre, L, b);
+        int b, nxt;
+        const unsigned ne = octants(keys, t.start[node], t.end[node], pre, L, lane, b, nxt);
         const int first = nbase + t.offs[q];
-        t.first[node] = first;
-        int k = 0;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            if (b[o + 1] > b[o]) {
-                const int c = first + k++;
-                t.start[c] = b[o];
-                t.end[c] = b[o + 1];
-                t.prefix[c] = pre * 8u + o;
-                t.level[c] = L + 1;
-                t.nchild[c] = 0;
-                t.first[c] = -1;
-            }
+        if (lane == 0) t.first[node] = first;
+        if (lane < 8 && ((ne >> lane) & 1u)) {
+            const int c = first + __popc(ne & lt);
+            t.start[c] = b;
+            t.end[c] = nxt;
+            t.prefix[c] = pre * 8u + lane;
+            t.level[c] = L + 1;
+            t.nchild[c] = 0;
+            t.first[c] = -1;
         }
     }
 }
@@ -453,15 +440,17 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
         }
         const float cr = crit2[Lv];
         bool accept = has && cube_box_dist2(blo, bhi, mn, mx) >= cr;
-        if (__ballot_sync(FULL, has && !accept)) {
-            bool ok = has && !accept;
-            for (int b = 0; b < nvalid; ++b) {
-                const float px = __shfl_sync(FULL, h.x, b), py = __shfl_sync(FULL, h.y, b),
-                            pz = __shfl_sync(FULL, h.z, b);
-                if (ok) ok = cube_dist2(blo, bhi, px, py, pz) >= cr;
-                if (!__ballot_sync(FULL, ok)) break;
-            }
-            accept = accept || ok;
+        // undecided nodes one at a time, every lane testing its own body
+        unsigned und = __ballot_sync(FULL, has && !accept);
+        while (und) {
+            const int j = __ffs(und) - 1;
+            und &= und - 1;
+            const float4 jlo = make_float4(__shfl_sync(FULL, blo.x, j), __shfl_sync(FULL, blo.y, j),
+                                           __shfl_sync(FULL, blo.z, j), 0.f);
+            const float4 jhi = make_float4(__shfl_sync(FULL, bhi.x, j), __shfl_sync(FULL, bhi.y, j),
+                                           __shfl_sync(FULL, bhi.z, j), 0.f);
+            const bool all = __all_sync(FULL, !valid || cube_dist2(jlo, jhi, h.x, h.y, h.z) >= cr);
+            if (lane == j) accept = all;
         }
         const int nch = has ? __float_as_int(blo.w) : 0;
         const bool open = has && !accept && nch > 0;
