@@ -77,6 +77,11 @@ def parse():
                              "tree"])
     ap.add_argument("--theta", type=float, default=None, help="tree workload: opening angle")
     ap.add_argument("--leaf-cap", type=int, default=None, help="tree workload: leaf capacity")
+    ap.add_argument("--group", type=int, default=None, choices=[32, 64],
+                    help="tree workload: bodies walking the tree together")
+    ap.add_argument("--tree-sched", default="dynamic", choices=["static", "dynamic", "guided"],
+                    help="tree workload: walk schedule of the timed steps")
+    ap.add_argument("--tree-chunk", type=int, default=1, help="tree workload: schedule chunk")
     ap.add_argument("--fp64-n", type=int, default=262_144,
                     help="bodies for the float64-form rate (first bodies of the workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -231,18 +236,19 @@ def reference_arm(args, ws, rank):
         w = TREE
         theta = w["theta"] if args.theta is None else args.theta
         lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+        grp = w["group"] if args.group is None else args.group
         b = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
         for _ in range(args.warmup):
-            oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, 32)
+            oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, grp)
         tot, inter = 0.0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            _, st = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, 32)
+            _, st = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, lc, grp)
             tot += time.perf_counter() - t0
             inter += st["cell_interactions"] + st["body_interactions"]
         value = inter / tot / 1e9
         sample = (f"one tree build + walk of two-plummer N={b.n} (same recipe), theta {theta}, "
-                  f"leaves <= {lc}, groups of 32, per step")
+                  f"leaves <= {lc}, groups of {grp}, per step")
         line = {
             "impl": "reference", "metric": TREE_METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -394,10 +400,10 @@ def measure_forms(torch, dev, tune, table, peak_tflops):
 PRECISION = {"name": "Plummer N=65536, eps 0.005, fp32 Kahan-compensated, 1 force eval + 100 KDK "
                      "steps of dt 5e-4", "n": 65536, "seed": 1, "eps": 0.005, "dt": 5e-4,
              "steps": 100}
-TREE = {"name": "two-plummer N=1048576, Barnes-Hut theta 0.5, leaves <= 16 bodies, groups of 32, "
+TREE = {"name": "two-plummer N=1048576, Barnes-Hut theta 0.5, leaves <= 16 bodies, groups of 64, "
                 "1 force eval + 10 KDK steps (tree rebuilt per eval), fp32 walk, f64 state",
         "seed": 2, "eps": 0.002, "dt": 1e-3, "steps": 10, "theta": 0.5, "leaf_cap": 16,
-        "cpu_n_per": 65_536}
+        "group": 64, "cpu_n_per": 65_536}
 TREE_METRIC = "tree interactions/s (cell + body, G/s)"
 PLAIN = {"name": "Plummer N=1024, eps 0.01, fp64, 1 force eval + 10 KDK steps of dt 1e-3 "
                  "(one graph launch)", "n": 1024, "seed": 0, "eps": 0.01, "dt": 1e-3, "steps": 10}
@@ -412,17 +418,18 @@ def _line(args, ws, value, ms_step, cfg, extra, dtype="f32", scaling="weak"):
     print(json.dumps(line), flush=True)
 
 
-def tree_oracle_rate(w, theta, leaf_cap):
+def tree_oracle_rate(w, theta, leaf_cap, group):
     """The oracle's (single-threaded) tree code on the same recipe at 2 x cpu_n_per bodies."""
     import oracle
     from paper_1211_2292_gb300 import inputs
     b = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
     t0 = time.perf_counter()
-    _, st, cnt = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, leaf_cap, 32, counts=True)
+    _, st, cnt = oracle.bh_forces(b.pos, b.mass, 1.0, w["eps"], theta, leaf_cap, group,
+                                   counts=True)
     el = time.perf_counter() - t0
     inter = st["cell_interactions"] + st["body_interactions"]
     sample = (f"two-plummer N={b.n} (same recipe), theta {theta}, leaves <= {leaf_cap}, groups "
-              f"of 32: one tree build + walk, {el:.1f} s")
+              f"of {group}: one tree build + walk, {el:.1f} s")
     return inter / el / 1e9, sample, b, cnt
 
 
@@ -434,33 +441,36 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
     w = TREE
     theta = w["theta"] if args.theta is None else args.theta
     lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+    grp = w["group"] if args.group is None else args.group
     b = inputs.two_plummer(args.n_per, seed=w["seed"])
     x0, v0, m = T(b.pos), T(b.vel), T(b.mass)
     G, eps, dt, K = 1.0, w["eps"], w["dt"], w["steps"]
     with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+        nb.tree_schedule(args.tree_sched, args.tree_chunk)
         x, v = x0.clone(), v0.clone()
         a = torch.empty_like(x)
 
         def step():
             x.copy_(x0)
             v.copy_(v0)
-            nb.tree_step(x, v, m, G, eps, theta, lc, dt, K, a)
+            nb.tree_step(x, v, m, G, eps, theta, lc, dt, K, a, group=grp)
 
         # interactions of one step, eval by eval (the walk is deterministic)
         inter = []
         step_evals = []
         x.copy_(x0)
         v.copy_(v0)
-        nb.tree_forces(x, m, G, eps, theta, lc, out=a)
+        nb.tree_forces(x, m, G, eps, theta, lc, out=a, group=grp)
         st = nb.tree_stats()
         inter.append(st["cell_interactions"] + st["body_interactions"])
         step_evals.append(st)
         for _ in range(K):
-            nb.tree_step(x, v, m, G, eps, theta, lc, dt, 1, a, acc_valid=True)
+            nb.tree_step(x, v, m, G, eps, theta, lc, dt, 1, a, acc_valid=True, group=grp)
             st = nb.tree_stats()
             inter.append(st["cell_interactions"] + st["body_interactions"])
         per_step = float(sum(inter))
-        for _ in range(args.warmup):
+        warm = max(args.warmup, 10)  # about a second of GPU work before timing
+        for _ in range(warm):
             step()
         nb.profile(True)
         l0 = nb.launches
@@ -479,10 +489,24 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
         wn, wms = nb.profile_read(4)
         bn, bms = nb.profile_read(5)
         nb.profile(False)
+        # walk time per schedule (the paper's Table VI study of loop schedules,
+        # here on the tree walk): eager evaluations of the initial state
+        study = []
+        for sched, chunk in (("static", 1), ("dynamic", 1), ("dynamic", 4), ("dynamic", 16),
+                             ("dynamic", 64), ("guided", 1), ("guided", 4)):
+            nb.tree_schedule(sched, chunk)
+            nb.tree_forces(x0, m, G, eps, theta, lc, out=a, group=grp)
+            nb.profile(True)
+            for _ in range(3):
+                nb.tree_forces(x0, m, G, eps, theta, lc, out=a, group=grp)
+            sn, sms = nb.profile_read(4)
+            nb.profile(False)
+            study.append({"sched": sched, "chunk": chunk, "walk_ms": sms / max(sn, 1)})
+        nb.tree_schedule(args.tree_sched, args.tree_chunk)
         # accuracy of the first evaluation: tree vs the exact sum on sampled bodies
         rows = inputs.sample_rows(b.n, 4096, seed=1)
         ref = oracle.accel_rows(b.pos, b.mass, rows, G, eps)
-        at = nb.tree_forces(x0, m, G, eps, theta, lc).cpu().numpy()[rows]
+        at = nb.tree_forces(x0, m, G, eps, theta, lc, group=grp).cpu().numpy()[rows]
         e = np.linalg.norm(at - ref, axis=1) / np.linalg.norm(ref, axis=1)
     value = per_step * args.steps / (t.ms / 1e3) / 1e9
     evals = K + 1
@@ -494,21 +518,23 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
     cpu = None
     parity = None
     if not args.no_cpu_baseline:
-        rate, sample, bs, rcnt = tree_oracle_rate(w, theta, lc)
+        rate, sample, bs, rcnt = tree_oracle_rate(w, theta, lc, grp)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
         with nbody.NBody(bs.n, "fp32_comp", device=dev.index) as nb:
-            _, gcnt = nb.tree_forces(T(bs.pos), T(bs.mass), G, eps, theta, lc, counts=True)
+            _, gcnt = nb.tree_forces(T(bs.pos), T(bs.mass), G, eps, theta, lc, counts=True,
+                                     group=grp)
             nb.sync()
         parity = {"counts_equal_oracle": bool(np.array_equal(gcnt.cpu().numpy(), rcnt)),
                   "n": bs.n}
     n = float(b.n)
     line = {"metric": TREE_METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t.ms / args.steps,
+            "steps": args.steps, "warmup": warm, "ms_per_step": t.ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Plummer spheres)",
             "config": {"workload": w["name"] if args.n_per == WORKLOAD["n_per"] else
                        f"two-plummer N={b.n} tree", "n": b.n, "theta": theta, "leaf_cap": lc,
-                       "group": 32, "force_evals_per_step": evals,
+                       "group": grp, "schedule": f"{args.tree_sched}, chunk {args.tree_chunk}",
+                       "force_evals_per_step": evals,
                        "l2": "256 MiB buffer written between steps"},
             "interactions_per_step": per_step,
             "first_eval": {"nodes": step_evals[0]["nodes"], "leaves": step_evals[0]["leaves"],
@@ -527,6 +553,7 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
                          "note": f"{FLOPS_PER_INTERACTION} flops per cell or body interaction; "
                                  "walk kernel event-timed inside the timed region; peak = SMs x "
                                  "128 FP32 lanes x 2 x max SM clock"},
+            "schedule_study": study,
             "parity": parity, "cpu_baseline": cpu, "clocks": ck, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     return 0
@@ -548,6 +575,7 @@ def other_workload(args, ws, rank, local):
     timer = lambda: Timer(torch, dev, stream, lambda: None)  # noqa: E731
     T = lambda a: torch.as_tensor(a, device=dev).contiguous()  # noqa: E731
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush.fill_(1.0)  # first use outside the timed region (kernel load / JIT)
     cpu = None
 
     if args.workload == "precision":
@@ -787,6 +815,7 @@ def main():
             nb.step(pos, vel, mass, G, eps, dt, nk, acc)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush.fill_(1.0)  # first use outside the timed region (kernel load / JIT)
     for _ in range(args.warmup):
         step()
         flush.fill_(1.0)

@@ -247,19 +247,20 @@ nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm)
  *     the top 3L bits of its 30-bit Morton key, q = floor((x - lo) 1024/ext)
  *     clamped to [0, 1023] per axis;
  *   - a cell is a leaf when it holds at most leaf_cap bodies or is at level 10;
- *   - bodies are taken 32 at a time in key order, and the 32 walk the tree
- *     together: a cell acts as its monopole only when, for every one of the
- *     32, the float32 distance from the body to the cell's cube is at least
- *     edge / theta (theta = 0 opens every cell: the direct sum through the
- *     tree);
+ *   - bodies are taken `group` (32 or 64) at a time in key order, and the
+ *     group walks the tree together: a cell acts as its monopole only when,
+ *     for every body of the group, the float32 distance from the body to the
+ *     cell's cube is at least edge / theta (theta = 0 opens every cell: the
+ *     direct sum through the tree);
  *   - cell masses and centres of mass are float64; pair terms are float32 in
- *     coordinates relative to the 32 bodies' centre, summed per cell and
- *     leaf, and folded into Kahan-compensated sums; acc is float64.
+ *     coordinates relative to the group's centre, summed per 32 sources and
+ *     folded into Kahan-compensated sums; acc is float64.
  * The tree is rebuilt on every call, fully on the device (no host
  * synchronisation, so nb_tree_step can run as one captured graph).
  *
  * nb_tree_forces: acc [n][3] (out).  theta >= 0 and finite; 1 <= leaf_cap <=
- * NB_TREE_MAX_LEAF; counts (optional, int32 [n][2], 8-byte aligned) receives
+ * NB_TREE_MAX_LEAF; group 32 or 64 (64 shares each walk among more bodies:
+ * faster, a little more conservative); counts (optional, int32 [n][2], 8-byte aligned) receives
  * per body the number of cells and of bodies (itself included) it met.
  * Any precision mode (the walk is float32 in each).  The first call (and a
  * call whose leaf_cap needs more nodes than any before) allocates the tree
@@ -279,12 +280,23 @@ nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm)
  */
 #define NB_TREE_MAX_LEAF 65536
 nb_status nb_tree_forces(nb_ctx *ctx, int64_t n, const double *pos, const double *mass,
-                         double G, double eps, double theta, int leaf_cap, double *acc,
-                         int32_t *counts);
+                         double G, double eps, double theta, int leaf_cap, int group,
+                         double *acc, int32_t *counts);
 nb_status nb_tree_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
-                       double G, double eps, double theta, int leaf_cap, double dt,
+                       double G, double eps, double theta, int leaf_cap, int group, double dt,
                        int64_t nsteps, double *acc, unsigned flags);
 nb_status nb_tree_stats(nb_ctx *ctx, int64_t *out);
+
+/*
+ * How the tree walk deals its groups of bodies to warps, after the paper's
+ * OpenMP loop schedules (Sec. II; Sec. V-C compares them on the tree code):
+ * sched 0 static (one warp per group, a grid covering every group), 1
+ * dynamic (the default: resident warps take `chunk` consecutive groups at a
+ * time from an atomic counter), 2 guided (chunks of max(chunk, remaining /
+ * (2 x warps))).  1 <= chunk <= 2^20 (default 1).  Results do not depend on
+ * the schedule, only the time does.  Drops the context's captured graphs.
+ */
+nb_status nb_tree_schedule(nb_ctx *ctx, int sched, int chunk);
 
 /*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form

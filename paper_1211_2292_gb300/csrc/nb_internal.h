@@ -158,6 +158,9 @@ struct TreeWalkParams {
     const int *perm;        // tree rank -> body index
     const double *box;      // {lo_x, lo_y, lo_z, ext}
     int n;
+    int group;              // bodies per walking warp: 32 or 64
+    int sched, chunk;       // group schedule: 0 static, 1 dynamic, 2 guided; chunk size
+    int num_sms;
     float theta, eps2f;
     double G;
     double *acc, *vel;      // vel != NULL: vel += half_dt * acc
@@ -248,7 +251,7 @@ struct nb_ctx {
         unsigned flags;
         uint64_t plan_gen;
         double theta = 0.0;  // tree code only
-        int leaf_cap = 0;
+        int leaf_cap = 0;    // tree code only: leaf_cap * 128 + group
         bool operator<(const GraphKey &o) const;
     };
     struct GraphVal { cudaGraphExec_t exec; int64_t kernels; };
@@ -256,6 +259,7 @@ struct nb_ctx {
 
     // tree code scratch (allocated on first use; bodies sized for n_max)
     nb::TreeView tree{};
+    int tree_sched = 1, tree_chunk = 1;  // walk schedule (nb_tree_schedule)
     float4 *tree_P = nullptr, *tree_Plo = nullptr;
     int *tree_perm = nullptr;
     double *tree_box = nullptr;

@@ -586,8 +586,9 @@ nb_status ensure_tree(nb_ctx *c, int leaf_cap)
     return NB_OK;
 }
 
-nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap)
+nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap, int group)
 {
+    if (group != 32 && group != 64) return failf(c, NB_EINVAL, "group = %d is not 32 or 64", group);
     if (!std::isfinite(theta) || theta < 0)
         return failf(c, NB_EINVAL, "theta must be finite and >= 0");
     if (leaf_cap < 1 || leaf_cap > NB_TREE_MAX_LEAF)
@@ -627,7 +628,8 @@ struct TreeTimer {
 // Sort, pack, build and walk: acc = G * (tree sum); vel += half_dt * acc when vel.
 nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos,
                               const double *mass, double G, double eps, double theta,
-                              int leaf_cap, double *acc, double *vel, double half_dt, int *counts)
+                              int leaf_cap, int group, double *acc, double *vel, double half_dt,
+                              int *counts)
 {
     if (n == 0) return NB_OK;
     int k = 0;
@@ -649,6 +651,10 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
     p.perm = c->tree_perm;
     p.box = c->tree_box;
     p.n = (int)n;
+    p.group = group;
+    p.sched = c->tree_sched;
+    p.chunk = c->tree_chunk;
+    p.num_sms = c->num_sms;
     p.theta = (float)theta;
     p.eps2f = (float)(eps * eps);
     p.G = G;
@@ -666,17 +672,17 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
 
 nb_status tree_step_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, double *vel,
                             const double *mass, double G, double eps, double theta, int leaf_cap,
-                            double dt, int64_t nsteps, double *acc, unsigned flags)
+                            int group, double dt, int64_t nsteps, double *acc, unsigned flags)
 {
     if (n == 0) return NB_OK;
     if (!(flags & NB_ACC_VALID))
-        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, acc, nullptr, 0.0,
-                                   nullptr));
+        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, group, acc,
+                                   nullptr, 0.0, nullptr));
     for (int64_t st = 0; st < nsteps; ++st) {
         NB_LAUNCHED(c, nb::launch_kdp(s, is_f64(c), (int)n, pos, vel, acc, mass, 0.5 * dt, dt,
                                       nullptr, nullptr, nullptr, nullptr));
-        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, acc, vel, 0.5 * dt,
-                                   nullptr));
+        NB_TRY(tree_forces_enqueue(c, s, n, pos, mass, G, eps, theta, leaf_cap, group, acc, vel,
+                                   0.5 * dt, nullptr));
     }
     return NB_OK;
 }
@@ -1239,13 +1245,14 @@ nb_status nb_profile_read(nb_ctx *c, int kind, int64_t *launches, double *total_
 }
 
 nb_status nb_tree_forces(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
-                         double eps, double theta, int leaf_cap, double *acc, int32_t *counts)
+                         double eps, double theta, int leaf_cap, int group, double *acc,
+                         int32_t *counts)
 {
     if (!c) return NB_EINVAL;
     DeviceGuard guard(c->device);
     NB_TRY(check_n(c, n));
     NB_TRY(check_scalars(c, G, eps));
-    NB_TRY(check_tree_args(c, theta, leaf_cap));
+    NB_TRY(check_tree_args(c, theta, leaf_cap, group));
     const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
     NB_TRY(check_dev(c, pos, v3, "pos"));
     NB_TRY(check_dev(c, mass, v1, "mass"));
@@ -1253,19 +1260,19 @@ nb_status nb_tree_forces(nb_ctx *c, int64_t n, const double *pos, const double *
     if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 2 * sizeof(int32_t), "counts"));
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
-    return tree_forces_enqueue(c, c->stream, n, pos, mass, G, eps, theta, leaf_cap, acc, nullptr,
-                               0.0, counts);
+    return tree_forces_enqueue(c, c->stream, n, pos, mass, G, eps, theta, leaf_cap, group, acc,
+                               nullptr, 0.0, counts);
 }
 
 nb_status nb_tree_step(nb_ctx *c, int64_t n, double *pos, double *vel, const double *mass,
-                       double G, double eps, double theta, int leaf_cap, double dt,
+                       double G, double eps, double theta, int leaf_cap, int group, double dt,
                        int64_t nsteps, double *acc, unsigned flags)
 {
     if (!c) return NB_EINVAL;
     DeviceGuard guard(c->device);
     NB_TRY(check_n(c, n));
     NB_TRY(check_scalars(c, G, eps));
-    NB_TRY(check_tree_args(c, theta, leaf_cap));
+    NB_TRY(check_tree_args(c, theta, leaf_cap, group));
     if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
     if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
     if (flags & ~(NB_ACC_VALID | NB_USE_GRAPH)) return failf(c, NB_EINVAL, "unknown flags");
@@ -1280,14 +1287,25 @@ nb_status nb_tree_step(nb_ctx *c, int64_t n, double *pos, double *vel, const dou
         nb_ctx::GraphKey key{2,   pos, vel, mass,   acc, nullptr, nullptr, G,
                              eps, dt,  n,   nsteps, 0,   flags,   0};
         key.theta = theta;
-        key.leaf_cap = leaf_cap;
+        key.leaf_cap = leaf_cap * 128 + group;
         return run_graph(c, key, [&](cudaStream_t s) {
-            return tree_step_enqueue(c, s, n, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps,
-                                     acc, flags);
+            return tree_step_enqueue(c, s, n, pos, vel, mass, G, eps, theta, leaf_cap, group, dt,
+                                     nsteps, acc, flags);
         });
     }
-    return tree_step_enqueue(c, c->stream, n, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps,
-                             acc, flags);
+    return tree_step_enqueue(c, c->stream, n, pos, vel, mass, G, eps, theta, leaf_cap, group, dt,
+                             nsteps, acc, flags);
+}
+
+nb_status nb_tree_schedule(nb_ctx *c, int sched, int chunk)
+{
+    if (!c) return NB_EINVAL;
+    if (sched < 0 || sched > 2) return failf(c, NB_EINVAL, "schedule %d is not 0, 1 or 2", sched);
+    if (chunk < 1 || chunk > (1 << 20)) return failf(c, NB_EINVAL, "chunk %d out of range", chunk);
+    c->tree_sched = sched;
+    c->tree_chunk = chunk;
+    drop_graphs(c);  // captured walks hold the old schedule
+    return NB_OK;
 }
 
 nb_status nb_tree_stats(nb_ctx *c, int64_t *out)

@@ -40,7 +40,7 @@ namespace {
 constexpr int TTPB = 256;
 constexpr int WALK_WARPS = 4;
 
-enum { META_COUNT = 0, META_BASE = 12, META_OVERFLOW = 24, META_INTS = 32 };
+enum { META_COUNT = 0, META_BASE = 12, META_OVERFLOW = 24, META_QUEUE = 25, META_INTS = 32 };
 
 inline int grid_cap(int64_t work)
 {
@@ -285,79 +285,118 @@ __device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const floa
 }
 
 // Interaction list of a warp: up to LIST_CAP sources (cells or bodies) as
-// (x, y, z, m), coordinates relative to the warp's centre, stored in pairs
-// so that one pair is two float4 loads, already in float32x2 order:
-// {x0, x1, y0, y1}, {z0, z1, m0, m1}.
+// (x, y, z, m), coordinates relative to the group's centre, laid out for
+// float32x2 arithmetic.  With one body per lane (BPL = 1) two sources share
+// an instruction: a pair of sources is {x0, x1, y0, y1}, {z0, z1, m0, m1}.
+// With two bodies per lane (BPL = 2) one source meets both bodies: a source
+// is stored twice over, {x, x, y, y}, {z, z, m, m}.
 constexpr int LIST_CAP = 64;
 constexpr int LEVELS = 11;
 
+template <int BPL>
 __device__ __forceinline__ void list_put(float *L, int q, float x, float y, float z, float m)
 {
-    float *b = L + 8 * (q >> 1) + (q & 1);
-    b[0] = x;
-    b[2] = y;
-    b[4] = z;
-    b[6] = m;
-}
-
-// Accumulate the first 2 * npairs sources of the list onto this lane's body
-// (float32x2 over source pairs: one instruction covers two sources).
-template <bool ZEPS>
-__device__ __forceinline__ void list_eval(const float4 *L4, int npairs, float2 nx, float2 ny,
-                                          float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az)
-{
-#pragma unroll 4
-    for (int q = 0; q < npairs; ++q) {
-        const float4 A = L4[2 * q], B = L4[2 * q + 1];
-        const float2 dx = add2(make_float2(A.x, A.y), nx);
-        const float2 dy = add2(make_float2(A.z, A.w), ny);
-        const float2 dz = add2(make_float2(B.x, B.y), nz);
-        float2 r2 = fma2(dx, dx, e2);
-        r2 = fma2(dy, dy, r2);
-        r2 = fma2(dz, dz, r2);
-        float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        if (ZEPS) {
-            ri.x = r2.x > 0.f ? ri.x : 0.f;
-            ri.y = r2.y > 0.f ? ri.y : 0.f;
-        }
-        const float2 s = mul2(mul2(make_float2(B.z, B.w), ri), mul2(ri, ri));
-        ax = fma2(dx, s, ax);
-        ay = fma2(dy, s, ay);
-        az = fma2(dz, s, az);
+    if (BPL == 1) {
+        float *b = L + 8 * (q >> 1) + (q & 1);
+        b[0] = x;
+        b[2] = y;
+        b[4] = z;
+        b[6] = m;
+    } else {
+        float4 *b = reinterpret_cast<float4 *>(L) + 2 * q;
+        b[0] = make_float4(x, x, y, y);
+        b[1] = make_float4(z, z, m, m);
     }
 }
 
-// One warp per 32 consecutive bodies in key order.  The warp walks the tree
-// level by level, deepest level first, 32 nodes per round (one per lane):
-// the opening test against the 32 bodies decides, per node, between the
-// interaction list (accepted cell: its monopole; leaf: its bodies) and
-// descending (its children, a contiguous range, go on the next level's
-// stack).  Each level's stack holds at most 32 ranges, the children of one
-// round's nodes, since a level is refilled only once every deeper level is
-// empty.  Whenever 32 sources are listed, every lane adds them to its body.
 template <bool ZEPS>
-__global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWalkParams p)
+__device__ __forceinline__ void pair_terms(float2 dx, float2 dy, float2 dz, float2 m, float2 e2,
+                                           float2 &ax, float2 &ay, float2 &az)
 {
-    __shared__ float4 list_s[WALK_WARPS][LIST_CAP];
-    __shared__ int2 ranges_s[WALK_WARPS][LEVELS][32];
-    __shared__ int slot_s[WALK_WARPS][32];
-    __shared__ float crit2[LEVELS];
-    const TreeView t = p.tree;
-    if (threadIdx.x < LEVELS) crit2[threadIdx.x] = open_dist2(p.box[3], threadIdx.x, p.theta);
-    __syncthreads();
+    float2 r2 = fma2(dx, dx, e2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+    if (ZEPS) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 s = mul2(mul2(m, ri), mul2(ri, ri));
+    ax = fma2(dx, s, ax);
+    ay = fma2(dy, s, ay);
+    az = fma2(dz, s, az);
+}
 
+// Add the first `cnt` listed sources (cnt even for BPL = 1) onto this lane's
+// bodies.  BPL = 1: nx = (-x_i, -x_i); BPL = 2: nx = (-x_i0, -x_i1).
+template <bool ZEPS, int BPL>
+__device__ __forceinline__ void list_eval(const float4 *L4, int cnt, float2 nx, float2 ny,
+                                          float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az)
+{
+    const int steps = BPL == 1 ? cnt >> 1 : cnt;
+#pragma unroll 4
+    for (int q = 0; q < steps; ++q) {
+        const float4 A = L4[2 * q], B = L4[2 * q + 1];
+        pair_terms<ZEPS>(add2(make_float2(A.x, A.y), nx), add2(make_float2(A.z, A.w), ny),
+                         add2(make_float2(B.x, B.y), nz), make_float2(B.z, B.w), e2, ax, ay, az);
+    }
+}
+
+// One warp per group of 32 * BPL consecutive bodies in key order (BPL per
+// lane: bodies base + lane and base + 32 + lane).  The warp walks the tree
+// level by level, deepest level first, 32 nodes per round (one per lane).
+// The opening test against every body of the group decides, per node,
+// between the interaction list (accepted cell: its monopole; leaf: its
+// bodies) and descending (its children, a contiguous range, go on the next
+// level's stack).  The test runs in three exact stages: the group's box
+// (passing it implies every body passes), then the group's first and last
+// bodies (failing either rejects), then, for the nodes still undecided, every
+// body.  Each level's stack holds at most 32 ranges, the children of one
+// round's nodes, since a level is refilled only once every deeper level is
+// empty.  Whenever 32 sources are listed, every lane adds them to its bodies.
+template <int BPL>
+struct WalkShared {
+    float4 list[WALK_WARPS][LIST_CAP * BPL];  // float4 slots of the lists
+    int2 ranges[WALK_WARPS][LEVELS][32];
+    int slot[WALK_WARPS][32];
+    float crit2[LEVELS];
+};
+
+// The walk of group g (bodies [g * 32 * BPL, ...) in key order) by one warp.
+template <bool ZEPS, int BPL>
+__device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<BPL> &sh, int g)
+{
+    constexpr int GROUP = 32 * BPL;
+    constexpr int LIST_F4 = LIST_CAP * BPL;
+    const TreeView &t = p.tree;
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n;
-    const int base = (blockIdx.x * WALK_WARPS + warp) * 32;
+    const int base = g * GROUP;
     if (base >= n) return;  // whole warp past the end
-    const int k = base + lane;
-    const int nvalid = min(32, n - base);
-    const bool valid = k < n;
-    const float4 h = valid ? __ldg(p.P + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 l = valid ? __ldg(p.Plo + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float mn[3] = {valid ? h.x : INFINITY, valid ? h.y : INFINITY, valid ? h.z : INFINITY};
-    float mx[3] = {valid ? h.x : -INFINITY, valid ? h.y : -INFINITY, valid ? h.z : -INFINITY};
+    const int nvalid = min(GROUP, n - base);
+    const float *crit2 = sh.crit2;
+    float4(*list_s)[LIST_F4] = sh.list;
+
+    bool valid[BPL];
+    float4 h[BPL];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float4 lo_[BPL];
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) {
+        const int k = base + 32 * b + lane;
+        valid[b] = k < n;
+        h[b] = valid[b] ? __ldg(p.P + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        lo_[b] = valid[b] ? __ldg(p.Plo + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid[b]) {
+            mn[0] = fminf(mn[0], h[b].x);
+            mn[1] = fminf(mn[1], h[b].y);
+            mn[2] = fminf(mn[2], h[b].z);
+            mx[0] = fmaxf(mx[0], h[b].x);
+            mx[1] = fmaxf(mx[1], h[b].y);
+            mx[2] = fmaxf(mx[2], h[b].z);
+        }
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -368,35 +407,69 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
     }
     const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]),
                 cz = 0.5f * (mn[2] + mx[2]);
-    const float xi = rel(h.x, l.x, cx), yi = rel(h.y, l.y, cy), zi = rel(h.z, l.z, cz);
-    const float2 nx = make_float2(-xi, -xi), ny = make_float2(-yi, -yi), nz = make_float2(-zi, -zi);
+    float xi[BPL], yi[BPL], zi[BPL];
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) {
+        xi[b] = rel(h[b].x, lo_[b].x, cx);
+        yi[b] = rel(h[b].y, lo_[b].y, cy);
+        zi[b] = rel(h[b].z, lo_[b].z, cz);
+    }
+    const float2 nx = BPL == 1 ? make_float2(-xi[0], -xi[0]) : make_float2(-xi[0], -xi[BPL - 1]);
+    const float2 ny = BPL == 1 ? make_float2(-yi[0], -yi[0]) : make_float2(-yi[0], -yi[BPL - 1]);
+    const float2 nz = BPL == 1 ? make_float2(-zi[0], -zi[0]) : make_float2(-zi[0], -zi[BPL - 1]);
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
+    // the group's first and last bodies, for the quick rejection
+    const int lastb = (nvalid - 1) >> 5, lastl = (nvalid - 1) & 31;
+    float r0[3], r1[3];
+    {
+        const float4 hl = lastb == 0 ? h[0] : h[BPL - 1];
+        r0[0] = __shfl_sync(FULL, h[0].x, 0);
+        r0[1] = __shfl_sync(FULL, h[0].y, 0);
+        r0[2] = __shfl_sync(FULL, h[0].z, 0);
+        r1[0] = __shfl_sync(FULL, hl.x, lastl);
+        r1[1] = __shfl_sync(FULL, hl.y, lastl);
+        r1[2] = __shfl_sync(FULL, hl.z, lastl);
+    }
 
     float *L = reinterpret_cast<float *>(list_s[warp]);
     const float4 *L4 = list_s[warp];
-    int2(*rs)[32] = ranges_s[warp];
-    int *slot = slot_s[warp];
+    int2(*rs)[32] = sh.ranges[warp];
+    int *slot = sh.slot[warp];
     const unsigned lt = (1u << lane) - 1u;
 
     float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-    float sx = 0.f, sy = 0.f, sz = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
+    // Kahan (sum, carry) per body and axis: BPL = 1 folds both halves of the
+    // float32x2 accumulators into one body; BPL = 2 keeps .x and .y apart.
+    float sx[BPL], sy[BPL], sz[BPL], qx[BPL], qy[BPL], qz[BPL];
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) sx[b] = sy[b] = sz[b] = qx[b] = qy[b] = qz[b] = 0.f;
     auto fold = [&]() {
-        kahan_add(sx, qx, ax.x);
-        kahan_add(sx, qx, ax.y);
-        kahan_add(sy, qy, ay.x);
-        kahan_add(sy, qy, ay.y);
-        kahan_add(sz, qz, az.x);
-        kahan_add(sz, qz, az.y);
+        if (BPL == 1) {
+            kahan_add(sx[0], qx[0], ax.x);
+            kahan_add(sx[0], qx[0], ax.y);
+            kahan_add(sy[0], qy[0], ay.x);
+            kahan_add(sy[0], qy[0], ay.y);
+            kahan_add(sz[0], qz[0], az.x);
+            kahan_add(sz[0], qz[0], az.y);
+        } else {
+            kahan_add(sx[0], qx[0], ax.x);
+            kahan_add(sy[0], qy[0], ay.x);
+            kahan_add(sz[0], qz[0], az.x);
+            kahan_add(sx[BPL - 1], qx[BPL - 1], ax.y);
+            kahan_add(sy[BPL - 1], qy[BPL - 1], ay.y);
+            kahan_add(sz[BPL - 1], qz[BPL - 1], az.y);
+        }
         ax = ay = az = make_float2(0.f, 0.f);
     };
     int cnt = 0;  // listed sources (warp-uniform)
     // 32 sources listed: add them, move the rest (< 32) to the front
     auto flush32 = [&]() {
         __syncwarp();
-        list_eval<ZEPS>(L4, 16, nx, ny, nz, e2, ax, ay, az);
+        list_eval<ZEPS, BPL>(L4, 32, nx, ny, nz, e2, ax, ay, az);
         fold();
         __syncwarp();
-        list_s[warp][lane] = list_s[warp][LIST_CAP / 2 + lane];
+#pragma unroll
+        for (int c = lane; c < LIST_F4 / 2; c += 32) list_s[warp][c] = list_s[warp][LIST_F4 / 2 + c];
         cnt -= 32;
         __syncwarp();
     };
@@ -431,7 +504,7 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
         if (lane == Lv) lsize -= __popc(done);
         __syncwarp();
 
-        // opening test: the warp's box first, then body by body
+        // opening test
         const bool has = node >= 0;
         float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
         if (has) {
@@ -440,8 +513,13 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
         }
         const float cr = crit2[Lv];
         bool accept = has && cube_box_dist2(blo, bhi, mn, mx) >= cr;
-        // undecided nodes one at a time, every lane testing its own body
         unsigned und = __ballot_sync(FULL, has && !accept);
+        if (und) {
+            const bool rej = cube_dist2(blo, bhi, r0[0], r0[1], r0[2]) < cr ||
+                             cube_dist2(blo, bhi, r1[0], r1[1], r1[2]) < cr;
+            und = __ballot_sync(FULL, has && !accept && !rej);
+        }
+        // undecided nodes one at a time, every lane testing its own bodies
         while (und) {
             const int j = __ffs(und) - 1;
             und &= und - 1;
@@ -449,7 +527,11 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
                                            __shfl_sync(FULL, blo.z, j), 0.f);
             const float4 jhi = make_float4(__shfl_sync(FULL, bhi.x, j), __shfl_sync(FULL, bhi.y, j),
                                            __shfl_sync(FULL, bhi.z, j), 0.f);
-            const bool all = __all_sync(FULL, !valid || cube_dist2(jlo, jhi, h.x, h.y, h.z) >= cr);
+            bool ok = true;
+#pragma unroll
+            for (int b = 0; b < BPL; ++b)
+                ok = ok && (!valid[b] || cube_dist2(jlo, jhi, h[b].x, h[b].y, h[b].z) >= cr);
+            const bool all = __all_sync(FULL, ok);
             if (lane == j) accept = all;
         }
         const int nch = has ? __float_as_int(blo.w) : 0;
@@ -471,8 +553,8 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
         if (am) {
             if (accept) {
                 const float4 ch = __ldg(t.chi + node), cl = __ldg(t.clo + node);
-                list_put(L, cnt + __popc(am & lt), rel(ch.x, cl.x, cx), rel(ch.y, cl.y, cy),
-                         rel(ch.z, cl.z, cz), ch.w);
+                list_put<BPL>(L, cnt + __popc(am & lt), rel(ch.x, cl.x, cx), rel(ch.y, cl.y, cy),
+                              rel(ch.z, cl.z, cz), ch.w);
             }
             cnt += __popc(am);
             nc += __popc(am);
@@ -494,25 +576,27 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
                 const int kk = min(32, e0 - j0);
                 if (lane < kk) {
                     const float4 bh = __ldg(p.P + j0 + lane), bl = __ldg(p.Plo + j0 + lane);
-                    list_put(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
-                             rel(bh.z, bl.z, cz), bh.w);
+                    list_put<BPL>(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
+                                  rel(bh.z, bl.z, cz), bh.w);
                 }
                 cnt += kk;
                 if (cnt >= 32) flush32();
             }
         }
     }
-    if (cnt > 0) {  // the rest, padded to a pair with a massless source
-        if (lane == 0 && (cnt & 1)) list_put(L, cnt, 0.f, 0.f, 0.f, 0.f);
+    if (cnt > 0) {  // the rest (BPL = 1: padded to a pair with a massless source)
+        if (BPL == 1 && lane == 0 && (cnt & 1)) list_put<BPL>(L, cnt, 0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        list_eval<ZEPS>(L4, (cnt + 1) >> 1, nx, ny, nz, e2, ax, ay, az);
+        list_eval<ZEPS, BPL>(L4, BPL == 1 ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay, az);
         fold();
     }
-    if (valid) {
-        const int i = p.perm[k];
-        const double gx = p.G * ((double)sx - (double)qx);
-        const double gy = p.G * ((double)sy - (double)qy);
-        const double gz = p.G * ((double)sz - (double)qz);
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) {
+        if (!valid[b]) continue;
+        const int i = p.perm[base + 32 * b + lane];
+        const double gx = p.G * ((double)sx[b] - (double)qx[b]);
+        const double gy = p.G * ((double)sy[b] - (double)qy[b]);
+        const double gz = p.G * ((double)sz[b] - (double)qz[b]);
         double *a = p.acc + 3 * (size_t)i;
         a[0] = gx;
         a[1] = gy;
@@ -532,6 +616,42 @@ __global__ void __launch_bounds__(32 * WALK_WARPS) tree_walk_kernel(const TreeWa
     if (lane == 0) {  // nc, nb are the same for the group's nvalid bodies
         atomicAdd(t.stats + 2, (unsigned long long)nc * nvalid);
         atomicAdd(t.stats + 3, (unsigned long long)nb * nvalid);
+    }
+    __syncwarp();  // the next group reuses this warp's lists and stacks
+}
+
+// Scheduling of the groups over the warps (the paper's OpenMP loop
+// schedules, Sec. II, applied to the walk): static, one group per warp of a
+// grid covering all groups; dynamic, a grid of resident warps taking `chunk`
+// groups at a time from an atomic counter; guided, the same with chunks of
+// max(chunk, remaining / (2 x warps)).
+template <bool ZEPS, int BPL>
+__global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? 8 : 7)
+    tree_walk_kernel(const TreeWalkParams p)
+{
+    __shared__ WalkShared<BPL> sh;
+    if (threadIdx.x < LEVELS) sh.crit2[threadIdx.x] = open_dist2(p.box[3], threadIdx.x, p.theta);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * WALK_WARPS + warp;
+    if (p.sched == 0) {
+        walk_group<ZEPS, BPL>(p, sh, gw);
+        return;
+    }
+    const int ngroups = (p.n + 32 * BPL - 1) / (32 * BPL);
+    const int nwarps = gridDim.x * WALK_WARPS;
+    int *queue = p.tree.meta + META_QUEUE;
+    int seen = 0;
+    for (;;) {
+        int c = p.chunk;
+        if (p.sched == 2) c = max(c, (ngroups - seen) / (2 * nwarps));
+        int g0 = 0;
+        if (lane == 0) g0 = atomicAdd(queue, c);
+        g0 = __shfl_sync(0xffffffffu, g0, 0);
+        if (g0 >= ngroups) break;
+        seen = g0 + c;
+        const int g1 = min(g0 + c, ngroups);
+        for (int g = g0; g < g1; ++g) walk_group<ZEPS, BPL>(p, sh, g);
     }
 }
 
@@ -589,12 +709,19 @@ cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps,
 {
     kernels = 0;
     if (p.n <= 0) return cudaSuccess;
-    const int groups = (p.n + 31) / 32;
-    const int blocks = (groups + WALK_WARPS - 1) / WALK_WARPS;
-    if (zeps)
-        tree_walk_kernel<true><<<blocks, 32 * WALK_WARPS, 0, s>>>(p);
-    else
-        tree_walk_kernel<false><<<blocks, 32 * WALK_WARPS, 0, s>>>(p);
+    const int G = p.group;
+    const int groups = (p.n + G - 1) / G;
+    void (*fn)(const TreeWalkParams) =
+        G == 32 ? (zeps ? tree_walk_kernel<true, 1> : tree_walk_kernel<false, 1>)
+                : (zeps ? tree_walk_kernel<true, 2> : tree_walk_kernel<false, 2>);
+    int blocks = (groups + WALK_WARPS - 1) / WALK_WARPS;
+    if (p.sched != 0) {  // resident blocks only
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * WALK_WARPS, 0);
+        if (e != cudaSuccess) return e;
+        blocks = min(blocks, max(per_sm, 1) * p.num_sms);
+    }
+    fn<<<blocks, 32 * WALK_WARPS, 0, s>>>(p);
     kernels = 1;
     return cudaGetLastError();
 }

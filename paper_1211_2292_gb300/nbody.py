@@ -63,11 +63,12 @@ SIGNATURES = {
     "nb_profile": (_c_int, [_c_vp, _c_int]),
     "nb_profile_read": (_c_int, [_c_vp, _c_int, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_dbl)]),
     "nb_device_info": (_c_int, [_c_vp, _c_i64, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
-    "nb_tree_forces": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_vp,
-                                _c_vp]),
+    "nb_tree_forces": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_int,
+                                _c_vp, _c_vp]),
     "nb_tree_step": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
-                              _c_dbl, _c_i64, _c_vp, _c_uint]),
+                              _c_int, _c_dbl, _c_i64, _c_vp, _c_uint]),
     "nb_tree_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
+    "nb_tree_schedule": (_c_int, [_c_vp, _c_int, _c_int]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
@@ -299,9 +300,11 @@ class NBody:
         self._call("nb_profile_read", int(kind), ctypes.byref(cnt), ctypes.byref(ms))
         return cnt.value, ms.value
 
-    def tree_forces(self, pos, mass, G, eps, theta, leaf_cap=16, out=None, counts=False):
-        """Barnes-Hut accelerations (paper Sec. IV-A); with counts=True also
-        the int32 [n, 2] cells and bodies each body met."""
+    def tree_forces(self, pos, mass, G, eps, theta, leaf_cap=16, out=None, counts=False,
+                    group=64):
+        """Barnes-Hut accelerations (paper Sec. IV-A), bodies walking the tree
+        `group` (32 or 64) at a time; with counts=True also the int32 [n, 2]
+        cells and bodies each body met."""
         import torch
         n = mass.shape[0]
         if out is None:
@@ -310,17 +313,22 @@ class NBody:
         if counts:
             cnt = torch.empty((n, 2), dtype=torch.int32, device=pos.device)
         self._call("nb_tree_forces", n, _ptr(pos, "pos", 3 * n), _ptr(mass, "mass", n), float(G),
-                   float(eps), float(theta), int(leaf_cap), _ptr(out, "acc", 3 * n),
+                   float(eps), float(theta), int(leaf_cap), int(group), _ptr(out, "acc", 3 * n),
                    _ptr_i32(cnt, "counts", 2 * n))
         return (out, cnt) if counts else out
 
     def tree_step(self, pos, vel, mass, G, eps, theta, leaf_cap, dt, nsteps, acc,
-                  acc_valid=False, graph=False):
+                  acc_valid=False, graph=False, group=64):
         n = mass.shape[0]
         flags = (NB_ACC_VALID if acc_valid else 0) | (NB_USE_GRAPH if graph else 0)
         self._call("nb_tree_step", n, _ptr(pos, "pos", 3 * n), _ptr(vel, "vel", 3 * n),
                    _ptr(mass, "mass", n), float(G), float(eps), float(theta), int(leaf_cap),
-                   float(dt), int(nsteps), _ptr(acc, "acc", 3 * n), flags)
+                   int(group), float(dt), int(nsteps), _ptr(acc, "acc", 3 * n), flags)
+
+    def tree_schedule(self, sched="dynamic", chunk=1):
+        """Walk schedule: "static", "dynamic" or "guided" (or 0, 1, 2), chunk >= 1."""
+        names = {"static": 0, "dynamic": 1, "guided": 2}
+        self._call("nb_tree_schedule", names.get(sched, sched), int(chunk))
 
     def tree_stats(self):
         """{nodes, leaves, cell_interactions, body_interactions} of the last tree call."""

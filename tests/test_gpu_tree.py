@@ -17,30 +17,33 @@ pytestmark = pytest.mark.gpu
 RMS_TOL, MAX_TOL = 1e-5, 1e-4  # float32 pair terms, as the direct-sum float32 forms
 
 
-def _gpu_tree(cuda, b, G, eps, theta, leaf_cap, prec="fp32_comp"):
+def _gpu_tree(cuda, b, G, eps, theta, leaf_cap, prec="fp32_comp", group=64):
     x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
     with nbody.NBody(b.n, prec) as nb:
-        a, cnt = nb.tree_forces(x, m, G, eps, theta, leaf_cap, counts=True)
+        a, cnt = nb.tree_forces(x, m, G, eps, theta, leaf_cap, counts=True, group=group)
         nb.sync()
         st = nb.tree_stats()
     return host(a), host(cnt).astype(np.int64), st
 
 
+@pytest.mark.parametrize("group", [32, 64])
 @pytest.mark.parametrize("n,theta,leaf_cap", [(1000, 0.5, 16), (4099, 0.7, 8), (20000, 0.5, 16),
                                               (20000, 0.3, 32), (777, 1.0, 1)])
-def test_matches_oracle_tree(cuda, n, theta, leaf_cap):
+def test_matches_oracle_tree(cuda, n, theta, leaf_cap, group):
     b = inputs.plummer(n, seed=61)
-    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, theta, leaf_cap)
-    ref, rst, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.01, theta, leaf_cap, 32, counts=True)
+    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, theta, leaf_cap, group=group)
+    ref, rst, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.01, theta, leaf_cap, group,
+                                      counts=True)
     assert np.array_equal(cnt, rcnt)
     assert st == rst
     e = relerr_per_body(a, ref)
     assert np.sqrt((e ** 2).mean()) <= RMS_TOL and e.max() <= MAX_TOL
 
 
-def test_theta_zero_is_the_direct_sum(cuda):
+@pytest.mark.parametrize("group", [32, 64])
+def test_theta_zero_is_the_direct_sum(cuda, group):
     b = inputs.plummer(3000, seed=62)
-    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, 0.0, 16)
+    a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.01, 0.0, 16, group=group)
     ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
     assert np.all(cnt[:, 0] == 0) and np.all(cnt[:, 1] == b.n)
     assert st["cell_interactions"] == 0 and st["body_interactions"] == b.n * b.n
@@ -51,7 +54,7 @@ def test_theta_zero_is_the_direct_sum(cuda):
 def test_two_clusters_and_every_precision_mode(cuda):
     # Two distant clusters: whole subtrees are accepted as monopoles.
     b = inputs.two_plummer(2500, seed=63)
-    ref, _, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.005, 0.6, 16, 32, counts=True)
+    ref, _, rcnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.005, 0.6, 16, 64, counts=True)
     for prec in ("fp64", "fp32", "fp32_comp"):
         a, cnt, _ = _gpu_tree(cuda, b, 1.0, 0.005, 0.6, 16, prec)
         assert np.array_equal(cnt, rcnt), prec
@@ -77,13 +80,14 @@ def test_degenerate_inputs(cuda):
     m = np.full(100, 0.01)
     b = inputs.Bodies(pos, np.zeros_like(pos), m)
     a, cnt, st = _gpu_tree(cuda, b, 1.0, 0.1, 0.5, 4)
-    _, rst, rcnt = oracle.bh_forces(pos, m, 1.0, 0.1, 0.5, 4, 32, counts=True)
+    _, rst, rcnt = oracle.bh_forces(pos, m, 1.0, 0.1, 0.5, 4, 64, counts=True)
     assert np.all(a == 0) and np.array_equal(cnt, rcnt) and st == rst and st["nodes"] == 11
-    # one body; a pair with zero softening (self pair skipped); ragged 33
-    for n, eps in ((1, 0.1), (2, 0.0), (33, 0.0)):
+    # one body; a pair with zero softening (self pair skipped); ragged sizes
+    for n, eps, group in ((1, 0.1, 64), (2, 0.0, 64), (33, 0.0, 32), (33, 0.0, 64),
+                          (65, 0.0, 64), (100, 0.01, 32)):
         bb = inputs.random_system(n, seed=65 + n)
-        a, cnt, _ = _gpu_tree(cuda, bb, 1.3, eps, 0.5, 1)
-        ref, _, rcnt = oracle.bh_forces(bb.pos, bb.mass, 1.3, eps, 0.5, 1, 32, counts=True)
+        a, cnt, _ = _gpu_tree(cuda, bb, 1.3, eps, 0.5, 1, group=group)
+        ref, _, rcnt = oracle.bh_forces(bb.pos, bb.mass, 1.3, eps, 0.5, 1, group, counts=True)
         assert np.array_equal(cnt, rcnt) and np.isfinite(a).all()
         if n == 1:
             assert np.all(a == 0)
@@ -110,11 +114,12 @@ def test_argument_checks(cuda):
     with nbody.NBody(64, "fp32_comp") as nb:
         lib, before = nb.lib, nb.launches
         args = (nb.h, 64, x.data_ptr(), m.data_ptr(), 1.0, 0.01)
-        assert lib.nb_tree_forces(*args, -0.1, 16, a.data_ptr(), None) == 1
-        assert lib.nb_tree_forces(*args, float("inf"), 16, a.data_ptr(), None) == 1
-        assert lib.nb_tree_forces(*args, 0.5, 0, a.data_ptr(), None) == 1
-        assert lib.nb_tree_forces(*args, 0.5, 65537, a.data_ptr(), None) == 1
-        assert lib.nb_tree_forces(nb.h, 65, x.data_ptr(), m.data_ptr(), 1.0, 0.01, 0.5, 16,
+        assert lib.nb_tree_forces(*args, -0.1, 16, 64, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, float("inf"), 16, 64, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, 0.5, 0, 64, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, 0.5, 65537, 64, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(*args, 0.5, 16, 48, a.data_ptr(), None) == 1
+        assert lib.nb_tree_forces(nb.h, 65, x.data_ptr(), m.data_ptr(), 1.0, 0.01, 0.5, 16, 64,
                                   a.data_ptr(), None) == 1
         assert nb.launches == before
 
@@ -134,14 +139,41 @@ def test_tree_step_matches_oracle_kdk_at_theta_zero(cuda):
 def test_tree_step_graph_equals_eager(cuda):
     b = inputs.plummer(6000, seed=69)
     outs = []
-    for graph in (False, True, True):
+    for graph, group in ((False, 64), (True, 64), (True, 64), (False, 32), (True, 32)):
         x, v, m = (to_dev(t, cuda) for t in (b.pos, b.vel, b.mass))
         acc = to_dev(np.zeros((b.n, 3)), cuda)
         with nbody.NBody(b.n, "fp32_comp") as nb:
-            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, graph=graph)
-            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, acc_valid=True, graph=graph)
+            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, graph=graph, group=group)
+            nb.tree_step(x, v, m, 1.0, 0.01, 0.6, 16, 1e-3, 3, acc, acc_valid=True, graph=graph,
+                         group=group)
             nb.sync()
         outs.append((host(x), host(v), host(acc)))
-    for o in outs[1:]:
-        for p, q in zip(outs[0], o):
+    for ref, o in ((0, 1), (0, 2), (3, 4)):
+        for p, q in zip(outs[ref], outs[o]):
             assert np.array_equal(p, q)
+    # The two group sizes accept different cells, so they differ by the
+    # approximation error itself (a few 1e-3 of |a| at theta 0.6, |a| < 10
+    # here): over 6 steps of 1e-3, |dx| <= 0.5 * 0.03 * (6e-3)^2 ~ 5e-7.
+    assert np.abs(outs[0][0] - outs[3][0]).max() <= 1e-6
+
+
+def test_schedules_give_identical_results(cuda):
+    # static / dynamic / guided dealing of the groups changes only the time
+    b = inputs.two_plummer(6000, seed=70)
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    outs = []
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        for sched, chunk in (("static", 1), ("dynamic", 1), ("dynamic", 7), ("guided", 1),
+                             ("guided", 3)):
+            nb.tree_schedule(sched, chunk)
+            for group in (32, 64):
+                a, c = nb.tree_forces(x, m, 1.0, 0.01, 0.5, 16, counts=True, group=group)
+                outs.append((group, host(a), host(c)))
+        with pytest.raises(nbody.NBodyError):
+            nb.tree_schedule(3, 1)
+        with pytest.raises(nbody.NBodyError):
+            nb.tree_schedule("dynamic", 0)
+    for group in (32, 64):
+        ref = [o for o in outs if o[0] == group]
+        for o in ref[1:]:
+            assert np.array_equal(o[1], ref[0][1]) and np.array_equal(o[2], ref[0][2])
