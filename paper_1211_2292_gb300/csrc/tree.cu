@@ -38,7 +38,18 @@ namespace nb {
 namespace {
 
 constexpr int TTPB = 256;
-constexpr int WALK_WARPS = 4;
+// Walk launch shape: warps per block, and the resident blocks per SM the
+// register allocation is sized for (one and two bodies per lane).
+#ifndef NB_WALK_WARPS
+#define NB_WALK_WARPS 4
+#endif
+#ifndef NB_WALK_MINB1
+#define NB_WALK_MINB1 8
+#endif
+#ifndef NB_WALK_MINB2
+#define NB_WALK_MINB2 7
+#endif
+constexpr int WALK_WARPS = NB_WALK_WARPS;
 
 enum { META_COUNT = 0, META_BASE = 12, META_OVERFLOW = 24, META_QUEUE = 25, META_INTS = 32 };
 
@@ -342,6 +353,31 @@ __device__ __forceinline__ void list_eval(const float4 *L4, int cnt, float2 nx, 
     }
 }
 
+// Inclusive warp scan of v (lanes in order).
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += u;
+    }
+    return v;
+}
+
+// Given inclusive prefix sums `incl` of per-lane counts (non-decreasing over
+// the lanes), the lane whose span holds position pos: the number of lanes
+// with incl <= pos (a binary search over the lanes, five shuffles).
+__device__ __forceinline__ int warp_span_of(int incl, int pos)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+        if (v <= pos) lo += step;
+    }
+    return lo;
+}
+
 // One warp per group of 32 * BPL consecutive bodies in key order (BPL per
 // lane: bodies base + lane and base + 32 + lane).  The warp walks the tree
 // level by level, deepest level first, 32 nodes per round (one per lane).
@@ -358,7 +394,6 @@ template <int BPL>
 struct WalkShared {
     float4 list[WALK_WARPS][LIST_CAP * BPL];  // float4 slots of the lists
     int2 ranges[WALK_WARPS][LEVELS][32];
-    int slot[WALK_WARPS][32];
     float crit2[LEVELS];
 };
 
@@ -434,7 +469,6 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
     float *L = reinterpret_cast<float *>(list_s[warp]);
     const float4 *L4 = list_s[warp];
     int2(*rs)[32] = sh.ranges[warp];
-    int *slot = sh.slot[warp];
     const unsigned lt = (1u << lane) - 1u;
 
     float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
@@ -486,21 +520,15 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         // take up to 32 nodes from the top ranges of level Lv
         const int R = min(size, 32);
         const int2 r = lane < R ? rs[Lv][size - 1 - lane] : make_int2(0, 0);
-        int incl = r.y;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(FULL, incl, off);
-            if (lane >= off) incl += v;
-        }
+        const int incl = warp_incl_scan(r.y, lane);
         const int excl = incl - r.y;
         const int take = min(__shfl_sync(FULL, incl, 31), 32);
-        if (lane < R)
-            for (int q = excl; q < incl && q < 32; ++q) slot[q] = r.x + (q - excl);
+        const int src = warp_span_of(incl, lane);  // range holding this lane's node
+        const int first_src = __shfl_sync(FULL, r.x, src), excl_src = __shfl_sync(FULL, excl, src);
+        const int node = lane < take ? first_src + (lane - excl_src) : -1;
         const unsigned done = __ballot_sync(FULL, lane < R && incl <= 32);
         if (lane < R && excl < 32 && incl > 32)
             rs[Lv][size - 1 - lane] = make_int2(r.x + (32 - excl), incl - 32);
-        __syncwarp();
-        const int node = lane < take ? slot[lane] : -1;
         if (lane == Lv) lsize -= __popc(done);
         __syncwarp();
 
@@ -560,22 +588,25 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
             nc += __popc(am);
             if (cnt >= 32) flush32();
         }
-        // leaves: their bodies, 32 at a time
-        unsigned lm = __ballot_sync(FULL, leaf);
-        int ls = 0, le = 0;
-        if (leaf) {
-            ls = t.start[node];
-            le = t.end[node];
-        }
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int s0 = __shfl_sync(FULL, ls, src), e0 = __shfl_sync(FULL, le, src);
-            nb += e0 - s0;
-            for (int j0 = s0; j0 < e0; j0 += 32) {
-                const int kk = min(32, e0 - j0);
+        // leaves: the bodies of all of this round's leaves, 32 list slots at a
+        // time (lane l of a chunk fetches the chunk's l-th body)
+        if (__ballot_sync(FULL, leaf)) {
+            int ls = 0, lsz = 0;
+            if (leaf) {
+                ls = t.start[node];
+                lsz = t.end[node] - ls;
+            }
+            const int linc = warp_incl_scan(lsz, lane);
+            const int lexc = linc - lsz;
+            const int T = __shfl_sync(FULL, linc, 31);
+            nb += T;
+            for (int c0 = 0; c0 < T; c0 += 32) {
+                const int pos = c0 + lane;
+                const int j = warp_span_of(linc, pos);
+                const int body = __shfl_sync(FULL, ls, j & 31) + (pos - __shfl_sync(FULL, lexc, j & 31));
+                const int kk = min(32, T - c0);
                 if (lane < kk) {
-                    const float4 bh = __ldg(p.P + j0 + lane), bl = __ldg(p.Plo + j0 + lane);
+                    const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
                     list_put<BPL>(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
                                   rel(bh.z, bl.z, cz), bh.w);
                 }
@@ -626,7 +657,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
 // groups at a time from an atomic counter; guided, the same with chunks of
 // max(chunk, remaining / (2 x warps)).
 template <bool ZEPS, int BPL>
-__global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? 8 : 7)
+__global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB_WALK_MINB2)
     tree_walk_kernel(const TreeWalkParams p)
 {
     __shared__ WalkShared<BPL> sh;
