@@ -185,11 +185,11 @@ class ClockSampler:
                 "power_w_median": statistics.median(power) if power else None}
 
 
-def traffic_from_profile():
-    """DRAM bytes per force launch from the committed ncu summary, or None
-    when the force kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "force_f32comp_two_plummer_n1048576.md")
-    src = os.path.join(ROOT, "paper_1211_2292_gb300", "csrc", "force_f32.cuh")
+def traffic_from_profile(profile="force_f32comp_two_plummer_n1048576.md", source="force_f32.cuh"):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel's source file changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", profile)
+    src = os.path.join(ROOT, "paper_1211_2292_gb300", "csrc", source)
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -200,7 +200,7 @@ def traffic_from_profile():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("force_f32.cuh sha256[:16]") != sha:
+    if vals.get(f"{source} sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -549,7 +549,9 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
                                           "sample": "4096 bodies, FP64 oracle direct sum"},
             "roofline": {"bound": "alu", "kernel": "tree_walk_kernel", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": traffic_from_profile("tree_walk_two_plummer_n1048576_dram.md",
+                                                         "tree.cu")
+                         if (b.n, theta, lc, grp) == (1 << 20, 0.5, 16, 64) else None,
                          "note": f"{FLOPS_PER_INTERACTION} flops per cell or body interaction; "
                                  "walk kernel event-timed inside the timed region; peak = SMs x "
                                  "128 FP32 lanes x 2 x max SM clock"},

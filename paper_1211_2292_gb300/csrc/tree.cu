@@ -10,24 +10,24 @@
 //    30-bit Morton key (order.cu: launch_tree_sort);
 //  * a cell is a leaf when it holds at most `leaf_cap` bodies or is at
 //    level 10;
-//  * bodies are taken 32 at a time in key order (one warp); the warp walks
-//    the tree depth first with a shared stack, and a cell is used as a
-//    monopole only when it is distant enough from every body of the warp:
-//    distance from the body to the cell's cube >= edge / theta, computed in
-//    float32 with the same operations as the oracle (no contraction), so
-//    both take the same decisions;
+//  * bodies are taken 32 or 64 at a time in key order (one warp per
+//    group); a cell is used as a monopole only when it is distant enough
+//    from every body of the group: distance from the body to the cell's
+//    cube >= edge / theta, computed in float32 with the same operations as
+//    the oracle (no contraction), so both take the same decisions;
 //  * cell moments are float64 (mass, centre of mass).
 //
 // Build (all on the device, no host synchronisation, so it can be captured
 // in a graph): level by level from the root, each node of level L with more
 // than leaf_cap bodies finds its octant ranges by binary search on the
-// sorted keys; one block scans the child counts of the level; children are
-// written contiguously in octant order.  Moments are summed bottom-up.
+// sorted keys (one warp per node); one block scans the child counts of the
+// level; children are written contiguously in octant order.  Moments are
+// summed bottom-up.
 //
-// Walk arithmetic: float32 pair terms in coordinates relative to the warp's
-// centre (hi/lo packed positions and centres of mass, as in the direct-sum
-// kernel), float32 partial sums folded into Kahan (sum, carry) pairs after
-// every node.
+// Walk arithmetic: float32 pair terms in coordinates relative to the
+// group's centre (hi/lo packed positions and centres of mass, as in the
+// direct-sum kernel), float32 partial sums over every 32 listed sources
+// folded into Kahan (sum, carry) pairs.
 #include <cuda_runtime.h>
 #include <float.h>
 
