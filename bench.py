@@ -506,8 +506,21 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
         # accuracy of the first evaluation: tree vs the exact sum on sampled bodies
         rows = inputs.sample_rows(b.n, 4096, seed=1)
         ref = oracle.accel_rows(b.pos, b.mass, rows, G, eps)
-        at = nb.tree_forces(x0, m, G, eps, theta, lc, group=grp).cpu().numpy()[rows]
+        at_all, cnt_all = nb.tree_forces(x0, m, G, eps, theta, lc, group=grp, counts=True)
+        at_all, cnt_all = at_all.cpu().numpy(), cnt_all.cpu().numpy().astype(np.int64)
+        at = at_all[rows]
         e = np.linalg.norm(at - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        # parity at full size: 48 seeded groups against the oracle's tree code
+        ngroups = (b.n + grp - 1) // grp
+        gsel = np.sort(np.random.default_rng(5).choice(ngroups, min(48, ngroups), replace=False))
+        gidx, ga, gc = oracle.bh_groups(b.pos, b.mass, G, eps, theta, lc, grp, gsel)
+        gi = gidx[gidx >= 0]
+        ge = np.linalg.norm(at_all[gi] - ga[gi], axis=1) / np.linalg.norm(ga[gi], axis=1)
+        parity = {"sampled_groups": int(gsel.size), "bodies": int(gi.size), "n": b.n,
+                  "counts_equal_oracle": bool(np.array_equal(cnt_all[gi], gc[gi])),
+                  "force_rel_err_max": float(ge.max()),
+                  "force_rel_err_rms": float(np.sqrt((ge ** 2).mean())),
+                  "vs": "oracle tree code (oracle_bh_groups), same tree and groups"}
     value = per_step * args.steps / (t.ms / 1e3) / 1e9
     evals = K + 1
     walk_ms = wms / max(wn, 1)
@@ -516,7 +529,6 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
     peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOPS_PER_INTERACTION * per_step / evals / (walk_ms / 1e3) / 1e12
     cpu = None
-    parity = None
     if not args.no_cpu_baseline:
         rate, sample, bs, rcnt = tree_oracle_rate(w, theta, lc, grp)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -524,8 +536,8 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
             _, gcnt = nb.tree_forces(T(bs.pos), T(bs.mass), G, eps, theta, lc, counts=True,
                                      group=grp)
             nb.sync()
-        parity = {"counts_equal_oracle": bool(np.array_equal(gcnt.cpu().numpy(), rcnt)),
-                  "n": bs.n}
+        parity["counts_equal_oracle_whole_run"] = {
+            "n": bs.n, "equal": bool(np.array_equal(gcnt.cpu().numpy(), rcnt))}
     n = float(b.n)
     line = {"metric": TREE_METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": warm, "ms_per_step": t.ms / args.steps,

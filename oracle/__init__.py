@@ -61,6 +61,9 @@ def _bind(lib):
     lib.oracle_bh_forces.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                      _D, _I, _I]
     lib.oracle_bh_forces.restype = ctypes.c_int
+    lib.oracle_bh_groups.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                     i64, _I, _I, _D, _I]
+    lib.oracle_bh_groups.restype = ctypes.c_int
     for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
               lib.oracle_kdk, lib.oracle_force_vjp):
         f.restype = None
@@ -189,3 +192,23 @@ def bh_forces(pos, mass, G=1.0, eps=0.0, theta=0.5, leaf_cap=16, group=32, count
     stats = dict(zip(("nodes", "leaves", "cell_interactions", "body_interactions"),
                      (int(v) for v in st)))
     return (out, stats, cnt) if counts else (out, stats)
+
+
+def bh_groups(pos, mass, G, eps, theta, leaf_cap, group, sel):
+    """The tree code of bh_forces for the groups `sel` only (indices in key
+    order), over the tree of all bodies.  Returns (idx, acc, counts): idx
+    (len(sel), group) body indices (-1 past the last body), acc (n, 3) and
+    counts (n, 2) filled for those bodies (NaN / -1 elsewhere)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    idx = np.full((sel.size, group), -1, dtype=np.int64)
+    acc = np.full((n, 3), np.nan)
+    cnt = np.full((n, 2), -1, dtype=np.int64)
+    rc = _load().oracle_bh_groups(n, _p(x), _p(m), float(G), float(eps), float(theta),
+                                  int(leaf_cap), int(group), sel.size, sel.ctypes.data_as(_I),
+                                  idx.ctypes.data_as(_I), _p(acc), cnt.ctypes.data_as(_I))
+    if rc != 0:
+        raise ValueError("oracle_bh_groups: bad leaf_cap/group or group index")
+    return idx, acc, cnt

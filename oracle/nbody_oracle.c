@@ -341,12 +341,18 @@ static int64_t bh_build(bh_tree *t, int level, uint32_t prefix, int64_t start, i
     return id;
 }
 
-int oracle_bh_forces(int64_t n, const double *x, const double *m, double G, double eps,
-                     double theta, int leaf_cap, int group, double *acc, int64_t *stats,
-                     int64_t *cnt)
+/* The tree of readings above, with everything the walks need. */
+typedef struct {
+    bh_tree t;
+    int64_t *perm;
+    uint32_t *key0, *key;
+    float crit2[11];
+    int64_t leaves;
+} bh_prep;
+
+static void bh_prepare(bh_prep *P, int64_t n, const double *x, const double *m, double theta,
+                       int leaf_cap)
 {
-    if (n <= 0) return 0;
-    if (leaf_cap < 1 || group < 1) return -1;
     double lo[3], hi[3];
     for (int c = 0; c < 3; ++c) lo[c] = hi[c] = x[c];
     for (int64_t i = 0; i < n; ++i)
@@ -411,101 +417,186 @@ int oracle_bh_forces(int64_t n, const double *x, const double *m, double G, doub
         leaves += leaf;
     }
     /* squared opening distance per level, in float32 */
-    float crit2[11];
     const float th = (float)theta;
     for (int L = 0; L <= 10; ++L) {
         float edge = (float)(ext / (double)(1u << L));
         float d = edge / th;
-        crit2[L] = d * d;
+        P->crit2[L] = d * d;
     }
+    P->t = t;
+    P->perm = perm;
+    P->key0 = key0;
+    P->key = key;
+    P->leaves = leaves;
+}
 
-    int64_t ncell = 0, nbody = 0;
-    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(8 * 11 + 8));
-    int64_t lcap = 1024, *lst = (int64_t *)malloc(sizeof(int64_t) * (size_t)lcap);
-    float *xf = (float *)malloc(sizeof(float) * 3 * (size_t)group);
-    for (int64_t g0 = 0; g0 < n; g0 += group) {
-        int64_t g1 = g0 + group < n ? g0 + group : n;
-        for (int64_t k = g0; k < g1; ++k)
-            for (int c = 0; c < 3; ++c) xf[3 * (k - g0) + c] = (float)x[3 * perm[k] + c];
-        /* walk: list entries >= 0 are cells, < 0 encode leaf nodes as ~id */
-        int64_t nl = 0, sp = 0;
-        stack[sp++] = 0;
-        while (sp > 0) {
-            int64_t id = stack[--sp];
-            const bh_node *nd = &t.nodes[id];
-            int all = 1;
-            for (int64_t k = g0; k < g1 && all; ++k) {
-                const float *p = xf + 3 * (k - g0);
-                float d2 = 0.0f;
-                for (int c = 0; c < 3; ++c) {
-                    float a = nd->lo[c] - p[c];
-                    float b = p[c] - nd->hi[c];
-                    float dd = a > b ? a : b;
-                    dd = dd > 0.0f ? dd : 0.0f;
-                    float sq = dd * dd;
-                    d2 = d2 + sq;
-                }
-                if (!(d2 >= crit2[nd->level])) all = 0;
+static void bh_release(bh_prep *P)
+{
+    free(P->key0); free(P->perm); free(P->key); free(P->t.nodes);
+}
+
+/* Walk of the group holding sorted bodies [g0, g1): its list, then each of
+ * its bodies' sums.  Writes acc and cnt at the original body indices; adds
+ * to the interaction totals. */
+typedef struct {
+    int64_t *stack, *lst, lcap;
+    float *xf;
+} bh_work;
+
+static void bh_walk_group(const bh_prep *P, bh_work *W, int64_t g0, int64_t g1, const double *x,
+                          const double *m, double G, double eps, double *acc, int64_t *cnt,
+                          int64_t *ncell, int64_t *nbody)
+{
+    const bh_tree *t = &P->t;
+    const int64_t *perm = P->perm;
+    const float *crit2 = P->crit2;
+    float *xf = W->xf;
+    int64_t *stack = W->stack;
+    for (int64_t k = g0; k < g1; ++k)
+        for (int c = 0; c < 3; ++c) xf[3 * (k - g0) + c] = (float)x[3 * perm[k] + c];
+    /* walk: list entries >= 0 are cells, < 0 encode leaf nodes as ~id */
+    int64_t nl = 0, sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        int64_t id = stack[--sp];
+        const bh_node *nd = &t->nodes[id];
+        int all = 1;
+        for (int64_t k = g0; k < g1 && all; ++k) {
+            const float *p = xf + 3 * (k - g0);
+            float d2 = 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                float a = nd->lo[c] - p[c];
+                float b = p[c] - nd->hi[c];
+                float dd = a > b ? a : b;
+                dd = dd > 0.0f ? dd : 0.0f;
+                float sq = dd * dd;
+                d2 = d2 + sq;
             }
-            int leaf = 1;
-            for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
-            if (all || leaf) {
-                if (nl == lcap) {
-                    lcap *= 2;
-                    lst = (int64_t *)realloc(lst, sizeof(int64_t) * (size_t)lcap);
-                }
-                lst[nl++] = all ? id : ~id;
-            } else {
-                for (int o = 7; o >= 0; --o)
-                    if (nd->child[o] >= 0) stack[sp++] = nd->child[o];
-            }
+            if (!(d2 >= crit2[nd->level])) all = 0;
         }
-        for (int64_t k = g0; k < g1; ++k) {
-            int64_t i = perm[k];
-            double a[3] = {0, 0, 0};
-            int64_t nc = 0, nb = 0;
-            for (int64_t q = 0; q < nl; ++q) {
-                if (lst[q] >= 0) {
-                    const bh_node *nd = &t.nodes[lst[q]];
+        int leaf = 1;
+        for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
+        if (all || leaf) {
+            if (nl == W->lcap) {
+                W->lcap *= 2;
+                W->lst = (int64_t *)realloc(W->lst, sizeof(int64_t) * (size_t)W->lcap);
+            }
+            W->lst[nl++] = all ? id : ~id;
+        } else {
+            for (int o = 7; o >= 0; --o)
+                if (nd->child[o] >= 0) stack[sp++] = nd->child[o];
+        }
+    }
+    const int64_t *lst = W->lst;
+    for (int64_t k = g0; k < g1; ++k) {
+        int64_t i = perm[k];
+        double a[3] = {0, 0, 0};
+        int64_t nc = 0, nb = 0;
+        for (int64_t q = 0; q < nl; ++q) {
+            if (lst[q] >= 0) {
+                const bh_node *nd = &t->nodes[lst[q]];
+                double d[3], s2 = eps * eps;
+                for (int c = 0; c < 3; ++c) {
+                    d[c] = nd->com[c] - x[3 * i + c];
+                    s2 += d[c] * d[c];
+                }
+                double w = nd->M / (s2 * sqrt(s2));
+                for (int c = 0; c < 3; ++c) a[c] += w * d[c];
+                ++nc;
+            } else {
+                const bh_node *nd = &t->nodes[~lst[q]];
+                for (int64_t kk = nd->start; kk < nd->end; ++kk) {
+                    int64_t j = perm[kk];
+                    ++nb;
+                    if (j == i) continue;
                     double d[3], s2 = eps * eps;
                     for (int c = 0; c < 3; ++c) {
-                        d[c] = nd->com[c] - x[3 * i + c];
+                        d[c] = x[3 * j + c] - x[3 * i + c];
                         s2 += d[c] * d[c];
                     }
-                    double w = nd->M / (s2 * sqrt(s2));
+                    double w = m[j] / (s2 * sqrt(s2));
                     for (int c = 0; c < 3; ++c) a[c] += w * d[c];
-                    ++nc;
-                } else {
-                    const bh_node *nd = &t.nodes[~lst[q]];
-                    for (int64_t kk = nd->start; kk < nd->end; ++kk) {
-                        int64_t j = perm[kk];
-                        ++nb;
-                        if (j == i) continue;
-                        double d[3], s2 = eps * eps;
-                        for (int c = 0; c < 3; ++c) {
-                            d[c] = x[3 * j + c] - x[3 * i + c];
-                            s2 += d[c] * d[c];
-                        }
-                        double w = m[j] / (s2 * sqrt(s2));
-                        for (int c = 0; c < 3; ++c) a[c] += w * d[c];
-                    }
                 }
             }
-            for (int c = 0; c < 3; ++c) acc[3 * i + c] = G * a[c];
-            if (cnt) {
-                cnt[2 * i] = nc;
-                cnt[2 * i + 1] = nb;
-            }
-            ncell += nc;
-            nbody += nb;
         }
+        for (int c = 0; c < 3; ++c) acc[3 * i + c] = G * a[c];
+        if (cnt) {
+            cnt[2 * i] = nc;
+            cnt[2 * i + 1] = nb;
+        }
+        *ncell += nc;
+        *nbody += nb;
+    }
+}
+
+static void bh_work_init(bh_work *W, int group)
+{
+    W->stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(8 * 11 + 8));
+    W->lcap = 1024;
+    W->lst = (int64_t *)malloc(sizeof(int64_t) * (size_t)W->lcap);
+    W->xf = (float *)malloc(sizeof(float) * 3 * (size_t)group);
+}
+
+static void bh_work_free(bh_work *W)
+{
+    free(W->stack); free(W->lst); free(W->xf);
+}
+
+int oracle_bh_forces(int64_t n, const double *x, const double *m, double G, double eps,
+                     double theta, int leaf_cap, int group, double *acc, int64_t *stats,
+                     int64_t *cnt)
+{
+    if (n <= 0) return 0;
+    if (leaf_cap < 1 || group < 1) return -1;
+    bh_prep P;
+    bh_prepare(&P, n, x, m, theta, leaf_cap);
+    bh_work W;
+    bh_work_init(&W, group);
+    int64_t ncell = 0, nbody = 0;
+    for (int64_t g0 = 0; g0 < n; g0 += group) {
+        int64_t g1 = g0 + group < n ? g0 + group : n;
+        bh_walk_group(&P, &W, g0, g1, x, m, G, eps, acc, cnt, &ncell, &nbody);
     }
     if (stats) {
-        stats[0] = t.nnodes;
-        stats[1] = leaves;
+        stats[0] = P.t.nnodes;
+        stats[1] = P.leaves;
         stats[2] = ncell;
         stats[3] = nbody;
     }
-    free(key0); free(perm); free(key); free(t.nodes); free(stack); free(lst); free(xf);
+    bh_work_free(&W);
+    bh_release(&P);
+    return 0;
+}
+
+/*
+ * The same tree code for a subset of the groups: the tree is built over all
+ * n bodies and only the groups sel[0..nsel) (indices in key order) walk it.
+ * acc (n,3) and cnt (n,2) are written for the bodies of those groups only;
+ * idx[q * group + r] receives the body index of the r-th body of group
+ * sel[q] (-1 past the last body).  Returns -1 for bad arguments or a group
+ * index out of range.
+ */
+int oracle_bh_groups(int64_t n, const double *x, const double *m, double G, double eps,
+                     double theta, int leaf_cap, int group, int64_t nsel, const int64_t *sel,
+                     int64_t *idx, double *acc, int64_t *cnt)
+{
+    if (n <= 0 || nsel <= 0) return 0;
+    if (leaf_cap < 1 || group < 1) return -1;
+    const int64_t ngroups = (n + group - 1) / group;
+    for (int64_t q = 0; q < nsel; ++q)
+        if (sel[q] < 0 || sel[q] >= ngroups) return -1;
+    bh_prep P;
+    bh_prepare(&P, n, x, m, theta, leaf_cap);
+    bh_work W;
+    bh_work_init(&W, group);
+    int64_t ncell = 0, nbody = 0;
+    for (int64_t q = 0; q < nsel; ++q) {
+        int64_t g0 = sel[q] * group;
+        int64_t g1 = g0 + group < n ? g0 + group : n;
+        for (int64_t r = 0; r < group; ++r) idx[q * group + r] = g0 + r < n ? P.perm[g0 + r] : -1;
+        bh_walk_group(&P, &W, g0, g1, x, m, G, eps, acc, cnt, &ncell, &nbody);
+    }
+    bh_work_free(&W);
+    bh_release(&P);
     return 0;
 }

@@ -146,3 +146,28 @@ def test_differentiation_workload_n16384(cuda):
         args_m[which] = args_m[which] - h * u
         fd = (L(*args_p) - L(*args_m)) / (2 * h)
         assert abs(fd - np.linalg.norm(g)) <= 1e-3 * np.linalg.norm(g), (which, fd, np.linalg.norm(g))
+
+
+@pytest.mark.parametrize("group", [64, 32])
+def test_tree_workload_n2p20_sampled_groups(cuda, group):
+    # The tree bench's workload and launch configuration (two-Plummer 2^20,
+    # theta 0.5, leaves <= 16, dynamic schedule): every body of 48 seeded
+    # groups meets exactly the oracle tree's lists, with forces within the
+    # float32 bound; the totals agree with the per-body counts.
+    b = inputs.two_plummer(524_288, seed=2)
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        a, cnt = nb.tree_forces(x, m, 1.0, 0.002, 0.5, 16, counts=True, group=group)
+        nb.sync()
+        st = nb.tree_stats()
+    a, cnt = host(a), host(cnt).astype(np.int64)
+    ngroups = (b.n + group - 1) // group
+    sel = np.sort(np.random.default_rng(5).choice(ngroups, 48, replace=False))
+    idx, ra, rc = oracle.bh_groups(b.pos, b.mass, 1.0, 0.002, 0.5, 16, group, sel)
+    ii = idx[idx >= 0]
+    assert ii.size == 48 * group
+    assert np.array_equal(cnt[ii], rc[ii])
+    e = relerr_per_body(a[ii], ra[ii])
+    assert np.sqrt((e ** 2).mean()) <= 1e-5 and e.max() <= 1e-4
+    assert st["cell_interactions"] == cnt[:, 0].sum()
+    assert st["body_interactions"] == cnt[:, 1].sum()

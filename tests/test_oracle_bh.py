@@ -69,3 +69,23 @@ def test_bad_arguments():
         oracle.bh_forces(b.pos, b.mass, 1.0, 0.01, 0.5, 0, 32)
     a, st = oracle.bh_forces(np.zeros((0, 3)), np.zeros(0), 1.0, 0.1, 0.5, 16, 32)
     assert a.shape == (0, 3)
+
+
+def test_group_subset_equals_the_full_run():
+    # The subset walk reuses the full tree: its bodies, lists and sums must be
+    # those of the full run exactly, and idx must list the groups' bodies in
+    # key order (consecutive groups tile the bodies once).
+    b = inputs.plummer(3001, seed=54)
+    a, _, cnt = oracle.bh_forces(b.pos, b.mass, 1.0, 0.01, 0.6, 8, 64, counts=True)
+    ngroups = (b.n + 63) // 64
+    idx, a2, c2 = oracle.bh_groups(b.pos, b.mass, 1.0, 0.01, 0.6, 8, 64, np.arange(ngroups))
+    flat = idx.ravel()
+    assert np.array_equal(np.sort(flat[flat >= 0]), np.arange(b.n))
+    assert np.array_equal(a2, a) and np.array_equal(c2, cnt)
+    sel = np.array([ngroups - 1, 3])
+    idx, a3, c3 = oracle.bh_groups(b.pos, b.mass, 1.0, 0.01, 0.6, 8, 64, sel)
+    assert (idx[0] >= 0).sum() == b.n - 64 * (ngroups - 1) and (idx[1] >= 0).all()
+    ii = idx[idx >= 0]
+    assert np.array_equal(a3[ii], a[ii]) and np.isnan(a3[np.setdiff1d(np.arange(b.n), ii)]).all()
+    with pytest.raises(ValueError):
+        oracle.bh_groups(b.pos, b.mass, 1.0, 0.01, 0.6, 8, 64, [ngroups])
