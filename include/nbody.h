@@ -264,7 +264,7 @@ nb_status nb_device_info(nb_ctx *ctx, int64_t n, int *num_sms, int *ctas_per_sm)
  * per body the number of cells and of bodies (itself included) it met.
  * Any precision mode (the walk is float32 in each).  The first call (and a
  * call whose leaf_cap needs more nodes than any before) allocates the tree
- * scratch: 124 bytes per node for 1 + sum_{L=1..10} min(8^L, n_max,
+ * scratch: 132 bytes per node for 1 + sum_{L=1..10} min(8^L, n_max,
  * 8 floor(n_max / (leaf_cap + 1))) nodes, a bound no tree exceeds (about
  * 2.3e6 nodes for n_max = 2^20, leaf_cap = 16), plus 40 bytes per body; this
  * synchronises the device and drops the context's captured graphs.  nb_sync

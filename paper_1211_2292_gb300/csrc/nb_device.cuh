@@ -59,7 +59,8 @@ __device__ __forceinline__ double rsqrt_f64(double x)
 }
 
 // Exclusive scan of in[0..total) into out[0..total) (in == out allowed) by
-// one block of 1024 threads, in index order; returns the sum (every thread).
+// one block of 1024 threads, in index order, starting from carry0; returns
+// carry0 plus the sum (every thread).
 // Tiles of 8192 entries pass through shared memory (coalesced loads and
 // stores), 8 consecutive entries per thread, a two-level warp scan of the
 // thread sums and a carry from tile to tile.  tile: 8192 + 256 entries,
@@ -68,10 +69,10 @@ constexpr int BSCAN_PER = 8, BSCAN_TILE = 1024 * BSCAN_PER;
 __device__ __forceinline__ int bscan_pad(int i) { return i + (i >> 5); }  // no bank conflicts
 
 template <typename T>
-__device__ T block_scan_exclusive(const T *in, T *out, int total, T *tile, T *wsum)
+__device__ T block_scan_exclusive(const T *in, T *out, int total, T *tile, T *wsum, T carry0 = 0)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T carry = 0;
+    T carry = carry0;
     for (int base = 0; base < total; base += BSCAN_TILE) {
         for (int q = threadIdx.x; q < BSCAN_TILE; q += 1024)
             tile[bscan_pad(q)] = base + q < total ? in[base + q] : T(0);

@@ -122,9 +122,10 @@ struct OrderScratch {
     double *box;        // [1024][6]: bounding-box partials of up to 1023 blocks, then the folded box
     unsigned *keys[2];  // [n] Morton keys (ping-pong)
     int *vals[2];       // [n] body indices (ping-pong)
-    unsigned *hist;     // [256][chunks] digit counts / offsets
+    unsigned *hist;     // [256][chunks] digit counts / offsets, then scan partials
 };
 int sort_chunks(int n);
+size_t sort_hist_entries(int n);  // entries of OrderScratch::hist for n bodies
 // perm_out[k] = body at Morton rank k (stable in body index); `kernels` = launches made.
 cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
                                int *perm_out, int &kernels);
@@ -146,6 +147,7 @@ struct TreeView {
     int cap;
     int *meta;            // [tree_meta_ints()] per-level node counts and bases, overflow flag
     int *start, *end, *level, *nchild, *first, *offs;
+    int *parent, *arrive;     // parent node (-1 at the root); children counted in by the moments
     unsigned *prefix;
     double *M, *com;      // float64 monopoles: mass, centre of mass [cap][3]
     float4 *box_lo, *box_hi;  // float32 cell cube corners; .w = nchild, first (int bits)
@@ -173,6 +175,7 @@ int tree_meta_ints();
 // most leaf_cap bodies (no build can exceed it).
 int64_t tree_node_bound(int64_t n, int leaf_cap);
 // Build over sorted keys (launch_tree_sort), float64 moments, float32 walk data.
+// box = {lo_x, lo_y, lo_z, ext} from launch_tree_sort.
 cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const unsigned *keys,
                               const double *box, const double *pos, const double *mass,
                               const int *perm, int leaf_cap, int *err, int &kernels);

@@ -479,10 +479,10 @@ T *dev_alloc(nb_ctx *c, size_t count, nb_status &st)
 void free_tree_nodes(nb_ctx *c)
 {
     nb::TreeView &t = c->tree;
-    void *arrays[] = {t.start, t.end,   t.level,  t.nchild, t.first, t.offs, t.prefix,
-                      t.M,     t.com,   t.box_lo, t.box_hi, t.chi,   t.clo};
+    void *arrays[] = {t.start, t.end,   t.level,  t.nchild, t.first, t.offs, t.parent,
+                      t.arrive, t.prefix, t.M,  t.com,    t.box_lo, t.box_hi, t.chi, t.clo};
     for (void *a : arrays) cudaFree(a);
-    t.start = t.end = t.level = t.nchild = t.first = t.offs = nullptr;
+    t.start = t.end = t.level = t.nchild = t.first = t.offs = t.parent = t.arrive = nullptr;
     t.prefix = nullptr;
     t.M = t.com = nullptr;
     t.box_lo = t.box_hi = t.chi = t.clo = nullptr;
@@ -539,7 +539,7 @@ nb_status ensure_order(nb_ctx *c)
         if (st == NB_OK && !c->order.vals[q]) c->order.vals[q] = dev_alloc<int>(c, nc, st);
     }
     if (st == NB_OK)
-        c->order.hist = dev_alloc<unsigned>(c, (size_t)256 * nb::sort_chunks((int)nc), st);
+        c->order.hist = dev_alloc<unsigned>(c, nb::sort_hist_entries((int)nc), st);
     return st;
 }
 
@@ -569,7 +569,7 @@ nb_status ensure_tree(nb_ctx *c, int leaf_cap)
     free_tree_nodes(c);
     nb::TreeView &t = c->tree;
     const size_t m = (size_t)need;
-    int **ints[] = {&t.start, &t.end, &t.level, &t.nchild, &t.first, &t.offs};
+    int **ints[] = {&t.start, &t.end, &t.level, &t.nchild, &t.first, &t.offs, &t.parent, &t.arrive};
     for (int **a : ints)
         if (st == NB_OK) *a = dev_alloc<int>(c, m, st);
     if (st == NB_OK) t.prefix = dev_alloc<unsigned>(c, m, st);
@@ -866,7 +866,7 @@ nb_status nb_create(nb_ctx **out, int64_t n_max, nb_precision p, int device, voi
             if (st == NB_OK) c->order.vals[q] = dev_alloc<int>(c, nc, st);
         }
         if (st == NB_OK)
-            c->order.hist = dev_alloc<unsigned>(c, (size_t)256 * nb::sort_chunks((int)ncap), st);
+            c->order.hist = dev_alloc<unsigned>(c, nb::sort_hist_entries((int)ncap), st);
     }
     if (st != NB_OK) return bail(st);
     if (cudaMallocHost(&c->host_out, 16 * sizeof(double)) != cudaSuccess)

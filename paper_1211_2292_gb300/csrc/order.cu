@@ -180,12 +180,54 @@ __global__ void __launch_bounds__(OTPB) radix_hist_kernel(int n, const unsigned 
     }
 }
 
-// In-place exclusive scan of hist[0..total) by one block, in index order.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(unsigned *__restrict__ hist, int total)
+// In-place exclusive scan of hist[0..total) over several blocks: block b
+// sums its segment of BSCAN_TILE entries into part[b] (radix_part_kernel),
+// then scans it starting from the sum of the segments before it.
+__global__ void __launch_bounds__(1024) radix_part_kernel(const unsigned *__restrict__ hist,
+                                                          int total, unsigned *__restrict__ part)
+{
+    __shared__ unsigned ws[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = blockIdx.x * BSCAN_TILE;
+    unsigned v = 0u;
+    for (int q = threadIdx.x; q < BSCAN_TILE; q += 1024)
+        if (base + q < total) v += hist[base + q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = ws[lane];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) radix_scan_kernel(unsigned *__restrict__ hist, int total,
+                                                          const unsigned *__restrict__ part)
 {
     __shared__ unsigned tile[BSCAN_TILE + BSCAN_TILE / 32];
     __shared__ unsigned wsum[32];
-    block_scan_exclusive<unsigned>(hist, hist, total, tile, wsum);
+    __shared__ unsigned offset;
+    if (threadIdx.x < 32) {
+        unsigned v = 0u;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) v += part[b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0) offset = v;
+    }
+    __syncthreads();
+    const int base = blockIdx.x * BSCAN_TILE;
+    block_scan_exclusive<unsigned>(hist + base, hist + base, min(BSCAN_TILE, total - base), tile,
+                                   wsum, offset);
+}
+
+inline void launch_radix_scan(cudaStream_t s, unsigned *hist, int total)
+{
+    const int blocks = (total + BSCAN_TILE - 1) / BSCAN_TILE;
+    radix_part_kernel<<<blocks, 1024, 0, s>>>(hist, total, hist + total);
+    radix_scan_kernel<<<blocks, 1024, 0, s>>>(hist, total, hist + total);
 }
 
 // Stable scatter: one warp per chunk, keys taken 32 at a time in order.
@@ -252,6 +294,13 @@ inline int grid_for(int n)
 
 int sort_chunks(int n) { return (n + SORT_CHUNK - 1) / SORT_CHUNK; }
 
+size_t sort_hist_entries(int n)
+{
+    // digit counts, then one partial sum per scan block
+    const size_t total = (size_t)256 * sort_chunks(n);
+    return total + (total + BSCAN_TILE - 1) / BSCAN_TILE + 32;
+}
+
 cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
                                int *perm_out, int &kernels)
 {
@@ -268,11 +317,11 @@ cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderSc
     for (int pass = 0; pass < 3; ++pass) {
         const int shift = 8 * pass;
         radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
-        radix_scan_kernel<<<1, 1024, 0, s>>>(o.hist, 256 * nchunks);
+        launch_radix_scan(s, o.hist, 256 * nchunks);
         int *vout = pass == 2 ? perm_out : o.vals[cur ^ 1];
         radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
                                                      vout, shift, nchunks, o.hist);
-        kernels += 3;
+        kernels += 4;
         cur ^= 1;
     }
     return cudaGetLastError();
@@ -294,11 +343,11 @@ cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScra
     for (int pass = 0; pass < 4; ++pass) {  // 30-bit keys: 4 passes, sorted keys end in keys[0]
         const int shift = 8 * pass;
         radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
-        radix_scan_kernel<<<1, 1024, 0, s>>>(o.hist, 256 * nchunks);
+        launch_radix_scan(s, o.hist, 256 * nchunks);
         int *vout = pass == 3 ? perm_out : o.vals[cur ^ 1];
         radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
                                                      vout, shift, nchunks, o.hist);
-        kernels += 3;
+        kernels += 4;
         cur ^= 1;
     }
     return cudaGetLastError();

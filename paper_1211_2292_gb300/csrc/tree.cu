@@ -59,7 +59,31 @@ inline int grid_cap(int64_t work)
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
-__global__ void tree_init_kernel(TreeView t, int n)
+// Float32 cube of the level-L cell with key prefix `pre`, exactly as the
+// oracle forms it (float64 lo + edge * index, rounded); .w of the corners
+// carries the child count (0) and first child (-1) until the node's own
+// level is built.
+__device__ __forceinline__ void cube_corners(const double *__restrict__ box, int L, unsigned pre,
+                                             float4 &lo4, float4 &hi4)
+{
+    unsigned ic[3] = {0u, 0u, 0u};
+    for (int bb = 0; bb < L; ++bb) {
+        const unsigned trip = (pre >> (3 * bb)) & 7u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << bb;
+    }
+    const double cell = __ddiv_rn(box[3], (double)(1u << L));
+    float blo[3], bhi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        blo[c] = (float)__dadd_rn(box[c], __dmul_rn(cell, (double)ic[c]));
+        bhi[c] = (float)__dadd_rn(box[c], __dmul_rn(cell, (double)(ic[c] + 1u)));
+    }
+    lo4 = make_float4(blo[0], blo[1], blo[2], __int_as_float(0));
+    hi4 = make_float4(bhi[0], bhi[1], bhi[2], __int_as_float(-1));
+}
+
+__global__ void tree_init_kernel(TreeView t, int n, const double *box)
 {
     if (threadIdx.x < META_INTS) t.meta[threadIdx.x] = 0;
     if (threadIdx.x < 4) t.stats[threadIdx.x] = 0ull;
@@ -71,6 +95,9 @@ __global__ void tree_init_kernel(TreeView t, int n)
         t.level[0] = 0;
         t.nchild[0] = 0;
         t.first[0] = -1;
+        t.parent[0] = -1;
+        t.arrive[0] = 0;
+        cube_corners(box, 0, 0u, t.box_lo[0], t.box_hi[0]);
     }
 }
 
@@ -139,7 +166,8 @@ __global__ void __launch_bounds__(1024) tree_scan_kernel(TreeView t, int L)
     }
 }
 
-__global__ void __launch_bounds__(TTPB) tree_emit_kernel(TreeView t, const unsigned *keys, int L)
+__global__ void __launch_bounds__(TTPB) tree_emit_kernel(TreeView t, const unsigned *keys,
+                                                         const double *__restrict__ box, int L)
 {
     const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
     const int nbase = t.meta[META_BASE + L + 1];
@@ -161,7 +189,11 @@ __global__ void __launch_bounds__(TTPB) tree_emit_kernel(TreeView t, const unsig
         int b, nxt;
         const unsigned ne = octants(keys, t.start[node], t.end[node], pre, L, lane, b, nxt);
         const int first = nbase + t.offs[q];
-        if (lane == 0) t.first[node] = first;
+        if (lane == 0) {
+            t.first[node] = first;
+            reinterpret_cast<int *>(t.box_lo + node)[3] = nch;  // the walk's child count
+            reinterpret_cast<int *>(t.box_hi + node)[3] = first;
+        }
         if (lane < 8 && ((ne >> lane) & 1u)) {
             const int c = first + __popc(ne & lt);
             t.start[c] = b;
@@ -170,81 +202,70 @@ __global__ void __launch_bounds__(TTPB) tree_emit_kernel(TreeView t, const unsig
             t.level[c] = L + 1;
             t.nchild[c] = 0;
             t.first[c] = -1;
+            t.parent[c] = node;
+            t.arrive[c] = 0;
+            cube_corners(box, L + 1, pre * 8u + lane, t.box_lo[c], t.box_hi[c]);
         }
     }
 }
 
-// Float64 monopoles of level L (children first: call from level 10 up).
+// Walk data of a node whose float64 moments are final: mass and centre of
+// mass as a float32 hi/lo pair.
+__device__ __forceinline__ void put_walk_moments(const TreeView &t, int node, double M, double cx,
+                                                 double cy, double cz)
+{
+    t.M[node] = M;
+    t.com[3 * (size_t)node] = cx;
+    t.com[3 * (size_t)node + 1] = cy;
+    t.com[3 * (size_t)node + 2] = cz;
+    const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+    t.chi[node] = make_float4(hx, hy, hz, (float)M);
+    t.clo[node] = make_float4((float)(cx - (double)hx), (float)(cy - (double)hy),
+                              (float)(cz - (double)hz), 0.f);
+}
+
+// Float64 monopoles of every node in one launch, bottom-up without any wait:
+// a thread per leaf sums its bodies, then climbs; at each parent it counts
+// itself in with an atomic, and only the last child to arrive goes on to
+// sum the parent's children (in child order, so the result does not depend
+// on who arrives last).  Fences order the moments before the arrival.
 __global__ void __launch_bounds__(TTPB) tree_moments_kernel(TreeView t, const double *__restrict__ pos,
                                                             const double *__restrict__ mass,
-                                                            const int *__restrict__ perm, int L)
-{
-    const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
-    for (int q = blockIdx.x * TTPB + threadIdx.x; q < cnt; q += gridDim.x * TTPB) {
-        const int node = base + q;
-        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        const int nch = t.nchild[node];
-        if (nch == 0) {
-            for (int k = t.start[node]; k < t.end[node]; ++k) {
-                const int j = perm[k];
-                const double m = mass[j];
-                M += m;
-                sx += m * pos[3 * (size_t)j];
-                sy += m * pos[3 * (size_t)j + 1];
-                sz += m * pos[3 * (size_t)j + 2];
-            }
-        } else {
-            const int f = t.first[node];
-            for (int c = f; c < f + nch; ++c) {
-                const double m = t.M[c];
-                M += m;
-                sx += m * t.com[3 * (size_t)c];
-                sy += m * t.com[3 * (size_t)c + 1];
-                sz += m * t.com[3 * (size_t)c + 2];
-            }
-        }
-        t.M[node] = M;
-        t.com[3 * (size_t)node] = M > 0.0 ? sx / M : 0.0;
-        t.com[3 * (size_t)node + 1] = M > 0.0 ? sy / M : 0.0;
-        t.com[3 * (size_t)node + 2] = M > 0.0 ? sz / M : 0.0;
-    }
-}
-
-// Walk data of every node: float32 cube (exactly as the oracle forms it),
-// centre of mass as a float32 hi/lo pair and mass.
-__global__ void __launch_bounds__(TTPB) tree_walkdata_kernel(TreeView t, const double *__restrict__ box)
+                                                            const int *__restrict__ perm)
 {
     const int total = t.meta[META_BASE + 10] + t.meta[META_COUNT + 10];
-    const double lo[3] = {box[0], box[1], box[2]};
-    const double ext = box[3];
     if (blockIdx.x == 0 && threadIdx.x == 0) t.stats[0] = (unsigned long long)total;
     int leaves = 0;
-    for (int node = blockIdx.x * TTPB + threadIdx.x; node < total; node += gridDim.x * TTPB) {
-        const int L = t.level[node];
-        leaves += t.nchild[node] == 0;
-        const unsigned pre = t.prefix[node];
-        unsigned ic[3] = {0u, 0u, 0u};
-        for (int bb = 0; bb < L; ++bb) {
-            const unsigned trip = (pre >> (3 * bb)) & 7u;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << bb;
+    for (int leaf = blockIdx.x * TTPB + threadIdx.x; leaf < total; leaf += gridDim.x * TTPB) {
+        if (t.nchild[leaf] != 0) continue;
+        ++leaves;
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int k = t.start[leaf]; k < t.end[leaf]; ++k) {
+            const int j = perm[k];
+            const double m = mass[j];
+            M += m;
+            sx += m * pos[3 * (size_t)j];
+            sy += m * pos[3 * (size_t)j + 1];
+            sz += m * pos[3 * (size_t)j + 2];
         }
-        const double cell = __ddiv_rn(ext, (double)(1u << L));
-        float blo[3], bhi[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            blo[c] = (float)__dadd_rn(lo[c], __dmul_rn(cell, (double)ic[c]));
-            bhi[c] = (float)__dadd_rn(lo[c], __dmul_rn(cell, (double)(ic[c] + 1u)));
+        put_walk_moments(t, leaf, M, M > 0.0 ? sx / M : 0.0, M > 0.0 ? sy / M : 0.0,
+                         M > 0.0 ? sz / M : 0.0);
+        for (int node = t.parent[leaf]; node >= 0; node = t.parent[node]) {
+            __threadfence();
+            if (atomicAdd(t.arrive + node, 1) != t.nchild[node] - 1) break;
+            __threadfence();
+            const int f = t.first[node], nch = t.nchild[node];
+            M = sx = sy = sz = 0.0;
+            for (int c = f; c < f + nch; ++c) {
+                const double m = __ldcg(t.M + c);
+                M += m;
+                sx += m * __ldcg(t.com + 3 * (size_t)c);
+                sy += m * __ldcg(t.com + 3 * (size_t)c + 1);
+                sz += m * __ldcg(t.com + 3 * (size_t)c + 2);
+            }
+            put_walk_moments(t, node, M, M > 0.0 ? sx / M : 0.0, M > 0.0 ? sy / M : 0.0,
+                             M > 0.0 ? sz / M : 0.0);
         }
-        // .w carries the child count and first child for the walk
-        t.box_lo[node] = make_float4(blo[0], blo[1], blo[2], __int_as_float(t.nchild[node]));
-        t.box_hi[node] = make_float4(bhi[0], bhi[1], bhi[2], __int_as_float(t.first[node]));
-        const double cx = t.com[3 * (size_t)node], cy = t.com[3 * (size_t)node + 1],
-                     cz = t.com[3 * (size_t)node + 2];
-        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-        t.chi[node] = make_float4(hx, hy, hz, (float)t.M[node]);
-        t.clo[node] = make_float4((float)(cx - (double)hx), (float)(cy - (double)hy),
-                                  (float)(cz - (double)hz), 0.f);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) leaves += __shfl_xor_sync(0xffffffffu, leaves, off);
@@ -717,20 +738,16 @@ cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const un
                               const int *perm, int leaf_cap, int *err, int &kernels)
 {
     kernels = 0;
-    tree_init_kernel<<<1, 32, 0, s>>>(t, n);
+    tree_init_kernel<<<1, 32, 0, s>>>(t, n, box);
     ++kernels;
     const int g = grid_cap(n);
     for (int L = 0; L < 10; ++L) {
         tree_count_kernel<<<g, TTPB, 0, s>>>(t, keys, L, leaf_cap);
         tree_scan_kernel<<<1, 1024, 0, s>>>(t, L);
-        tree_emit_kernel<<<g, TTPB, 0, s>>>(t, keys, L);
+        tree_emit_kernel<<<g, TTPB, 0, s>>>(t, keys, box, L);
         kernels += 3;
     }
-    for (int L = 10; L >= 0; --L) {
-        tree_moments_kernel<<<g, TTPB, 0, s>>>(t, pos, mass, perm, L);
-        ++kernels;
-    }
-    tree_walkdata_kernel<<<grid_cap(t.cap), TTPB, 0, s>>>(t, box);
+    tree_moments_kernel<<<grid_cap(t.cap), TTPB, 0, s>>>(t, pos, mass, perm);
     tree_flag_kernel<<<1, 32, 0, s>>>(t, err);
     kernels += 2;
     return cudaGetLastError();
