@@ -333,8 +333,8 @@ class Timer:
         self.ms = self.e0.elapsed_time(self.e1)
 
 
-def measure_forms(torch, dev, tune, table, peak_tflops):
-    """Rates of the batched and adjoint forms (rank-local, after the timed region)."""
+def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None):
+    """Rates of the batched, adjoint and tree forms (rank-local, after the timed region)."""
     from paper_1211_2292_gb300 import inputs, nbody
     from paper_1211_2292_gb300.autograd import rollout
     stream = torch.cuda.current_stream(dev)
@@ -394,6 +394,33 @@ def measure_forms(torch, dev, tune, table, peak_tflops):
                           "gradient_ms": t.ms,
                           "gradient": f"{a_['steps']} steps, checkpoints every {a_['every']}, "
                                       "forward + recompute + reverse sweep"}
+    if tree_bodies is not None:  # Barnes-Hut on the same bodies (full line: --workload tree)
+        t_ = TREE
+        x = torch.as_tensor(tree_bodies.pos, device=dev).contiguous()
+        m = torch.as_tensor(tree_bodies.mass, device=dev).contiguous()
+        with nbody.NBody(tree_bodies.n, "fp32_comp", device=dev.index) as nb:
+            a = nb.tree_forces(x, m, 1.0, t_["eps"], t_["theta"], t_["leaf_cap"],
+                               group=t_["group"])
+            nb.profile(True)
+            for _ in range(5):
+                nb.tree_forces(x, m, 1.0, t_["eps"], t_["theta"], t_["leaf_cap"], out=a,
+                               group=t_["group"])
+            wn, wms = nb.profile_read(4)
+            bn, bms = nb.profile_read(5)
+            nb.profile(False)
+            st = nb.tree_stats()
+        inter = st["cell_interactions"] + st["body_interactions"]
+        walk, build = wms / max(wn, 1), bms / max(bn, 1)
+        n = float(tree_bodies.n)
+        out["tree"] = {"theta": t_["theta"], "leaf_cap": t_["leaf_cap"], "group": t_["group"],
+                       "ms_per_eval": walk + build, "walk_ms": walk, "build_ms": build,
+                       "interactions": inter, "walk_value": inter / (walk / 1e3) / 1e9,
+                       "unit": UNIT,
+                       "walk_frac_of_fp32_peak": FLOPS_PER_INTERACTION * inter
+                       / (walk / 1e3) / 1e12 / peak_tflops,
+                       "direct_sum_equivalent": n * n / ((walk + build) / 1e3) / 1e9,
+                       "note": "one tree build + walk of the throughput workload's bodies; "
+                               "error and parity in bench.py --workload tree"}
     return out
 
 
@@ -908,7 +935,7 @@ def main():
 
     forms = None
     if not args.no_forms and rank == 0 and args.workload == "throughput":
-        forms = measure_forms(torch, dev, tune, table, peak_tflops)
+        forms = measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=b)
 
     # end to end through the public API with pinned host buffers
     e2e = None
