@@ -177,3 +177,42 @@ def test_schedules_give_identical_results(cuda):
         ref = [o for o in outs if o[0] == group]
         for o in ref[1:]:
             assert np.array_equal(o[1], ref[0][1]) and np.array_equal(o[2], ref[0][2])
+
+
+def _both(cuda, pos, mass, G, eps, theta, leaf_cap, group):
+    b = inputs.Bodies(pos, np.zeros_like(pos), mass)
+    a, cnt, st = _gpu_tree(cuda, b, G, eps, theta, leaf_cap, group=group)
+    ref, rst, rcnt = oracle.bh_forces(pos, mass, G, eps, theta, leaf_cap, group, counts=True)
+    return a, cnt, st, ref, rcnt, rst
+
+
+@pytest.mark.parametrize("group", [32, 64])
+def test_shapes_the_tree_can_take(cuda, group):
+    rng = np.random.default_rng(71)
+    # a flat disc (one axis constant), a single leaf holding everything,
+    # a dense clump that reaches level 10 with more than leaf_cap bodies,
+    # and massless bodies (cells of zero mass keep their centre at 0).  The
+    # clump runs at eps = 0.1: for pairs closer than eps a float32 form errs
+    # by about m * ulp(|x - origin|) / eps^3 per pair, which at eps = 0.01 and
+    # 300 coincident bodies of mass 4e-4 reaches 5e-3 of |a| in the direct
+    # float32 kernel as well (an input for the float64 form, not a tree issue).
+    disc = np.column_stack([rng.normal(size=(3000, 2)), np.zeros(3000)])
+    clump = np.vstack([rng.normal(size=(2000, 3)), 1e-9 * rng.normal(size=(300, 3)) + 0.3])
+    cases = [
+        (disc, rng.uniform(0.5, 1.5, 3000) / 3000, 0.5, 16),
+        (rng.normal(size=(500, 3)), rng.uniform(0.5, 1.5, 500) / 500, 0.5, 1000),
+        (clump, rng.uniform(0.5, 1.5, 2300) / 2300, 0.5, 8),
+        (rng.normal(size=(2000, 3)), np.where(rng.random(2000) < 0.3, 0.0, 1.0 / 2000), 0.6, 4),
+    ]
+    for k, (pos, mass, theta, lc) in enumerate(cases):
+        eps = 0.1 if k == 2 else 0.01
+        a, cnt, st, ref, rcnt, rst = _both(cuda, pos, mass, 1.0, eps, theta, lc, group)
+        assert np.array_equal(cnt, rcnt) and st == rst
+        # error against the rms acceleration (the disc has bodies of near-zero
+        # |a| at its centre, where a per-body ratio is ill-conditioned)
+        rms = np.sqrt((np.linalg.norm(ref, axis=1) ** 2).mean())
+        e = np.linalg.norm(a - ref, axis=1) / rms
+        assert e.max() <= MAX_TOL and np.sqrt((e ** 2).mean()) <= RMS_TOL
+    # one leaf: the walk is the direct sum for every body
+    _, cnt, st, _, _, _ = _both(cuda, cases[1][0], cases[1][1], 1.0, 0.01, 0.5, 1000, group)
+    assert st["nodes"] == 1 and np.all(cnt[:, 1] == 500) and np.all(cnt[:, 0] == 0)
