@@ -26,7 +26,7 @@
 //
 // Walk arithmetic: float32 pair terms in coordinates relative to the
 // group's centre (hi/lo packed positions and centres of mass, as in the
-// direct-sum kernel), float32 partial sums over every 32 listed sources
+// direct-sum kernel), float32 partial sums over every FLUSH listed sources
 // folded into Kahan (sum, carry) pairs.
 #include <cuda_runtime.h>
 #include <float.h>
@@ -322,7 +322,11 @@ __device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const floa
 // an instruction: a pair of sources is {x0, x1, y0, y1}, {z0, z1, m0, m1}.
 // With two bodies per lane (BPL = 2) one source meets both bodies: a source
 // is stored twice over, {x, x, y, y}, {z, z, m, m}.
-constexpr int LIST_CAP = 64;
+#ifndef NB_WALK_FLUSH
+#define NB_WALK_FLUSH 64
+#endif
+constexpr int FLUSH = NB_WALK_FLUSH;  // sources evaluated per flush (a multiple of 32)
+constexpr int LIST_CAP = 2 * FLUSH;
 constexpr int LEVELS = 11;
 
 template <int BPL>
@@ -410,7 +414,7 @@ __device__ __forceinline__ int warp_span_of(int incl, int pos)
 // bodies (failing either rejects), then, for the nodes still undecided, every
 // body.  Each level's stack holds at most 32 ranges, the children of one
 // round's nodes, since a level is refilled only once every deeper level is
-// empty.  Whenever 32 sources are listed, every lane adds them to its bodies.
+// empty.  Whenever FLUSH sources are listed, every lane adds them to its bodies.
 template <int BPL>
 struct WalkShared {
     float4 list[WALK_WARPS][LIST_CAP * BPL];  // float4 slots of the lists
@@ -517,15 +521,15 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         ax = ay = az = make_float2(0.f, 0.f);
     };
     int cnt = 0;  // listed sources (warp-uniform)
-    // 32 sources listed: add them, move the rest (< 32) to the front
-    auto flush32 = [&]() {
+    // FLUSH sources listed: add them, move the rest (< FLUSH) to the front
+    auto flush = [&]() {
         __syncwarp();
-        list_eval<ZEPS, BPL>(L4, 32, nx, ny, nz, e2, ax, ay, az);
+        list_eval<ZEPS, BPL>(L4, FLUSH, nx, ny, nz, e2, ax, ay, az);
         fold();
         __syncwarp();
 #pragma unroll
         for (int c = lane; c < LIST_F4 / 2; c += 32) list_s[warp][c] = list_s[warp][LIST_F4 / 2 + c];
-        cnt -= 32;
+        cnt -= FLUSH;
         __syncwarp();
     };
 
@@ -607,7 +611,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
             }
             cnt += __popc(am);
             nc += __popc(am);
-            if (cnt >= 32) flush32();
+            if (cnt >= FLUSH) flush();
         }
         // leaves: the bodies of all of this round's leaves, 32 list slots at a
         // time (lane l of a chunk fetches the chunk's l-th body)
@@ -632,7 +636,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
                                   rel(bh.z, bl.z, cz), bh.w);
                 }
                 cnt += kk;
-                if (cnt >= 32) flush32();
+                if (cnt >= FLUSH) flush();
             }
         }
     }
