@@ -59,6 +59,12 @@ inline int grid_cap(int64_t work)
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
+// 2^-L exactly (0 <= L <= 10), from its bit pattern.
+__device__ __forceinline__ double pow2_neg(int L)
+{
+    return __longlong_as_double((long long)(1023 - L) << 52);
+}
+
 // Float32 cube of the level-L cell with key prefix `pre`, exactly as the
 // oracle forms it (float64 lo + edge * index, rounded); .w of the corners
 // carries the child count (0) and first child (-1) until the node's own
@@ -72,7 +78,9 @@ __device__ __forceinline__ void cube_corners(const double *__restrict__ box, int
 #pragma unroll
         for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << bb;
     }
-    const double cell = __ddiv_rn(box[3], (double)(1u << L));
+    // ext / 2^L: the product with the exact power 2^-L rounds the same real
+    // value as the quotient, so it is the same number, without a division
+    const double cell = __dmul_rn(box[3], pow2_neg(L));
     float blo[3], bhi[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(TTPB) tree_moments_kernel(TreeView t, const do
 // Squared opening distance of a level, as the oracle computes it.
 __device__ __forceinline__ float open_dist2(double ext, int L, float theta)
 {
-    const float edge = (float)__ddiv_rn(ext, (double)(1u << L));
+    const float edge = (float)__dmul_rn(ext, pow2_neg(L));  // = ext / 2^L
     const float d = __fdiv_rn(edge, theta);
     return __fmul_rn(d, d);
 }
