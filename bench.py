@@ -932,6 +932,28 @@ def main():
                 "fp32_over_fp64": (pairs_per_eval / (avg_ms / 1e3) / 1e9) / v64,
                 "note": "one FP64 force evaluation of the first n bodies (the rate does not "
                         "depend on N once the GPU is full); FP64 error <= 1e-12 in the tests"}
+        # the same bodies in double-float arithmetic (float64 accuracy on the
+        # float32 pipe), with both errors against the oracle on sampled rows
+        with nbody.NBody(n64, "df64", device=dev.index) as nbd:
+            ad = torch.empty_like(p64)
+            nbd.forces(p64, m64, G, eps, out=ad)
+            nbd.profile(True)
+            nbd.forces(p64, m64, G, eps, out=ad)
+            kd, msd = nbd.profile_read(0)
+            nbd.profile(False)
+        hp64, hm64 = p64.cpu().numpy(), m64.cpu().numpy()
+        rows64 = inputs.sample_rows(n64, 256, seed=3)
+        ref64 = oracle.accel_rows(hp64, hm64, rows64, G, eps)
+        def _err(t):
+            v = t.cpu().numpy()[rows64]
+            return float((np.linalg.norm(v - ref64, axis=1) / np.linalg.norm(ref64, axis=1)).max())
+        vd = float(n64) ** 2 / (msd / 1e3) / 1e9
+        fp64["max_err"] = _err(a64)
+        fp64["df64_form"] = {"value": vd, "unit": UNIT, "n": n64, "kernel_ms": msd,
+                             "over_fp64": vd / v64, "max_err": _err(ad),
+                             "note": "double-float pair arithmetic (error-free sums and products "
+                                     "of float32 pairs), Morton order; max_err on 256 sampled "
+                                     "bodies vs the FP64 oracle"}
 
     forms = None
     if not args.no_forms and rank == 0 and args.workload == "throughput":

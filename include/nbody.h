@@ -53,8 +53,15 @@ typedef enum {
     NB_FP32 = 1,      /* float32 pair terms, one float32 running sum per body;
                          float32 modes need masses >= 0 (a negative mass can give
                          NB_ENONFINITE with the log-domain kernel variants) */
-    NB_FP32_COMP = 2  /* float32 pair terms, float32 sums per j-tile added into
+    NB_FP32_COMP = 2, /* float32 pair terms, float32 sums per j-tile added into
                          per-body Kahan-compensated (sum, carry) pairs */
+    NB_DF64 = 3       /* float64 accuracy on the float32 pipe: every pair term in
+                         double-float arithmetic (hi + lo float32 pairs formed with
+                         error-free sums and products, ~48 significant bits), bodies
+                         in Morton order with tile-local origins, float64 sums per
+                         j-tile; forces, steps and rollouts (the adjoint and the
+                         diagnostics run in float64, the batched kernel is
+                         float32 only) */
 } nb_precision;
 
 /* Flags for nb_step / nb_rollout / nb_step_batched. */

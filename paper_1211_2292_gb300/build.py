@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
-SOURCES = ["force_f32.cu", "force_f32_b.cu", "force_f32_batched.cu", "force_f64.cu",
+SOURCES = ["force_f32.cu", "force_f32_b.cu", "force_f32_batched.cu", "force_f64.cu", "force_df.cu",
            "adjoint.cu", "integrate.cu", "order.cu", "tree.cu", "noalloc.cu", "nbody_abi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -41,11 +41,12 @@ __device__ __forceinline__ void put_hilo(float4 *P, float4 *Plo, int i, double x
 
 template <typename V>
 __global__ void pack_kernel(int n, const double *__restrict__ pos, const double *__restrict__ mass,
-                            V *__restrict__ P)
+                            const int *__restrict__ perm, V *__restrict__ P)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = perm ? perm[k] : k;
         const double *x = pos + 3 * (size_t)i;
-        put(P, i, x[0], x[1], x[2], mass[i]);
+        put(P, k, x[0], x[1], x[2], mass[i]);
     }
 }
 
@@ -165,14 +166,14 @@ __global__ void energy_final_kernel(const double *__restrict__ red, int nparts, 
 
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P)
 {
-    pack_kernel<float4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, P);
+    pack_kernel<float4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, nullptr, P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const double *mass,
-                            double4 *P)
+                            double4 *P, const int *perm)
 {
-    pack_kernel<double4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, P);
+    pack_kernel<double4><<<grid_for(n), TPB, 0, s>>>(n, pos, mass, perm, P);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,8 @@ int f32_batched_variants();
 const KernelEntry &f32_batched_kernel(int variant, bool comp, bool zeps);
 int f64_force_variants();
 const KernelEntry &f64_force_kernel(int variant, bool zeps);
+int df_force_variants();  // double-float (float32-pipe, float64-accurate) force kernels
+const KernelEntry &df_force_kernel(int variant, bool zeps);
 const KernelEntry &f64_energy_kernel(bool zeps);
 int f32_vjp_variants();
 const KernelEntry &f32_vjp_kernel(int variant, bool zeps);
@@ -183,7 +185,9 @@ cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps,
 
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
-cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const double *mass, double4 *P);
+// P[k] = (x, y, z, m) of body perm[k] (perm NULL = identity).
+cudaError_t launch_pack_f64(cudaStream_t s, int n, const double *pos, const double *mass, double4 *P,
+                            const int *perm = nullptr);
 // v += half_dt a; x += dt v; then repack into P (double4) when f64, into the
 // float32 hi/lo pair (P, Plo) otherwise; P == NULL skips the packing.  Records
 // (x, v) before the update when rec_* is set.

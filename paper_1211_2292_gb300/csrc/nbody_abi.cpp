@@ -128,14 +128,20 @@ nb_status check_n(nb_ctx *c, int64_t n)
 }
 
 // ----------------------------------------------------------- kernel choice
-bool is_f64(const nb_ctx *c) { return c->prec == NB_FP64; }
+// Float64 state in the packed bodies (double4), float64 adjoint: NB_FP64 and
+// the double-float NB_DF64.
+bool f64_like(nb_precision p) { return p == NB_FP64 || p == NB_DF64; }
+bool is_f64(const nb_ctx *c) { return f64_like(c->prec); }
 
 int variant_count(int kind, nb_precision p)
 {
     switch (kind) {
-    case nb::KIND_FORCE: return p == NB_FP64 ? nb::f64_force_variants() : nb::f32_force_variants();
-    case nb::KIND_BATCHED: return p == NB_FP64 ? 0 : nb::f32_batched_variants();
-    case nb::KIND_VJP: return p == NB_FP64 ? nb::f64_vjp_variants() : nb::f32_vjp_variants();
+    case nb::KIND_FORCE:
+        return p == NB_FP64   ? nb::f64_force_variants()
+               : p == NB_DF64 ? nb::df_force_variants()
+                              : nb::f32_force_variants();
+    case nb::KIND_BATCHED: return f64_like(p) ? 0 : nb::f32_batched_variants();
+    case nb::KIND_VJP: return f64_like(p) ? nb::f64_vjp_variants() : nb::f32_vjp_variants();
     default: return 0;
     }
 }
@@ -145,17 +151,19 @@ const KernelEntry &kernel_for(int kind, nb_precision p, int v, bool zeps)
     const bool comp = p == NB_FP32_COMP;
     switch (kind) {
     case nb::KIND_FORCE:
-        return p == NB_FP64 ? nb::f64_force_kernel(v, zeps) : nb::f32_force_kernel(v, comp, zeps);
+        return p == NB_FP64   ? nb::f64_force_kernel(v, zeps)
+               : p == NB_DF64 ? nb::df_force_kernel(v, zeps)
+                              : nb::f32_force_kernel(v, comp, zeps);
     case nb::KIND_BATCHED: return nb::f32_batched_kernel(v, comp, zeps);
-    default: return p == NB_FP64 ? nb::f64_vjp_kernel(v, zeps) : nb::f32_vjp_kernel(v, zeps);
+    default: return f64_like(p) ? nb::f64_vjp_kernel(v, zeps) : nb::f32_vjp_kernel(v, zeps);
     }
 }
 
 // Untuned defaults.
 int default_variant(int kind, nb_precision p, int64_t n)
 {
-    (void)n;
-    if (kind == nb::KIND_FORCE) return p == NB_FP64 ? 0 : 0;
+    // double-float: 128-body tiles (more CTAs, more compact tiles) below 4096 bodies
+    if (kind == nb::KIND_FORCE && p == NB_DF64) return n < 4096 ? 2 : 0;
     return 0;
 }
 
@@ -267,7 +275,7 @@ nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double ep
     nb::ForceParams p;
     p.P = c->pack;
     p.Plo = is_f64(c) ? nullptr : lo_half(c);
-    p.perm = (!is_f64(c) && c->perm_active) ? c->perm : nullptr;
+    p.perm = c->perm_active ? c->perm : nullptr;
     p.n = (int)n;
     p.nsplit = S;
     p.eps2f = (float)(eps * eps);
@@ -283,10 +291,13 @@ nb_status force_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double ep
     return launch(c, k, (n + tile - 1) / tile * S, &p, s, 0);
 }
 
-// Whether float32 force calls with n bodies process them in Morton order.
+// Whether force calls with n bodies process them in Morton order: float32
+// modes from order_min_n bodies on; the double-float mode always (unless
+// mode 0), as its accuracy on close pairs rests on compact tiles.
 bool use_order(const nb_ctx *c, int64_t n)
 {
     if (c->prec == NB_FP64 || !c->perm) return false;
+    if (c->prec == NB_DF64) return c->order_mode != 0;
     return c->order_mode == 1 || (c->order_mode == 2 && n >= c->order_min_n);
 }
 
@@ -297,11 +308,17 @@ nb_status pack(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos, const do
                bool allow_order = true)
 {
     if (n == 0) return NB_OK;
+    c->perm_active = allow_order && use_order(c, n);
     if (is_f64(c)) {
-        NB_LAUNCHED(c, nb::launch_pack_f64(s, (int)n, pos, mass, (double4 *)c->pack));
+        if (c->perm_active) {
+            int k = 0;
+            NB_CUDA(c, nb::launch_morton_sort(s, (int)n, pos, c->order, c->perm, k));
+            c->launches += k;
+        }
+        NB_LAUNCHED(c, nb::launch_pack_f64(s, (int)n, pos, mass, (double4 *)c->pack,
+                                           c->perm_active ? c->perm : nullptr));
         return NB_OK;
     }
-    c->perm_active = allow_order && use_order(c, n);
     if (c->perm_active) {
         int k = 0;
         NB_CUDA(c, nb::launch_morton_sort(s, (int)n, pos, c->order, c->perm, k));
@@ -690,7 +707,7 @@ nb_status tree_step_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, d
 int min_tile_bodies()
 {
     int m = 1 << 30;
-    const nb_precision ps[] = {NB_FP64, NB_FP32, NB_FP32_COMP};
+    const nb_precision ps[] = {NB_FP64, NB_FP32, NB_FP32_COMP, NB_DF64};
     for (nb_precision p : ps)
         for (int kind = 0; kind < nb::KIND_COUNT; ++kind)
             for (int v = 0; v < variant_count(kind, p); ++v) {
@@ -798,7 +815,7 @@ const char *nb_last_error(const nb_ctx *ctx)
 
 int nb_variant_count(int kind, nb_precision p)
 {
-    if (kind < 0 || kind >= nb::KIND_COUNT || p < NB_FP64 || p > NB_FP32_COMP) return 0;
+    if (kind < 0 || kind >= nb::KIND_COUNT || p < NB_FP64 || p > NB_DF64) return 0;
     return variant_count(kind, p);
 }
 
@@ -818,7 +835,7 @@ nb_status nb_create(nb_ctx **out, int64_t n_max, nb_precision p, int device, voi
     *out = nullptr;
     if (n_max < 0 || n_max > (int64_t)0x7fffffff / 4)
         return failf(nullptr, NB_EINVAL, "n_max = %lld out of range", (long long)n_max);
-    if (p < NB_FP64 || p > NB_FP32_COMP) return failf(nullptr, NB_EINVAL, "bad precision %d", (int)p);
+    if (p < NB_FP64 || p > NB_DF64) return failf(nullptr, NB_EINVAL, "bad precision %d", (int)p);
     int count = 0;
     cudaError_t e = cudaGetDeviceCount(&count);
     if (e != cudaSuccess) {
@@ -1081,7 +1098,7 @@ nb_status nb_batch_plan(nb_ctx *c, int64_t nsys, const int64_t *offsets)
 {
     if (!c) return NB_EINVAL;
     DeviceGuard guard(c->device);
-    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    if (is_f64(c)) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
     if (nsys < 0 || !offsets) return failf(c, NB_EINVAL, "bad nsys/offsets");
     if (offsets[0] != 0) return failf(c, NB_EINVAL, "offsets[0] must be 0");
     for (int64_t k = 0; k < nsys; ++k)
@@ -1131,7 +1148,7 @@ nb_status nb_forces_batched(nb_ctx *c, const double *pos, const double *mass, do
 {
     if (!c) return NB_EINVAL;
     DeviceGuard guard(c->device);
-    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    if (is_f64(c)) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
     NB_TRY(check_scalars(c, G, eps));
     const int64_t n = c->batch_n;
     const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
@@ -1148,7 +1165,7 @@ nb_status nb_step_batched(nb_ctx *c, double *pos, double *vel, const double *mas
 {
     if (!c) return NB_EINVAL;
     DeviceGuard guard(c->device);
-    if (c->prec == NB_FP64) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
+    if (is_f64(c)) return failf(c, NB_EINVAL, "the batched kernel needs an FP32 context");
     NB_TRY(check_scalars(c, G, eps));
     if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
     if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");

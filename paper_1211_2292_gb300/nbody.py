@@ -16,8 +16,8 @@ import threading
 
 from . import build as _build
 
-NB_FP64, NB_FP32, NB_FP32_COMP = 0, 1, 2
-PRECISIONS = {"fp64": NB_FP64, "fp32": NB_FP32, "fp32_comp": NB_FP32_COMP}
+NB_FP64, NB_FP32, NB_FP32_COMP, NB_DF64 = 0, 1, 2, 3
+PRECISIONS = {"fp64": NB_FP64, "fp32": NB_FP32, "fp32_comp": NB_FP32_COMP, "df64": NB_DF64}
 NB_ACC_VALID, NB_USE_GRAPH = 1, 2
 NB_BWD_AT_END, NB_BWD_AT_START = 1, 2
 KIND_FORCE, KIND_BATCHED, KIND_VJP = 0, 1, 2

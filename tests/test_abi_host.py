@@ -52,13 +52,17 @@ def test_create_without_device_fails_cleanly():
 
 
 def test_variant_tables():
-    for prec in ("fp64", "fp32", "fp32_comp"):
+    for prec in ("fp64", "fp32", "fp32_comp", "df64"):
         v = nbody.variants(nbody.KIND_FORCE, prec)
         assert v and all(t % 32 == 0 and j % t == 0 for t, i, j in v)
         if prec != "fp64":
             assert all(i % 2 == 0 for _, i, _ in v)  # float32x2 pairs
     assert nbody.variants(nbody.KIND_BATCHED, "fp64") == []
+    assert nbody.variants(nbody.KIND_BATCHED, "df64") == []
+    # the double-float context differentiates in float64
+    assert nbody.variants(nbody.KIND_VJP, "df64") == nbody.variants(nbody.KIND_VJP, "fp64")
     assert nbody.load().nb_variant_count(9, 0) == 0
+    assert nbody.load().nb_variant_count(0, 4) == 0
 
 
 def _waves_eff(items, slots):

@@ -2,6 +2,7 @@
 
 Tolerances (per-body relative error e_i = |a_i - a_i^ref| / |a_i^ref|):
   FP64 form:        max e_i <= 1e-12
+  double-float:     max e_i <= 1e-12, RMS e_i <= 1e-13 (48-bit pair arithmetic)
   FP32 compensated: RMS e_i <= 1e-5, max e_i <= 1e-4
   FP32 plain:       RMS e_i <= 1e-4 at N <= 4097 (one float32 running sum)
 Sizes span one and several tiles with ragged tails; every compiled variant
@@ -40,6 +41,29 @@ def test_fp64_matches_oracle(cuda, n):
 
 
 @pytest.mark.parametrize("n", SIZES)
+def test_df64_matches_oracle(cuda, n):
+    b = inputs.plummer(n, seed=300 + n)
+    ref = oracle.accel(b.pos, b.mass, 1.0, 0.01)
+    a = _forces(cuda, "df64", b, 1.0, 0.01)
+    if n == 1:
+        assert np.all(a == 0)
+        return
+    e = relerr_per_body(a, ref)
+    assert e.max() <= 1e-12 and np.sqrt((e ** 2).mean()) <= 1e-13
+
+
+def test_df64_at_the_precision_and_throughput_workloads(cuda):
+    # N = 65,536 Plummer (eps 0.005) and the first 262,144 bodies of the
+    # two-sphere workload (eps 0.002): 2048 sampled bodies each
+    for b, eps in ((inputs.plummer(65536, seed=1), 0.005),
+                   (inputs.two_plummer(131072, seed=2), 0.002)):
+        rows = inputs.sample_rows(b.n, 2048, seed=1)
+        ref = oracle.accel_rows(b.pos, b.mass, rows, 1.0, eps)
+        e = relerr_per_body(_forces(cuda, "df64", b, 1.0, eps)[rows], ref)
+        assert e.max() <= 1e-12 and np.sqrt((e ** 2).mean()) <= 1e-13
+
+
+@pytest.mark.parametrize("n", SIZES)
 def test_fp32_comp_matches_oracle(cuda, n):
     b = inputs.plummer(n, seed=100 + n)
     ref = oracle.accel(b.pos, b.mass, 1.0, 0.005)
@@ -59,11 +83,11 @@ def test_fp32_plain_matches_oracle(cuda, n):
     assert np.sqrt((e ** 2).mean()) <= 1e-4
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp", "df64"])
 def test_every_variant_and_forced_splits(cuda, prec):
     b = inputs.plummer(3001, seed=7)
     ref = oracle.accel(b.pos, b.mass, 1.3, 0.02)
-    tol = 1e-12 if prec == "fp64" else 1e-4
+    tol = 1e-12 if prec in ("fp64", "df64") else 1e-4
     nvar = len(nbody.variants(nbody.KIND_FORCE, prec))
     for v in range(nvar):
         for split in (1, 3, 7):
@@ -72,20 +96,21 @@ def test_every_variant_and_forced_splits(cuda, prec):
             assert e.max() <= tol, (v, split, e.max())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_comp", "df64"])
 def test_zero_softening_skips_self_pair(cuda, prec):
     x = np.array([[0.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
     m = np.array([1.0, 3.0])
     b = inputs.Bodies(x, np.zeros_like(x), m)
     a = _forces(cuda, prec, b, 1.0, 0.0)
-    np.testing.assert_allclose(a, [[0, 0.75, 0], [0, -0.25, 0]], rtol=1e-6 if prec != "fp64" else 1e-15)
+    rtol = {"fp64": 1e-15, "df64": 1e-13}.get(prec, 1e-6)
+    np.testing.assert_allclose(a, [[0, 0.75, 0], [0, -0.25, 0]], rtol=rtol)
     b = inputs.random_system(33, seed=3)
     ref = oracle.accel(b.pos, b.mass, 1.0, 0.0)
     e = relerr_per_body(_forces(cuda, prec, b, 1.0, 0.0), ref)
-    assert np.isfinite(e).all() and e.max() <= (1e-12 if prec == "fp64" else 1e-4)
+    assert np.isfinite(e).all() and e.max() <= (1e-12 if prec in ("fp64", "df64") else 1e-4)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_comp"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_comp", "df64"])
 def test_deterministic_across_calls(cuda, prec):
     b = inputs.plummer(5000, seed=9)
     with nbody.NBody(b.n, prec) as nb:

@@ -42,7 +42,18 @@ def test_plain_fp64_config_n1024(cuda):
     assert np.abs(e[6:9]).max() <= 1e-13
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_comp"])
+def test_plain_config_in_double_float(cuda):
+    # The same run through the double-float form: float64 accuracy (forces
+    # <= 1e-12) from the float32 pipe, Morton-ordered, over 10 steps
+    b = inputs.plummer(1024, seed=0)
+    rx, rv, ra = oracle.kdk(b.pos, b.vel, b.mass, 1.0, 0.01, 1e-3, 10)
+    x, v, a = _run(cuda, "df64", b, 1.0, 0.01, 1e-3, 10)
+    assert relerr_per_body(a, ra).max() <= 1e-12
+    assert np.abs(x - rx).max() <= 1e-13
+    assert np.abs(v - rv).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_comp", "df64"])
 @pytest.mark.parametrize("n", [1, 2, 33, 1000])
 def test_energy_matches_oracle(cuda, prec, n):
     b = inputs.plummer(n, seed=30 + n)
@@ -79,7 +90,7 @@ def test_zero_steps_is_force_only(cuda):
     assert relerr_per_body(a, oracle.accel(b.pos, b.mass, 1.0, 0.01)).max() <= 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_comp"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_comp", "df64"])
 def test_graph_matches_eager_and_acc_valid(cuda, prec):
     b = inputs.plummer(777, seed=7)
     x1, v1, a1 = _run(cuda, prec, b, 1.0, 0.01, 1e-3, 6)
