@@ -35,12 +35,11 @@ struct DF2 {
     float2 h, l;
 };
 
-__device__ __forceinline__ float2 neg2(float2 a) { return mul2(a, make_float2(-1.f, -1.f)); }
+// Negation as a sign change of both halves (the compiler can fold it into
+// the consuming instruction's operand).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 // b - a, one rounding
-__device__ __forceinline__ float2 sub_from(float2 a, float2 b)
-{
-    return fma2(a, make_float2(-1.f, -1.f), b);
-}
+__device__ __forceinline__ float2 sub_from(float2 a, float2 b) { return add2(b, neg2(a)); }
 
 // s + e == a + b exactly (six operations, no ordering of |a|, |b| needed)
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
