@@ -15,7 +15,8 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_comp", 5e-5), ("fp32", 5e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_comp", 5e-5), ("fp32", 5e-5),
+                                      ("df64", 1e-12)])
 @pytest.mark.parametrize("n", [2, 33, 1000, 2049])
 def test_force_vjp_matches_oracle(cuda, prec, tol, n):
     # FP32 tolerance: the float32 rounding of the positions perturbs each
@@ -125,7 +126,7 @@ def test_rollout_grad_central_differences_n64(cuda):
         assert abs(fd - gm[i]) <= 1e-6 * np.abs(gm).max()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32_comp", 1e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32_comp", 1e-3), ("df64", 1e-10)])
 def test_rollout_grad_oracle_adjoint_n1024(cuda, prec, tol):
     # Differentiation workload at N = 1024: 200 steps of dt = 1e-3, eps = 0.01,
     # checkpoints every 20 steps, target from the oracle run of a perturbed start.
