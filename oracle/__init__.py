@@ -64,6 +64,13 @@ def _bind(lib):
     lib.oracle_bh_groups.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                      i64, _I, _I, _D, _I]
     lib.oracle_bh_groups.restype = ctypes.c_int
+    lib.oracle_fmm_forces.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                      _D, _I, _I]
+    lib.oracle_fmm_forces.restype = ctypes.c_int
+    lib.oracle_fmm_deriv.argtypes = [ctypes.c_int, _D, dbl, _D]
+    lib.oracle_fmm_deriv.restype = ctypes.c_int
+    lib.oracle_fmm_pair.argtypes = [ctypes.c_int, _D, _D, dbl, i64, _D, _D, i64, _D, _D]
+    lib.oracle_fmm_pair.restype = ctypes.c_int
     for f in (lib.oracle_accel, lib.oracle_accel_rows, lib.oracle_energy,
               lib.oracle_kdk, lib.oracle_force_vjp):
         f.restype = None
@@ -212,3 +219,57 @@ def bh_groups(pos, mass, G, eps, theta, leaf_cap, group, sel):
     if rc != 0:
         raise ValueError("oracle_bh_groups: bad leaf_cap/group or group index")
     return idx, acc, cnt
+
+
+def fmm_multi_indices(p):
+    """Multi-indices (a, b, c) of order <= p in the oracle's slot order
+    (order by order; within an order a descending, then b descending)."""
+    return [(a, k - a - c, c) for k in range(p + 1) for a in range(k, -1, -1)
+            for c in range(0, k - a + 1)]
+
+
+def fmm_deriv(p, r, eps=0.0):
+    """d^n g(r) for g(r) = (|r|^2 + eps^2)^{-1/2}, every |n| <= p, in the
+    slot order of fmm_multi_indices."""
+    r = _f64(r, (3,))
+    out = np.zeros((p + 1) * (p + 2) * (p + 3) // 6)
+    if _load().oracle_fmm_deriv(int(p), _p(r), float(eps), _p(out)) != 0:
+        raise ValueError("oracle_fmm_deriv: order out of range")
+    return out
+
+
+def fmm_pair(p, zA, zB, eps, xs, ms, xt):
+    """The FMM's expansion chain alone: sources (xs, ms) expanded about zB,
+    translated to a local expansion about zA and differentiated at the
+    targets xt; accelerations (G = 1), (len(xt), 3)."""
+    ms = _f64(ms)
+    xs = _f64(xs, (ms.shape[0], 3))
+    xt = np.ascontiguousarray(xt, dtype=np.float64).reshape(-1, 3)
+    zA, zB = _f64(zA, (3,)), _f64(zB, (3,))
+    out = np.zeros((xt.shape[0], 3))
+    if _load().oracle_fmm_pair(int(p), _p(zA), _p(zB), float(eps), ms.shape[0], _p(xs), _p(ms),
+                               xt.shape[0], _p(xt), _p(out)) != 0:
+        raise ValueError("oracle_fmm_pair: order out of range")
+    return out
+
+
+def fmm_forces(pos, mass, G=1.0, eps=0.0, theta=0.5, order=4, leaf_cap=16, counts=False):
+    """Fast-multipole accelerations (readings in nbody_oracle.c).
+
+    Returns acc (n, 3), stats {nodes, leaves, expansions, direct_pairs} and,
+    with counts=True, per body (source cells, bodies in them, direct
+    partners) (n, 3).
+    """
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    out = np.zeros((n, 3))
+    st = np.zeros(4, dtype=np.int64)
+    cnt = np.zeros((n, 3), dtype=np.int64) if counts else None
+    rc = _load().oracle_fmm_forces(n, _p(x), _p(m), float(G), float(eps), float(theta),
+                                   int(order), int(leaf_cap), _p(out), st.ctypes.data_as(_I),
+                                   cnt.ctypes.data_as(_I) if counts else None)
+    if rc != 0:
+        raise ValueError(f"oracle_fmm_forces: bad arguments ({rc})")
+    stats = dict(zip(("nodes", "leaves", "expansions", "direct_pairs"), (int(v) for v in st)))
+    return (out, stats, cnt) if counts else (out, stats)

@@ -348,6 +348,7 @@ typedef struct {
     uint32_t *key0, *key;
     float crit2[11];
     int64_t leaves;
+    double box_lo[3], ext;  /* the root cube: corner and edge */
 } bh_prep;
 
 static void bh_prepare(bh_prep *P, int64_t n, const double *x, const double *m, double theta,
@@ -424,6 +425,8 @@ static void bh_prepare(bh_prep *P, int64_t n, const double *x, const double *m, 
         P->crit2[L] = d * d;
     }
     P->t = t;
+    for (int c = 0; c < 3; ++c) P->box_lo[c] = lo[c];
+    P->ext = ext;
     P->perm = perm;
     P->key0 = key0;
     P->key = key;
@@ -599,4 +602,447 @@ int oracle_bh_groups(int64_t n, const double *x, const double *m, double G, doub
     bh_work_free(&W);
     bh_release(&P);
     return 0;
+}
+
+/*
+ * Fast multipole method: the O(N) method the paper names as the successor
+ * of its tree code (Sec. VI, after Greengard and Rokhlin, ref. [20]).  The
+ * paper gives no formulation; the readings here are:
+ *  - the tree is the Barnes-Hut tree above (same cube, keys and leaf rule);
+ *  - every cell carries a Cartesian Taylor expansion about its cube's centre
+ *    z, with multi-indices n = (a, b, c), x^n = x^a y^b z^c, n! = a! b! c!
+ *    and order p: the multipole moments
+ *        Mh_n = sum_{j in cell} m_j (-(x_j - z))^n / n!,      |n| <= p;
+ *  - the kernel is the softened one, g(r) = (|r|^2 + eps^2)^{-1/2}: the
+ *    acceleration is G times the gradient of sum_j m_j g(x - x_j).  Its
+ *    derivatives T_n = d^n g follow from g = f(|r|^2 / 2), whose m-th
+ *    derivative is D_m = (-1)^m (2m-1)!! (|r|^2 + eps^2)^{-(2m+1)/2}, by
+ *        d^n f_m = r_c d^{n-e_c} f_{m+1} + (n_c - 1) d^{n-2e_c} f_{m+1}
+ *    (Leibniz's rule on d^n f_m = d^{n-e_c} (r_c f_{m+1}), c any axis with
+ *    n_c >= 1; the first such axis here);
+ *  - a source cell B acts on a target cell A through the local expansion
+ *        L_k = sum_{|n| <= p - |k|} Mh_n T_{n+k}(z_A - z_B),    |k| <= p,
+ *    the Taylor polynomial sum_k L_k u^k / k! (u = x - z_A) of B's potential
+ *    in A; a body's far-field acceleration is G times the gradient of the
+ *    polynomials of its leaf and of every ancestor of its leaf:
+ *        a_c = G sum_{A'} sum_{|k| <= p-1} L^{A'}_{k+e_c} u^k / k!;
+ *  - A and B are well separated when |z_A - z_B| >= (r_A + r_B) / theta,
+ *    r the cube's circumradius (sqrt(3)/2 of its edge).  In units of
+ *    h = ext / 2048 a level-L centre is an odd multiple of 2^(10-L) and its
+ *    edge is 2^(11-L), so the test is exact: the integer
+ *    D2 = |c_A - c_B|^2 against 0.75 (e_A + e_B)^2 / theta^2 in double;
+ *  - which pairs interact: the dual-tree traversal from (root, root).
+ *    Each target cell takes the candidates its parent handed down (the root
+ *    takes the root).  For target A and candidate B: well separated -> B's
+ *    expansion acts on A; else if A and B are leaves -> their bodies
+ *    interact directly (self pair excluded); else if A is a leaf -> B's
+ *    children are candidates of A; else if B is a leaf or smaller than A ->
+ *    B goes down to A's children; else (B as large as A) B's children go
+ *    down to A's children.
+ * Every body so meets every other body exactly once: directly, or inside a
+ * source cell acting on its leaf or on an ancestor of its leaf.
+ *
+ * The oracle takes the definitions as written: moments summed over each
+ * cell's own bodies, every local polynomial evaluated at the body.  It does
+ * not translate expansions between cells (the moment and local translations
+ * of an FMM are exact rewritings of these sums).
+ */
+#define FMM_MAX_ORDER 12
+
+typedef struct {
+    int p, nt;        /* order; multi-indices of order <= p */
+    int (*mi)[3];     /* multi-index of each slot, graded (order by order) */
+    double *inv_fact; /* 1 / n! per slot */
+} fmm_basis;
+
+/* Slot of (a, b, c): orders below k first, then a descending, b descending. */
+static int fmm_slot(int a, int b, int c)
+{
+    int k = a + b + c, s = b + c;
+    return k * (k + 1) * (k + 2) / 6 + s * (s + 1) / 2 + c;
+}
+
+static void fmm_basis_init(fmm_basis *B, int p)
+{
+    B->p = p;
+    B->nt = (p + 1) * (p + 2) * (p + 3) / 6;
+    B->mi = (int(*)[3])malloc(sizeof(int[3]) * (size_t)B->nt);
+    B->inv_fact = (double *)malloc(sizeof(double) * (size_t)B->nt);
+    double f[FMM_MAX_ORDER + 1];
+    f[0] = 1.0;
+    for (int e = 1; e <= FMM_MAX_ORDER; ++e) f[e] = f[e - 1] * (double)e;
+    for (int k = 0; k <= p; ++k)
+        for (int a = k; a >= 0; --a)
+            for (int b = k - a; b >= 0; --b) {
+                int c = k - a - b, q = fmm_slot(a, b, c);
+                B->mi[q][0] = a;
+                B->mi[q][1] = b;
+                B->mi[q][2] = c;
+                B->inv_fact[q] = 1.0 / (f[a] * f[b] * f[c]);
+            }
+}
+
+static void fmm_basis_free(fmm_basis *B)
+{
+    free(B->mi);
+    free(B->inv_fact);
+}
+
+/* T_n(r) = d^n g(r) for every slot; work holds (p + 1) * nt doubles. */
+static void fmm_deriv(const fmm_basis *B, const double r[3], double eps, double *out, double *work)
+{
+    const int p = B->p, nt = B->nt;
+    double s2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps * eps;
+    double *T = work; /* T[m * nt + q] = d^n f_m */
+    T[0] = 1.0 / sqrt(s2);
+    for (int m = 1; m <= p; ++m) T[m * nt] = -(double)(2 * m - 1) * T[(m - 1) * nt] / s2;
+    for (int q = 1; q < nt; ++q) {
+        const int *n = B->mi[q];
+        int k = n[0] + n[1] + n[2];
+        int c = n[0] > 0 ? 0 : (n[1] > 0 ? 1 : 2);
+        int d[3] = {n[0], n[1], n[2]};
+        d[c] -= 1;
+        int q1 = fmm_slot(d[0], d[1], d[2]), q2 = -1;
+        if (n[c] >= 2) {
+            d[c] -= 1;
+            q2 = fmm_slot(d[0], d[1], d[2]);
+        }
+        for (int m = 0; m + k <= p; ++m) {
+            double v = r[c] * T[(m + 1) * nt + q1];
+            if (q2 >= 0) v += (double)(n[c] - 1) * T[(m + 1) * nt + q2];
+            T[m * nt + q] = v;
+        }
+    }
+    memcpy(out, T, sizeof(double) * (size_t)nt);
+}
+
+/* Public form of fmm_deriv for the pins: out receives (p+1)(p+2)(p+3)/6
+ * values in slot order.  Returns -1 for p outside [0, FMM_MAX_ORDER]. */
+int oracle_fmm_deriv(int p, const double *r, double eps, double *out)
+{
+    if (p < 0 || p > FMM_MAX_ORDER) return -1;
+    fmm_basis B;
+    fmm_basis_init(&B, p);
+    double *work = (double *)malloc(sizeof(double) * (size_t)((p + 1) * B.nt));
+    fmm_deriv(&B, r, eps, out, work);
+    free(work);
+    fmm_basis_free(&B);
+    return 0;
+}
+
+/* Mh += the moments about z of a body of mass mj at xj. */
+static void fmm_moments_add(const fmm_basis *B, const double *xj, double mj, const double *z,
+                            double *Mh)
+{
+    double pw[3][FMM_MAX_ORDER + 1];
+    for (int c = 0; c < 3; ++c) {
+        double y = -(xj[c] - z[c]);
+        pw[c][0] = 1.0;
+        for (int e = 1; e <= B->p; ++e) pw[c][e] = pw[c][e - 1] * y;
+    }
+    for (int q = 0; q < B->nt; ++q)
+        Mh[q] += mj * pw[0][B->mi[q][0]] * pw[1][B->mi[q][1]] * pw[2][B->mi[q][2]] * B->inv_fact[q];
+}
+
+/* L += the local expansion, about z_A, of the moments Mh about z_B;
+ * r = z_A - z_B.  Tn holds nt doubles, work (p + 1) nt. */
+static void fmm_local_add(const fmm_basis *B, const double *Mh, const double *r, double eps,
+                          double *L, double *Tn, double *work)
+{
+    const int p = B->p;
+    fmm_deriv(B, r, eps, Tn, work);
+    for (int kq = 0; kq < B->nt; ++kq) {
+        const int *k = B->mi[kq];
+        int kk = k[0] + k[1] + k[2];
+        double s = 0.0;
+        for (int nq = 0; nq < B->nt; ++nq) {
+            const int *n = B->mi[nq];
+            if (n[0] + n[1] + n[2] > p - kk) break; /* slots are graded */
+            s += Mh[nq] * Tn[fmm_slot(n[0] + k[0], n[1] + k[1], n[2] + k[2])];
+        }
+        L[kq] += s;
+    }
+}
+
+/* a += the gradient of sum_k L_k u^k / k! at u. */
+static void fmm_grad_add(const fmm_basis *B, const double *L, const double *u, double *a)
+{
+    double pw[3][FMM_MAX_ORDER + 1];
+    for (int c = 0; c < 3; ++c) {
+        pw[c][0] = 1.0;
+        for (int e = 1; e <= B->p; ++e) pw[c][e] = pw[c][e - 1] * u[c];
+    }
+    for (int kq = 0; kq < B->nt; ++kq) {
+        const int *k = B->mi[kq];
+        if (k[0] + k[1] + k[2] > B->p - 1) break;
+        double w = pw[0][k[0]] * pw[1][k[1]] * pw[2][k[2]] * B->inv_fact[kq];
+        a[0] += L[fmm_slot(k[0] + 1, k[1], k[2])] * w;
+        a[1] += L[fmm_slot(k[0], k[1] + 1, k[2])] * w;
+        a[2] += L[fmm_slot(k[0], k[1], k[2] + 1)] * w;
+    }
+}
+
+/* The expansion chain alone, for the pins: sources (xs, ms) expanded about
+ * zB act, through the local expansion about zA, on the targets xt; acc
+ * [nt][3] receives the accelerations with G = 1.  Returns -1 for p outside
+ * [1, FMM_MAX_ORDER]. */
+int oracle_fmm_pair(int p, const double *zA, const double *zB, double eps, int64_t ns,
+                    const double *xs, const double *ms, int64_t ntg, const double *xt,
+                    double *acc)
+{
+    if (p < 1 || p > FMM_MAX_ORDER) return -1;
+    fmm_basis B;
+    fmm_basis_init(&B, p);
+    double *Mh = (double *)calloc((size_t)B.nt, sizeof(double));
+    double *L = (double *)calloc((size_t)B.nt, sizeof(double));
+    double *Tn = (double *)malloc(sizeof(double) * (size_t)B.nt);
+    double *work = (double *)malloc(sizeof(double) * (size_t)((p + 1) * B.nt));
+    for (int64_t j = 0; j < ns; ++j) fmm_moments_add(&B, xs + 3 * j, ms[j], zB, Mh);
+    double r[3] = {zA[0] - zB[0], zA[1] - zB[1], zA[2] - zB[2]};
+    fmm_local_add(&B, Mh, r, eps, L, Tn, work);
+    for (int64_t i = 0; i < ntg; ++i) {
+        double u[3] = {xt[3 * i] - zA[0], xt[3 * i + 1] - zA[1], xt[3 * i + 2] - zA[2]};
+        acc[3 * i] = acc[3 * i + 1] = acc[3 * i + 2] = 0.0;
+        fmm_grad_add(&B, L, u, acc + 3 * i);
+    }
+    free(Mh); free(L); free(Tn); free(work);
+    fmm_basis_free(&B);
+    return 0;
+}
+
+typedef struct {
+    int32_t *v;
+    int64_t n, cap;
+} fmm_list;
+
+static void fmm_push(fmm_list *l, int32_t x)
+{
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 16;
+        l->v = (int32_t *)realloc(l->v, sizeof(int32_t) * (size_t)l->cap);
+    }
+    l->v[l->n++] = x;
+}
+
+typedef struct {
+    const bh_prep *P;
+    int64_t nn;
+    int *leaf, (*ci)[3];
+    double crit[11][11];
+    fmm_list *m2l, *p2p; /* per node: source cells of its expansion; source leaves */
+    int err;
+} fmm_trav;
+
+static int fmm_separated(const fmm_trav *T, int64_t a, int64_t b)
+{
+    int64_t d2 = 0;
+    for (int c = 0; c < 3; ++c) {
+        int64_t d = (int64_t)T->ci[a][c] - (int64_t)T->ci[b][c];
+        d2 += d * d;
+    }
+    return (double)d2 >= T->crit[T->P->t.nodes[a].level][T->P->t.nodes[b].level];
+}
+
+/* Candidate b of the leaf a: b's subtree is walked. */
+static void fmm_leaf_visit(fmm_trav *T, int64_t a, int64_t b)
+{
+    if (fmm_separated(T, a, b)) {
+        fmm_push(&T->m2l[a], (int32_t)b);
+    } else if (T->leaf[b]) {
+        fmm_push(&T->p2p[a], (int32_t)b);
+    } else {
+        const bh_node *nb = &T->P->t.nodes[b];
+        for (int o = 0; o < 8; ++o)
+            if (nb->child[o] >= 0) fmm_leaf_visit(T, a, nb->child[o]);
+    }
+}
+
+/* Target a with the candidates handed down to it. */
+static void fmm_down(fmm_trav *T, int64_t a, const int32_t *cand, int64_t ncand)
+{
+    if (T->leaf[a]) {
+        for (int64_t q = 0; q < ncand; ++q) fmm_leaf_visit(T, a, cand[q]);
+        return;
+    }
+    const bh_node *na = &T->P->t.nodes[a];
+    fmm_list down = {0, 0, 0};
+    for (int64_t q = 0; q < ncand; ++q) {
+        int64_t b = cand[q];
+        const bh_node *nb = &T->P->t.nodes[b];
+        if (fmm_separated(T, a, b)) {
+            fmm_push(&T->m2l[a], (int32_t)b);
+        } else if (T->leaf[b] || nb->level > na->level) {
+            fmm_push(&down, (int32_t)b);
+        } else if (nb->level == na->level) {
+            for (int o = 0; o < 8; ++o)
+                if (nb->child[o] >= 0) fmm_push(&down, (int32_t)nb->child[o]);
+        } else {
+            T->err = 1; /* a larger non-leaf candidate never reaches a non-leaf */
+        }
+    }
+    for (int o = 0; o < 8; ++o)
+        if (na->child[o] >= 0) fmm_down(T, na->child[o], down.v, down.n);
+    free(down.v);
+}
+
+/*
+ * Accelerations by the FMM of the readings above, order p (1..12), opening
+ * parameter theta >= 0 (theta = 0: nothing is well separated, every pair
+ * interacts directly).  stats (optional) receives {nodes, leaves,
+ * cell-cell expansions, body-body pairs (self pairs included)}; cnt
+ * (optional, [n][3]) receives per body the number of source cells acting on
+ * its leaf and the leaf's ancestors, the bodies those cells hold, and the
+ * bodies it meets directly (itself included): the last two sum to n.
+ * Returns -1 for bad arguments.
+ */
+int oracle_fmm_forces(int64_t n, const double *x, const double *m, double G, double eps,
+                      double theta, int p, int leaf_cap, double *acc, int64_t *stats,
+                      int64_t *cnt)
+{
+    if (leaf_cap < 1 || p < 1 || p > FMM_MAX_ORDER || !(theta >= 0.0)) return -1;
+    if (n <= 0) return 0;
+    bh_prep P;
+    bh_prepare(&P, n, x, m, theta, leaf_cap);
+    const bh_tree *t = &P.t;
+    const int64_t nn = t->nnodes;
+    fmm_basis B;
+    fmm_basis_init(&B, p);
+    const int nt = B.nt;
+
+    fmm_trav T;
+    T.P = &P;
+    T.nn = nn;
+    T.err = 0;
+    T.leaf = (int *)malloc(sizeof(int) * (size_t)nn);
+    T.ci = (int(*)[3])malloc(sizeof(int[3]) * (size_t)nn);
+    T.m2l = (fmm_list *)calloc((size_t)nn, sizeof(fmm_list));
+    T.p2p = (fmm_list *)calloc((size_t)nn, sizeof(fmm_list));
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
+    double(*z)[3] = (double(*)[3])malloc(sizeof(double[3]) * (size_t)nn);
+    parent[0] = -1;
+    for (int64_t id = 0; id < nn; ++id) {
+        const bh_node *nd = &t->nodes[id];
+        int leaf = 1;
+        for (int o = 0; o < 8; ++o)
+            if (nd->child[o] >= 0) {
+                leaf = 0;
+                parent[nd->child[o]] = id;
+            }
+        T.leaf[id] = leaf;
+        uint32_t ic[3] = {0, 0, 0};
+        for (int b = 0; b < nd->level; ++b) {
+            uint32_t trip = (nd->prefix >> (3 * b)) & 7u;
+            for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << b;
+        }
+        double cell = P.ext / (double)(1u << nd->level);
+        for (int c = 0; c < 3; ++c) {
+            T.ci[id][c] = (int)((2u * ic[c] + 1u) << (10 - nd->level));
+            z[id][c] = P.box_lo[c] + cell * ((double)ic[c] + 0.5);
+        }
+    }
+    for (int la = 0; la <= 10; ++la)
+        for (int lb = 0; lb <= 10; ++lb) {
+            double s = (double)((1 << (11 - la)) + (1 << (11 - lb)));
+            T.crit[la][lb] = 0.75 * s * s / (theta * theta);
+        }
+    int32_t root = 0;
+    fmm_down(&T, 0, &root, 1);
+
+    /* moments of every cell, from its own bodies */
+    double *Mh = (double *)calloc((size_t)(nn * nt), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t id = 0; id < nn; ++id) {
+        const bh_node *nd = &t->nodes[id];
+        for (int64_t k = nd->start; k < nd->end; ++k) {
+            int64_t j = P.perm[k];
+            fmm_moments_add(&B, x + 3 * j, m[j], z[id], Mh + id * nt);
+        }
+    }
+    /* local expansion of every cell from its own source cells */
+    double *L = (double *)calloc((size_t)(nn * nt), sizeof(double));
+#pragma omp parallel
+    {
+        double *Tn = (double *)malloc(sizeof(double) * (size_t)nt);
+        double *work = (double *)malloc(sizeof(double) * (size_t)((p + 1) * nt));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t a = 0; a < nn; ++a) {
+            for (int64_t q = 0; q < T.m2l[a].n; ++q) {
+                int64_t b = T.m2l[a].v[q];
+                double r[3];
+                for (int c = 0; c < 3; ++c) r[c] = z[a][c] - z[b][c];
+                fmm_local_add(&B, Mh + b * nt, r, eps, L + a * nt, Tn, work);
+            }
+        }
+        free(Tn);
+        free(work);
+    }
+    /* every body: the far field of its leaf and the leaf's ancestors, and
+     * its direct partners */
+    int64_t npairs = 0, nexp = 0, nleaves = 0;
+    for (int64_t a = 0; a < nn; ++a) {
+        nexp += T.m2l[a].n;
+        nleaves += T.leaf[a];
+    }
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : npairs)
+    for (int64_t a = 0; a < nn; ++a) {
+        if (!T.leaf[a]) continue;
+        const bh_node *na = &t->nodes[a];
+        int64_t ncells = 0, nfar = 0, nnear = 0;
+        for (int64_t q = 0; q < T.p2p[a].n; ++q) {
+            const bh_node *nb = &t->nodes[T.p2p[a].v[q]];
+            nnear += nb->end - nb->start;
+        }
+        for (int64_t an = a; an >= 0; an = parent[an])
+            for (int64_t q = 0; q < T.m2l[an].n; ++q) {
+                const bh_node *nb = &t->nodes[T.m2l[an].v[q]];
+                ++ncells;
+                nfar += nb->end - nb->start;
+            }
+        npairs += nnear * (na->end - na->start);
+        for (int64_t k = na->start; k < na->end; ++k) {
+            int64_t i = P.perm[k];
+            double ai[3] = {0, 0, 0};
+            for (int64_t an = a; an >= 0; an = parent[an]) {
+                double u[3];
+                for (int c = 0; c < 3; ++c) u[c] = x[3 * i + c] - z[an][c];
+                fmm_grad_add(&B, L + an * nt, u, ai);
+            }
+            for (int64_t q = 0; q < T.p2p[a].n; ++q) {
+                const bh_node *nb = &t->nodes[T.p2p[a].v[q]];
+                for (int64_t kk = nb->start; kk < nb->end; ++kk) {
+                    int64_t j = P.perm[kk];
+                    if (j == i) continue;
+                    double d[3], s2 = eps * eps;
+                    for (int c = 0; c < 3; ++c) {
+                        d[c] = x[3 * j + c] - x[3 * i + c];
+                        s2 += d[c] * d[c];
+                    }
+                    double w = m[j] / (s2 * sqrt(s2));
+                    for (int c = 0; c < 3; ++c) ai[c] += w * d[c];
+                }
+            }
+            for (int c = 0; c < 3; ++c) acc[3 * i + c] = G * ai[c];
+            if (cnt) {
+                cnt[3 * i] = ncells;
+                cnt[3 * i + 1] = nfar;
+                cnt[3 * i + 2] = nnear;
+            }
+        }
+    }
+    if (stats) {
+        stats[0] = nn;
+        stats[1] = nleaves;
+        stats[2] = nexp;
+        stats[3] = npairs;
+    }
+    int err = T.err;
+    for (int64_t a = 0; a < nn; ++a) {
+        free(T.m2l[a].v);
+        free(T.p2p[a].v);
+    }
+    free(T.m2l); free(T.p2p); free(T.leaf); free(T.ci);
+    free(parent); free(z); free(Mh); free(L);
+    fmm_basis_free(&B);
+    bh_release(&P);
+    return err ? -2 : 0;
 }

@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of the oracle's C source (a flipped
 sign, a wrong power of s, a dropped softening term, a swapped index, a wrong
-kick factor, a wrong adjoint term), builds it, swaps it in for the real
+kick factor, a wrong adjoint term, a wrong expansion term or traversal
+rule of the fast multipole method), builds it, swaps it in for the real
 oracle, and runs the pins of test_oracle_pins.py against it: at least one pin
 must fail.  The real oracle is restored afterwards.  Only the oracle (CPU)
 is mutated.
@@ -15,6 +16,7 @@ import pytest
 
 import oracle
 import test_oracle_bh as bhpins
+import test_oracle_fmm as fmmpins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "nbody_oracle.c")
@@ -51,6 +53,27 @@ MUTANTS = {
                         "while (e < end && (t->key[e] >> (shift + 3)) == cp) ++e;"),
     "bh key axis": ("key0[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);",
                     "key0[i] = spread10(q[0]) | (spread10(q[0]) << 1) | (spread10(q[2]) << 2);"),
+    "fmm derivative factor": ("if (q2 >= 0) v += (double)(n[c] - 1) * T[(m + 1) * nt + q2];",
+                              "if (q2 >= 0) v += (double)(n[c]) * T[(m + 1) * nt + q2];"),
+    "fmm derivative sign": ("T[m * nt] = -(double)(2 * m - 1) * T[(m - 1) * nt] / s2;",
+                            "T[m * nt] = (double)(2 * m - 1) * T[(m - 1) * nt] / s2;"),
+    "fmm moment sign": ("double y = -(xj[c] - z[c]);", "double y = xj[c] - z[c];"),
+    "fmm moment factorial": ("pw[2][B->mi[q][2]] * B->inv_fact[q];", "pw[2][B->mi[q][2]];"),
+    "fmm truncation": ("if (n[0] + n[1] + n[2] > p - kk) break;",
+                       "if (n[0] + n[1] + n[2] > p - kk - 1) break;"),
+    "fmm gradient axis": ("a[1] += L[fmm_slot(k[0], k[1] + 1, k[2])] * w;",
+                          "a[1] += L[fmm_slot(k[0] + 1, k[1], k[2])] * w;"),
+    "fmm separation inverted": ("return (double)d2 >= T->crit", "return (double)d2 < T->crit"),
+    "fmm ancestors skipped": ("for (int64_t an = a; an >= 0; an = parent[an]) {\n                double u[3];",
+                              "for (int64_t an = a; an >= 0; an = -1) {\n                double u[3];"),
+    "fmm equal cells not split": ("if (nb->child[o] >= 0) fmm_push(&down, (int32_t)nb->child[o]);",
+                                  "if (nb->child[o] >= 0) fmm_push(&down, (int32_t)b);"),
+    "fmm octant skipped": ("if (nb->child[o] >= 0) fmm_leaf_visit(T, a, nb->child[o]);",
+                           "if (nb->child[o] >= 0 && o > 0) fmm_leaf_visit(T, a, nb->child[o]);"),
+    "fmm centre at corner": ("z[id][c] = P.box_lo[c] + cell * ((double)ic[c] + 0.5);",
+                             "z[id][c] = P.box_lo[c] + cell * (double)ic[c];"),
+    "fmm inscribed radius": ("T.crit[la][lb] = 0.75 * s * s / (theta * theta);",
+                             "T.crit[la][lb] = 0.25 * s * s / (theta * theta);"),
 }
 
 PINS = [
@@ -63,6 +86,14 @@ PINS = [
     pins.test_force_vjp_central_differences, pins.test_kdk_grad_central_differences,
     lambda: bhpins.test_theta_zero_is_the_direct_sum(8, 32), bhpins.test_error_falls_with_theta,
     bhpins.test_far_cluster_is_its_monopole, bhpins.test_tree_counts_and_cost,
+    fmmpins.test_derivatives_closed_forms, lambda: fmmpins.test_derivatives_finite_differences(0.4),
+    fmmpins.test_derivatives_harmonic_without_softening,
+    lambda: fmmpins.test_expansion_order_of_accuracy(0.3),
+    fmmpins.test_expansion_converges_to_the_direct_sum,
+    lambda: fmmpins.test_theta_zero_is_the_direct_sum(16, 6),
+    lambda: fmmpins.test_every_body_meets_every_other_once(0.6),
+    fmmpins.test_power_of_two_scaling_is_exact, fmmpins.test_error_falls_with_theta_and_order,
+    fmmpins.test_far_cluster_through_expansions_only,
 ]
 
 
