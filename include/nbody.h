@@ -232,7 +232,8 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * clears the record and starts recording, nb_profile(ctx, 0) stops.
  * nb_profile_read synchronises the stream and returns, for `kind`
  * (0 force, 1 batched force, 2 force VJP, 3 energy, 4 tree walk, 5 tree
- * build: sort, pack, levels, moments), the launches (sequences, for 5)
+ * build: sort, pack, levels, moments, 6 fast multipole passes: upward,
+ * downward levels, near field), the launches (sequences, for 5 and 6)
  * recorded and their summed duration in milliseconds.
  */
 nb_status nb_profile(nb_ctx *ctx, int enable);
@@ -304,6 +305,51 @@ nb_status nb_tree_stats(nb_ctx *ctx, int64_t *out);
  * the schedule, only the time does.  Drops the context's captured graphs.
  */
 nb_status nb_tree_schedule(nb_ctx *ctx, int sched, int chunk);
+
+/*
+ * Fast multipole method: the O(N) method the paper names as the successor of
+ * its tree code (Sec. VI, after Greengard and Rokhlin).  The paper gives no
+ * formulation; the one here (the same as the oracle's):
+ *  - the Barnes-Hut tree above (same cube, keys, leaf rule, leaf_cap);
+ *  - per cell a Cartesian Taylor expansion of order `order` (2..6) of the
+ *    softened potential about the cube's centre: moments of the cell's
+ *    bodies, local coefficients of the potential of its sources;
+ *  - target cell A and source cell B are well separated when
+ *    |z_A - z_B| >= (r_A + r_B) / theta, z the cube centre, r = sqrt(3)/2 of
+ *    the edge (decided exactly on integer centres);
+ *  - the pairs come from the dual-tree traversal from (root, root): a cell
+ *    takes the candidates its parent handed down; separated -> B's expansion
+ *    acts on A; both leaves -> the bodies interact directly; A a leaf -> B's
+ *    children are candidates; B a leaf or smaller than A -> B is handed to
+ *    A's children; else B's children are;
+ *  - a body's acceleration is G times (the direct sum over the bodies of the
+ *    leaves it meets directly, self pair excluded, plus the gradient of the
+ *    local expansion of its leaf, which holds its ancestors' translated).
+ * theta = 0 separates nothing: the direct sum.  The series converge for
+ * theta < 1; the error falls with smaller theta and larger order.
+ *
+ * nb_fmm_forces: acc [n][3] (out).  theta >= 0 and finite; 2 <= order <= 6;
+ * 1 <= leaf_cap <= 64.  counts (optional, int32 [n][3], 4-byte aligned)
+ * receives per body the source cells acting on its leaf and the leaf's
+ * ancestors, the bodies those cells hold, and the bodies it meets directly
+ * (itself included); the last two sum to n.  Float32 arithmetic in every
+ * precision mode, float64 output.  Allocates on first use (the tree scratch
+ * of nb_tree_forces, plus (2 (order+1)(order+2)(order+3)/6 + 12) floats per
+ * tree node and a pool of candidate lists, 4 (2^20 + 32 n_max) bytes to
+ * start).  Synchronises the context's stream at the end: if the candidate
+ * lists outgrew the pool, the pool is doubled and the passes run again.
+ * Non-finite results are reported by nb_sync.
+ *
+ * nb_fmm_stats: {nodes, leaves, cell-to-cell expansions, direct body pairs
+ * (self pairs included)} of the last FMM evaluation on the context.
+ */
+#define NB_FMM_MIN_ORDER 2
+#define NB_FMM_MAX_ORDER 6
+#define NB_FMM_MAX_LEAF 64
+nb_status nb_fmm_forces(nb_ctx *ctx, int64_t n, const double *pos, const double *mass, double G,
+                        double eps, double theta, int order, int leaf_cap, double *acc,
+                        int32_t *counts);
+nb_status nb_fmm_stats(nb_ctx *ctx, int64_t *out);
 
 /*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form

@@ -1,0 +1,909 @@
+// Fast multipole method on the GPU: the O(N) method the paper names as the
+// successor of its tree code (Sec. VI, after Greengard and Rokhlin).  The
+// paper gives no formulation; the readings (shared with the oracle, which
+// computes the same sums by their definitions) are:
+//  * the tree is the Barnes-Hut tree of tree.cu (same cube, keys, leaves);
+//  * each cell carries a Cartesian Taylor expansion of order p about its
+//    cube's centre z, for the softened kernel g(r) = (|r|^2 + eps^2)^-1/2;
+//  * target A and source B are well separated when
+//    |z_A - z_B| >= (r_A + r_B) / theta, r = sqrt(3)/2 edge; in units of
+//    h = ext / 2048 the centres are integers, so the test is exact: the
+//    integer D2 against 0.75 (e_A + e_B)^2 / theta^2 in float64;
+//  * the pairs come from the dual-tree traversal from (root, root): each
+//    target takes the candidates its parent handed down; separated -> B's
+//    expansion acts on A; both leaves -> direct sum; A a leaf -> B's
+//    children; B a leaf or smaller -> B to A's children; else B's children
+//    to A's children.
+//
+// Scaled expansions (all factors exact powers of two, so float32 holds any
+// system size; e = cell edge, v = (x - z) / e):
+//   moments  Mc_n = sum_j m_j (-v_j)^n / n!
+//   locals   Lc_k = e_A^|k| d^k Phi(z_A)   (Phi = sum of the sources' potentials)
+//   P2M  from the bodies (positions read in float64, v rounded once);
+//   M2M  Mc^P_n = sum_{k<=n} (-s/4)^(n-k)/(n-k)! 2^-|k| Mc^c_k, s = child octant signs;
+//   M2L  with rho = h 2^E, E = floor(log2 |c_A - c_B|), q = (c_A - c_B)/2^E
+//        (exact, 1 <= |q| < 2), T'_m = d^m g'(q) for eps' = eps / rho,
+//        U_m = (e_A/rho)^|m| T'_m / rho:
+//        Lc_k += sum_{|n| <= p-|k|} Mc^B_n 2^((L_A - L_B)|n|) U_{n+k};
+//   L2L  Lc^c_k = sum_{n>=k} Lc^P_n 2^-|n| (s/2)^(n-k)/(n-k)!;
+//   L2P  a = (G/e_A) sum_{|k|<=p-1} Lc_{k+e_c} v^k/k!.
+// The derivatives use g = f(|r|^2/2), f^(m) = (-1)^m (2m-1)!! s^-(2m+1) and
+// d^n f_m = q_c d^(n-e_c) f_(m+1) + (n_c - 1) d^(n-2e_c) f_(m+1).
+//
+// Launches: one upward pass (P2M at the leaves, M2M climbing: the last child
+// to arrive sums its parent), one downward launch per level (L2L from the
+// parent, the candidates' classification, M2L with one source per lane, the
+// hand-down lists; leaves walk their candidates' subtrees for their M2L),
+// and one near-field launch over the leaves (the same walk collecting the
+// leaves to sum directly, float32x2 pair terms over sliced lanes, then L2P).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "nb_device.cuh"
+#include "nb_internal.h"
+
+namespace nb {
+namespace fmm {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int LEVELS = 11;
+constexpr int WARPS = 4;  // warps per block of the downward and near-field kernels
+constexpr int FLUSH = 64;  // directly summed sources per flush (32 pairs)
+
+// ------------------------------------------------------------ multi-indices
+// Slots in graded order: orders below k first, then a descending, b descending.
+__host__ __device__ constexpr int nterms(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
+__host__ __device__ constexpr int slot_of(int a, int b, int c)
+{
+    return nterms(a + b + c - 1) + (b + c) * (b + c + 1) / 2 + c;
+}
+__host__ __device__ constexpr int ord_of(int q)
+{
+    int k = 0;
+    while (nterms(k) <= q) ++k;
+    return k;
+}
+__host__ __device__ constexpr int mi_of(int q, int axis)
+{
+    const int k = ord_of(q), r = q - nterms(k - 1);
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= r) ++s;
+    const int c = r - s * (s + 1) / 2, b = s - c, a = k - s;
+    return axis == 0 ? a : (axis == 1 ? b : c);
+}
+__host__ __device__ constexpr double fact(int a) { return a <= 1 ? 1.0 : a * fact(a - 1); }
+__host__ __device__ constexpr float inv_fact3(int q)
+{
+    return (float)(1.0 / (fact(mi_of(q, 0)) * fact(mi_of(q, 1)) * fact(mi_of(q, 2))));
+}
+__host__ __device__ constexpr int padded(int p) { return (nterms(p) + 3) & ~3; }
+
+template <int I, int E, class F>
+__device__ __forceinline__ void sfor(F &&f)
+{
+    if constexpr (I < E) {
+        f(std::integral_constant<int, I>());
+        sfor<I + 1, E>(f);
+    }
+}
+
+// 2^e for -126 <= e <= 127, exactly.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// ------------------------------------------------------------ kernel parts
+// T[q] = d^n g'(q) for the slots of order <= P, g' = (|q|^2 + e2)^-1/2.
+template <int P>
+__device__ __forceinline__ void derivs(float qx, float qy, float qz, float e2, float (&T)[nterms(P)])
+{
+    constexpr int N = nterms(P);
+    float W[P + 1][N];  // W[m][slot] = d^n f_m, only m + |n| <= P
+    const float s2 = fmaf(qz, qz, fmaf(qy, qy, fmaf(qx, qx, e2)));
+    const float is = rsqrt_mufu(s2);
+    const float is2 = is * is;
+    W[0][0] = is;
+    sfor<1, P + 1>([&](auto mI) {
+        constexpr int m = decltype(mI)::value;
+        W[m][0] = -(float)(2 * m - 1) * W[m - 1][0] * is2;
+    });
+    sfor<1, N>([&](auto qI) {
+        constexpr int q = decltype(qI)::value;
+        constexpr int a = mi_of(q, 0), b = mi_of(q, 1), c = mi_of(q, 2), k = a + b + c;
+        constexpr int ax = a > 0 ? 0 : (b > 0 ? 1 : 2);
+        constexpr int na = ax == 0 ? a : (ax == 1 ? b : c);
+        constexpr int q1 = slot_of(a - (ax == 0), b - (ax == 1), c - (ax == 2));
+        constexpr int q2 =
+            na >= 2 ? slot_of(a - 2 * (ax == 0), b - 2 * (ax == 1), c - 2 * (ax == 2)) : -1;
+        const float r = ax == 0 ? qx : (ax == 1 ? qy : qz);
+        sfor<0, P - k + 1>([&](auto mI) {
+            constexpr int m = decltype(mI)::value;
+            float v = r * W[m + 1][q1];
+            if constexpr (q2 >= 0) v = fmaf((float)(na - 1), W[m + 1][q2], v);
+            W[m][q] = v;
+        });
+    });
+    sfor<0, N>([&](auto qI) {
+        constexpr int q = decltype(qI)::value;
+        T[q] = W[0][q];
+    });
+}
+
+struct Consts {
+    float inv_h;     // 2048 / ext
+    float eps2_h;    // eps^2 (2048 / ext)^2
+};
+
+// acc += the scaled local expansion about A of source cell B's moments Mb.
+template <int P>
+__device__ __forceinline__ void m2l_add(float (&acc)[nterms(P)], const float *__restrict__ Mb,
+                                        int4 cA, int4 cB, const Consts &K)
+{
+    constexpr int N = nterms(P);
+    const int dx = cA.x - cB.x, dy = cA.y - cB.y, dz = cA.z - cB.z;
+    const int D2 = dx * dx + dy * dy + dz * dz;  // >= 1 for distinct cells
+    const int E = (31 - __clz(D2)) >> 1;         // floor(log2 sqrt(D2))
+    const float sc = pow2f(-E);
+    float T[N];
+    derivs<P>((float)dx * sc, (float)dy * sc, (float)dz * sc, K.eps2_h * sc * sc, T);
+    // U_m = sA^|m| T_m / rho, sA = e_A / rho = 2^(11 - L_A - E)
+    const float sA = pow2f(11 - cA.w - E);
+    float pa[P + 1];
+    pa[0] = K.inv_h * sc;
+#pragma unroll
+    for (int j = 1; j <= P; ++j) pa[j] = pa[j - 1] * sA;
+    sfor<0, N>([&](auto mI) {
+        constexpr int m = decltype(mI)::value;
+        T[m] *= pa[mi_of(m, 0) + mi_of(m, 1) + mi_of(m, 2)];
+    });
+    const float g = pow2f(cA.w - cB.w);
+    float pg[P + 1];
+    pg[0] = 1.0f;
+#pragma unroll
+    for (int j = 1; j <= P; ++j) pg[j] = pg[j - 1] * g;
+    const float4 *Mb4 = reinterpret_cast<const float4 *>(Mb);
+    sfor<0, (N + 3) / 4>([&](auto n4I) {
+        constexpr int n4 = decltype(n4I)::value;
+        const float4 mv = __ldg(Mb4 + n4);
+        const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+        sfor<0, 4>([&](auto jI) {
+            constexpr int j = decltype(jI)::value;
+            constexpr int n = 4 * n4 + j;
+            if constexpr (n < N) {
+                constexpr int na = mi_of(n, 0), nb = mi_of(n, 1), nc = mi_of(n, 2);
+                constexpr int kmax = P - (na + nb + nc);
+                const float w = mm[j] * pg[na + nb + nc];
+                sfor<0, nterms(kmax)>([&](auto kI) {
+                    constexpr int k = decltype(kI)::value;
+                    constexpr int m = slot_of(na + mi_of(k, 0), nb + mi_of(k, 1), nc + mi_of(k, 2));
+                    acc[k] = fmaf(w, T[m], acc[k]);
+                });
+            }
+        });
+    });
+}
+
+// out += the child's share of its parent's local coefficients Lp (L2L), or
+// (MOMENTS) out += the parent's share of the child's moments (M2M): both
+// sum_{k <= n} t(n - k) x_k with per-axis factors t_c(j) = (s_c d)^j / j!,
+// d = 1/2 (L2L, x = 2^-|n| Lp_n, into slot k) or d = -1/4 (M2M, x = 2^-|k|
+// Mc_k, into slot n).
+template <int P, bool MOMENTS>
+__device__ __forceinline__ void translate_add(float (&out)[nterms(P)], const float *__restrict__ x,
+                                              int octant)
+{
+    constexpr int N = nterms(P);
+    float t[3][P + 1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float st = ((octant >> c) & 1) ? 1.0f : -1.0f;
+        const float d = MOMENTS ? -0.25f * st : 0.5f * st;
+        t[c][0] = 1.0f;
+#pragma unroll
+        for (int j = 1; j <= P; ++j) t[c][j] = t[c][j - 1] * d / (float)j;
+    }
+    float xs[N];
+    sfor<0, N>([&](auto qI) {
+        constexpr int q = decltype(qI)::value;
+        xs[q] = x[q] * pow2f(-(mi_of(q, 0) + mi_of(q, 1) + mi_of(q, 2)));
+    });
+    // pairs (hi, lo) with lo <= hi componentwise
+    sfor<0, N>([&](auto hI) {
+        constexpr int hq = decltype(hI)::value;
+        constexpr int ha = mi_of(hq, 0), hb = mi_of(hq, 1), hc = mi_of(hq, 2);
+        sfor<0, nterms(ha + hb + hc)>([&](auto lI) {
+            constexpr int lq = decltype(lI)::value;
+            constexpr int la = mi_of(lq, 0), lb = mi_of(lq, 1), lc = mi_of(lq, 2);
+            if constexpr (la <= ha && lb <= hb && lc <= hc) {
+                const float coef = t[0][ha - la] * t[1][hb - lb] * t[2][hc - lc];
+                if constexpr (MOMENTS)
+                    out[hq] = fmaf(coef, xs[lq], out[hq]);
+                else
+                    out[lq] = fmaf(coef, xs[hq], out[lq]);
+            }
+        });
+    });
+}
+
+// Powers v^j / j! of one coordinate, j <= P.
+template <int P>
+__device__ __forceinline__ void scaled_powers(float v, float (&pw)[P + 1])
+{
+    pw[0] = 1.0f;
+#pragma unroll
+    for (int j = 1; j <= P; ++j) pw[j] = pw[j - 1] * v / (float)j;
+}
+
+// Double centre of a node from its integer centre.
+__device__ __forceinline__ void centre_of(const double *box, int4 ci, double (&z)[3])
+{
+    const double h = __dmul_rn(box[3], 0x1p-11);
+    z[0] = __dadd_rn(box[0], __dmul_rn((double)ci.x, h));
+    z[1] = __dadd_rn(box[1], __dmul_rn((double)ci.y, h));
+    z[2] = __dadd_rn(box[2], __dmul_rn((double)ci.z, h));
+}
+
+// Integer centre and level of a node from its key prefix.
+__device__ __forceinline__ int4 icentre(unsigned prefix, int L)
+{
+    unsigned ic[3] = {0u, 0u, 0u};
+    for (int b = 0; b < L; ++b) {
+        const unsigned trip = (prefix >> (3 * b)) & 7u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ic[c] |= ((trip >> c) & 1u) << b;
+    }
+    return make_int4((int)((2u * ic[0] + 1u) << (10 - L)), (int)((2u * ic[1] + 1u) << (10 - L)),
+                     (int)((2u * ic[2] + 1u) << (10 - L)), L);
+}
+
+template <int P>
+__device__ __forceinline__ void store_exp(float *dst, const float (&v)[nterms(P)])
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    sfor<0, NP / 4>([&](auto iI) {
+        constexpr int i = decltype(iI)::value;
+        float e[4];
+        sfor<0, 4>([&](auto jI) {
+            constexpr int j = decltype(jI)::value;
+            constexpr int q = 4 * i + j;
+            if constexpr (q < N)
+                e[j] = v[q];
+            else
+                e[j] = 0.0f;
+        });
+        d4[i] = make_float4(e[0], e[1], e[2], e[3]);
+    });
+}
+
+// ------------------------------------------------------------ upward pass
+// A thread per leaf forms its moments from its bodies, then climbs: at each
+// parent it counts itself in, and only the last child to arrive goes on to
+// translate the children's moments (in child order) into the parent's.
+template <int P>
+__global__ void __launch_bounds__(256) fmm_up_kernel(const FmmParams p)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const int total = t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10];
+    const double ext = p.box[3];
+    for (int leaf = blockIdx.x * blockDim.x + threadIdx.x; leaf < total;
+         leaf += gridDim.x * blockDim.x) {
+        if (t.nchild[leaf] != 0) continue;
+        const int L = t.level[leaf];
+        const int4 ci = icentre(t.prefix[leaf], L);
+        f.ci[leaf] = ci;
+        double z[3];
+        centre_of(p.box, ci, z);
+        const double inv_e = (double)(1 << L) / ext;
+        float Mc[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
+        for (int k = t.start[leaf]; k < t.end[leaf]; ++k) {
+            const int j = p.perm[k];
+            const float m = (float)p.mass[j];
+            float pw[3][P + 1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                scaled_powers<P>((float)((z[c] - p.pos[3 * (size_t)j + c]) * inv_e), pw[c]);
+            sfor<0, N>([&](auto qI) {
+                constexpr int q = decltype(qI)::value;
+                Mc[q] = fmaf(m * pw[0][mi_of(q, 0)], pw[1][mi_of(q, 1)] * pw[2][mi_of(q, 2)], Mc[q]);
+            });
+        }
+        store_exp<P>(f.M + (size_t)leaf * NP, Mc);
+        for (int node = t.parent[leaf]; node >= 0; node = t.parent[node]) {
+            __threadfence();
+            if (atomicAdd(f.arrive + node, 1) != t.nchild[node] - 1) break;
+            __threadfence();
+            f.ci[node] = icentre(t.prefix[node], t.level[node]);
+#pragma unroll
+            for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
+            const int c0 = t.first[node], nch = t.nchild[node];
+            for (int c = c0; c < c0 + nch; ++c) {
+                float xc[N];
+                const float *src = f.M + (size_t)c * NP;
+#pragma unroll
+                for (int q = 0; q < N; ++q) xc[q] = __ldcg(src + q);
+                translate_add<P, true>(Mc, xc, (int)(t.prefix[c] & 7u));
+            }
+            store_exp<P>(f.M + (size_t)node * NP, Mc);
+        }
+    }
+}
+
+// ------------------------------------------------------------ the walks
+// Per warp: stacks of child ranges per level (each holds at most 32 ranges:
+// a level is refilled only from the level above once every deeper level is
+// empty, or from the handed-down list once all are empty).
+struct WalkSh {
+    int2 rs[LEVELS][32];
+    int lsz[LEVELS];
+};
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(FULL, v, off);
+        if (lane >= off) v += u;
+    }
+    return v;
+}
+
+// The lane whose span of the inclusive sums `incl` holds position pos.
+__device__ __forceinline__ int warp_span_of(int incl, int pos)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(FULL, incl, lo + step - 1);
+        if (v <= pos) lo += step;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// Next round of up to 32 candidates (one per lane, -1 for none) of a leaf
+// target's walk: from the deepest non-empty level stack, else the next 32
+// handed-down candidates.  False when the walk is over.
+__device__ __forceinline__ bool next_round(WalkSh &w, const int *inh, int ninh, int &cursor,
+                                           int lane, int &node)
+{
+    const int sz = lane < LEVELS ? w.lsz[lane] : 0;
+    const unsigned nonempty = __ballot_sync(FULL, sz > 0);
+    if (!nonempty) {
+        if (cursor >= ninh) return false;
+        const int k = cursor + lane;
+        node = k < ninh ? __ldg(inh + k) : -1;
+        cursor += 32;
+        return true;
+    }
+    const int Lv = 31 - __clz(nonempty);
+    const int size = __shfl_sync(FULL, sz, Lv);
+    const int R = min(size, 32);
+    const int2 r = lane < R ? w.rs[Lv][size - 1 - lane] : make_int2(0, 0);
+    const int incl = warp_incl_scan(r.y, lane);
+    const int excl = incl - r.y;
+    const int take = min(__shfl_sync(FULL, incl, 31), 32);
+    const int src = warp_span_of(incl, lane) & 31;
+    const int first_src = __shfl_sync(FULL, r.x, src), excl_src = __shfl_sync(FULL, excl, src);
+    node = lane < take ? first_src + (lane - excl_src) : -1;
+    const unsigned done = __ballot_sync(FULL, lane < R && incl <= 32);
+    __syncwarp();
+    if (lane < R && excl < 32 && incl > 32)
+        w.rs[Lv][size - 1 - lane] = make_int2(r.x + (32 - excl), incl - 32);
+    if (lane == 0) w.lsz[Lv] = size - __popc(done);
+    __syncwarp();
+    return true;
+}
+
+// Push the child range (first, nch) of every opening lane onto the stack of
+// its node's level + 1.
+__device__ __forceinline__ void push_children(WalkSh &w, bool open, int tgt, int first, int nch,
+                                              int lane, int *err)
+{
+    if (!__ballot_sync(FULL, open)) return;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned grp = __match_any_sync(FULL, open ? tgt : -1);
+    int slot = 0;
+    if (open) slot = w.lsz[tgt] + __popc(grp & lt);
+    __syncwarp();
+    if (open) {
+        if (slot < 32)
+            w.rs[tgt][slot] = make_int2(first, nch);
+        else
+            atomicOr(err, ERR_TREE);  // never: at most 32 pushes onto an empty level
+    }
+    __syncwarp();
+    if (open && (grp & lt) == 0) w.lsz[tgt] = min(w.lsz[tgt] + __popc(grp), 32);
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool separated(int4 a, int4 b, const double (*crit)[LEVELS])
+{
+    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return (double)(dx * dx + dy * dy + dz * dz) >= crit[a.w][b.w];
+}
+
+__device__ __forceinline__ void crit_table(double (*crit)[LEVELS], double theta)
+{
+    for (int i = threadIdx.x; i < LEVELS * LEVELS; i += blockDim.x) {
+        const int la = i / LEVELS, lb = i % LEVELS;
+        const double s = (double)((1 << (11 - la)) + (1 << (11 - lb)));
+        crit[la][lb] = __ddiv_rn(__dmul_rn(__dmul_rn(0.75, s), s), __dmul_rn(theta, theta));
+    }
+}
+
+__device__ __forceinline__ Consts consts_of(const FmmParams &p)
+{
+    Consts K;
+    const double ih = 2048.0 / p.box[3];
+    K.inv_h = (float)ih;
+    K.eps2_h = (float)(p.eps2 * ih * ih);
+    return K;
+}
+
+// ------------------------------------------------------------ downward pass
+// Cells of level L, a warp each (dynamic): local coefficients = the parent's
+// translated + the M2L of the separated candidates; a non-leaf hands the
+// others down, a leaf walks their subtrees for more separated cells.
+template <int P>
+__global__ void __launch_bounds__(32 * WARPS) fmm_down_kernel(const FmmParams p, int L)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    __shared__ WalkSh wsh[WARPS];
+    __shared__ int mq[WARPS][64];
+    __shared__ double crit[LEVELS][LEVELS];
+    crit_table(crit, p.theta);
+    __syncthreads();
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const Consts K = consts_of(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int cnt = t.meta[TREE_META_COUNT + L], base = t.meta[TREE_META_BASE + L];
+    WalkSh &w = wsh[warp];
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_LEVEL + L, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= cnt) break;
+        const int A = base + qi;
+        const int4 cA = f.ci[A];
+        const int nchA = t.nchild[A], par = t.parent[A];
+        int inh_off = 0, inh_cnt = 1;  // the root's list: pool[0] = 0
+        if (par >= 0) {
+            const int2 d = f.down[par];
+            inh_off = d.x;
+            inh_cnt = d.y;
+        }
+        const int *inh = f.pool + inh_off;
+        float acc[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = 0.0f;
+        int mcnt = 0, own = 0, farb = 0;
+        auto m2l_round = [&](int k) {
+            if (lane < k) {
+                const int B = mq[warp][lane];
+                m2l_add<P>(acc, f.M + (size_t)B * NP, cA, __ldg(f.ci + B), K);
+            }
+        };
+        auto enqueue = [&](bool sep, int node) {
+            const unsigned sm = __ballot_sync(FULL, sep);
+            if (!sm) return;
+            if (sep) {
+                mq[warp][mcnt + __popc(sm & lt)] = node;
+                farb += t.end[node] - t.start[node];
+            }
+            mcnt += __popc(sm);
+            own += __popc(sm);
+            __syncwarp();
+            if (mcnt >= 32) {
+                m2l_round(32);
+                __syncwarp();
+                if (lane < mcnt - 32) mq[warp][lane] = mq[warp][32 + lane];
+                mcnt -= 32;
+                __syncwarp();
+            }
+        };
+        if (nchA > 0) {
+            // pass 1: how many candidates go down
+            int total = 0;
+            for (int c0 = 0; c0 < inh_cnt; c0 += 32) {
+                const int k = c0 + lane;
+                const int B = k < inh_cnt ? __ldg(inh + k) : -1;
+                int outc = 0;
+                if (B >= 0) {
+                    const int4 cB = __ldg(f.ci + B);
+                    if (!separated(cA, cB, crit)) {
+                        const int nchB = t.nchild[B];
+                        outc = (nchB == 0 || cB.w > cA.w) ? 1 : nchB;
+                    }
+                }
+                total += warp_sum(outc);
+            }
+            long long off = 0;
+            if (lane == 0) off = atomicAdd(f.meta + FMM_META_POOL, total);
+            off = __shfl_sync(FULL, off, 0);
+            const bool fits = off + total <= f.pool_cap;
+            if (lane == 0) {
+                f.down[A] = make_int2(fits ? (int)off : 0, fits ? total : 0);
+                if (!fits) atomicOr(f.meta + FMM_META_OVERFLOW, 1);
+            }
+            // pass 2: M2L of the separated ones, the others written down
+            int cur = 0;
+            for (int c0 = 0; c0 < inh_cnt; c0 += 32) {
+                const int k = c0 + lane;
+                const int B = k < inh_cnt ? __ldg(inh + k) : -1;
+                bool sep = false, self = false;
+                int outc = 0, firstB = 0;
+                if (B >= 0) {
+                    const int4 cB = __ldg(f.ci + B);
+                    sep = separated(cA, cB, crit);
+                    if (!sep) {
+                        const int nchB = t.nchild[B];
+                        self = nchB == 0 || cB.w > cA.w;
+                        outc = self ? 1 : nchB;
+                        firstB = t.first[B];
+                        if (!self && cB.w < cA.w) atomicOr(p.err, ERR_TREE);  // never
+                    }
+                }
+                enqueue(sep, B);
+                const int incl = warp_incl_scan(outc, lane);
+                if (fits && outc) {
+                    int *dst = f.pool + off + cur + (incl - outc);
+                    if (self)
+                        dst[0] = B;
+                    else
+                        for (int j = 0; j < outc; ++j) dst[j] = firstB + j;
+                }
+                cur += __shfl_sync(FULL, incl, 31);
+            }
+        } else {
+            // a leaf: walk the candidates' subtrees
+            if (lane < LEVELS) w.lsz[lane] = 0;
+            __syncwarp();
+            int cursor = 0, B = -1;
+            while (next_round(w, inh, inh_cnt, cursor, lane, B)) {
+                bool sep = false, open = false;
+                int nchB = 0, firstB = 0, lvB = 0;
+                if (B >= 0) {
+                    const int4 cB = __ldg(f.ci + B);
+                    sep = separated(cA, cB, crit);
+                    nchB = t.nchild[B];
+                    open = !sep && nchB > 0;
+                    firstB = t.first[B];
+                    lvB = cB.w;
+                }
+                push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
+                enqueue(sep, B);
+            }
+            if (lane == 0) f.leaves[atomicAdd(f.meta + FMM_META_NLEAVES, 1)] = A;
+        }
+        m2l_round(mcnt);
+        // lane 0 totals the lanes' sums (a fixed order), adds the parent's share
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+#pragma unroll
+            for (int off2 = 16; off2 > 0; off2 >>= 1) acc[q] += __shfl_down_sync(FULL, acc[q], off2);
+        }
+        farb = warp_sum(farb);
+        if (lane == 0) {
+            int2 cum = make_int2(own, farb);
+            if (par >= 0) {
+                float xp[N];
+                const float *src = f.L + (size_t)par * NP;
+#pragma unroll
+                for (int q = 0; q < N; ++q) xp[q] = src[q];
+                translate_add<P, false>(acc, xp, (int)(t.prefix[A] & 7u));
+                const int2 pc = f.cum[par];
+                cum.x += pc.x;
+                cum.y += pc.y;
+            }
+            store_exp<P>(f.L + (size_t)A * NP, acc);
+            f.cum[A] = cum;
+            if (own) atomicAdd(f.stats + 2, (unsigned long long)own);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------ near field
+template <bool ZEPS>
+__device__ __forceinline__ void pair_terms(float2 dx, float2 dy, float2 dz, float2 m, float2 e2,
+                                           float2 &ax, float2 &ay, float2 &az)
+{
+    float2 r2 = fma2(dx, dx, e2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+    if (ZEPS) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 s = mul2(mul2(m, ri), mul2(ri, ri));
+    ax = fma2(dx, s, ax);
+    ay = fma2(dy, s, ay);
+    az = fma2(dz, s, az);
+}
+
+// Source q of a warp's list, in pairs {x0, x1, y0, y1}, {z0, z1, m0, m1}.
+__device__ __forceinline__ void list_put(float *Lf, int q, float x, float y, float z, float m)
+{
+    float *b = Lf + 8 * (q >> 1) + (q & 1);
+    b[0] = x;
+    b[2] = y;
+    b[4] = z;
+    b[6] = m;
+}
+
+// A warp per leaf (dynamic over the leaves): the candidates' subtrees walked
+// again for the leaves to sum directly, their bodies listed (coordinates
+// relative to the leaf's centre), every FLUSH of them added onto the leaf's
+// bodies: with nb <= 32 bodies, lane = body + T * slice (T = nb rounded up to
+// a power of two) and the slices share the source pairs; with nb > 32 two
+// bodies per lane.  Then the slices' sums are combined (a fixed order), the
+// far field evaluated, and G (near + far) written.
+template <int P, bool ZEPS>
+__global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    __shared__ WalkSh wsh[WARPS];
+    __shared__ __align__(16) float4 lists[WARPS][2 * FLUSH];  // 2 * FLUSH sources as pairs
+    __shared__ double crit[LEVELS][LEVELS];
+    crit_table(crit, p.theta);
+    __syncthreads();
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nleaves = f.meta[FMM_META_NLEAVES];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        f.stats[0] = (unsigned long long)(t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10]);
+        f.stats[1] = (unsigned long long)nleaves;
+    }
+    WalkSh &w = wsh[warp];
+    float *Lf = reinterpret_cast<float *>(lists[warp]);
+    const float4 *L4 = lists[warp];
+    const float2 e2 = make_float2(p.eps2f, p.eps2f);
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_NEAR, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= nleaves) break;
+        const int A = f.leaves[qi];
+        const int4 cA = f.ci[A];
+        const int par = t.parent[A];
+        // a level-10 leaf may hold more than 64 bodies: 64 at a time
+        for (int s0 = t.start[A]; s0 < t.end[A]; s0 += 64) {
+            const int nb = min(64, t.end[A] - s0);
+            int inh_off = 0, inh_cnt = 1;
+            if (par >= 0) {
+                const int2 d = f.down[par];
+                inh_off = d.x;
+                inh_cnt = d.y;
+            }
+            const int *inh = f.pool + inh_off;
+            double z[3];
+            centre_of(p.box, cA, z);
+            const float cx = (float)z[0], cy = (float)z[1], cz = (float)z[2];
+            const bool two = nb > 32;
+            const int T = two ? 32 : (nb <= 1 ? 1 : 1 << (32 - __clz(nb - 1)));
+            const int S = 32 / T;
+            const int slice = lane / T, b0 = lane % T;
+            const bool v0 = b0 < nb, v1 = two && b0 + 32 < nb;
+            float2 nx0 = make_float2(0.f, 0.f), ny0 = nx0, nz0 = nx0, nx1 = nx0, ny1 = nx0, nz1 = nx0;
+            if (v0) {
+                const float4 h = __ldg(p.P + s0 + b0), l = __ldg(p.Plo + s0 + b0);
+                const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
+                nx0 = make_float2(x, x);
+                ny0 = make_float2(y, y);
+                nz0 = make_float2(zz, zz);
+            }
+            if (v1) {
+                const float4 h = __ldg(p.P + s0 + b0 + 32), l = __ldg(p.Plo + s0 + b0 + 32);
+                const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
+                nx1 = make_float2(x, x);
+                ny1 = make_float2(y, y);
+                nz1 = make_float2(zz, zz);
+            }
+            float2 ax0 = make_float2(0.f, 0.f), ay0 = ax0, az0 = ax0, ax1 = ax0, ay1 = ax0, az1 = ax0;
+            float ks[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, kc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            auto fold = [&]() {
+                kahan_add(ks[0][0], kc[0][0], ax0.x);
+                kahan_add(ks[0][0], kc[0][0], ax0.y);
+                kahan_add(ks[0][1], kc[0][1], ay0.x);
+                kahan_add(ks[0][1], kc[0][1], ay0.y);
+                kahan_add(ks[0][2], kc[0][2], az0.x);
+                kahan_add(ks[0][2], kc[0][2], az0.y);
+                if (two) {
+                    kahan_add(ks[1][0], kc[1][0], ax1.x);
+                    kahan_add(ks[1][0], kc[1][0], ax1.y);
+                    kahan_add(ks[1][1], kc[1][1], ay1.x);
+                    kahan_add(ks[1][1], kc[1][1], ay1.y);
+                    kahan_add(ks[1][2], kc[1][2], az1.x);
+                    kahan_add(ks[1][2], kc[1][2], az1.y);
+                }
+                ax0 = ay0 = az0 = ax1 = ay1 = az1 = make_float2(0.f, 0.f);
+            };
+            auto eval = [&](int npairs) {
+                for (int q = slice; q < npairs; q += S) {
+                    const float4 a = L4[2 * q], bq = L4[2 * q + 1];
+                    const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+                    const float2 sz = make_float2(bq.x, bq.y), sm = make_float2(bq.z, bq.w);
+                    pair_terms<ZEPS>(add2(sx, nx0), add2(sy, ny0), add2(sz, nz0), sm, e2, ax0, ay0, az0);
+                    if (two)
+                        pair_terms<ZEPS>(add2(sx, nx1), add2(sy, ny1), add2(sz, nz1), sm, e2, ax1, ay1,
+                                         az1);
+                }
+            };
+            int cnt = 0, nnear = 0;
+            auto flush = [&]() {
+                __syncwarp();
+                eval(FLUSH / 2);
+                fold();
+                __syncwarp();
+                for (int c = lane; c < FLUSH; c += 32) lists[warp][c] = lists[warp][FLUSH + c];
+                cnt -= FLUSH;
+                __syncwarp();
+            };
+            if (lane < LEVELS) w.lsz[lane] = 0;
+            __syncwarp();
+            int cursor = 0, B = -1;
+            while (next_round(w, inh, inh_cnt, cursor, lane, B)) {
+                bool open = false, leafB = false;
+                int nchB = 0, firstB = 0, lvB = 0;
+                if (B >= 0) {
+                    const int4 cB = __ldg(f.ci + B);
+                    const bool sep = separated(cA, cB, crit);
+                    nchB = t.nchild[B];
+                    open = !sep && nchB > 0;
+                    leafB = !sep && nchB == 0;
+                    firstB = t.first[B];
+                    lvB = cB.w;
+                }
+                push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
+                if (__ballot_sync(FULL, leafB)) {
+                    int ls = 0, lsz = 0;
+                    if (leafB) {
+                        ls = t.start[B];
+                        lsz = t.end[B] - ls;
+                    }
+                    const int linc = warp_incl_scan(lsz, lane);
+                    const int lexc = linc - lsz;
+                    const int tot = __shfl_sync(FULL, linc, 31);
+                    nnear += tot;
+                    for (int c0 = 0; c0 < tot; c0 += 32) {
+                        const int pos = c0 + lane;
+                        const int j = warp_span_of(linc, pos) & 31;
+                        const int body = __shfl_sync(FULL, ls, j) + (pos - __shfl_sync(FULL, lexc, j));
+                        const int kk = min(32, tot - c0);
+                        if (lane < kk) {
+                            const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
+                            list_put(Lf, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
+                                     rel(bh.z, bl.z, cz), bh.w);
+                        }
+                        cnt += kk;
+                        if (cnt >= FLUSH) flush();
+                    }
+                }
+            }
+            if (cnt > 0) {
+                if (lane == 0 && (cnt & 1)) list_put(Lf, cnt, 0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                eval((cnt + 1) >> 1);
+                fold();
+            }
+            // combine the slices (lane b0 of slice 0 ends with the total)
+            double ns[2][3];
+    #pragma unroll
+            for (int b = 0; b < 2; ++b)
+    #pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double v = (double)ks[b][c] - (double)kc[b][c];
+                    for (int off = 16; off >= T; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+                    ns[b][c] = v;
+                }
+            if (slice == 0) {
+                const float *Lc = f.L + (size_t)A * NP;
+                const double inv_e = (double)(1 << cA.w) / p.box[3];
+    #pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const bool valid = b == 0 ? v0 : v1;
+                    if (!valid) continue;
+                    const int k = s0 + b0 + 32 * b;
+                    const int i = p.perm[k];
+                    float pw[3][P + 1];
+    #pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        scaled_powers<P>((float)((p.pos[3 * (size_t)i + c] - z[c]) * inv_e), pw[c]);
+                    float fa[3] = {0.f, 0.f, 0.f};
+                    sfor<0, nterms(P - 1)>([&](auto kI) {
+                        constexpr int q = decltype(kI)::value;
+                        constexpr int a = mi_of(q, 0), bb = mi_of(q, 1), c = mi_of(q, 2);
+                        const float wv = pw[0][a] * pw[1][bb] * pw[2][c];
+                        fa[0] = fmaf(__ldg(Lc + slot_of(a + 1, bb, c)), wv, fa[0]);
+                        fa[1] = fmaf(__ldg(Lc + slot_of(a, bb + 1, c)), wv, fa[1]);
+                        fa[2] = fmaf(__ldg(Lc + slot_of(a, bb, c + 1)), wv, fa[2]);
+                    });
+                    const double gx = p.G * (ns[b][0] + (double)fa[0] * inv_e);
+                    const double gy = p.G * (ns[b][1] + (double)fa[1] * inv_e);
+                    const double gz = p.G * (ns[b][2] + (double)fa[2] * inv_e);
+                    double *a = p.acc + 3 * (size_t)i;
+                    a[0] = gx;
+                    a[1] = gy;
+                    a[2] = gz;
+                    if (p.counts) {
+                        const int2 cm = f.cum[A];
+                        p.counts[3 * (size_t)i] = cm.x;
+                        p.counts[3 * (size_t)i + 1] = cm.y;
+                        p.counts[3 * (size_t)i + 2] = nnear;
+                    }
+                    if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+                }
+            }
+            if (lane == 0) atomicAdd(f.stats + 3, (unsigned long long)nb * (unsigned long long)nnear);
+            __syncwarp();
+        }
+    }
+}
+
+template <int P>
+__global__ void fmm_init_kernel(FmmView f)
+{
+    if (threadIdx.x < FMM_META_INTS) f.meta[threadIdx.x] = 0;
+    if (threadIdx.x < 4) f.stats[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+        f.pool[0] = 0;  // the root is its own candidate
+        f.meta[FMM_META_POOL] = 1;
+    }
+}
+
+// Upward pass, the downward levels and the near field, on stream s.
+template <int P>
+cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, int &kernels)
+{
+    kernels = 0;
+    cudaError_t e = cudaMemsetAsync(p.f.arrive, 0, sizeof(int) * (size_t)p.tree.cap, s);
+    if (e != cudaSuccess) return e;
+    fmm_init_kernel<P><<<1, 32, 0, s>>>(p.f);
+    ++kernels;
+    const int up_grid = (int)std::min<long long>(4096, ((long long)p.tree.cap + 255) / 256);
+    fmm_up_kernel<P><<<up_grid, 256, 0, s>>>(p);
+    ++kernels;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_down_kernel<P>, 32 * WARPS, 0);
+    if (e != cudaSuccess) return e;
+    const int down_grid = std::max(1, per_sm) * p.num_sms;
+    for (int L = 0; L < LEVELS; ++L) {
+        fmm_down_kernel<P><<<down_grid, 32 * WARPS, 0, s>>>(p, L);
+        ++kernels;
+    }
+    const bool zeps = p.eps2f == 0.0f;
+    if (zeps)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_near_kernel<P, true>,
+                                                          32 * WARPS, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_near_kernel<P, false>,
+                                                          32 * WARPS, 0);
+    if (e != cudaSuccess) return e;
+    const int near_grid = std::max(1, per_sm) * p.num_sms;
+    if (zeps)
+        fmm_near_kernel<P, true><<<near_grid, 32 * WARPS, 0, s>>>(p);
+    else
+        fmm_near_kernel<P, false><<<near_grid, 32 * WARPS, 0, s>>>(p);
+    ++kernels;
+    return cudaGetLastError();
+}
+
+}  // namespace fmm
+}  // namespace nb

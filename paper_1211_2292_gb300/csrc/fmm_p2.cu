@@ -1,0 +1,8 @@
+// Fast multipole method kernels of expansion order 2.
+#include "fmm_impl.cuh"
+
+namespace nb {
+namespace fmm {
+template cudaError_t launch_fmm_order<2>(cudaStream_t, const FmmParams &, int &);
+}  // namespace fmm
+}  // namespace nb

@@ -1,0 +1,8 @@
+// Fast multipole method kernels of expansion order 3.
+#include "fmm_impl.cuh"
+
+namespace nb {
+namespace fmm {
+template cudaError_t launch_fmm_order<3>(cudaStream_t, const FmmParams &, int &);
+}  // namespace fmm
+}  // namespace nb

@@ -18,7 +18,7 @@ enum : int { ERR_NONFINITE = 1, ERR_TREE = 2 };
 // Kernel families with autotuned variants (the `kind` of nb_variant_*).
 enum Kind : int { KIND_FORCE = 0, KIND_BATCHED = 1, KIND_VJP = 2, KIND_COUNT = 3 };
 // Event-timing tags of nb_profile_read: 0-2 the kinds above, then these.
-enum ProfKind : int { PROF_ENERGY = 3, PROF_TREE_WALK = 4, PROF_TREE_BUILD = 5 };
+enum ProfKind : int { PROF_ENERGY = 3, PROF_TREE_WALK = 4, PROF_TREE_BUILD = 5, PROF_FMM = 6 };
 
 // One compiled kernel: CTA shape plus the function to launch.  Every kernel
 // of a family takes a single by-value parameter struct.
@@ -182,6 +182,46 @@ cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const un
                               const double *box, const double *pos, const double *mass,
                               const int *perm, int leaf_cap, int *err, int &kernels);
 cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps, int &kernels);
+// Where tree.cu keeps each level's node count and first node in TreeView::meta.
+constexpr int TREE_META_COUNT = 0, TREE_META_BASE = 12;
+
+// ------------------------------------------------- fast multipole method (fmm.cu)
+// Expansion orders with compiled kernels, and floats per expansion (the
+// (p+1)(p+2)(p+3)/6 coefficients padded to a multiple of 4).
+constexpr int FMM_MIN_ORDER = 2, FMM_MAX_ORDER = 6, FMM_MAX_LEAF = 64;
+int fmm_floats(int order);
+enum : int { FMM_META_LEVEL = 0, FMM_META_NEAR = 11, FMM_META_POOL = 12, FMM_META_OVERFLOW = 13,
+             FMM_META_NLEAVES = 14, FMM_META_INTS = 16 };
+struct FmmView {
+    int order, np;         // expansion order p; floats per expansion
+    int4 *ci;              // per node: integer centre in units ext/2048 (.xyz), level (.w)
+    float *M, *L;          // [cap][np]: scaled moments, scaled local coefficients
+    int2 *down;            // per node: (offset, count) in pool of the candidates handed to its children
+    int2 *cum;             // per node: source cells acting on it and its ancestors, bodies they hold
+    int *arrive;           // upward-pass arrival counters (zeroed before each pass)
+    int *leaves;           // leaf ids, in the order the downward pass meets them
+    int *pool;             // candidate lists; pool[0] = 0, the root's own list
+    long long pool_cap;
+    int *meta;             // [FMM_META_INTS] queues, pool top, overflow flag, leaf count
+    unsigned long long *stats;  // [4] nodes, leaves, expansions, direct body pairs
+};
+struct FmmParams {
+    TreeView tree;
+    FmmView f;
+    const float4 *P, *Plo;  // bodies in tree order, float32 hi/lo
+    const int *perm;        // tree rank -> body index
+    const double *pos, *mass;
+    const double *box;      // {lo_x, lo_y, lo_z, ext}
+    int n;
+    double theta, eps2;
+    float eps2f;
+    double G;
+    double *acc;
+    int *counts;            // optional [n][3]
+    int *err;
+    int num_sms;
+};
+cudaError_t launch_fmm(cudaStream_t s, const FmmParams &p, int &kernels);
 
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
@@ -270,6 +310,11 @@ struct nb_ctx {
     float4 *tree_P = nullptr, *tree_Plo = nullptr;
     int *tree_perm = nullptr;
     double *tree_box = nullptr;
+
+    // fast multipole scratch (on first use; node arrays follow the tree's capacity)
+    nb::FmmView fmm{};
+    int fmm_cap = 0;             // nodes the expansion arrays hold
+    int fmm_np = 0;              // floats per expansion they hold
 
     std::map<const void *, int> occ;  // resident CTAs per SM, per kernel
 

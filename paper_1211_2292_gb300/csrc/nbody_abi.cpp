@@ -506,6 +506,19 @@ void free_tree_nodes(nb_ctx *c)
     t.cap = 0;
 }
 
+void free_fmm(nb_ctx *c)
+{
+    nb::FmmView &f = c->fmm;
+    void *arrays[] = {f.ci, f.M, f.L, f.down, f.cum, f.arrive, f.leaves, f.pool};
+    for (void *a : arrays) cudaFree(a);
+    f.ci = nullptr;
+    f.M = f.L = nullptr;
+    f.down = f.cum = nullptr;
+    f.arrive = f.leaves = f.pool = nullptr;
+    f.pool_cap = 0;
+    c->fmm_cap = c->fmm_np = 0;
+}
+
 void free_ctx(nb_ctx *c)
 {
     drop_graphs(c);
@@ -530,6 +543,9 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->order.vals[1]);
     cudaFree(c->order.hist);
     free_tree_nodes(c);
+    free_fmm(c);
+    cudaFree(c->fmm.meta);
+    cudaFree(c->fmm.stats);
     cudaFree(c->tree.meta);
     cudaFree(c->tree.stats);
     cudaFree(c->tree_P);
@@ -613,6 +629,53 @@ nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap, int group)
     return NB_OK;
 }
 
+// Expansion, list and candidate-pool scratch of the fast multipole method
+// for the tree's node capacity and `order`; the pool holds at least
+// pool_need entries.  Growing frees the old arrays (cudaFree synchronises).
+nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
+{
+    nb_status st = NB_OK;
+    nb::FmmView &f = c->fmm;
+    if (!f.meta) {
+        f.meta = dev_alloc<int>(c, nb::FMM_META_INTS, st);
+        if (st == NB_OK) f.stats = dev_alloc<unsigned long long>(c, 4, st);
+        if (st != NB_OK) return st;
+    }
+    const int np = nb::fmm_floats(order);
+    const int cap = c->tree.cap;
+    if (cap > c->fmm_cap || np > c->fmm_np) {
+        const long long keep_pool = f.pool_cap;
+        free_fmm(c);
+        const size_t m = (size_t)cap;
+        f.ci = dev_alloc<int4>(c, m, st);
+        if (st == NB_OK) f.M = dev_alloc<float>(c, m * (size_t)np, st);
+        if (st == NB_OK) f.L = dev_alloc<float>(c, m * (size_t)np, st);
+        if (st == NB_OK) f.down = dev_alloc<int2>(c, m, st);
+        if (st == NB_OK) f.cum = dev_alloc<int2>(c, m, st);
+        if (st == NB_OK) f.arrive = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) f.leaves = dev_alloc<int>(c, m, st);
+        if (st != NB_OK) {
+            free_fmm(c);
+            return st;
+        }
+        c->fmm_cap = cap;
+        c->fmm_np = np;
+        pool_need = std::max(pool_need, keep_pool);
+    }
+    if (pool_need > f.pool_cap) {
+        if (pool_need > 0x7fffffffLL)
+            return failf(c, NB_ENOMEM, "FMM candidate lists of %lld entries too large", pool_need);
+        cudaFree(f.pool);
+        f.pool = dev_alloc<int>(c, (size_t)pool_need, st);
+        if (st != NB_OK) {
+            f.pool_cap = 0;
+            return st;
+        }
+        f.pool_cap = pool_need;
+    }
+    return NB_OK;
+}
+
 // Events around a tree-code launch sequence (nb_profile), outside captures.
 struct TreeTimer {
     nb_ctx *c;
@@ -685,6 +748,64 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
     c->launches += k;
     tm.done();
     return NB_OK;
+}
+
+// Sort, pack and build the tree, then the FMM passes; synchronises to see
+// whether the candidate pool sufficed, and runs the FMM passes again with a
+// larger pool if not.
+nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
+                         double eps, double theta, int order, int leaf_cap, double *acc,
+                         int *counts)
+{
+    cudaStream_t s = c->stream;
+    int k = 0;
+    {
+        TreeTimer tm(c, nb::PROF_TREE_BUILD, s);
+        NB_CUDA(c, nb::launch_tree_sort(s, (int)n, pos, c->order, c->tree_perm, c->tree_box, k));
+        c->launches += k;
+        NB_LAUNCHED(c, nb::launch_pack_hilo(s, (int)n, pos, mass, c->tree_perm, c->tree_P,
+                                            c->tree_Plo));
+        NB_CUDA(c, nb::launch_tree_build(s, c->tree, (int)n, c->order.keys[0], c->tree_box, pos,
+                                         mass, c->tree_perm, leaf_cap, c->err, k));
+        c->launches += k;
+        tm.done();
+    }
+    for (int attempt = 0;; ++attempt) {
+        nb::FmmParams p;
+        p.tree = c->tree;
+        p.f = c->fmm;
+        p.f.order = order;
+        p.f.np = nb::fmm_floats(order);
+        p.P = c->tree_P;
+        p.Plo = c->tree_Plo;
+        p.perm = c->tree_perm;
+        p.pos = pos;
+        p.mass = mass;
+        p.box = c->tree_box;
+        p.n = (int)n;
+        p.theta = theta;
+        p.eps2 = eps * eps;
+        p.eps2f = (float)(eps * eps);
+        p.G = G;
+        p.acc = acc;
+        p.counts = counts;
+        p.err = c->err;
+        p.num_sms = c->num_sms;
+        {
+            TreeTimer tm(c, nb::PROF_FMM, s);
+            NB_CUDA(c, nb::launch_fmm(s, p, k));
+            c->launches += k;
+            tm.done();
+        }
+        int meta[nb::FMM_META_INTS];
+        NB_CUDA(c, cudaMemcpyAsync(meta, c->fmm.meta, sizeof(meta), cudaMemcpyDeviceToHost, s));
+        NB_CUDA(c, cudaStreamSynchronize(s));
+        if (!meta[nb::FMM_META_OVERFLOW]) return NB_OK;
+        if (attempt == 8) return failf(c, NB_ENOMEM, "FMM candidate lists keep overflowing");
+        const long long need = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_POOL],
+                                                   c->fmm.pool_cap) * 2;
+        NB_TRY(ensure_fmm(c, order, need));
+    }
 }
 
 nb_status tree_step_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, double *pos, double *vel,
@@ -1322,6 +1443,44 @@ nb_status nb_tree_schedule(nb_ctx *c, int sched, int chunk)
     c->tree_sched = sched;
     c->tree_chunk = chunk;
     drop_graphs(c);  // captured walks hold the old schedule
+    return NB_OK;
+}
+
+nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
+                        double eps, double theta, int order, int leaf_cap, double *acc,
+                        int32_t *counts)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    if (!std::isfinite(theta) || theta < 0)
+        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
+    if (order < nb::FMM_MIN_ORDER || order > nb::FMM_MAX_ORDER)
+        return failf(c, NB_EINVAL, "order = %d outside [%d, %d]", order, nb::FMM_MIN_ORDER,
+                     nb::FMM_MAX_ORDER);
+    if (leaf_cap < 1 || leaf_cap > nb::FMM_MAX_LEAF)
+        return failf(c, NB_EINVAL, "leaf_cap = %d outside [1, %d]", leaf_cap, nb::FMM_MAX_LEAF);
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 3 * sizeof(int32_t), "counts"));
+    if (n == 0) return NB_OK;
+    NB_TRY(ensure_tree(c, leaf_cap));
+    NB_TRY(ensure_fmm(c, order, (long long)(1 << 20) + 32LL * c->n_max));
+    return fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, counts);
+}
+
+nb_status nb_fmm_stats(nb_ctx *c, int64_t *out)
+{
+    if (!c || !out) return failf(c, NB_EINVAL, "ctx or out is NULL");
+    DeviceGuard guard(c->device);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (c->fmm.stats)
+        NB_CUDA(c, cudaMemcpyAsync(h, c->fmm.stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < 4; ++q) out[q] = (int64_t)h[q];
     return NB_OK;
 }
 

@@ -69,6 +69,9 @@ SIGNATURES = {
                               _c_int, _c_dbl, _c_i64, _c_vp, _c_uint]),
     "nb_tree_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
     "nb_tree_schedule": (_c_int, [_c_vp, _c_int, _c_int]),
+    "nb_fmm_forces": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_int,
+                               _c_vp, _c_vp]),
+    "nb_fmm_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
@@ -295,7 +298,7 @@ class NBody:
 
     def profile_read(self, kind: int):
         """(launches, total milliseconds) recorded for kind 0 force, 1 batched,
-        2 VJP, 3 energy, 4 tree walk, 5 tree build."""
+        2 VJP, 3 energy, 4 tree walk, 5 tree build, 6 fast multipole passes."""
         cnt, ms = ctypes.c_int64(), ctypes.c_double()
         self._call("nb_profile_read", int(kind), ctypes.byref(cnt), ctypes.byref(ms))
         return cnt.value, ms.value
@@ -329,6 +332,30 @@ class NBody:
         """Walk schedule: "static", "dynamic" or "guided" (or 0, 1, 2), chunk >= 1."""
         names = {"static": 0, "dynamic": 1, "guided": 2}
         self._call("nb_tree_schedule", names.get(sched, sched), int(chunk))
+
+    def fmm_forces(self, pos, mass, G, eps, theta=0.5, order=5, leaf_cap=32, out=None,
+                   counts=False):
+        """Fast-multipole accelerations (order 2..6 Cartesian expansions over
+        the tree, leaves of up to leaf_cap <= 64 bodies); with counts=True also
+        the int32 [n, 3] source cells acting on each body's leaf and its
+        ancestors, the bodies they hold, and the bodies met directly."""
+        import torch
+        n = mass.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+        cnt = None
+        if counts:
+            cnt = torch.empty((n, 3), dtype=torch.int32, device=pos.device)
+        self._call("nb_fmm_forces", n, _ptr(pos, "pos", 3 * n), _ptr(mass, "mass", n), float(G),
+                   float(eps), float(theta), int(order), int(leaf_cap), _ptr(out, "acc", 3 * n),
+                   _ptr_i32(cnt, "counts", 3 * n))
+        return (out, cnt) if counts else out
+
+    def fmm_stats(self):
+        """{nodes, leaves, expansions, direct_pairs} of the last FMM call."""
+        out = (ctypes.c_int64 * 4)()
+        self._call("nb_fmm_stats", out)
+        return dict(zip(("nodes", "leaves", "expansions", "direct_pairs"), out))
 
     def tree_stats(self):
         """{nodes, leaves, cell_interactions, body_interactions} of the last tree call."""
