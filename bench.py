@@ -9,7 +9,7 @@ evaluations) in the float32 Kahan-compensated form with float64 state.
 Metric: pairwise interactions per second, N^2 per force evaluation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload throughput|batched|precision|plain|differentiation|tree]
+                  [--workload throughput|batched|precision|plain|differentiation|tree|fmm]
 
 The other workloads (single-GPU lines with the same metric): "precision"
 (N = 65,536 Plummer, eps 0.005, FP32 compensated, 1 + 100 steps of dt 5e-4,
@@ -74,9 +74,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="throughput",
                     choices=["throughput", "batched", "precision", "plain", "differentiation",
-                             "tree"])
+                             "tree", "fmm"])
     ap.add_argument("--theta", type=float, default=None, help="tree workload: opening angle")
     ap.add_argument("--leaf-cap", type=int, default=None, help="tree workload: leaf capacity")
+    ap.add_argument("--order", type=int, default=None, help="fmm workload: expansion order 2..6")
     ap.add_argument("--group", type=int, default=None, choices=[32, 64],
                     help="tree workload: bodies walking the tree together")
     ap.add_argument("--tree-sched", default="dynamic", choices=["static", "dynamic", "guided"],
@@ -262,6 +263,35 @@ def reference_arm(args, ws, rank):
         }
         print(json.dumps(line), flush=True)
         return 0
+    if args.workload == "fmm":
+        w = FMM
+        theta = w["theta"] if args.theta is None else args.theta
+        lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+        order = w["order"] if args.order is None else args.order
+        b = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
+        for _ in range(args.warmup):
+            oracle.fmm_forces(b.pos, b.mass, 1.0, w["eps"], theta, order, lc)
+        tot = 0.0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            oracle.fmm_forces(b.pos, b.mass, 1.0, w["eps"], theta, order, lc)
+            tot += time.perf_counter() - t0
+        value = float(b.n) * args.steps / tot / 1e9
+        sample = (f"one fast-multipole evaluation of two-plummer N={b.n} (same recipe), theta "
+                  f"{theta}, order {order}, leaves <= {lc}, per step")
+        line = {
+            "impl": "reference", "metric": FMM_METRIC, "value": value, "unit": FMM_UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer spheres)",
+            "config": {"workload": w["name"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": FMM_UNIT, "cores": oracle.threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": FMM_UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "batched":
         w = BATCHED
         bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
@@ -421,6 +451,26 @@ def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None):
                        "direct_sum_equivalent": n * n / ((walk + build) / 1e3) / 1e9,
                        "note": "one tree build + walk of the throughput workload's bodies; "
                                "error and parity in bench.py --workload tree"}
+        f_ = FMM
+        with nbody.NBody(tree_bodies.n, "fp32_comp", device=dev.index) as nb:
+            a = nb.fmm_forces(x, m, 1.0, f_["eps"], f_["theta"], f_["order"], f_["leaf_cap"])
+            nb.profile(True)
+            for _ in range(5):
+                nb.fmm_forces(x, m, 1.0, f_["eps"], f_["theta"], f_["order"], f_["leaf_cap"],
+                              out=a)
+            bn, bms = nb.profile_read(5)
+            fn, fms = nb.profile_read(6)
+            qn, qms = nb.profile_read(7)
+            nb.profile(False)
+            st = nb.fmm_stats()
+        build, far, near = bms / max(bn, 1), fms / max(fn, 1), qms / max(qn, 1)
+        out["fmm"] = {"theta": f_["theta"], "order": f_["order"], "leaf_cap": f_["leaf_cap"],
+                      "ms_per_eval": build + far + near, "build_ms": build, "far_ms": far,
+                      "near_ms": near, "expansions": st["expansions"],
+                      "direct_pairs": st["direct_pairs"],
+                      "bodies_per_s": n / ((build + far + near) / 1e3) / 1e9, "unit": FMM_UNIT,
+                      "note": "one tree build + fast multipole evaluation of the throughput "
+                              "workload's bodies; error and parity in bench.py --workload fmm"}
     return out
 
 
@@ -432,6 +482,19 @@ TREE = {"name": "two-plummer N=1048576, Barnes-Hut theta 0.5, leaves <= 16 bodie
         "seed": 2, "eps": 0.002, "dt": 1e-3, "steps": 10, "theta": 0.5, "leaf_cap": 16,
         "group": 64, "cpu_n_per": 65_536}
 TREE_METRIC = "tree interactions/s (cell + body, G/s)"
+FMM = {"name": "two-plummer N=1048576, fast multipole theta 0.5, order 5, leaves <= 64 bodies, "
+               "one force evaluation per step (tree rebuilt), fp32 expansions and pair terms, "
+               "f64 output",
+       "seed": 2, "eps": 0.002, "theta": 0.5, "order": 5, "leaf_cap": 64, "cpu_n_per": 65_536}
+FMM_METRIC = "FMM force evaluations: bodies/s (N per evaluation / time, G/s; an O(N) method)"
+FMM_UNIT = "Gbodies/s"
+
+
+def m2l_flops(order):
+    """Multiply-adds of one cell-to-cell expansion's contraction, x 2: the
+    sum over |n| + |k| <= p of moment x derivative (C(p+6, 6) terms)."""
+    from math import comb
+    return 2 * comb(order + 6, 6)
 PLAIN = {"name": "Plummer N=1024, eps 0.01, fp64, 1 force eval + 10 KDK steps of dt 1e-3 "
                  "(one graph launch)", "n": 1024, "seed": 0, "eps": 0.01, "dt": 1e-3, "steps": 10}
 
@@ -600,6 +663,125 @@ def tree_workload(args, ws, torch, dev, stream, T, flush, table):
     return 0
 
 
+def fmm_workload(args, ws, torch, dev, stream, T, flush):
+    """Fast multipole line: value = bodies per evaluation / time (a rate that
+    does not grow with N for an O(N) method), K evaluations with the tree
+    rebuilt each time; the direct-sum-equivalent N^2 rate beside it."""
+    import numpy as np
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody
+    w = FMM
+    theta = w["theta"] if args.theta is None else args.theta
+    lc = w["leaf_cap"] if args.leaf_cap is None else args.leaf_cap
+    order = w["order"] if args.order is None else args.order
+    b = inputs.two_plummer(args.n_per, seed=w["seed"])
+    x, m = T(b.pos), T(b.mass)
+    G, eps = 1.0, w["eps"]
+    with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+        a = nb.fmm_forces(x, m, G, eps, theta, order, lc)
+        st = nb.fmm_stats()
+        warm = max(args.warmup, 10)  # about a tenth of a second of GPU work before timing
+        for _ in range(warm):
+            nb.fmm_forces(x, m, G, eps, theta, order, lc, out=a)
+        nb.profile(True)
+        l0 = nb.launches
+        try:
+            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            gpu_id = None
+        clocks = ClockSampler(gpu_id)
+        clocks.wait_ready()
+        with Timer(torch, dev, stream, lambda: None) as t:
+            for _ in range(args.steps):
+                nb.fmm_forces(x, m, G, eps, theta, order, lc, out=a)
+                flush.fill_(1.0)
+        ck = clocks.stop()
+        launches = nb.launches - l0
+        bn, bms = nb.profile_read(5)
+        fn, fms = nb.profile_read(6)
+        qn, qms = nb.profile_read(7)
+        nb.profile(False)
+        # accuracy against the exact sum on sampled bodies; every body must
+        # meet every other once (through an expansion or directly)
+        rows = inputs.sample_rows(b.n, 4096, seed=1)
+        ref = oracle.accel_rows(b.pos, b.mass, rows, G, eps)
+        af, cnt = nb.fmm_forces(x, m, G, eps, theta, order, lc, counts=True)
+        af, cnt = af.cpu().numpy(), cnt.cpu().numpy().astype(np.int64)
+        e = np.linalg.norm(af[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        covers = bool(np.all(cnt[:, 1] + cnt[:, 2] == b.n))
+    n = float(b.n)
+    value = n * args.steps / (t.ms / 1e3) / 1e9
+    far_ms, near_ms, build_ms = fms / max(fn, 1), qms / max(qn, 1), bms / max(bn, 1)
+    sm_max = (ck or {}).get("sm_max_mhz") or NOMINAL_SM_MAX_MHZ
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    far_tf = st["expansions"] * m2l_flops(order) / (far_ms / 1e3) / 1e12
+    near_tf = FLOPS_PER_INTERACTION * st["direct_pairs"] / (near_ms / 1e3) / 1e12
+    phases = {
+        "far": {"kernels": "fmm_up_kernel, fmm_down_kernel x 11 levels, fmm_items_kernel",
+                "ms": far_ms, "expansions": st["expansions"], "achieved_tflops": far_tf,
+                "flops_per_expansion": m2l_flops(order)},
+        "near": {"kernels": "fmm_near_kernel, fmm_combine_kernel", "ms": near_ms,
+                 "direct_pairs": st["direct_pairs"], "achieved_tflops": near_tf,
+                 "pairs_per_s": st["direct_pairs"] / (near_ms / 1e3) / 1e9},
+        "build_ms": build_ms}
+    far_dominant = far_ms >= near_ms
+    roof = {"bound": "alu",
+            "kernel": "fmm_down_kernel (11 level launches) with the upward pass" if far_dominant
+            else "fmm_near_kernel",
+            "achieved": far_tf if far_dominant else near_tf, "peak": peak, "unit": "TFLOP/s",
+            "frac": (far_tf if far_dominant else near_tf) / peak,
+            "traffic": traffic_from_profile(
+                "fmm_down_two_plummer_n1048576_dram.md" if far_dominant
+                else "fmm_near_two_plummer_n1048576_dram.md", "fmm_impl.cuh")
+            if (b.n, theta, lc, order) == (1 << 20, 0.5, 64, 5) else None,
+            "note": f"far: {m2l_flops(order)} flops per cell-to-cell expansion (its contraction); "
+                    f"near: {FLOPS_PER_INTERACTION} per pair; phases event-timed inside the timed "
+                    "region; peak = SMs x 128 FP32 lanes x 2 x max SM clock"}
+    cpu, parity = None, None
+    if not args.no_cpu_baseline:
+        bs = inputs.two_plummer(w["cpu_n_per"], seed=w["seed"])
+        t0 = time.perf_counter()
+        ra, rst, rc = oracle.fmm_forces(bs.pos, bs.mass, G, eps, theta, order, lc, counts=True)
+        el = time.perf_counter() - t0
+        sample = (f"two-plummer N={bs.n} (same recipe), theta {theta}, order {order}, leaves <= "
+                  f"{lc}: one evaluation, {el:.1f} s")
+        cpu = {"value": float(bs.n) / el / 1e9, "unit": FMM_UNIT, "cores": oracle.threads(),
+               "kind": "oracle", "sample": sample}
+        with nbody.NBody(bs.n, "fp32_comp", device=dev.index) as nb:
+            ga, gc = nb.fmm_forces(T(bs.pos), T(bs.mass), G, eps, theta, order, lc, counts=True)
+            nb.sync()
+            gst = nb.fmm_stats()
+        ga, gc = ga.cpu().numpy(), gc.cpu().numpy().astype(np.int64)
+        rms_a = np.sqrt((np.linalg.norm(ra, axis=1) ** 2).mean())
+        pe = np.linalg.norm(ga - ra, axis=1) / rms_a
+        parity = {"n": bs.n, "counts_equal_oracle": bool(np.array_equal(gc, rc)),
+                  "stats_equal_oracle": gst == rst,
+                  "force_err_max": float(pe.max()), "force_err_rms": float(np.sqrt((pe ** 2).mean())),
+                  "norm": "per body |a - a_oracle| / rms |a_oracle|",
+                  "vs": "oracle fast multipole method, whole run"}
+    line = {"metric": FMM_METRIC, "value": value, "unit": FMM_UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": warm, "ms_per_step": t.ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Plummer spheres)",
+            "config": {"workload": w["name"] if args.n_per == WORKLOAD["n_per"] else
+                       f"two-plummer N={b.n} fmm", "n": b.n, "theta": theta, "order": order,
+                       "leaf_cap": lc, "force_evals_per_step": 1,
+                       "l2": "256 MiB buffer written between steps"},
+            "first_eval": st, "phases": phases,
+            "ms_per_force_eval": t.ms / args.steps,
+            "direct_sum_equivalent": {"value": n * n * args.steps / (t.ms / 1e3) / 1e9,
+                                      "unit": UNIT, "note": "N^2 per evaluation / time"},
+            "force_error_vs_direct_sum": {"rms": float(np.sqrt((e ** 2).mean())),
+                                          "max": float(e.max()),
+                                          "sample": "4096 bodies, FP64 oracle direct sum"},
+            "every_pair_met_once": covers,
+            "roofline": roof, "parity": parity, "cpu_baseline": cpu, "clocks": ck,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def other_workload(args, ws, rank, local):
     """precision / plain / differentiation: single-GPU lines (rank 0 only)."""
     if rank != 0:
@@ -717,6 +899,8 @@ def other_workload(args, ws, rank, local):
 
     if args.workload == "tree":
         return tree_workload(args, ws, torch, dev, stream, T, flush, table)
+    if args.workload == "fmm":
+        return fmm_workload(args, ws, torch, dev, stream, T, flush)
 
     # differentiation
     a_ = ADJOINT
@@ -763,7 +947,7 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
-    if args.workload in ("precision", "plain", "differentiation", "tree"):
+    if args.workload in ("precision", "plain", "differentiation", "tree", "fmm"):
         if args.warmup < 3:
             args.warmup = 3
         return other_workload(args, ws, rank, local)

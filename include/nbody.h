@@ -232,8 +232,8 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * clears the record and starts recording, nb_profile(ctx, 0) stops.
  * nb_profile_read synchronises the stream and returns, for `kind`
  * (0 force, 1 batched force, 2 force VJP, 3 energy, 4 tree walk, 5 tree
- * build: sort, pack, levels, moments, 6 fast multipole passes: upward,
- * downward levels, near field), the launches (sequences, for 5 and 6)
+ * build: sort, pack, levels, moments, 6 fast multipole upward and downward
+ * passes, 7 fast multipole near field), the launches (sequences, for 5 to 7)
  * recorded and their summed duration in milliseconds.
  */
 nb_status nb_profile(nb_ctx *ctx, int enable);

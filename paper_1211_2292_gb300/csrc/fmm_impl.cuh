@@ -52,7 +52,7 @@ namespace fmm {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int LEVELS = 11;
 constexpr int WARPS = 4;  // warps per block of the downward and near-field kernels
-constexpr int FLUSH = 64;  // directly summed sources per flush (32 pairs)
+constexpr int FLUSH = 256;  // directly summed sources per flush (128 pairs)
 
 // ------------------------------------------------------------ multi-indices
 // Slots in graded order: orders below k first, then a descending, b descending.
@@ -435,6 +435,21 @@ __device__ __forceinline__ bool separated(int4 a, int4 b, const double (*crit)[L
     return (double)(dx * dx + dy * dy + dz * dz) >= crit[a.w][b.w];
 }
 
+// No descendant of the unseparated candidate B can be separated from target
+// A: with k = sqrt(3)/2 and edges in units of h, a descendant C's centre lies
+// within k (e_B - e_C) of B's, so |z_A - z_C| < D + k e_B, while separation
+// needs more than k e_A / theta.  The margin puts the float64 rounding of
+// both this test and the separation test out of play, so walking B's subtree
+// would meet exactly B's bodies directly.
+__device__ __forceinline__ bool all_direct(int4 a, int4 b, double theta)
+{
+    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const double D = __dsqrt_rn((double)(dx * dx + dy * dy + dz * dz));
+    const double k = 0.8660254037844386;
+    const double eA = (double)(1 << (11 - a.w)), eB = (double)(1 << (11 - b.w));
+    return D + k * eB < (1.0 - 1e-9) * (k * eA / theta);
+}
+
 __device__ __forceinline__ void crit_table(double (*crit)[LEVELS], double theta)
 {
     for (int i = threadIdx.x; i < LEVELS * LEVELS; i += blockDim.x) {
@@ -457,8 +472,14 @@ __device__ __forceinline__ Consts consts_of(const FmmParams &p)
 // Cells of level L, a warp each (dynamic): local coefficients = the parent's
 // translated + the M2L of the separated candidates; a non-leaf hands the
 // others down, a leaf walks their subtrees for more separated cells.
+// Resident blocks per SM the downward kernel's registers are sized for: four
+// (16 warps) up to order 5 (order 5 spills 84 bytes a thread), two at order 6.
 template <int P>
-__global__ void __launch_bounds__(32 * WARPS) fmm_down_kernel(const FmmParams p, int L)
+constexpr int down_min_blocks() { return P <= 5 ? 4 : 2; }
+
+template <int P>
+__global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
+    fmm_down_kernel(const FmmParams p, int L)
 {
     constexpr int N = nterms(P), NP = padded(P);
     __shared__ WalkSh wsh[WARPS];
@@ -491,33 +512,11 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_down_kernel(const FmmParams p,
         float acc[N];
 #pragma unroll
         for (int q = 0; q < N; ++q) acc[q] = 0.0f;
-        int mcnt = 0, own = 0, farb = 0;
-        auto m2l_round = [&](int k) {
-            if (lane < k) {
-                const int B = mq[warp][lane];
-                m2l_add<P>(acc, f.M + (size_t)B * NP, cA, __ldg(f.ci + B), K);
-            }
-        };
-        auto enqueue = [&](bool sep, int node) {
-            const unsigned sm = __ballot_sync(FULL, sep);
-            if (!sm) return;
-            if (sep) {
-                mq[warp][mcnt + __popc(sm & lt)] = node;
-                farb += t.end[node] - t.start[node];
-            }
-            mcnt += __popc(sm);
-            own += __popc(sm);
-            __syncwarp();
-            if (mcnt >= 32) {
-                m2l_round(32);
-                __syncwarp();
-                if (lane < mcnt - 32) mq[warp][lane] = mq[warp][32 + lane];
-                mcnt -= 32;
-                __syncwarp();
-            }
-        };
+        int mcnt = 0, own = 0, farb = 0, nearc = 0;
+        // a non-leaf: how many candidates go down (pass 1), and where
+        long long off = 0;
+        bool fits = true;
         if (nchA > 0) {
-            // pass 1: how many candidates go down
             int total = 0;
             for (int c0 = 0; c0 < inh_cnt; c0 += 32) {
                 const int k = c0 + lane;
@@ -532,65 +531,105 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_down_kernel(const FmmParams p,
                 }
                 total += warp_sum(outc);
             }
-            long long off = 0;
             if (lane == 0) off = atomicAdd(f.meta + FMM_META_POOL, total);
             off = __shfl_sync(FULL, off, 0);
-            const bool fits = off + total <= f.pool_cap;
+            fits = off + total <= f.pool_cap;
             if (lane == 0) {
                 f.down[A] = make_int2(fits ? (int)off : 0, fits ? total : 0);
                 if (!fits) atomicOr(f.meta + FMM_META_OVERFLOW, 1);
             }
-            // pass 2: M2L of the separated ones, the others written down
-            int cur = 0;
-            for (int c0 = 0; c0 < inh_cnt; c0 += 32) {
-                const int k = c0 + lane;
-                const int B = k < inh_cnt ? __ldg(inh + k) : -1;
-                bool sep = false, self = false;
-                int outc = 0, firstB = 0;
-                if (B >= 0) {
-                    const int4 cB = __ldg(f.ci + B);
-                    sep = separated(cA, cB, crit);
-                    if (!sep) {
-                        const int nchB = t.nchild[B];
-                        self = nchB == 0 || cB.w > cA.w;
-                        outc = self ? 1 : nchB;
-                        firstB = t.first[B];
-                        if (!self && cB.w < cA.w) atomicOr(p.err, ERR_TREE);  // never
-                    }
-                }
-                enqueue(sep, B);
-                const int incl = warp_incl_scan(outc, lane);
-                if (fits && outc) {
-                    int *dst = f.pool + off + cur + (incl - outc);
-                    if (self)
-                        dst[0] = B;
-                    else
-                        for (int j = 0; j < outc; ++j) dst[j] = firstB + j;
-                }
-                cur += __shfl_sync(FULL, incl, 31);
-            }
         } else {
-            // a leaf: walk the candidates' subtrees
             if (lane < LEVELS) w.lsz[lane] = 0;
             __syncwarp();
-            int cursor = 0, B = -1;
-            while (next_round(w, inh, inh_cnt, cursor, lane, B)) {
-                bool sep = false, open = false;
-                int nchB = 0, firstB = 0, lvB = 0;
-                if (B >= 0) {
-                    const int4 cB = __ldg(f.ci + B);
-                    sep = separated(cA, cB, crit);
-                    nchB = t.nchild[B];
-                    open = !sep && nchB > 0;
-                    firstB = t.first[B];
-                    lvB = cB.w;
-                }
-                push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
-                enqueue(sep, B);
-            }
-            if (lane == 0) f.leaves[atomicAdd(f.meta + FMM_META_NLEAVES, 1)] = A;
         }
-        m2l_round(mcnt);
+        // Rounds of 32 candidates fill the queue of separated cells; each
+        // time it holds 32 (or the candidates are done) every lane takes one
+        // source's M2L.  A non-leaf classifies its handed-down candidates and
+        // writes the others down (pass 2); a leaf walks their subtrees.
+        int c0 = 0, cur = 0, cursor = 0;
+        bool more = true;
+        while (more || mcnt > 0) {
+            while (more && mcnt < 32) {
+                bool sep = false;
+                int B = -1;
+                if (nchA > 0) {
+                    if (c0 >= inh_cnt) {
+                        more = false;
+                        break;
+                    }
+                    const int k = c0 + lane;
+                    B = k < inh_cnt ? __ldg(inh + k) : -1;
+                    c0 += 32;
+                    bool self = false;
+                    int outc = 0, firstB = 0;
+                    if (B >= 0) {
+                        const int4 cB = __ldg(f.ci + B);
+                        sep = separated(cA, cB, crit);
+                        if (!sep) {
+                            const int nchB = t.nchild[B];
+                            self = nchB == 0 || cB.w > cA.w;
+                            outc = self ? 1 : nchB;
+                            firstB = t.first[B];
+                            if (!self && cB.w < cA.w) atomicOr(p.err, ERR_TREE);  // never
+                        }
+                    }
+                    const int incl = warp_incl_scan(outc, lane);
+                    if (fits && outc) {
+                        int *dst = f.pool + off + cur + (incl - outc);
+                        if (self)
+                            dst[0] = B;
+                        else
+                            for (int j = 0; j < outc; ++j) dst[j] = firstB + j;
+                    }
+                    cur += __shfl_sync(FULL, incl, 31);
+                } else {
+                    if (!next_round(w, inh, inh_cnt, cursor, lane, B)) {
+                        more = false;
+                        break;
+                    }
+                    bool open = false;
+                    int nchB = 0, firstB = 0, lvB = 0;
+                    if (B >= 0) {
+                        const int4 cB = __ldg(f.ci + B);
+                        sep = separated(cA, cB, crit);
+                        nchB = t.nchild[B];
+                        if (!sep) {
+                            open = nchB > 0 && !all_direct(cA, cB, p.theta);
+                            if (!open) nearc += t.end[B] - t.start[B];
+                        }
+                        firstB = t.first[B];
+                        lvB = cB.w;
+                    }
+                    push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
+                }
+                const unsigned sm = __ballot_sync(FULL, sep);
+                if (sep) {
+                    mq[warp][mcnt + __popc(sm & lt)] = B;
+                    farb += t.end[B] - t.start[B];
+                }
+                mcnt += __popc(sm);
+                own += __popc(sm);
+                __syncwarp();
+            }
+            const int k = min(mcnt, 32);
+            if (k > 0) {
+                if (lane < k) {
+                    const int B = mq[warp][lane];
+                    m2l_add<P>(acc, f.M + (size_t)B * NP, cA, __ldg(f.ci + B), K);
+                }
+                __syncwarp();
+                if (lane < mcnt - k) mq[warp][lane] = mq[warp][k + lane];
+                mcnt -= k;
+                __syncwarp();
+            }
+        }
+        if (nchA == 0) {
+            nearc = warp_sum(nearc);
+            if (lane == 0) {
+                f.nearc[A] = nearc;
+                f.leaves[atomicAdd(f.meta + FMM_META_NLEAVES, 1)] = A;
+            }
+        }
         // lane 0 totals the lanes' sums (a fixed order), adds the parent's share
 #pragma unroll
         for (int q = 0; q < N; ++q) {
@@ -647,17 +686,97 @@ __device__ __forceinline__ void list_put(float *Lf, int q, float x, float y, flo
     b[6] = m;
 }
 
-// A warp per leaf (dynamic over the leaves): the candidates' subtrees walked
-// again for the leaves to sum directly, their bodies listed (coordinates
-// relative to the leaf's centre), every FLUSH of them added onto the leaf's
-// bodies: with nb <= 32 bodies, lane = body + T * slice (T = nb rounded up to
-// a power of two) and the slices share the source pairs; with nb > 32 two
-// bodies per lane.  Then the slices' sums are combined (a fixed order), the
-// far field evaluated, and G (near + far) written.
+// Work items of the near field: a leaf's bodies 64 at a time (a level-10 leaf
+// may hold more), times its directly met sources in up to 64 slices of about
+// CHUNK, so that no warp is left alone with a large leaf's sum.
+constexpr int CHUNK = 8192, MAX_SLICES = 64;
+__device__ __forceinline__ int body_chunks(int nb) { return (nb + 63) >> 6; }
+__device__ __forceinline__ int src_slices(int nearc)
+{
+    return min(MAX_SLICES, max(1, (nearc + CHUNK - 1) / CHUNK));
+}
+
+// One block: work items and partial-sum slots per leaf, scanned.
+template <int P>
+__global__ void __launch_bounds__(1024) fmm_items_kernel(FmmParams p)
+{
+    __shared__ int tile[BSCAN_TILE + BSCAN_TILE / 32];
+    __shared__ int wsum[32];
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const int nl = f.meta[FMM_META_NLEAVES];
+    for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+        const int A = f.leaves[q];
+        const int nb = t.end[A] - t.start[A], ns = src_slices(f.nearc[A]);
+        f.item_off[q] = body_chunks(nb) * ns;
+        f.part_off[q] = ns > 1 ? nb * ns : 0;
+    }
+    __syncthreads();
+    const int items = block_scan_exclusive<int>(f.item_off, f.item_off, nl, tile, wsum);
+    __syncthreads();
+    const int slots = block_scan_exclusive<int>(f.part_off, f.part_off, nl, tile, wsum);
+    if (threadIdx.x == 0) {
+        f.item_off[nl] = items;
+        f.part_off[nl] = slots;
+        f.meta[FMM_META_ITEMS] = items;
+        f.meta[FMM_META_PSLOTS] = slots;
+    }
+}
+
+// G (near + far) into acc for the body at tree rank k of leaf A; the far
+// field is the gradient of A's local expansion (L2P).
+template <int P>
+__device__ __forceinline__ void write_body(const FmmParams &p, int A, int4 cA, int k, double nx,
+                                           double ny, double nz, int nnear)
+{
+    constexpr int NP = padded(P);
+    const FmmView &f = p.f;
+    double z[3];
+    centre_of(p.box, cA, z);
+    const float *Lc = f.L + (size_t)A * NP;
+    const double inv_e = (double)(1 << cA.w) / p.box[3];
+    const int i = p.perm[k];
+    float pw[3][P + 1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        scaled_powers<P>((float)((p.pos[3 * (size_t)i + c] - z[c]) * inv_e), pw[c]);
+    float fa[3] = {0.f, 0.f, 0.f};
+    sfor<0, nterms(P - 1)>([&](auto kI) {
+        constexpr int q = decltype(kI)::value;
+        constexpr int a = mi_of(q, 0), b = mi_of(q, 1), c = mi_of(q, 2);
+        const float wv = pw[0][a] * pw[1][b] * pw[2][c];
+        fa[0] = fmaf(__ldg(Lc + slot_of(a + 1, b, c)), wv, fa[0]);
+        fa[1] = fmaf(__ldg(Lc + slot_of(a, b + 1, c)), wv, fa[1]);
+        fa[2] = fmaf(__ldg(Lc + slot_of(a, b, c + 1)), wv, fa[2]);
+    });
+    const double gx = p.G * (nx + (double)fa[0] * inv_e);
+    const double gy = p.G * (ny + (double)fa[1] * inv_e);
+    const double gz = p.G * (nz + (double)fa[2] * inv_e);
+    double *a = p.acc + 3 * (size_t)i;
+    a[0] = gx;
+    a[1] = gy;
+    a[2] = gz;
+    if (p.counts) {
+        const int2 cm = f.cum[A];
+        p.counts[3 * (size_t)i] = cm.x;
+        p.counts[3 * (size_t)i + 1] = cm.y;
+        p.counts[3 * (size_t)i + 2] = nnear;
+    }
+    if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+}
+
+// A warp per work item (dynamic): the leaf's candidates' subtrees walked
+// again, in the downward pass's order, for the bodies it meets directly
+// (pruned subtrees as whole body ranges); the item's slice of them is
+// listed (coordinates relative to the leaf's centre) and every FLUSH of them
+// added onto its bodies: two bodies per lane (b and b + T, T = nb / 2 rounded
+// up to a power of two), lane = b + T * slice, the 32 / T slices sharing the
+// source pairs.  The slices' sums are combined in a fixed
+// order; a leaf in one item gets its result written, a split one its
+// partial sums stored for fmm_combine_kernel.
 template <int P, bool ZEPS>
 __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
 {
-    constexpr int N = nterms(P), NP = padded(P);
     __shared__ WalkSh wsh[WARPS];
     __shared__ __align__(16) float4 lists[WARPS][2 * FLUSH];  // 2 * FLUSH sources as pairs
     __shared__ double crit[LEVELS][LEVELS];
@@ -666,7 +785,7 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
     const TreeView &t = p.tree;
     const FmmView &f = p.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nleaves = f.meta[FMM_META_NLEAVES];
+    const int nleaves = f.meta[FMM_META_NLEAVES], nitems = f.meta[FMM_META_ITEMS];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         f.stats[0] = (unsigned long long)(t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10]);
         f.stats[1] = (unsigned long long)nleaves;
@@ -676,183 +795,205 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
     const float4 *L4 = lists[warp];
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
     for (;;) {
-        int qi = 0;
-        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_NEAR, 1);
-        qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= nleaves) break;
-        const int A = f.leaves[qi];
+        int it = 0;
+        if (lane == 0) it = atomicAdd(f.meta + FMM_META_NEAR, 1);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= nitems) break;
+        // the leaf holding item `it`: the last qi with item_off[qi] <= it
+        int lo = 0, hi = nleaves;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (f.item_off[mid] <= it)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int qi = lo, A = f.leaves[qi];
         const int4 cA = f.ci[A];
         const int par = t.parent[A];
-        // a level-10 leaf may hold more than 64 bodies: 64 at a time
-        for (int s0 = t.start[A]; s0 < t.end[A]; s0 += 64) {
-            const int nb = min(64, t.end[A] - s0);
-            int inh_off = 0, inh_cnt = 1;
-            if (par >= 0) {
-                const int2 d = f.down[par];
-                inh_off = d.x;
-                inh_cnt = d.y;
+        const int nearc = f.nearc[A], ns = src_slices(nearc);
+        const int j = it - f.item_off[qi], bc = j / ns, sc = j % ns;
+        const int nbt = t.end[A] - t.start[A];
+        const int s0 = t.start[A] + 64 * bc, nb = min(64, t.end[A] - s0);
+        const int per = (nearc + ns - 1) / ns;
+        const int src_lo = sc * per, src_hi = min(nearc, src_lo + per);
+        int inh_off = 0, inh_cnt = 1;
+        if (par >= 0) {
+            const int2 d = f.down[par];
+            inh_off = d.x;
+            inh_cnt = d.y;
+        }
+        const int *inh = f.pool + inh_off;
+        double z[3];
+        centre_of(p.box, cA, z);
+        const float cx = (float)z[0], cy = (float)z[1], cz = (float)z[2];
+        // two bodies per lane, b0 and b0 + T (T = nb / 2 rounded up to a power
+        // of two), and 32 / T slices of the sources
+        const int half = (nb + 1) >> 1;
+        const int T = half <= 1 ? 1 : 1 << (32 - __clz(half - 1));
+        const int S = 32 / T;
+        const int slice = lane / T, b0 = lane % T;
+        const bool v0 = b0 < nb, v1 = b0 + T < nb;
+        float2 nx0 = make_float2(0.f, 0.f), ny0 = nx0, nz0 = nx0, nx1 = nx0, ny1 = nx0, nz1 = nx0;
+        if (v0) {
+            const float4 h = __ldg(p.P + s0 + b0), l = __ldg(p.Plo + s0 + b0);
+            const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
+            nx0 = make_float2(x, x);
+            ny0 = make_float2(y, y);
+            nz0 = make_float2(zz, zz);
+        }
+        if (v1) {
+            const float4 h = __ldg(p.P + s0 + b0 + T), l = __ldg(p.Plo + s0 + b0 + T);
+            const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
+            nx1 = make_float2(x, x);
+            ny1 = make_float2(y, y);
+            nz1 = make_float2(zz, zz);
+        }
+        float2 ax0 = make_float2(0.f, 0.f), ay0 = ax0, az0 = ax0, ax1 = ax0, ay1 = ax0, az1 = ax0;
+        float ks[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        float kc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        auto fold = [&]() {
+            kahan_add(ks[0][0], kc[0][0], ax0.x);
+            kahan_add(ks[0][0], kc[0][0], ax0.y);
+            kahan_add(ks[0][1], kc[0][1], ay0.x);
+            kahan_add(ks[0][1], kc[0][1], ay0.y);
+            kahan_add(ks[0][2], kc[0][2], az0.x);
+            kahan_add(ks[0][2], kc[0][2], az0.y);
+            kahan_add(ks[1][0], kc[1][0], ax1.x);
+            kahan_add(ks[1][0], kc[1][0], ax1.y);
+            kahan_add(ks[1][1], kc[1][1], ay1.x);
+            kahan_add(ks[1][1], kc[1][1], ay1.y);
+            kahan_add(ks[1][2], kc[1][2], az1.x);
+            kahan_add(ks[1][2], kc[1][2], az1.y);
+            ax0 = ay0 = az0 = ax1 = ay1 = az1 = make_float2(0.f, 0.f);
+        };
+        auto eval = [&](int npairs) {
+            for (int q = slice; q < npairs; q += S) {
+                const float4 a = L4[2 * q], bq = L4[2 * q + 1];
+                const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+                const float2 sz = make_float2(bq.x, bq.y), sm = make_float2(bq.z, bq.w);
+                pair_terms<ZEPS>(add2(sx, nx0), add2(sy, ny0), add2(sz, nz0), sm, e2, ax0, ay0, az0);
+                pair_terms<ZEPS>(add2(sx, nx1), add2(sy, ny1), add2(sz, nz1), sm, e2, ax1, ay1, az1);
             }
-            const int *inh = f.pool + inh_off;
-            double z[3];
-            centre_of(p.box, cA, z);
-            const float cx = (float)z[0], cy = (float)z[1], cz = (float)z[2];
-            const bool two = nb > 32;
-            const int T = two ? 32 : (nb <= 1 ? 1 : 1 << (32 - __clz(nb - 1)));
-            const int S = 32 / T;
-            const int slice = lane / T, b0 = lane % T;
-            const bool v0 = b0 < nb, v1 = two && b0 + 32 < nb;
-            float2 nx0 = make_float2(0.f, 0.f), ny0 = nx0, nz0 = nx0, nx1 = nx0, ny1 = nx0, nz1 = nx0;
-            if (v0) {
-                const float4 h = __ldg(p.P + s0 + b0), l = __ldg(p.Plo + s0 + b0);
-                const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
-                nx0 = make_float2(x, x);
-                ny0 = make_float2(y, y);
-                nz0 = make_float2(zz, zz);
-            }
-            if (v1) {
-                const float4 h = __ldg(p.P + s0 + b0 + 32), l = __ldg(p.Plo + s0 + b0 + 32);
-                const float x = -rel(h.x, l.x, cx), y = -rel(h.y, l.y, cy), zz = -rel(h.z, l.z, cz);
-                nx1 = make_float2(x, x);
-                ny1 = make_float2(y, y);
-                nz1 = make_float2(zz, zz);
-            }
-            float2 ax0 = make_float2(0.f, 0.f), ay0 = ax0, az0 = ax0, ax1 = ax0, ay1 = ax0, az1 = ax0;
-            float ks[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, kc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-            auto fold = [&]() {
-                kahan_add(ks[0][0], kc[0][0], ax0.x);
-                kahan_add(ks[0][0], kc[0][0], ax0.y);
-                kahan_add(ks[0][1], kc[0][1], ay0.x);
-                kahan_add(ks[0][1], kc[0][1], ay0.y);
-                kahan_add(ks[0][2], kc[0][2], az0.x);
-                kahan_add(ks[0][2], kc[0][2], az0.y);
-                if (two) {
-                    kahan_add(ks[1][0], kc[1][0], ax1.x);
-                    kahan_add(ks[1][0], kc[1][0], ax1.y);
-                    kahan_add(ks[1][1], kc[1][1], ay1.x);
-                    kahan_add(ks[1][1], kc[1][1], ay1.y);
-                    kahan_add(ks[1][2], kc[1][2], az1.x);
-                    kahan_add(ks[1][2], kc[1][2], az1.y);
-                }
-                ax0 = ay0 = az0 = ax1 = ay1 = az1 = make_float2(0.f, 0.f);
-            };
-            auto eval = [&](int npairs) {
-                for (int q = slice; q < npairs; q += S) {
-                    const float4 a = L4[2 * q], bq = L4[2 * q + 1];
-                    const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
-                    const float2 sz = make_float2(bq.x, bq.y), sm = make_float2(bq.z, bq.w);
-                    pair_terms<ZEPS>(add2(sx, nx0), add2(sy, ny0), add2(sz, nz0), sm, e2, ax0, ay0, az0);
-                    if (two)
-                        pair_terms<ZEPS>(add2(sx, nx1), add2(sy, ny1), add2(sz, nz1), sm, e2, ax1, ay1,
-                                         az1);
-                }
-            };
-            int cnt = 0, nnear = 0;
-            auto flush = [&]() {
-                __syncwarp();
-                eval(FLUSH / 2);
-                fold();
-                __syncwarp();
-                for (int c = lane; c < FLUSH; c += 32) lists[warp][c] = lists[warp][FLUSH + c];
-                cnt -= FLUSH;
-                __syncwarp();
-            };
-            if (lane < LEVELS) w.lsz[lane] = 0;
+        };
+        int cnt = 0, seen = 0;  // listed sources; direct sources met so far in walk order
+        auto flush = [&]() {
             __syncwarp();
-            int cursor = 0, B = -1;
-            while (next_round(w, inh, inh_cnt, cursor, lane, B)) {
-                bool open = false, leafB = false;
-                int nchB = 0, firstB = 0, lvB = 0;
-                if (B >= 0) {
-                    const int4 cB = __ldg(f.ci + B);
-                    const bool sep = separated(cA, cB, crit);
+            eval(FLUSH / 2);
+            fold();
+            __syncwarp();
+            for (int c = lane; c < FLUSH; c += 32) lists[warp][c] = lists[warp][FLUSH + c];
+            cnt -= FLUSH;
+            __syncwarp();
+        };
+        if (lane < LEVELS) w.lsz[lane] = 0;
+        __syncwarp();
+        int cursor = 0, B = -1;
+        while (seen < src_hi && next_round(w, inh, inh_cnt, cursor, lane, B)) {
+            bool open = false, direct = false;
+            int nchB = 0, firstB = 0, lvB = 0;
+            if (B >= 0) {
+                const int4 cB = __ldg(f.ci + B);
+                if (!separated(cA, cB, crit)) {
                     nchB = t.nchild[B];
-                    open = !sep && nchB > 0;
-                    leafB = !sep && nchB == 0;
-                    firstB = t.first[B];
-                    lvB = cB.w;
+                    open = nchB > 0 && !all_direct(cA, cB, p.theta);
+                    direct = !open;
                 }
-                push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
-                if (__ballot_sync(FULL, leafB)) {
-                    int ls = 0, lsz = 0;
-                    if (leafB) {
-                        ls = t.start[B];
-                        lsz = t.end[B] - ls;
-                    }
-                    const int linc = warp_incl_scan(lsz, lane);
-                    const int lexc = linc - lsz;
-                    const int tot = __shfl_sync(FULL, linc, 31);
-                    nnear += tot;
-                    for (int c0 = 0; c0 < tot; c0 += 32) {
-                        const int pos = c0 + lane;
-                        const int j = warp_span_of(linc, pos) & 31;
-                        const int body = __shfl_sync(FULL, ls, j) + (pos - __shfl_sync(FULL, lexc, j));
-                        const int kk = min(32, tot - c0);
-                        if (lane < kk) {
-                            const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
-                            list_put(Lf, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
-                                     rel(bh.z, bl.z, cz), bh.w);
-                        }
-                        cnt += kk;
-                        if (cnt >= FLUSH) flush();
-                    }
-                }
+                firstB = t.first[B];
+                lvB = cB.w;
             }
-            if (cnt > 0) {
-                if (lane == 0 && (cnt & 1)) list_put(Lf, cnt, 0.f, 0.f, 0.f, 0.f);
-                __syncwarp();
-                eval((cnt + 1) >> 1);
-                fold();
-            }
-            // combine the slices (lane b0 of slice 0 ends with the total)
-            double ns[2][3];
-    #pragma unroll
-            for (int b = 0; b < 2; ++b)
-    #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    double v = (double)ks[b][c] - (double)kc[b][c];
-                    for (int off = 16; off >= T; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-                    ns[b][c] = v;
+            push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
+            if (__ballot_sync(FULL, direct)) {
+                int ls = 0, lsz = 0;
+                if (direct) {
+                    ls = t.start[B];
+                    lsz = t.end[B] - ls;
                 }
-            if (slice == 0) {
-                const float *Lc = f.L + (size_t)A * NP;
-                const double inv_e = (double)(1 << cA.w) / p.box[3];
-    #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const bool valid = b == 0 ? v0 : v1;
-                    if (!valid) continue;
-                    const int k = s0 + b0 + 32 * b;
-                    const int i = p.perm[k];
-                    float pw[3][P + 1];
-    #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        scaled_powers<P>((float)((p.pos[3 * (size_t)i + c] - z[c]) * inv_e), pw[c]);
-                    float fa[3] = {0.f, 0.f, 0.f};
-                    sfor<0, nterms(P - 1)>([&](auto kI) {
-                        constexpr int q = decltype(kI)::value;
-                        constexpr int a = mi_of(q, 0), bb = mi_of(q, 1), c = mi_of(q, 2);
-                        const float wv = pw[0][a] * pw[1][bb] * pw[2][c];
-                        fa[0] = fmaf(__ldg(Lc + slot_of(a + 1, bb, c)), wv, fa[0]);
-                        fa[1] = fmaf(__ldg(Lc + slot_of(a, bb + 1, c)), wv, fa[1]);
-                        fa[2] = fmaf(__ldg(Lc + slot_of(a, bb, c + 1)), wv, fa[2]);
-                    });
-                    const double gx = p.G * (ns[b][0] + (double)fa[0] * inv_e);
-                    const double gy = p.G * (ns[b][1] + (double)fa[1] * inv_e);
-                    const double gz = p.G * (ns[b][2] + (double)fa[2] * inv_e);
-                    double *a = p.acc + 3 * (size_t)i;
-                    a[0] = gx;
-                    a[1] = gy;
-                    a[2] = gz;
-                    if (p.counts) {
-                        const int2 cm = f.cum[A];
-                        p.counts[3 * (size_t)i] = cm.x;
-                        p.counts[3 * (size_t)i + 1] = cm.y;
-                        p.counts[3 * (size_t)i + 2] = nnear;
+                const int linc = warp_incl_scan(lsz, lane);
+                const int lexc = linc - lsz;
+                const int tot = __shfl_sync(FULL, linc, 31);
+                // this round's direct sources are [seen, seen + tot) in walk order
+                const int a0 = max(src_lo - seen, 0), a1 = min(src_hi - seen, tot);
+                for (int c0 = a0; c0 < a1; c0 += 32) {
+                    const int pos = c0 + lane;
+                    const int jj = warp_span_of(linc, pos) & 31;
+                    const int body = __shfl_sync(FULL, ls, jj) + (pos - __shfl_sync(FULL, lexc, jj));
+                    const int kk = min(32, a1 - c0);
+                    if (lane < kk) {
+                        const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
+                        list_put(Lf, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
+                                 rel(bh.z, bl.z, cz), bh.w);
                     }
-                    if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+                    cnt += kk;
+                    if (cnt >= FLUSH) flush();
                 }
+                seen += tot;
             }
-            if (lane == 0) atomicAdd(f.stats + 3, (unsigned long long)nb * (unsigned long long)nnear);
+        }
+        if (cnt > 0) {
+            if (lane == 0 && (cnt & 1)) list_put(Lf, cnt, 0.f, 0.f, 0.f, 0.f);
             __syncwarp();
+            eval((cnt + 1) >> 1);
+            fold();
+        }
+        // combine the slices (lane b0 of slice 0 ends with the total)
+        double ns3[2][3];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = (double)ks[b][c] - (double)kc[b][c];
+                for (int off = 16; off >= T; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+                ns3[b][c] = v;
+            }
+        if (slice == 0) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (!(b == 0 ? v0 : v1)) continue;
+                const int k = s0 + b0 + T * b;
+                if (ns == 1) {
+                    write_body<P>(p, A, cA, k, ns3[b][0], ns3[b][1], ns3[b][2], nearc);
+                } else {
+                    double *d = f.part + 3 * ((size_t)f.part_off[qi] + (size_t)sc * nbt +
+                                              (size_t)(k - t.start[A]));
+                    d[0] = ns3[b][0];
+                    d[1] = ns3[b][1];
+                    d[2] = ns3[b][2];
+                }
+            }
+        }
+        if (lane == 0)
+            atomicAdd(f.stats + 3, (unsigned long long)nb * (unsigned long long)(src_hi - src_lo));
+        __syncwarp();
+    }
+}
+
+// Leaves whose direct sum was split: the slices' partial sums added in slice
+// order, then the far field, per body (a thread per body of each such leaf).
+template <int P>
+__global__ void __launch_bounds__(256) fmm_combine_kernel(const FmmParams p)
+{
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const int nleaves = f.meta[FMM_META_NLEAVES];
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int qi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); qi < nleaves; qi += warps) {
+        const int A = f.leaves[qi];
+        const int nearc = f.nearc[A], ns = src_slices(nearc);
+        if (ns == 1) continue;
+        const int4 cA = f.ci[A];
+        const int nbt = t.end[A] - t.start[A];
+        const double *base = f.part + 3 * (size_t)f.part_off[qi];
+        for (int b = lane; b < nbt; b += 32) {
+            double s[3] = {0.0, 0.0, 0.0};
+            for (int sc = 0; sc < ns; ++sc) {
+                const double *d = base + 3 * ((size_t)sc * nbt + b);
+                s[0] += d[0];
+                s[1] += d[1];
+                s[2] += d[2];
+            }
+            write_body<P>(p, A, cA, t.start[A] + b, s[0], s[1], s[2], nearc);
         }
     }
 }
@@ -868,40 +1009,44 @@ __global__ void fmm_init_kernel(FmmView f)
     }
 }
 
-// Upward pass, the downward levels and the near field, on stream s.
+template <class K>
+int resident_grid(K kernel, int threads, int num_sms, cudaError_t &e)
+{
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    return std::max(1, per_sm) * num_sms;
+}
+
+// near = false: upward pass, downward levels and the near-field work items;
+// near = true: the near field and the split leaves' combination.
 template <int P>
-cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, int &kernels)
+cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, bool near, int &kernels)
 {
     kernels = 0;
-    cudaError_t e = cudaMemsetAsync(p.f.arrive, 0, sizeof(int) * (size_t)p.tree.cap, s);
-    if (e != cudaSuccess) return e;
-    fmm_init_kernel<P><<<1, 32, 0, s>>>(p.f);
-    ++kernels;
-    const int up_grid = (int)std::min<long long>(4096, ((long long)p.tree.cap + 255) / 256);
-    fmm_up_kernel<P><<<up_grid, 256, 0, s>>>(p);
-    ++kernels;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_down_kernel<P>, 32 * WARPS, 0);
-    if (e != cudaSuccess) return e;
-    const int down_grid = std::max(1, per_sm) * p.num_sms;
-    for (int L = 0; L < LEVELS; ++L) {
-        fmm_down_kernel<P><<<down_grid, 32 * WARPS, 0, s>>>(p, L);
-        ++kernels;
+    cudaError_t e = cudaSuccess;
+    if (!near) {
+        e = cudaMemsetAsync(p.f.arrive, 0, sizeof(int) * (size_t)p.tree.cap, s);
+        if (e != cudaSuccess) return e;
+        fmm_init_kernel<P><<<1, 32, 0, s>>>(p.f);
+        const int up_grid = (int)std::min<long long>(4096, ((long long)p.tree.cap + 255) / 256);
+        fmm_up_kernel<P><<<up_grid, 256, 0, s>>>(p);
+        const int down_grid = resident_grid(fmm_down_kernel<P>, 32 * WARPS, p.num_sms, e);
+        if (e != cudaSuccess) return e;
+        for (int L = 0; L < LEVELS; ++L) fmm_down_kernel<P><<<down_grid, 32 * WARPS, 0, s>>>(p, L);
+        fmm_items_kernel<P><<<1, 1024, 0, s>>>(p);
+        kernels = 3 + LEVELS;
+        return cudaGetLastError();
     }
     const bool zeps = p.eps2f == 0.0f;
-    if (zeps)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_near_kernel<P, true>,
-                                                          32 * WARPS, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_near_kernel<P, false>,
-                                                          32 * WARPS, 0);
+    const int near_grid = zeps ? resident_grid(fmm_near_kernel<P, true>, 32 * WARPS, p.num_sms, e)
+                               : resident_grid(fmm_near_kernel<P, false>, 32 * WARPS, p.num_sms, e);
     if (e != cudaSuccess) return e;
-    const int near_grid = std::max(1, per_sm) * p.num_sms;
     if (zeps)
         fmm_near_kernel<P, true><<<near_grid, 32 * WARPS, 0, s>>>(p);
     else
         fmm_near_kernel<P, false><<<near_grid, 32 * WARPS, 0, s>>>(p);
-    ++kernels;
+    fmm_combine_kernel<P><<<4 * p.num_sms, 256, 0, s>>>(p);
+    kernels = 2;
     return cudaGetLastError();
 }
 

@@ -3,6 +3,6 @@
 
 namespace nb {
 namespace fmm {
-template cudaError_t launch_fmm_order<4>(cudaStream_t, const FmmParams &, int &);
+template cudaError_t launch_fmm_order<4>(cudaStream_t, const FmmParams &, bool, int &);
 }  // namespace fmm
 }  // namespace nb

@@ -18,7 +18,8 @@ enum : int { ERR_NONFINITE = 1, ERR_TREE = 2 };
 // Kernel families with autotuned variants (the `kind` of nb_variant_*).
 enum Kind : int { KIND_FORCE = 0, KIND_BATCHED = 1, KIND_VJP = 2, KIND_COUNT = 3 };
 // Event-timing tags of nb_profile_read: 0-2 the kinds above, then these.
-enum ProfKind : int { PROF_ENERGY = 3, PROF_TREE_WALK = 4, PROF_TREE_BUILD = 5, PROF_FMM = 6 };
+enum ProfKind : int { PROF_ENERGY = 3, PROF_TREE_WALK = 4, PROF_TREE_BUILD = 5, PROF_FMM_FAR = 6,
+                      PROF_FMM_NEAR = 7 };
 
 // One compiled kernel: CTA shape plus the function to launch.  Every kernel
 // of a family takes a single by-value parameter struct.
@@ -191,7 +192,7 @@ constexpr int TREE_META_COUNT = 0, TREE_META_BASE = 12;
 constexpr int FMM_MIN_ORDER = 2, FMM_MAX_ORDER = 6, FMM_MAX_LEAF = 64;
 int fmm_floats(int order);
 enum : int { FMM_META_LEVEL = 0, FMM_META_NEAR = 11, FMM_META_POOL = 12, FMM_META_OVERFLOW = 13,
-             FMM_META_NLEAVES = 14, FMM_META_INTS = 16 };
+             FMM_META_NLEAVES = 14, FMM_META_ITEMS = 15, FMM_META_PSLOTS = 16, FMM_META_INTS = 20 };
 struct FmmView {
     int order, np;         // expansion order p; floats per expansion
     int4 *ci;              // per node: integer centre in units ext/2048 (.xyz), level (.w)
@@ -200,6 +201,11 @@ struct FmmView {
     int2 *cum;             // per node: source cells acting on it and its ancestors, bodies they hold
     int *arrive;           // upward-pass arrival counters (zeroed before each pass)
     int *leaves;           // leaf ids, in the order the downward pass meets them
+    int *nearc;            // per node (leaves): bodies met directly
+    int *item_off;         // per leaf index: first near-field work item (exclusive scan)
+    int *part_off;         // per leaf index: first partial-sum slot (leaves split in several items)
+    double *part;          // [slots][3] partial direct sums of split leaves
+    long long part_cap;    // slots part holds
     int *pool;             // candidate lists; pool[0] = 0, the root's own list
     long long pool_cap;
     int *meta;             // [FMM_META_INTS] queues, pool top, overflow flag, leaf count
@@ -221,7 +227,9 @@ struct FmmParams {
     int *err;
     int num_sms;
 };
-cudaError_t launch_fmm(cudaStream_t s, const FmmParams &p, int &kernels);
+// near = false: upward pass, downward levels, near-field work items (the
+// host then reads the meta counters); near = true: the near field.
+cudaError_t launch_fmm(cudaStream_t s, const FmmParams &p, bool near, int &kernels);
 
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);

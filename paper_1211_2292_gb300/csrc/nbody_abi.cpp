@@ -509,13 +509,15 @@ void free_tree_nodes(nb_ctx *c)
 void free_fmm(nb_ctx *c)
 {
     nb::FmmView &f = c->fmm;
-    void *arrays[] = {f.ci, f.M, f.L, f.down, f.cum, f.arrive, f.leaves, f.pool};
+    void *arrays[] = {f.ci,    f.M,     f.L,        f.down,     f.cum, f.arrive,
+                      f.leaves, f.nearc, f.item_off, f.part_off, f.part, f.pool};
     for (void *a : arrays) cudaFree(a);
     f.ci = nullptr;
     f.M = f.L = nullptr;
     f.down = f.cum = nullptr;
-    f.arrive = f.leaves = f.pool = nullptr;
-    f.pool_cap = 0;
+    f.arrive = f.leaves = f.nearc = f.item_off = f.part_off = f.pool = nullptr;
+    f.part = nullptr;
+    f.pool_cap = f.part_cap = 0;
     c->fmm_cap = c->fmm_np = 0;
 }
 
@@ -654,6 +656,9 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
         if (st == NB_OK) f.cum = dev_alloc<int2>(c, m, st);
         if (st == NB_OK) f.arrive = dev_alloc<int>(c, m, st);
         if (st == NB_OK) f.leaves = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) f.nearc = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) f.item_off = dev_alloc<int>(c, m + 1, st);
+        if (st == NB_OK) f.part_off = dev_alloc<int>(c, m + 1, st);
         if (st != NB_OK) {
             free_fmm(c);
             return st;
@@ -750,9 +755,23 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
     return NB_OK;
 }
 
-// Sort, pack and build the tree, then the FMM passes; synchronises to see
-// whether the candidate pool sufficed, and runs the FMM passes again with a
-// larger pool if not.
+// Partial-sum slots for the near field's split leaves.
+nb_status ensure_fmm_part(nb_ctx *c, long long slots)
+{
+    nb::FmmView &f = c->fmm;
+    if (slots <= f.part_cap) return NB_OK;
+    nb_status st = NB_OK;
+    cudaFree(f.part);
+    const long long want = std::max(slots, f.part_cap * 3 / 2);
+    f.part = dev_alloc<double>(c, 3 * (size_t)want, st);
+    f.part_cap = st == NB_OK ? want : 0;
+    return st;
+}
+
+// Sort, pack and build the tree, then the FMM passes; synchronises after the
+// downward passes to see whether the candidate pool sufficed (if not, the
+// pool grows and those passes run again) and how many partial sums the near
+// field needs.
 nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
                          double eps, double theta, int order, int leaf_cap, double *acc,
                          int *counts)
@@ -791,16 +810,24 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
         p.counts = counts;
         p.err = c->err;
         p.num_sms = c->num_sms;
-        {
-            TreeTimer tm(c, nb::PROF_FMM, s);
-            NB_CUDA(c, nb::launch_fmm(s, p, k));
-            c->launches += k;
-            tm.done();
-        }
+        TreeTimer tm(c, nb::PROF_FMM_FAR, s);
+        NB_CUDA(c, nb::launch_fmm(s, p, false, k));
+        c->launches += k;
+        tm.done();
         int meta[nb::FMM_META_INTS];
         NB_CUDA(c, cudaMemcpyAsync(meta, c->fmm.meta, sizeof(meta), cudaMemcpyDeviceToHost, s));
         NB_CUDA(c, cudaStreamSynchronize(s));
-        if (!meta[nb::FMM_META_OVERFLOW]) return NB_OK;
+        if (!meta[nb::FMM_META_OVERFLOW]) {
+            NB_TRY(ensure_fmm_part(c, std::max(1, meta[nb::FMM_META_PSLOTS])));
+            p.f = c->fmm;
+            p.f.order = order;
+            p.f.np = nb::fmm_floats(order);
+            TreeTimer tn(c, nb::PROF_FMM_NEAR, s);
+            NB_CUDA(c, nb::launch_fmm(s, p, true, k));
+            c->launches += k;
+            tn.done();
+            return NB_OK;
+        }
         if (attempt == 8) return failf(c, NB_ENOMEM, "FMM candidate lists keep overflowing");
         const long long need = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_POOL],
                                                    c->fmm.pool_cap) * 2;

@@ -298,7 +298,8 @@ class NBody:
 
     def profile_read(self, kind: int):
         """(launches, total milliseconds) recorded for kind 0 force, 1 batched,
-        2 VJP, 3 energy, 4 tree walk, 5 tree build, 6 fast multipole passes."""
+        2 VJP, 3 energy, 4 tree walk, 5 tree build, 6 fast multipole upward and
+        downward passes, 7 fast multipole near field."""
         cnt, ms = ctypes.c_int64(), ctypes.c_double()
         self._call("nb_profile_read", int(kind), ctypes.byref(cnt), ctypes.byref(ms))
         return cnt.value, ms.value
