@@ -350,6 +350,10 @@ nb_status nb_fmm_forces(nb_ctx *ctx, int64_t n, const double *pos, const double 
                         double eps, double theta, int order, int leaf_cap, double *acc,
                         int32_t *counts);
 nb_status nb_fmm_stats(nb_ctx *ctx, int64_t *out);
+/* Replace the candidate pool by one of `entries` ints (1 <= entries < 2^31),
+ * e.g. to size it for a known workload; synchronises the stream.  A pool too
+ * small still gives the same results: the passes grow it and run again. */
+nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
 
 /*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form

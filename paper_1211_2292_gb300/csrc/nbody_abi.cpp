@@ -1495,8 +1495,25 @@ nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *m
     if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 3 * sizeof(int32_t), "counts"));
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
-    NB_TRY(ensure_fmm(c, order, (long long)(1 << 20) + 32LL * c->n_max));
+    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max));
     return fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, counts);
+}
+
+nb_status nb_fmm_reserve(nb_ctx *c, int64_t entries)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (entries < 1 || entries > 0x7fffffffLL)
+        return failf(c, NB_EINVAL, "pool of %lld entries outside [1, 2^31)", (long long)entries);
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    nb::FmmView &f = c->fmm;
+    cudaFree(f.pool);
+    f.pool = nullptr;
+    f.pool_cap = 0;
+    nb_status st = NB_OK;
+    f.pool = dev_alloc<int>(c, (size_t)entries, st);
+    if (st == NB_OK) f.pool_cap = entries;
+    return st;
 }
 
 nb_status nb_fmm_stats(nb_ctx *c, int64_t *out)

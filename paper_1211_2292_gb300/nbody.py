@@ -72,6 +72,7 @@ SIGNATURES = {
     "nb_fmm_forces": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_int,
                                _c_vp, _c_vp]),
     "nb_fmm_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
+    "nb_fmm_reserve": (_c_int, [_c_vp, _c_i64]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
@@ -351,6 +352,10 @@ class NBody:
                    float(eps), float(theta), int(order), int(leaf_cap), _ptr(out, "acc", 3 * n),
                    _ptr_i32(cnt, "counts", 3 * n))
         return (out, cnt) if counts else out
+
+    def fmm_reserve(self, entries):
+        """Replace the FMM candidate pool by one of `entries` ints."""
+        self._call("nb_fmm_reserve", int(entries))
 
     def fmm_stats(self):
         """{nodes, leaves, expansions, direct_pairs} of the last FMM call."""

@@ -147,3 +147,23 @@ def test_argument_checks(cuda):
         assert lib.nb_fmm_forces(nb.h, 65, x.data_ptr(), m.data_ptr(), 1.0, 0.01, 0.5, 4, 16,
                                  a.data_ptr(), None) == 1
         assert nb.launches == before
+
+
+def test_pool_overflow_reruns_with_a_larger_pool(cuda):
+    # A pool of 16 candidate ids overflows at the first non-leaf cells; the
+    # host doubles it and reruns the passes until it suffices, and the result
+    # is bit-identical to the run with the default pool.
+    b = inputs.plummer(20000, seed=89)
+    x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        a1, c1 = nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 4, 16, counts=True)
+        nb.sync()
+        st1 = nb.fmm_stats()
+        nb.fmm_reserve(16)
+        a2, c2 = nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 4, 16, counts=True)
+        nb.sync()
+        st2 = nb.fmm_stats()
+        with pytest.raises(nbody.NBodyError):
+            nb.fmm_reserve(0)
+    assert np.array_equal(host(a1), host(a2)) and np.array_equal(host(c1), host(c2))
+    assert st1 == st2
