@@ -350,6 +350,13 @@ nb_status nb_fmm_forces(nb_ctx *ctx, int64_t n, const double *pos, const double 
                         double eps, double theta, int order, int leaf_cap, double *acc,
                         int32_t *counts);
 nb_status nb_fmm_stats(nb_ctx *ctx, int64_t *out);
+/* nb_step with FMM forces: nsteps + 1 evaluations (the first skipped with
+ * NB_ACC_VALID), the closing half-kick fused into the kernel that writes the
+ * accelerations.  Synchronises like nb_fmm_forces, so NB_USE_GRAPH is
+ * refused (NB_EINVAL). */
+nb_status nb_fmm_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
+                      double G, double eps, double theta, int order, int leaf_cap, double dt,
+                      int64_t nsteps, double *acc, unsigned flags);
 /* Replace the candidate pool by one of `entries` ints (1 <= entries < 2^31),
  * e.g. to size it for a known workload; synchronises the stream.  A pool too
  * small still gives the same results: the passes grow it and run again. */

@@ -756,6 +756,12 @@ __device__ __forceinline__ void write_body(const FmmParams &p, int A, int4 cA, i
     a[0] = gx;
     a[1] = gy;
     a[2] = gz;
+    if (p.vel) {  // a step's closing half-kick
+        double *v = p.vel + 3 * (size_t)i;
+        v[0] += p.half_dt * gx;
+        v[1] += p.half_dt * gy;
+        v[2] += p.half_dt * gz;
+    }
     if (p.counts) {
         const int2 cm = f.cum[A];
         p.counts[3 * (size_t)i] = cm.x;

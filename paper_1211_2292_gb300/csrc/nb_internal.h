@@ -223,6 +223,8 @@ struct FmmParams {
     float eps2f;
     double G;
     double *acc;
+    double *vel;            // vel != NULL: vel += half_dt * acc
+    double half_dt;
     int *counts;            // optional [n][3]
     int *err;
     int num_sms;

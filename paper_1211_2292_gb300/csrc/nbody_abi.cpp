@@ -681,6 +681,18 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
     return NB_OK;
 }
 
+nb_status check_fmm_args(nb_ctx *c, double theta, int order, int leaf_cap)
+{
+    if (!std::isfinite(theta) || theta < 0)
+        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
+    if (order < nb::FMM_MIN_ORDER || order > nb::FMM_MAX_ORDER)
+        return failf(c, NB_EINVAL, "order = %d outside [%d, %d]", order, nb::FMM_MIN_ORDER,
+                     nb::FMM_MAX_ORDER);
+    if (leaf_cap < 1 || leaf_cap > nb::FMM_MAX_LEAF)
+        return failf(c, NB_EINVAL, "leaf_cap = %d outside [1, %d]", leaf_cap, nb::FMM_MAX_LEAF);
+    return NB_OK;
+}
+
 // Events around a tree-code launch sequence (nb_profile), outside captures.
 struct TreeTimer {
     nb_ctx *c;
@@ -774,7 +786,7 @@ nb_status ensure_fmm_part(nb_ctx *c, long long slots)
 // field needs.
 nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *mass, double G,
                          double eps, double theta, int order, int leaf_cap, double *acc,
-                         int *counts)
+                         int *counts, double *vel = nullptr, double half_dt = 0.0)
 {
     cudaStream_t s = c->stream;
     int k = 0;
@@ -807,6 +819,8 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
         p.eps2f = (float)(eps * eps);
         p.G = G;
         p.acc = acc;
+        p.vel = vel;
+        p.half_dt = half_dt;
         p.counts = counts;
         p.err = c->err;
         p.num_sms = c->num_sms;
@@ -1481,13 +1495,7 @@ nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *m
     DeviceGuard guard(c->device);
     NB_TRY(check_n(c, n));
     NB_TRY(check_scalars(c, G, eps));
-    if (!std::isfinite(theta) || theta < 0)
-        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
-    if (order < nb::FMM_MIN_ORDER || order > nb::FMM_MAX_ORDER)
-        return failf(c, NB_EINVAL, "order = %d outside [%d, %d]", order, nb::FMM_MIN_ORDER,
-                     nb::FMM_MAX_ORDER);
-    if (leaf_cap < 1 || leaf_cap > nb::FMM_MAX_LEAF)
-        return failf(c, NB_EINVAL, "leaf_cap = %d outside [1, %d]", leaf_cap, nb::FMM_MAX_LEAF);
+    NB_TRY(check_fmm_args(c, theta, order, leaf_cap));
     const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
     NB_TRY(check_dev(c, pos, v3, "pos"));
     NB_TRY(check_dev(c, mass, v1, "mass"));
@@ -1497,6 +1505,38 @@ nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *m
     NB_TRY(ensure_tree(c, leaf_cap));
     NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max));
     return fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, counts);
+}
+
+nb_status nb_fmm_step(nb_ctx *c, int64_t n, double *pos, double *vel, const double *mass,
+                      double G, double eps, double theta, int order, int leaf_cap, double dt,
+                      int64_t nsteps, double *acc, unsigned flags)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    NB_TRY(check_scalars(c, G, eps));
+    NB_TRY(check_fmm_args(c, theta, order, leaf_cap));
+    if (!std::isfinite(dt)) return failf(c, NB_EINVAL, "dt is not finite");
+    if (nsteps < 0) return failf(c, NB_EINVAL, "nsteps < 0");
+    if (flags & ~NB_ACC_VALID)
+        return failf(c, NB_EINVAL, "unknown flags (the FMM synchronises: no graph)");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, acc, v3, "acc"));
+    if (n == 0) return NB_OK;
+    NB_TRY(ensure_tree(c, leaf_cap));
+    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max));
+    if (!(flags & NB_ACC_VALID))
+        NB_TRY(fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, nullptr));
+    for (int64_t st = 0; st < nsteps; ++st) {
+        NB_LAUNCHED(c, nb::launch_kdp(c->stream, is_f64(c), (int)n, pos, vel, acc, mass, 0.5 * dt,
+                                      dt, nullptr, nullptr, nullptr, nullptr));
+        NB_TRY(fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, nullptr, vel,
+                              0.5 * dt));
+    }
+    return NB_OK;
 }
 
 nb_status nb_fmm_reserve(nb_ctx *c, int64_t entries)

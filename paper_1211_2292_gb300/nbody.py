@@ -73,6 +73,8 @@ SIGNATURES = {
                                _c_vp, _c_vp]),
     "nb_fmm_stats": (_c_int, [_c_vp, ctypes.POINTER(_c_i64)]),
     "nb_fmm_reserve": (_c_int, [_c_vp, _c_i64]),
+    "nb_fmm_step": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
+                             _c_int, _c_dbl, _c_i64, _c_vp, _c_uint]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
@@ -352,6 +354,15 @@ class NBody:
                    float(eps), float(theta), int(order), int(leaf_cap), _ptr(out, "acc", 3 * n),
                    _ptr_i32(cnt, "counts", 3 * n))
         return (out, cnt) if counts else out
+
+    def fmm_step(self, pos, vel, mass, G, eps, theta, order, leaf_cap, dt, nsteps, acc,
+                 acc_valid=False):
+        """Kick-drift-kick steps with FMM forces (eager; the FMM synchronises)."""
+        n = mass.shape[0]
+        self._call("nb_fmm_step", n, _ptr(pos, "pos", 3 * n), _ptr(vel, "vel", 3 * n),
+                   _ptr(mass, "mass", n), float(G), float(eps), float(theta), int(order),
+                   int(leaf_cap), float(dt), int(nsteps), _ptr(acc, "acc", 3 * n),
+                   NB_ACC_VALID if acc_valid else 0)
 
     def fmm_reserve(self, entries):
         """Replace the FMM candidate pool by one of `entries` ints."""

@@ -167,3 +167,45 @@ def test_pool_overflow_reruns_with_a_larger_pool(cuda):
             nb.fmm_reserve(0)
     assert np.array_equal(host(a1), host(a2)) and np.array_equal(host(c1), host(c2))
     assert st1 == st2
+
+
+def test_fmm_step_matches_oracle_kdk_at_theta_zero(cuda):
+    # theta = 0: every evaluation is the direct sum, so ten FMM steps follow
+    # the oracle's leapfrog.
+    b = inputs.plummer(2000, seed=90)
+    xr, vr, _ = oracle.kdk(b.pos, b.vel, b.mass, 1.0, 0.01, 1e-3, 10)
+    x, v, m = (to_dev(t, cuda) for t in (b.pos, b.vel, b.mass))
+    acc = to_dev(np.zeros((b.n, 3)), cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        nb.fmm_step(x, v, m, 1.0, 0.01, 0.0, 4, 16, 1e-3, 10, acc)
+        nb.sync()
+    assert np.abs(host(x) - xr).max() <= 1e-9
+    assert np.abs(host(v) - vr).max() <= 1e-6
+
+
+def test_fmm_step_is_the_kick_drift_kick_of_fmm_forces(cuda):
+    # One step at theta 0.5 checked against fmm_forces: x' = x + dt (v + dt/2
+    # a(x)), acc = a(x') exactly, v' = v + dt/2 (a(x) + a(x')); a second step
+    # with acc_valid starts from that cached acc; graphs are refused.
+    import torch
+    b = inputs.plummer(5000, seed=91)
+    dt = 2e-3
+    x, v, m = (to_dev(t, cuda) for t in (b.pos, b.vel, b.mass))
+    acc = to_dev(np.zeros((b.n, 3)), cuda)
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        a0 = nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 5, 32)
+        x0, v0 = x.clone(), v.clone()
+        nb.fmm_step(x, v, m, 1.0, 0.01, 0.5, 5, 32, dt, 1, acc)
+        a1 = nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 5, 32)
+        nb.sync()
+        assert torch.equal(acc, a1)
+        assert torch.allclose(x, x0 + dt * (v0 + 0.5 * dt * a0), rtol=0, atol=1e-13)
+        assert torch.allclose(v, v0 + 0.5 * dt * (a0 + a1), rtol=0, atol=1e-13)
+        x1, v1 = x.clone(), v.clone()
+        nb.fmm_step(x, v, m, 1.0, 0.01, 0.5, 5, 32, dt, 1, acc, acc_valid=True)
+        a2 = nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 5, 32)
+        nb.sync()
+        assert torch.equal(acc, a2)
+        assert torch.allclose(v, v1 + 0.5 * dt * (a1 + a2), rtol=0, atol=1e-13)
+        assert nb.lib.nb_fmm_step(nb.h, b.n, x.data_ptr(), v.data_ptr(), m.data_ptr(), 1.0, 0.01,
+                                  0.5, 5, 32, dt, 1, acc.data_ptr(), 2) == 1  # graph refused
