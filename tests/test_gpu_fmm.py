@@ -209,3 +209,23 @@ def test_fmm_step_is_the_kick_drift_kick_of_fmm_forces(cuda):
         assert torch.allclose(v, v1 + 0.5 * dt * (a1 + a2), rtol=0, atol=1e-13)
         assert nb.lib.nb_fmm_step(nb.h, b.n, x.data_ptr(), v.data_ptr(), m.data_ptr(), 1.0, 0.01,
                                   0.5, 5, 32, dt, 1, acc.data_ptr(), 2) == 1  # graph refused
+
+
+@pytest.mark.parametrize("method", ["tree", "fmm"])
+def test_nonfinite_input_is_reported(cuda, method):
+    # An infinite coordinate makes the box infinite: every key quantises to a
+    # valid cell (the structure stays consistent), the sums turn non-finite
+    # and nb_sync reports NB_ENONFINITE once.
+    b = inputs.plummer(300, seed=92)
+    pos = b.pos.copy()
+    pos[7, 1] = np.inf
+    with nbody.NBody(b.n, "fp32_comp") as nb:
+        x, m = to_dev(pos, cuda), to_dev(b.mass, cuda)
+        if method == "tree":
+            nb.tree_forces(x, m, 1.0, 0.01, 0.5, 16)
+        else:
+            nb.fmm_forces(x, m, 1.0, 0.01, 0.5, 4, 16)
+        with pytest.raises(nbody.NBodyError) as ei:
+            nb.sync()
+        assert ei.value.status == 4
+        nb.sync()  # flag cleared
