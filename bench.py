@@ -482,10 +482,10 @@ TREE = {"name": "two-plummer N=1048576, Barnes-Hut theta 0.5, leaves <= 16 bodie
         "seed": 2, "eps": 0.002, "dt": 1e-3, "steps": 10, "theta": 0.5, "leaf_cap": 16,
         "group": 64, "cpu_n_per": 65_536}
 TREE_METRIC = "tree interactions/s (cell + body, G/s)"
-FMM = {"name": "two-plummer N=1048576, fast multipole theta 0.5, order 5, leaves <= 64 bodies, "
+FMM = {"name": "two-plummer N=1048576, fast multipole theta 0.6, order 6, leaves <= 64 bodies, "
                "one force evaluation per step (tree rebuilt), fp32 expansions and pair terms, "
                "f64 output",
-       "seed": 2, "eps": 0.002, "theta": 0.5, "order": 5, "leaf_cap": 64, "cpu_n_per": 65_536}
+       "seed": 2, "eps": 0.002, "theta": 0.6, "order": 6, "leaf_cap": 64, "cpu_n_per": 65_536}
 FMM_METRIC = "FMM force evaluations: bodies/s (N per evaluation / time, G/s; an O(N) method)"
 FMM_UNIT = "Gbodies/s"
 
@@ -734,7 +734,7 @@ def fmm_workload(args, ws, torch, dev, stream, T, flush):
             "traffic": traffic_from_profile(
                 "fmm_down_two_plummer_n1048576_dram.md" if far_dominant
                 else "fmm_near_two_plummer_n1048576_dram.md", "fmm_impl.cuh")
-            if (b.n, theta, lc, order) == (1 << 20, 0.5, 64, 5) else None,
+            if (b.n, theta, lc, order) == (1 << 20, 0.6, 64, 6) else None,
             "note": f"far: {m2l_flops(order)} flops per cell-to-cell expansion (its contraction); "
                     f"near: {FLOPS_PER_INTERACTION} per pair; phases event-timed inside the timed "
                     "region; peak = SMs x 128 FP32 lanes x 2 x max SM clock"}

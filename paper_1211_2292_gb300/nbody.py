@@ -337,7 +337,7 @@ class NBody:
         names = {"static": 0, "dynamic": 1, "guided": 2}
         self._call("nb_tree_schedule", names.get(sched, sched), int(chunk))
 
-    def fmm_forces(self, pos, mass, G, eps, theta=0.5, order=5, leaf_cap=32, out=None,
+    def fmm_forces(self, pos, mass, G, eps, theta=0.6, order=6, leaf_cap=64, out=None,
                    counts=False):
         """Fast-multipole accelerations (order 2..6 Cartesian expansions over
         the tree, leaves of up to leaf_cap <= 64 bodies); with counts=True also

@@ -174,19 +174,19 @@ def test_tree_workload_n2p20_sampled_groups(cuda, group):
 
 
 def test_fmm_workload_n2p20_whole_run(cuda):
-    # The FMM bench's workload and configuration (two-Plummer 2^20, theta 0.5,
-    # order 5, leaves <= 64): the whole oracle FMM (about 20 s on the host
+    # The FMM bench's workload and configuration (two-Plummer 2^20, theta 0.6,
+    # order 6, leaves <= 64): the whole oracle FMM (about 20 s on the host
     # cores) against the GPU's, body by body: the same source cells, bodies
     # and direct partners for every body, the same totals, forces within the
     # float32 bound of the rms acceleration; every body meets all others once.
     b = inputs.two_plummer(524_288, seed=2)
     x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
     with nbody.NBody(b.n, "fp32_comp") as nb:
-        a, cnt = nb.fmm_forces(x, m, 1.0, 0.002, 0.5, 5, 64, counts=True)
+        a, cnt = nb.fmm_forces(x, m, 1.0, 0.002, 0.6, 6, 64, counts=True)
         nb.sync()
         st = nb.fmm_stats()
     a, cnt = host(a), host(cnt).astype(np.int64)
-    ra, rst, rc = oracle.fmm_forces(b.pos, b.mass, 1.0, 0.002, 0.5, 5, 64, counts=True)
+    ra, rst, rc = oracle.fmm_forces(b.pos, b.mass, 1.0, 0.002, 0.6, 6, 64, counts=True)
     assert st == rst
     assert np.array_equal(cnt, rc)
     assert np.all(cnt[:, 1] + cnt[:, 2] == b.n)
