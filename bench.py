@@ -29,9 +29,13 @@ the data path.  value = interactions of all ranks / slowest rank's time.
 
 The JSON line also carries the float32 force error against the FP64 oracle on
 4096 sampled bodies, the force kernel's roofline (event-timed inside the timed
-region), the float64 form's rate, the batched and adjoint forms, the oracle's
-CPU rate, an end-to-end rate with host buffers, the SM clocks sampled during
-the timed region and the number of library kernels launched.
+region), the same workload in the FP64 form (one force evaluation of all
+bodies) and in the double-float form (1 + 10 steps), each with its force
+error on the same sampled bodies; the batched, adjoint and precision forms
+beside the plain FP64 GPU form of the same work and their errors against it
+or the oracle; the tree and FMM forms; the oracle's CPU rate, an end-to-end
+rate with host buffers, the SM clocks sampled during the timed region and the
+number of library kernels launched.
 """
 from __future__ import annotations
 
@@ -83,8 +87,9 @@ def parse():
     ap.add_argument("--tree-sched", default="dynamic", choices=["static", "dynamic", "guided"],
                     help="tree workload: walk schedule of the timed steps")
     ap.add_argument("--tree-chunk", type=int, default=1, help="tree workload: schedule chunk")
-    ap.add_argument("--fp64-n", type=int, default=262_144,
-                    help="bodies for the float64-form rate (first bodies of the workload)")
+    ap.add_argument("--fp64-n", type=int, default=None,
+                    help="bodies for the float64 and double-float forms (default: the whole "
+                         "workload; a smaller value takes the first bodies, for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -363,21 +368,27 @@ class Timer:
         self.ms = self.e0.elapsed_time(self.e1)
 
 
-def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None):
-    """Rates of the batched, adjoint and tree forms (rank-local, after the timed region)."""
+def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None, tuning="default"):
+    """Rates of the batched, adjoint, precision and tree forms (rank-local,
+    after the timed region), the first three beside the plain FP64 GPU form
+    of the same work at its accuracy."""
+    import numpy as np
+    import oracle
     from paper_1211_2292_gb300 import inputs, nbody
     from paper_1211_2292_gb300.autograd import rollout
     stream = torch.cuda.current_stream(dev)
     out = {}
     w = BATCHED
     bodies, off = inputs.plummer_batch(w["nsys"], w["lo"], w["hi"], seed=w["seed"])
-    pairs = float(sum(int(off[k + 1] - off[k]) ** 2 for k in range(len(off) - 1)))
+    sizes = np.diff(off)
+    pairs = float(sum(int(z) ** 2 for z in sizes))
     with nbody.NBody(bodies.n, "fp32_comp", device=dev.index) as nb:
         tune.apply(nb, table)
         nb.batch_plan(off)
         x, v, m = (torch.as_tensor(a, device=dev).contiguous()
                    for a in (bodies.pos, bodies.vel, bodies.mass))
         a = nb.forces_batched(x, m, w["G"], w["eps"])
+        ab = a.cpu().numpy()
         nb.step_batched(x, v, m, w["G"], w["eps"], w["dt"], w["steps"], a, acc_valid=True,
                         graph=True)
         with Timer(torch, dev, stream, lambda: None) as t:
@@ -387,43 +398,113 @@ def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None):
         nb.forces_batched(x, m, w["G"], w["eps"], out=a)
         kn, kms = nb.profile_read(1)
         nb.profile(False)
-        out["batched"] = {"value": pairs * w["steps"] / (t.ms / 1e3) / 1e9, "unit": UNIT,
-                          "systems": w["nsys"], "bodies": bodies.n, "pairs_per_eval": pairs,
-                          "ms_per_100_steps_graph": t.ms, "kernel_ms": kms / max(kn, 1),
-                          "kernel_frac_of_fp32_peak": FLOPS_PER_INTERACTION * pairs
-                          / (kms / max(kn, 1) / 1e3) / 1e12 / peak_tflops}
+    # the plain FP64 GPU form of the same evaluation: one NB_FP64 call per
+    # system, in order, on the initial state
+    x, m = (torch.as_tensor(a_, device=dev).contiguous() for a_ in (bodies.pos, bodies.mass))
+    with nbody.NBody(int(sizes.max()), "fp64", device=dev.index) as nb64:
+        tune.apply(nb64, table)
+        a64 = torch.empty_like(x)
+
+        def fp64_batch():
+            for k in range(len(sizes)):
+                s_, e_ = int(off[k]), int(off[k + 1])
+                nb64.forces(x[s_:e_], m[s_:e_], w["G"], w["eps"], out=a64[s_:e_])
+
+        fp64_batch()
+        nb64.profile(True)
+        with Timer(torch, dev, stream, lambda: None) as t64:
+            fp64_batch()
+        k64, ms64 = nb64.profile_read(0)
+        nb64.profile(False)
+        nb64.sync()
+    a64 = a64.cpu().numpy()
+    # accuracy on sampled systems (the largest and 15 seeded others) vs the oracle
+    rng = np.random.default_rng(6)
+    sel = sorted(set(rng.choice(len(sizes), 15, replace=False).tolist()) |
+                 {int(np.argmax(sizes))})
+    e32, e64 = [], []
+    for k in sel:
+        s_, e_ = int(off[k]), int(off[k + 1])
+        ref = oracle.accel(bodies.pos[s_:e_], bodies.mass[s_:e_], w["G"], w["eps"])
+        e32.append(_relerr(ab[s_:e_], ref))
+        e64.append(_relerr(a64[s_:e_], ref))
+    e32, e64 = np.concatenate(e32), np.concatenate(e64)
+    kernel_ms = kms / max(kn, 1)
+    batched_rate = pairs / (kernel_ms / 1e3) / 1e9
+    fp64_rate = pairs / (t64.ms / 1e3) / 1e9
+    sample = (f"{len(sel)} systems ({e32.size} bodies: the largest and 15 seeded others), "
+              "per-body relative error vs the FP64 oracle")
+    out["batched"] = {"value": pairs * w["steps"] / (t.ms / 1e3) / 1e9, "unit": UNIT,
+                      "systems": w["nsys"], "bodies": bodies.n, "pairs_per_eval": pairs,
+                      "ms_per_100_steps_graph": t.ms, "kernel_ms": kernel_ms,
+                      "kernel_value": batched_rate,
+                      "kernel_frac_of_fp32_peak": FLOPS_PER_INTERACTION * pairs
+                      / (kernel_ms / 1e3) / 1e12 / peak_tflops,
+                      "force_error": {"rms": float(np.sqrt((e32 ** 2).mean())),
+                                      "max": float(e32.max()), "sample": sample},
+                      "fp64_form": {"value": fp64_rate, "unit": UNIT, "ms_per_eval": t64.ms,
+                                    "kernel_ms_sum": ms64, "launches": k64,
+                                    "force_error": {"rms": float(np.sqrt((e64 ** 2).mean())),
+                                                    "max": float(e64.max())},
+                                    "note": "one NB_FP64 force call per system, in order "
+                                            "(pack + kernel each), on the same stream"},
+                      "kernel_over_fp64": batched_rate / fp64_rate}
+    # adjoint: the 200-step gradient in the float32 form, and in the FP64 and
+    # double-float contexts (float64 adjoint), with the gradients' differences
     a_ = ADJOINT
     b, dx = inputs.plummer_with_perturbation(a_["n"], seed=a_["seed"])
-    with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
-        tune.apply(nb, table)
-        x = torch.as_tensor(b.pos, device=dev).contiguous()
-        v = torch.as_tensor(b.vel, device=dev).contiguous()
-        m = torch.as_tensor(b.mass, device=dev).contiguous()
-        lam = torch.ones_like(x)
-        nb.forces_backward(x, m, 1.0, a_["eps"], lam)
-        nb.profile(True)
-        for _ in range(5):
+    x = torch.as_tensor(b.pos, device=dev).contiguous()
+    v = torch.as_tensor(b.vel, device=dev).contiguous()
+    m = torch.as_tensor(b.mass, device=dev).contiguous()
+    tgt = x + torch.as_tensor(dx, device=dev)
+    lam = torch.ones_like(x)
+    grads, gms = {}, {}
+    for prec in ("fp32_comp", "fp64", "df64"):
+        with nbody.NBody(b.n, prec, device=dev.index) as nb:
+            if tuning != "none":
+                tune.apply(nb, table)
             nb.forces_backward(x, m, 1.0, a_["eps"], lam)
-        vn, vms = nb.profile_read(2)
-        nb.profile(False)
-        tgt = x + torch.as_tensor(dx, device=dev)
+            if prec == "fp32_comp":
+                nb.profile(True)
+                for _ in range(5):
+                    nb.forces_backward(x, m, 1.0, a_["eps"], lam)
+                vn, vms = nb.profile_read(2)
+                nb.profile(False)
 
-        def grad():
-            x0 = x.clone().requires_grad_()
-            v0 = v.clone().requires_grad_()
-            mm = m.clone().requires_grad_()
-            xT, _ = rollout(nb, x0, v0, mm, 1.0, a_["eps"], a_["dt"], a_["steps"], a_["every"])
-            ((xT - tgt) ** 2).sum(-1).mean().backward()
+            def grad():
+                x0 = x.clone().requires_grad_()
+                v0 = v.clone().requires_grad_()
+                mm = m.clone().requires_grad_()
+                xT, _ = rollout(nb, x0, v0, mm, 1.0, a_["eps"], a_["dt"], a_["steps"],
+                                a_["every"])
+                ((xT - tgt) ** 2).sum(-1).mean().backward()
+                return [g.detach().cpu().numpy() for g in (x0.grad, v0.grad, mm.grad)]
 
-        grad()
-        with Timer(torch, dev, stream, lambda: None) as t:
-            grad()
-        n = float(b.n)
-        out["adjoint"] = {"vjp_value": n * n / (vms / vn / 1e3) / 1e9, "unit": UNIT,
-                          "vjp_ms": vms / vn, "n": b.n,
-                          "gradient_ms": t.ms,
-                          "gradient": f"{a_['steps']} steps, checkpoints every {a_['every']}, "
-                                      "forward + recompute + reverse sweep"}
+            if prec == "fp32_comp":
+                grad()
+            else:
+                nb.forces(x, m, 1.0, a_["eps"])
+            with Timer(torch, dev, stream, lambda: None) as t:
+                grads[prec] = grad()
+            gms[prec] = t.ms
+            nb.sync()
+
+    def gerr(p):
+        return {name: float(np.linalg.norm(g - r) / np.linalg.norm(r))
+                for name, g, r in zip(("x0", "v0", "m"), grads[p], grads["fp64"])}
+
+    n = float(b.n)
+    out["adjoint"] = {"vjp_value": n * n / (vms / vn / 1e3) / 1e9, "unit": UNIT,
+                      "vjp_ms": vms / vn, "n": b.n,
+                      "gradient_ms": gms["fp32_comp"], "gradient_ms_fp64": gms["fp64"],
+                      "gradient_ms_df64": gms["df64"],
+                      "fp32_speedup_over_fp64": gms["fp64"] / gms["fp32_comp"],
+                      "gradient_rel_err_vs_fp64": {"fp32_comp": gerr("fp32_comp"),
+                                                   "df64": gerr("df64")},
+                      "gradient": f"{a_['steps']} steps, checkpoints every {a_['every']}, "
+                                  "forward + recompute + reverse sweep; relative errors are "
+                                  "||g - g_fp64|| / ||g_fp64|| per input"}
+    out["precision"] = precision_form(torch, dev, tune, table, tuning)
     if tree_bodies is not None:  # Barnes-Hut on the same bodies (full line: --workload tree)
         t_ = TREE
         x = torch.as_tensor(tree_bodies.pos, device=dev).contiguous()
@@ -806,50 +887,34 @@ def other_workload(args, ws, rank, local):
         b = inputs.plummer(w["n"], seed=w["seed"])
         rows = inputs.sample_rows(b.n, 4096, seed=1)
         t0 = time.perf_counter()
-        ref = oracle.accel_rows(b.pos, b.mass, rows, 1.0, w["eps"])
+        oracle.accel_rows(b.pos, b.mass, rows, 1.0, w["eps"])
         el = time.perf_counter() - t0
         cpu = {"value": rows.size * b.n / el / 1e9, "unit": UNIT, "cores": oracle.threads(),
                "kind": "oracle", "sample": f"4096 of {b.n} force rows ({el:.1f} s)"}
-        res = {}
-        for prec in ("fp64", "fp32_comp"):
-            with nbody.NBody(b.n, prec, device=dev.index) as nb:
-                if args.tuning != "none":
-                    tune.apply(nb, table)
-                x, v, m = T(b.pos), T(b.vel), T(b.mass)
-                a = nb.forces(x, m, 1.0, w["eps"])
-                e = np.linalg.norm(a.cpu().numpy()[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
-                e0 = nb.energy(x, v, m, 1.0, w["eps"])
-                if prec == "fp32_comp":
-                    for _ in range(args.warmup):
-                        xs, vs = x.clone(), v.clone()
-                        nb.step(xs, vs, m, 1.0, w["eps"], w["dt"], w["steps"], a)
-                    l0 = nb.launches
-                    with timer() as t:
-                        for _ in range(args.steps):
-                            nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a)
-                            flush.fill_(1.0)
-                    launches = nb.launches - l0
-                    # the timed steps advanced the state K times; measure the drift
-                    # of one 100-step run from the initial state
-                    x, v = T(b.pos), T(b.vel)
-                nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a)
-                e1 = nb.energy(x, v, m, 1.0, w["eps"])
-                res[prec] = {"err": e, "e0": e0, "e1": e1, "x": x.cpu().numpy()}
+        with nbody.NBody(b.n, "fp32_comp", device=dev.index) as nb:
+            if args.tuning != "none":
+                tune.apply(nb, table)
+            x, v, m = T(b.pos), T(b.vel), T(b.mass)
+            a = torch.empty_like(x)
+            for _ in range(args.warmup):
+                xs, vs = x.clone(), v.clone()
+                nb.step(xs, vs, m, 1.0, w["eps"], w["dt"], w["steps"], a)
+            l0 = nb.launches
+            with timer() as t:
+                for _ in range(args.steps):
+                    nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a)
+                    flush.fill_(1.0)
+            launches = nb.launches - l0
         evals = w["steps"] + 1
         value = float(b.n) ** 2 * evals * args.steps / (t.ms / 1e3) / 1e9
-        r32, r64 = res["fp32_comp"], res["fp64"]
-        extra = {
-            "force_error": {"rms": float(np.sqrt((r32["err"] ** 2).mean())),
-                            "max": float(r32["err"].max()),
-                            "fp64_max": float(r64["err"].max()),
-                            "sample": "4096 bodies (seeded), vs FP64 oracle"},
-            "energy": {"E0": r64["e0"][2],
-                       "drift_fp64_gpu": abs(r64["e1"][2] - r64["e0"][2]) / abs(r64["e0"][2]),
-                       "drift_fp32": abs(r32["e1"][2] - r32["e0"][2]) / abs(r32["e0"][2]),
-                       "fp32_vs_fp64_final": abs(r32["e1"][2] - r64["e1"][2]) / abs(r64["e0"][2]),
-                       "max_position_diff": float(np.abs(r32["x"] - r64["x"]).max()),
-                       "note": "100 steps of dt 5e-4 from the initial state; energies in FP64"},
-            "cpu_baseline": cpu, "gpu_launches": launches}
+        pf = precision_form(torch, dev, tune, table, args.tuning)
+        extra = {"force_error": dict(pf["fp32"]["force_error"],
+                                     fp64_max=pf["fp64"]["force_error"]["max"],
+                                     sample="4096 bodies (seeded), vs FP64 oracle"),
+                 "energy": dict(pf["energy"], note="100 steps of dt 5e-4 from the initial "
+                                                   "state; energies in FP64"),
+                 "fp64_form": pf["fp64"], "fp32_over_fp64": pf["fp32_over_fp64"],
+                 "cpu_baseline": cpu, "gpu_launches": launches}
         _line(args, ws, value, t.ms / args.steps,
               {"workload": w["name"], "n": b.n, "force_evals_per_step": evals,
                "precision": "fp32_comp", "state": "f64"}, extra)
@@ -940,6 +1005,122 @@ def other_workload(args, ws, rank, local):
           {"gradient_ms": t.ms / args.steps, "gpu_launches": launches,
            "note": "interactions counted for forward, recompute and VJP evaluations"})
     return 0
+
+
+def _relerr(a, ref):
+    import numpy as np
+    return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def _err_stats(a, ref):
+    import numpy as np
+    e = _relerr(a, ref)
+    return {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}
+
+
+def float64_forms(torch, dev, tune, table, args, b, n64, G, eps, dt, nk, err_idx, ref_rows,
+                  fp32_rate):
+    """The metric's comparison: the same workload in the FP64 form (one force
+    evaluation, kernel event-timed) and in the double-float form (1 + nk KDK
+    steps, as the float32 line), each with its per-body relative force error
+    against the FP64 oracle on the float32 line's 4096 sampled bodies."""
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody
+    x = torch.as_tensor(b.pos[:n64], device=dev).contiguous()
+    v = torch.as_tensor(b.vel[:n64], device=dev).contiguous()
+    m = torch.as_tensor(b.mass[:n64], device=dev).contiguous()
+    if n64 == b.n:
+        rows, ref = err_idx, ref_rows
+        sample = f"{rows.size} bodies (seeded, as the float32 line), vs FP64 oracle"
+    else:
+        rows = inputs.sample_rows(n64, 256, seed=3)
+        ref = oracle.accel_rows(b.pos[:n64], b.mass[:n64], rows, G, eps)
+        sample = f"{rows.size} of the first {n64} bodies (seeded), vs FP64 oracle"
+    pairs = float(n64) ** 2
+    with nbody.NBody(n64, "fp64", device=dev.index) as nb64:
+        if args.tuning != "none":
+            tune.apply(nb64, table)
+        a64 = torch.empty_like(x)
+        nb64.profile(True)
+        nb64.forces(x, m, G, eps, out=a64)
+        k64, ms64 = nb64.profile_read(0)
+        nb64.profile(False)
+        nb64.sync()
+    v64 = pairs / (ms64 / max(k64, 1) / 1e3) / 1e9
+    err64 = _err_stats(a64.cpu().numpy()[rows], ref)
+    out = {"value": v64, "unit": UNIT, "n": n64, "force_evals": 1,
+           "kernel_ms": ms64 / max(k64, 1), "fp32_over_fp64": fp32_rate / v64,
+           "force_error": dict(err64, sample=sample),
+           "note": "one FP64 force evaluation of the whole workload, kernel event-timed"}
+    with nbody.NBody(n64, "df64", device=dev.index) as nbd:
+        if args.tuning != "none":
+            tune.apply(nbd, table)
+        ad = nbd.forces(x, m, G, eps)
+        errd = _err_stats(ad.cpu().numpy()[rows], ref)
+        xs, vs = x.clone(), v.clone()
+        stream = torch.cuda.current_stream(dev)
+        nbd.profile(True)
+        with Timer(torch, dev, stream, lambda: None) as t:
+            nbd.step(xs, vs, m, G, eps, dt, nk, ad)
+        kd, msd = nbd.profile_read(0)
+        nbd.profile(False)
+        nbd.sync()
+    vd = pairs / (msd / max(kd, 1) / 1e3) / 1e9
+    out["df64_form"] = {
+        "value": vd, "unit": UNIT, "n": n64, "force_evals": kd, "kernel_ms": msd / max(kd, 1),
+        "step_value": pairs * kd / (t.ms / 1e3) / 1e9, "ms_per_step": t.ms,
+        "over_fp64": vd / v64, "fp32_over_df64": fp32_rate / vd,
+        "force_error": dict(errd, sample=sample),
+        "note": f"double-float pair arithmetic (error-free sums and products of float32 "
+                f"pairs), Morton order; one step = 1 + {nk} KDK steps as the float32 line"}
+    return out
+
+
+def precision_form(torch, dev, tune, table, tuning="default"):
+    """The precision workload (Plummer N = 65,536, eps 0.005, 100 KDK steps of
+    dt 5e-4) in the float32 compensated and FP64 forms on the GPU: force error
+    against the oracle on 4096 sampled bodies, energy drift of each run and the
+    float32 run's difference from the FP64 GPU run."""
+    import numpy as np
+    import oracle
+    from paper_1211_2292_gb300 import inputs, nbody
+    w = PRECISION
+    b = inputs.plummer(w["n"], seed=w["seed"])
+    rows = inputs.sample_rows(b.n, 4096, seed=1)
+    ref = oracle.accel_rows(b.pos, b.mass, rows, 1.0, w["eps"])
+    stream = torch.cuda.current_stream(dev)
+    T = lambda a: torch.as_tensor(a, device=dev).contiguous()  # noqa: E731
+    res = {}
+    for prec in ("fp64", "fp32_comp"):
+        with nbody.NBody(b.n, prec, device=dev.index) as nb:
+            if tuning != "none":
+                tune.apply(nb, table)
+            x, v, m = T(b.pos), T(b.vel), T(b.mass)
+            a = nb.forces(x, m, 1.0, w["eps"])
+            err = _err_stats(a.cpu().numpy()[rows], ref)
+            e0 = nb.energy(x, v, m, 1.0, w["eps"])
+            with Timer(torch, dev, stream, lambda: None) as t:
+                nb.step(x, v, m, 1.0, w["eps"], w["dt"], w["steps"], a, acc_valid=True)
+            e1 = nb.energy(x, v, m, 1.0, w["eps"])
+            nb.sync()
+            res[prec] = {"err": err, "e0": e0, "e1": e1, "x": x.cpu().numpy(), "ms": t.ms}
+    r32, r64 = res["fp32_comp"], res["fp64"]
+    pairs = float(b.n) ** 2 * w["steps"]
+    return {
+        "workload": w["name"], "n": b.n, "steps": w["steps"],
+        "fp32": {"value": pairs / (r32["ms"] / 1e3) / 1e9, "unit": UNIT, "ms": r32["ms"],
+                 "force_error": r32["err"]},
+        "fp64": {"value": pairs / (r64["ms"] / 1e3) / 1e9, "unit": UNIT, "ms": r64["ms"],
+                 "force_error": r64["err"]},
+        "fp32_over_fp64": r64["ms"] / r32["ms"],
+        "energy": {"E0": r64["e0"][2],
+                   "drift_fp64_gpu": abs(r64["e1"][2] - r64["e0"][2]) / abs(r64["e0"][2]),
+                   "drift_fp32": abs(r32["e1"][2] - r32["e0"][2]) / abs(r32["e0"][2]),
+                   "fp32_vs_fp64_final": abs(r32["e1"][2] - r64["e1"][2]) / abs(r64["e0"][2]),
+                   "max_position_diff": float(np.abs(r32["x"] - r64["x"]).max())},
+        "note": "force error on 4096 sampled bodies vs the FP64 oracle; energies (FP64 "
+                "diagnostics) before and after 100 steps from the initial state; value = "
+                "N^2 x 100 / the 100-step run's time (cached first force)"}
 
 
 def main():
@@ -1097,51 +1278,20 @@ def main():
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak_tflops * clk["sm_mhz"] / sm_max)
 
-    # float64 form (first fp64_n bodies of the workload)
+    # float64 forms at the workload's size: one FP64 force evaluation and the
+    # double-float form's 1 + 10 steps, with errors on the sampled bodies
     fp64 = None
-    n64 = min(args.fp64_n, n) if args.workload == "throughput" else 0
-    if n64 > 0:
-        with nbody.NBody(n64, "fp64", device=dev.index) as nb64:
-            if args.tuning != "none":
-                tune.apply(nb64, table)
-            p64, m64 = pos[:n64].contiguous(), mass[:n64].contiguous()
-            a64 = torch.empty_like(p64)
-            nb64.forces(p64, m64, G, eps, out=a64)
-            nb64.profile(True)
-            nb64.forces(p64, m64, G, eps, out=a64)
-            k64, ms64 = nb64.profile_read(0)
-            nb64.profile(False)
-        v64 = float(n64) ** 2 / (ms64 / 1e3) / 1e9
-        fp64 = {"value": v64, "unit": UNIT, "n": n64, "kernel_ms": ms64,
-                "fp32_over_fp64": (pairs_per_eval / (avg_ms / 1e3) / 1e9) / v64,
-                "note": "one FP64 force evaluation of the first n bodies (the rate does not "
-                        "depend on N once the GPU is full); FP64 error <= 1e-12 in the tests"}
-        # the same bodies in double-float arithmetic (float64 accuracy on the
-        # float32 pipe), with both errors against the oracle on sampled rows
-        with nbody.NBody(n64, "df64", device=dev.index) as nbd:
-            ad = torch.empty_like(p64)
-            nbd.forces(p64, m64, G, eps, out=ad)
-            nbd.profile(True)
-            nbd.forces(p64, m64, G, eps, out=ad)
-            kd, msd = nbd.profile_read(0)
-            nbd.profile(False)
-        hp64, hm64 = p64.cpu().numpy(), m64.cpu().numpy()
-        rows64 = inputs.sample_rows(n64, 256, seed=3)
-        ref64 = oracle.accel_rows(hp64, hm64, rows64, G, eps)
-        def _err(t):
-            v = t.cpu().numpy()[rows64]
-            return float((np.linalg.norm(v - ref64, axis=1) / np.linalg.norm(ref64, axis=1)).max())
-        vd = float(n64) ** 2 / (msd / 1e3) / 1e9
-        fp64["max_err"] = _err(a64)
-        fp64["df64_form"] = {"value": vd, "unit": UNIT, "n": n64, "kernel_ms": msd,
-                             "over_fp64": vd / v64, "max_err": _err(ad),
-                             "note": "double-float pair arithmetic (error-free sums and products "
-                                     "of float32 pairs), Morton order; max_err on 256 sampled "
-                                     "bodies vs the FP64 oracle"}
+    if args.workload == "throughput":
+        n64 = n if args.fp64_n is None else min(args.fp64_n, n)
+        if n64 > 0:
+            fp32_rate = pairs_per_eval / (avg_ms / 1e3) / 1e9
+            fp64 = float64_forms(torch, dev, tune, table, args, b, n64, G, eps, dt, nk,
+                                 err_idx, ref_rows, fp32_rate)
 
     forms = None
     if not args.no_forms and rank == 0 and args.workload == "throughput":
-        forms = measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=b)
+        forms = measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=b,
+                              tuning=args.tuning)
 
     # end to end through the public API with pinned host buffers
     e2e = None

@@ -49,7 +49,10 @@ typedef enum {
 } nb_status;
 
 typedef enum {
-    NB_FP64 = 0,      /* every pair term and sum in float64 */
+    NB_FP64 = 0,      /* every pair term and sum in float64; valid for any pair
+                         whose r^2 + eps^2 is a positive normal float64 and whose
+                         1/(r^2 + eps^2)^(3/2) does not overflow (e.g. eps = 0 and
+                         separations from 1e-100 to 1e100) */
     NB_FP32 = 1,      /* float32 pair terms, one float32 running sum per body;
                          float32 modes need masses >= 0 (a negative mass can give
                          NB_ENONFINITE with the log-domain kernel variants) */
@@ -61,7 +64,9 @@ typedef enum {
                          in Morton order with tile-local origins, float64 sums per
                          j-tile; forces, steps and rollouts (the adjoint and the
                          diagnostics run in float64, the batched kernel is
-                         float32 only) */
+                         float32 only).  Pair terms carry float32's exponent
+                         range: r^2 + eps^2 must lie within 1.2e-38 .. 3.4e38
+                         (use NB_FP64 beyond it) */
 } nb_precision;
 
 /* Flags for nb_step / nb_rollout / nb_step_batched. */
@@ -203,6 +208,10 @@ nb_status nb_step_batched(nb_ctx *ctx, double *pos, double *vel, const double *m
  * nb_variant_info fills threads per CTA, bodies per thread and j-tile size.
  * nb_tune_set makes calls with lo <= n < hi use `variant`, with `split`
  * j-splits across CTAs (0 = chosen by the scheduler); later entries win.
+ * For the batched kind, n is the planned bodies and `split` is the item-cap
+ * divisor d (0 = 4): when a plan has more items than resident CTAs, a work
+ * item holds at most 1/d of an even per-CTA share of the pairs; it takes
+ * effect at the next nb_batch_plan.
  * variant < 0 clears the kind's table.  nb_tune_get reports the variant and
  * split a call with n bodies would use.
  */
@@ -365,30 +374,37 @@ nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
 /*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form
  * (float32 pair terms, Kahan-compensated per-tile sums, float64 output), for
- * callers that cannot allocate device memory: code running inside a CUDA
- * stream capture that must not record allocations, code whose device memory
- * is owned by another allocator or capped, and latency-critical loops where
- * cudaMalloc could block.  The paper has no counterpart; this is a service of
- * the library.
+ * callers that cannot allocate device memory: code whose device memory is
+ * owned by another allocator (a framework's pool that must account for every
+ * byte) or capped by a fixed budget, and latency-critical loops in which a
+ * cudaMalloc could block or synchronise the device.  The paper has no
+ * counterpart; this is a service of the library.
  *
  * It allocates nothing: no context, no cudaMalloc/cudaFree.  Its scratch
  * (packed bodies, split partials, counters; about 8 MiB) is one fixed
  * __device__ array that every GPU loading the library holds until the
- * process exits, which bounds n to NB_NOALLOC_MAX_BODIES.  Work runs on the
- * calling thread's current device, enqueued on `cuda_stream` (NULL = legacy
- * default stream); pos [n][3], mass [n] and acc [n][3] are device arrays of
- * that device, acc is overwritten.  Bodies are processed in input order (no
- * spatial sort).
+ * process exits, which bounds n to NB_NOALLOC_MAX_BODIES.  Work runs in the
+ * calling thread's current CUDA context and device, enqueued on
+ * `cuda_stream` (NULL = legacy default stream); pos [n][3], mass [n] and
+ * acc [n][3] are device arrays of that device, acc is overwritten.  Bodies
+ * are processed in input order (no spatial sort).
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call on a device shares the one scratch array: calls whose work
- * overlaps on the GPU (different streams without ordering, several threads)
- * race and give wrong results; order them on one stream.  Each call clears
- * the counters it uses before its kernels run.  Returns NB_EINVAL (n < 0,
- * n > NB_NOALLOC_MAX_BODIES, NULL/misaligned/non-device arrays, non-finite G,
- * eps < 0) before enqueuing anything, NB_ECUDA if the runtime fails; there is
- * no message text.  n == 0 is a no-op.
+ * The first call in each CUDA context does a one-time set-up: it looks up
+ * the scratch array's device address in that context (cudaGetSymbolAddress)
+ * and keeps it, keyed by the context; make that first call before any stream
+ * capture.  Every call in a context shares the one scratch array and it keeps
+ * the last call's contents: each call clears the counters and the error word
+ * it uses before its kernels run, and calls whose work overlaps on the GPU
+ * (different streams without ordering, several threads) race and give wrong
+ * results; order them on one stream.
+ *
+ * Returns NB_EINVAL (n < 0, n > NB_NOALLOC_MAX_BODIES, NULL/misaligned/
+ * non-device arrays, non-finite G, eps < 0) before enqueuing anything,
+ * NB_ECUDA if the runtime fails or no CUDA context is current; there is no
+ * message text.  It never returns NB_ENONFINITE: with no context to hold an
+ * error word that a later call could read, non-finite accelerations are not
+ * reported, so check acc when the inputs may hold infinities or NaNs.  n == 0
+ * is a no-op.
  */
 #define NB_NOALLOC_MAX_BODIES 65536
 nb_status nb_forces_noalloc(int64_t n, const double *pos, const double *mass, double G,

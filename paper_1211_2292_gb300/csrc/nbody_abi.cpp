@@ -1266,18 +1266,20 @@ nb_status nb_batch_plan(nb_ctx *c, int64_t nsys, const int64_t *offsets)
     for (int64_t k = 0; k < nsys; ++k)
         if (offsets[k + 1] < offsets[k]) return failf(c, NB_EINVAL, "offsets must be non-decreasing");
     if (offsets[nsys] > c->n_max) return failf(c, NB_EINVAL, "offsets[nsys] > n_max");
-    int v, forced;
-    pick(c, nb::KIND_BATCHED, offsets[nsys], v, forced);
+    int v, divisor;
+    pick(c, nb::KIND_BATCHED, offsets[nsys], v, divisor);
+    if (divisor <= 0) divisor = 4;
     const KernelEntry &k = nb::f32_batched_kernel(v, c->prec == NB_FP32_COMP, false);
     // When the batch already has more items than resident CTAs, cap an item
-    // at 1/4 of an even share of the pairs per CTA to shorten the tail.
+    // at 1/divisor of an even share of the pairs per CTA to shorten the tail
+    // (the tuning entry's split field holds the divisor; 0 = 4).
     double pairs = 0.0;
     for (int64_t q = 0; q < nsys; ++q)
         pairs += (double)(offsets[q + 1] - offsets[q]) * (double)(offsets[q + 1] - offsets[q]);
     const int64_t slots = (int64_t)c->num_sms * occupancy(c, k);
     int64_t cap = 0;
     if (nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, 0, nullptr, 0) >= slots)
-        cap = (int64_t)(pairs / (double)(4 * std::max<int64_t>(slots, 1))) + 1;
+        cap = (int64_t)(pairs / ((double)divisor * (double)std::max<int64_t>(slots, 1))) + 1;
     const int64_t cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, nullptr, 0);
     if (cnt < 0) return failf(c, NB_EINVAL, "cannot plan these offsets");
     std::vector<int32_t> host((size_t)std::max<int64_t>(cnt, 1) * 8);

@@ -23,6 +23,8 @@ DEFAULT_SIZES = {
     nbody.KIND_FORCE: [1024, 4096, 16384, 65536, 262144, 1048576],
     nbody.KIND_VJP: [1024, 4096, 16384, 65536],
 }
+# item caps tried for the batched kernel (1/d of an even per-CTA share of the pairs)
+BATCH_DIVISORS = (1, 2, 4, 8)
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
@@ -66,8 +68,10 @@ def time_candidates(kind, precision, n, splits=(0,), reps=3, seed=0, device=0, l
     return sorted(out)
 
 
-def time_batched(precision, offsets, bodies, reps=3, device=0, log=None):
-    """[(ms per launch, variant)] of the batched kernel on one plan."""
+def time_batched(precision, offsets, bodies, reps=3, device=0, log=None, divisors=(0,)):
+    """[(ms per launch, variant, divisor)] of the batched kernel on one set of
+    systems; the divisor (a tuning entry's split field, 0 = the default 4)
+    caps a work item at 1/divisor of an even per-CTA share of the pairs."""
     import torch
     dev = torch.device("cuda", device)
     x = torch.as_tensor(bodies.pos, device=dev).contiguous()
@@ -76,15 +80,17 @@ def time_batched(precision, offsets, bodies, reps=3, device=0, log=None):
     with nbody.NBody(max(bodies.n, 1), precision, device=device) as nb:
         acc = torch.empty_like(x)
         for v in range(len(nbody.variants(nbody.KIND_BATCHED, precision))):
-            nb.tune_set(nbody.KIND_BATCHED, 0, 1 << 40, v, 0)
-            nb.batch_plan(offsets)
-            ms = _time_call(nb, lambda: nb.forces_batched(x, m, 1.0, 0.01, out=acc),
-                            nbody.KIND_BATCHED, reps)
-            out.append((ms, v))
-            if log:
-                log(f"batched {precision} variant={v}{nbody.variants(nbody.KIND_BATCHED, precision)[v]}:"
-                    f" {ms:.4f} ms")
-            nb.tune_set(nbody.KIND_BATCHED, 0, 1, -1, 0)
+            for d in divisors:
+                nb.tune_set(nbody.KIND_BATCHED, 0, 1 << 40, v, d)
+                nb.batch_plan(offsets)
+                ms = _time_call(nb, lambda: nb.forces_batched(x, m, 1.0, 0.01, out=acc),
+                                nbody.KIND_BATCHED, reps)
+                out.append((ms, v, d))
+                if log:
+                    log(f"batched {precision} variant={v}"
+                        f"{nbody.variants(nbody.KIND_BATCHED, precision)[v]} divisor={d}:"
+                        f" {ms:.4f} ms")
+                nb.tune_set(nbody.KIND_BATCHED, 0, 1, -1, 0)
     return sorted(out)
 
 
@@ -97,26 +103,33 @@ def _buckets(sizes):
     return list(zip(sizes, edges[:-1], edges[1:]))
 
 
-def autotune(precisions=("fp32_comp", "fp32", "fp64"), kinds=(nbody.KIND_FORCE, nbody.KIND_VJP),
-             sizes=None, splits=(0,), reps=3, batch=True, device=0, log=print):
+def autotune(precisions=("fp32_comp", "fp32", "fp64", "df64"),
+             kinds=(nbody.KIND_FORCE, nbody.KIND_VJP), sizes=None, splits=(0,), reps=3,
+             batch=True, device=0, log=print):
+    """Time every variant (and each split in `splits`) at the tuned sizes of
+    each precision and kind; the fastest per size becomes a table entry whose
+    bucket reaches to the geometric midpoints between tuned sizes.  The
+    float64-state modes (fp64, df64) are tuned up to 2^18 bodies, their last
+    bucket covering every larger size."""
     import torch
     table = {"device": torch.cuda.get_device_name(device), "entries": []}
     for prec in precisions:
         for kind in kinds:
             szs = (sizes or {}).get(kind, DEFAULT_SIZES[kind])
-            if prec == "fp64":  # float64 is ~90x slower: tune up to 2^18 bodies
+            if prec in ("fp64", "df64"):  # ~10-100x slower than float32: up to 2^18 bodies
                 szs = [z for z in szs if z <= 262144] or szs[:1]
             for n, lo, hi in _buckets(szs):
                 res = time_candidates(kind, prec, n, splits, reps, device=device, log=log)
                 ms, v, s = res[0]
                 table["entries"].append({"kind": kind, "precision": prec, "lo": lo, "hi": hi,
                                          "n": n, "variant": v, "split": s, "ms": ms})
-        if batch and prec != "fp64":
+        if batch and prec not in ("fp64", "df64"):  # the batched kernel is float32 only
             bodies, off = inputs.plummer_batch(512, 64, 8192, seed=3)
-            res = time_batched(prec, off, bodies, reps, device=device, log=log)
-            ms, v = res[0]
+            res = time_batched(prec, off, bodies, reps, device=device, log=log,
+                               divisors=BATCH_DIVISORS)
+            ms, v, d = res[0]
             table["entries"].append({"kind": nbody.KIND_BATCHED, "precision": prec, "lo": 0,
-                                     "hi": 1 << 40, "n": bodies.n, "variant": v, "split": 0,
+                                     "hi": 1 << 40, "n": bodies.n, "variant": v, "split": d,
                                      "ms": ms})
     return table
 
@@ -148,7 +161,7 @@ def apply(nb: nbody.NBody, table=None) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_TABLE)
-    ap.add_argument("--precisions", default="fp32_comp,fp32,fp64")
+    ap.add_argument("--precisions", default="fp32_comp,fp32,fp64,df64")
     ap.add_argument("--sizes", default="", help="force sizes, comma separated")
     ap.add_argument("--splits", default="0")
     ap.add_argument("--reps", type=int, default=3)
