@@ -48,10 +48,19 @@ __device__ __forceinline__ float ex2_mufu(float x)
 // f(y) = 1/y^2 - x.  With e = 1 - x*y0^2 the exact answer is
 // y0*(1-e)^(-1/2) = y0*(1 + e/2 + 3e^2/8 + ...); keeping two terms leaves a
 // relative error of about (5/16)e^3 ~ 1e-20, below float64 rounding.
-// Valid for x within the float32 normal range (1.2e-38 .. 3.4e38).
+// The seed is taken at x' = x 2^-2k in [1, 4) (2k the even part of x's
+// exponent) and scaled back by 2^-k, both exact edits of the exponent field
+// on the integer pipe, so every positive normal float64 x gets a normal seed
+// (a float32 seed of x itself would overflow or flush to zero outside
+// 1.2e-38 .. 3.4e38, e.g. for r^2 = 1e-40 at eps = 0).  Valid for positive
+// normal x; x = 0 gives a large finite value (callers mask the self pair).
 __device__ __forceinline__ double rsqrt_f64(double x)
 {
-    double y = (double)rsqrt_mufu((float)x);
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int k2 = ((int)(((unsigned)hi >> 20) & 0x7ffu) - 1023) & ~1;  // even part of the exponent
+    const double xs = __hiloint2double(hi - k2 * (1 << 20), lo);   // x 2^-k2, in [1, 4)
+    const double ys = (double)rsqrt_mufu((float)xs);
+    const double y = __hiloint2double(__double2hiint(ys) - (k2 / 2) * (1 << 20), __double2loint(ys));
     double h = x * y;
     double e = fma(-h, y, 1.0);
     double p = fma(e, 0.375, 0.5);

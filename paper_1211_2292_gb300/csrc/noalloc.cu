@@ -1,21 +1,24 @@
 // nb_forces_noalloc: the float32 Kahan-compensated force kernel for callers
 // that must not allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is unavailable or unsafe --
-// inside a CUDA stream capture whose graph must not contain allocation
-// nodes, under an external allocator that owns all device memory (a
-// framework's pool, a memory-capped sandbox), or in a real-time loop where an
-// allocation could block.  nb_create cannot serve them, because creating a
-// context allocates its scratch.
+// Who needs it: code whose device memory is owned by someone else -- a
+// framework's memory pool that must see every byte, a sandbox or service
+// with a fixed device-memory budget -- and latency-critical loops in which a
+// cudaMalloc could block or synchronise the device.  nb_create cannot serve
+// them, because creating a context allocates its scratch.
 //
 // How: the scratch the kernel needs (packed hi/lo bodies, j-split partial
 // sums, arrival counters, an error word) lives in one file-scope
 // __device__ array of fixed size, which every GPU that loads the library
 // holds until the process exits.  Host code cannot use the array's name as a
-// device address, so on the first call on each device (with that device
-// current) the entry point asks the runtime for the array's device address
-// with cudaGetSymbolAddress and keeps it.  Bodies are processed in input
-// order (no Morton sort, which would need more scratch).
+// device address.  The first call made in a CUDA context (with that context
+// current) asks the runtime for the array's device address with
+// cudaGetSymbolAddress and keeps it, keyed by the context's unique ID: the
+// address belongs to the module loaded in that context, so a call made in
+// another context of the same device, or after cudaDeviceReset has replaced
+// the primary context, does its own set-up instead of reusing a stale
+// address.  Bodies are processed in input order (no Morton sort, which would
+// need more scratch).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -42,10 +45,46 @@ constexpr size_t kScratchBytes = kErrOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+// Set-up results, one slot per CUDA context that has called the entry point
+// (slots are reused round-robin once all are taken).
+constexpr int kSlots = 64;
+struct Setup {
+    unsigned long long ctx_id;  // cuCtxGetId of the context; 0 = free slot
+    unsigned char *addr;        // device address of the scratch in that context
+    int sms;
+};
 std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {};  // device address of the scratch, per device
-int g_sms[kMaxDevices] = {};
+Setup g_setup[kSlots] = {};
+int g_next = 0;
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+void *driver_fn(const char *name, int version)
+{
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return f;
+}
+
+// Unique ID (never reused within the process) of the calling thread's
+// current CUDA context; 0 if there is none.
+unsigned long long current_ctx_id()
+{
+    static PfnCtxGetCurrent get_cur = (PfnCtxGetCurrent)driver_fn("cuCtxGetCurrent", 4000);
+    static PfnCtxGetId get_id = (PfnCtxGetId)driver_fn("cuCtxGetId", 12000);
+    if (!get_cur || !get_id) return 0;
+    CUcontext cur = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&cur) != CUDA_SUCCESS || !cur) return 0;
+    if (get_id(cur, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Errors are reported by status code only (there is no context to hold a
 // message); the text names the check for readers of this file.
@@ -64,15 +103,7 @@ bool is_device_array(const void *p, size_t bytes, int dev)
     }
     if (a.type != cudaMemoryTypeManaged && !(a.type == cudaMemoryTypeDevice && a.device == dev))
         return false;
-    static PfnRange range = [] {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 3020, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            f = nullptr;
-        return (PfnRange)f;
-    }();
+    static PfnRange range = (PfnRange)driver_fn("cuMemGetAddressRange", 3020);
     if (range) {
         CUdeviceptr base = 0;
         size_t size = 0;
@@ -94,7 +125,7 @@ extern "C" nb_status nb_forces_noalloc(int64_t n, const double *pos, const doubl
     if (!std::isfinite(eps) || eps < 0) return fail(NB_EINVAL, "eps must be finite and >= 0");
     if (n == 0) return NB_OK;
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return fail(NB_ECUDA, "no current CUDA device");
     }
@@ -108,28 +139,34 @@ extern "C" nb_status nb_forces_noalloc(int64_t n, const double *pos, const doubl
             return fail(NB_EINVAL, "array not n bodies of device memory of the current device");
     }
 
-    // Set-up, once per device: the scratch array's device address.
-    unsigned char *base;
-    int sms;
+    // Set-up, once per CUDA context (the argument checks above have run in
+    // the current one): the scratch array's device address in that context.
+    const unsigned long long ctx_id = current_ctx_id();
+    if (!ctx_id) return fail(NB_ECUDA, "no CUDA context is current");
+    unsigned char *base = nullptr;
+    int sms = 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
+        for (const Setup &e : g_setup)
+            if (e.ctx_id == ctx_id) {
+                base = e.addr;
+                sms = e.sms;
+            }
+        if (!base) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
                 cudaGetLastError();
                 return fail(NB_ECUDA, "cudaGetSymbolAddress failed");
             }
-            int s = 0;
-            if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(NB_ECUDA, "cannot read the SM count");
             }
-            g_sms[dev] = s;
-            g_addr[dev] = (unsigned char *)p;
+            base = (unsigned char *)p;
+            g_setup[g_next] = Setup{ctx_id, base, sms};
+            g_next = (g_next + 1) % kSlots;
         }
-        base = g_addr[dev];
-        sms = g_sms[dev];
     }
 
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -40,6 +40,27 @@ def test_fp64_matches_oracle(cuda, n):
     assert relerr_per_body(a, ref).max() <= 1e-12
 
 
+@pytest.mark.parametrize("sep", [1e-20, 1e-45, 1e-60, 1e20, 1e45, 1e60])
+def test_fp64_separations_outside_the_float32_range(cuda, sep):
+    # eps = 0: r^2 = sep^2 lies outside float32's normal range, where a
+    # float32 seed of the float64 rsqrt would flush to zero or overflow.
+    # Two bodies: a closed form, a_0 = G m_1 d / r^3 (and the oracle agrees).
+    pos = np.array([[0.0, 0.0, 0.0], [sep * 0.6, -sep * 0.8, 0.0]])
+    mass = np.array([0.75, 0.25])
+    b = inputs.Bodies(pos, np.zeros_like(pos), mass)
+    a = _forces(cuda, "fp64", b, 1.0, 0.0)
+    d = pos[1] - pos[0]
+    r = np.linalg.norm(d)
+    exact = np.array([mass[1] * d / r ** 3, -mass[0] * d / r ** 3])
+    assert np.all(np.isfinite(a))
+    assert relerr_per_body(a, exact).max() <= 1e-12
+    assert relerr_per_body(oracle.accel(pos, mass, 1.0, 0.0), exact).max() <= 1e-14
+    with nbody.NBody(2, "fp64") as nb:
+        e = nb.energy(to_dev(pos, cuda), to_dev(np.zeros_like(pos), cuda), to_dev(mass, cuda),
+                      1.0, 0.0)
+    assert abs(e[1] - (-mass[0] * mass[1] / r)) <= 1e-12 * abs(mass[0] * mass[1] / r)
+
+
 @pytest.mark.parametrize("n", SIZES)
 def test_df64_matches_oracle(cuda, n):
     b = inputs.plummer(n, seed=300 + n)

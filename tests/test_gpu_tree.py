@@ -40,6 +40,26 @@ def test_matches_oracle_tree(cuda, n, theta, leaf_cap, group):
     assert np.sqrt((e ** 2).mean()) <= RMS_TOL and e.max() <= MAX_TOL
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+def test_grouped_gpu_walk_against_the_per_body_walk(cuda, theta):
+    # The paper's walk is per body (the oracle with group = 1); the GPU walks
+    # groups of 32 or 64 bodies, accepting a cell only when all of them
+    # would.  Against the exact sum, with e_i the per-body relative error:
+    # rms(e_gpu) <= rms(e_per_body), max(e_gpu) <= 1.5 max(e_per_body), and
+    # per body |a_gpu - a_per_body| / |a_exact| <= 2 max(e_per_body).
+    for b, eps in ((inputs.two_plummer(4096, seed=31), 0.002), (inputs.plummer(8000, seed=32), 0.01)):
+        ex = oracle.accel(b.pos, b.mass, 1.0, eps)
+        pb, _ = oracle.bh_forces(b.pos, b.mass, 1.0, eps, theta, 16, 1)
+        e_pb = relerr_per_body(pb, ex)
+        for group in (32, 64):
+            a, _, _ = _gpu_tree(cuda, b, 1.0, eps, theta, 16, group=group)
+            e_g = relerr_per_body(a, ex)
+            assert np.sqrt((e_g ** 2).mean()) <= np.sqrt((e_pb ** 2).mean())
+            assert e_g.max() <= 1.5 * e_pb.max()
+            assert (np.linalg.norm(a - pb, axis=1) / np.linalg.norm(ex, axis=1)).max() \
+                <= 2.0 * e_pb.max()
+
+
 @pytest.mark.parametrize("group", [32, 64])
 def test_theta_zero_is_the_direct_sum(cuda, group):
     b = inputs.plummer(3000, seed=62)

@@ -89,3 +89,28 @@ def test_group_subset_equals_the_full_run():
     assert np.array_equal(a3[ii], a[ii]) and np.isnan(a3[np.setdiff1d(np.arange(b.n), ii)]).all()
     with pytest.raises(ValueError):
         oracle.bh_groups(b.pos, b.mass, 1.0, 0.01, 0.6, 8, 64, [ngroups])
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+def test_grouped_walk_is_a_refinement_of_the_per_body_walk(theta):
+    # group = 1 is the per-body walk the paper describes.  A group accepts a
+    # cell only when every one of its bodies would, so each body's grouped
+    # list refines its per-body list: more cells opened, fewer bodies
+    # approximated.  Stated bounds, against the exact sum (per-body relative
+    # error e_i): rms(e_grouped) <= rms(e_per_body), max(e_grouped) <=
+    # 1.5 max(e_per_body), and per body |a_grouped - a_per_body| / |a_exact|
+    # <= 2 max(e_per_body) (measured up to 1.35 on these inputs).
+    for b, eps in ((inputs.two_plummer(4096, seed=31), 0.002), (inputs.plummer(8000, seed=32), 0.01)):
+        ex = oracle.accel(b.pos, b.mass, 1.0, eps)
+        pb, st1, c1 = oracle.bh_forces(b.pos, b.mass, 1.0, eps, theta, 16, 1, counts=True)
+        e_pb = _err(pb, ex)
+        for group in (32, 64):
+            ag, stg, cg = oracle.bh_forces(b.pos, b.mass, 1.0, eps, theta, 16, group, counts=True)
+            e_g = _err(ag, ex)
+            assert np.sqrt((e_g ** 2).mean()) <= np.sqrt((e_pb ** 2).mean())
+            assert e_g.max() <= 1.5 * e_pb.max()
+            assert (np.linalg.norm(ag - pb, axis=1) / np.linalg.norm(ex, axis=1)).max() \
+                <= 2.0 * e_pb.max()
+            # a refinement meets at least as many bodies directly
+            assert np.all(cg[:, 1] >= c1[:, 1])
+
