@@ -425,17 +425,39 @@ __global__ void __launch_bounds__(T, MINB) force_f32_kernel(const ForceParams p)
 }
 
 // ----------------------------------------------------------- batched kernel
+// Final write of one body's acceleration from its float64 sum (G applied).
+__device__ __forceinline__ void batch_write(const BatchParams &p, int i, double x, double y,
+                                            double z)
+{
+    double *a = p.acc + 3 * (size_t)i;
+    const double gx = p.G * x, gy = p.G * y, gz = p.G * z;
+    a[0] = gx;
+    a[1] = gy;
+    a[2] = gz;
+    if (p.vel) {
+        double *v = p.vel + 3 * (size_t)i;
+        v[0] += p.half_dt * gx;
+        v[1] += p.half_dt * gy;
+        v[2] += p.half_dt * gz;
+    }
+    if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+}
+
 // Persistent: each CTA pops items (largest cost first) from an atomic
 // counter until the queue is empty, the GPU analogue of the paper's dynamic
-// loop schedule (Sec. V-C, Table VI).  The last CTA to finish resets the
-// counters for the next launch; nothing waits.
+// loop schedule (Sec. V-C, Table VI).  An item whose piece is split over
+// j-chunks stores its float64 partial sums; the last chunk of the piece to
+// arrive (arrival counter) adds the chunks in order and writes the result.
+// The last CTA to finish resets the queue counters for the next launch;
+// nothing waits.
 template <int T, int I, int J, bool COMP, bool ZEPS, int LP>
 __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams p)
 {
+    constexpr int TILE_I = T * I;
     __shared__ __align__(16) float4 tile[2][Slots<LP>::W * J];
     __shared__ float red[6][T / 32];
     __shared__ BatchItem s_item;
-    __shared__ int s_idx;
+    __shared__ int s_idx, s_last;
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
 
     for (;;) {
@@ -464,6 +486,8 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
         else
             sweep<T, I, J, COMP, ZEPS, LP, true, false, UNROLL_F32>(
                 p.P, p.Plo, c, it.j0, it.j1, 0, ntiles, lane, lanes, e2, nx, ny, nz, acc, tile);
+        const bool split = it.nchunks > 1;
+        double *slot = split ? p.partial + (size_t)(it.pbase + it.chunk) * TILE_I * 3 : nullptr;
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             double x, y, z;
@@ -476,18 +500,36 @@ __global__ void __launch_bounds__(T) force_f32_batched_kernel(const BatchParams 
             }
             const int i = it.i0 + group + k * groups;
             if (lane == 0 && i < it.i_end) {
-                double *a = p.acc + 3 * (size_t)i;
-                const double gx = p.G * x, gy = p.G * y, gz = p.G * z;
-                a[0] = gx;
-                a[1] = gy;
-                a[2] = gz;
-                if (p.vel) {
-                    double *v = p.vel + 3 * (size_t)i;
-                    v[0] += p.half_dt * gx;
-                    v[1] += p.half_dt * gy;
-                    v[2] += p.half_dt * gz;
+                if (split) {
+                    double *q = slot + 3 * (size_t)(i - it.i0);
+                    q[0] = x;
+                    q[1] = y;
+                    q[2] = z;
+                } else {
+                    batch_write(p, i, x, y, z);
                 }
-                if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
+            }
+        }
+        if (split) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0)
+                s_last = atomicAdd(p.counters + it.ctr, 1u) == (unsigned)(it.nchunks - 1);
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const double *base = p.partial + (size_t)it.pbase * TILE_I * 3;
+                for (int q = threadIdx.x; q < it.i_end - it.i0; q += T) {
+                    double x = 0.0, y = 0.0, z = 0.0;
+                    for (int ch = 0; ch < it.nchunks; ++ch) {
+                        const double *r = base + ((size_t)ch * TILE_I + q) * 3;
+                        x += __ldcg(r);
+                        y += __ldcg(r + 1);
+                        z += __ldcg(r + 2);
+                    }
+                    batch_write(p, it.i0 + q, x, y, z);
+                }
+                if (threadIdx.x == 0) p.counters[it.ctr] = 0u;
             }
         }
     }

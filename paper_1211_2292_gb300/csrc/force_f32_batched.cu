@@ -15,6 +15,10 @@ const Quad kBatched[] = {
     NB_F32B_ENTRY(64, 6, 128, 2),
     NB_F32B_ENTRY(128, 8, 128, 0),
     NB_F32B_ENTRY(128, 4, 128, 1),
+    // the solo kernel's mixed shapes on 128-body j-tiles (8..10)
+    NB_F32B_ENTRY(128, 6, 128, 2),
+    NB_F32B_ENTRY(128, 8, 128, 3),
+    NB_F32B_ENTRY(64, 8, 128, 3),
 };
 
 }  // namespace

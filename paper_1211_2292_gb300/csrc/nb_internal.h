@@ -49,13 +49,20 @@ struct ForceParams {
     int *err;             // error word
 };
 
-// One work item of the batched kernel: bodies [i0, i_end) of one system
-// (i_end clipped to the item), interacting with bodies [j0, j1) of the same
-// system, `lanes` threads splitting the j loop of each body.
+// One work item of the batched kernel: bodies [i0, i_end) of one system,
+// interacting with bodies [j0, j1) of the same system, `lanes` adjacent
+// threads splitting the j loop of each body (the CTA then covers
+// threads * bodies_per_thread / lanes bodies).  A piece of a system whose
+// j range is split over nchunks > 1 items ("chunks", j-tile aligned) has
+// arrival counter `ctr`; chunk c stores its float64 partial sums in partial
+// slot pbase + c, and the last chunk to arrive adds the slots in chunk order.
+// nchunks == 1: ctr = -1, the item writes its bodies' accelerations itself.
 struct BatchItem {
     int i0, i_end, j0, j1;
-    int lanes, sys, pad0, pad1;
+    int lanes, sys, ctr, pbase;
+    int chunk, nchunks, pad0, pad1;
 };
+constexpr int BATCH_ITEM_INTS = 12;
 
 struct BatchParams {
     const float4 *P;      // (x_hi,y_hi,z_hi,m)
@@ -63,6 +70,8 @@ struct BatchParams {
     const BatchItem *items;
     int n_items;
     unsigned *queue;      // [0] next item, [1] CTAs done; both zero between launches
+    double *partial;      // [slots][threads * bodies_per_thread][3] chunk partial sums
+    unsigned *counters;   // per split piece, zero between launches
     float eps2f;
     double G;
     double *acc;

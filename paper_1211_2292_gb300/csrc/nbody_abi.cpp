@@ -411,6 +411,8 @@ nb_status batched_force(nb_ctx *c, cudaStream_t s, double G, double eps, double 
     p.items = c->items;
     p.n_items = (int)c->n_items;
     p.queue = c->queue;
+    p.partial = c->partial;
+    p.counters = c->counters;
     p.eps2f = (float)(eps * eps);
     p.G = G;
     p.acc = acc;
@@ -934,38 +936,75 @@ int64_t nb_plan_batch_host(int64_t nsys, const int64_t *off, int T, int I, int J
     if (off[0] != 0) return -1;
     for (int64_t k = 0; k < nsys; ++k)
         if (off[k + 1] < off[k] || off[k + 1] > 0x7fffffffLL) return -1;
+    static_assert(sizeof(BatchItem) == nb::BATCH_ITEM_INTS * sizeof(int32_t), "item layout");
+    const int64_t TI = (int64_t)T * I;
+    int lmax = 1;  // lanes: a power of two, at most 32 (one warp), T and J
+    while (lmax * 2 <= 32 && lmax * 2 <= T && lmax * 2 <= J) lmax *= 2;
     struct Cand { BatchItem it; int64_t cost; };
     std::vector<Cand> v;
-    for (int64_t k = 0; k < nsys; ++k) {
-        const int64_t nk = off[k + 1] - off[k];
-        if (nk == 0) continue;
-        // lanes: as many as still cover the system with one item, and more
-        // while an item would cost more than max_item_pairs (shorter items
-        // leave a shorter tail when the queue runs dry)
-        int lanes = 1;
-        while (lanes < 32 && lanes * 2 <= T && lanes * 2 <= J &&
-               ((int64_t)T * I / (lanes * 2) >= nk ||
-                (max_item_pairs > 0 && (int64_t)T * I / lanes * nk > max_item_pairs)))
-            lanes *= 2;
-        const int64_t per = (int64_t)T * I / lanes;
-        const int64_t cost = (nk + J - 1) / J * J / lanes;  // j-pairs per thread
-        for (int64_t i0 = off[k]; i0 < off[k + 1]; i0 += per) {
+    int ctr = 0, pbase = 0;
+    // One piece: bodies [i0, i0 + cnt) of system k with `lanes` lanes, its j
+    // range split into chunks while a piece would exceed max_item_pairs (a
+    // shorter tail when the queue runs dry; the chunks' partial sums are
+    // added in order, so results do not depend on which CTA ran which).
+    auto piece = [&](int64_t k, int64_t i0, int64_t cnt, int lanes) {
+        const int64_t nj = off[k + 1] - off[k];
+        const int64_t ntiles = (nj + J - 1) / J;
+        int64_t S = 1;
+        if (max_item_pairs > 0) {
+            const int64_t pairs = TI / lanes * nj;
+            S = std::min<int64_t>((pairs + max_item_pairs - 1) / max_item_pairs, ntiles);
+            S = std::max<int64_t>(S, 1);
+        }
+        for (int64_t c = 0; c < S; ++c) {
+            const int64_t t0 = ntiles * c / S, t1 = ntiles * (c + 1) / S;
             BatchItem b;
             b.i0 = (int)i0;
-            b.i_end = (int)std::min(i0 + per, off[k + 1]);
-            b.j0 = (int)off[k];
-            b.j1 = (int)off[k + 1];
+            b.i_end = (int)(i0 + cnt);
+            b.j0 = (int)(off[k] + t0 * J);
+            b.j1 = (int)std::min(off[k] + t1 * J, off[k + 1]);
             b.lanes = lanes;
             b.sys = (int)k;
+            b.ctr = S > 1 ? ctr : -1;
+            b.pbase = S > 1 ? pbase : 0;
+            b.chunk = (int)c;
+            b.nchunks = (int)S;
             b.pad0 = b.pad1 = 0;
-            v.push_back({b, cost});
+            v.push_back({b, (t1 - t0) * J / lanes});  // j-pairs per thread
+        }
+        if (S > 1) {
+            ++ctr;
+            pbase += (int)S;
+        }
+    };
+    for (int64_t k = 0; k < nsys; ++k) {
+        int64_t i = off[k];
+        const int64_t e = off[k + 1];
+        // full tiles, one lane per body
+        for (; e - i >= TI; i += TI) piece(k, i, TI, 1);
+        // the remainder r < TI in pieces of TI/lanes bodies (lanes = 2, 4,
+        // ...): the smallest piece that covers r when it wastes at most an
+        // eighth of its slots (or lanes are exhausted), else the largest
+        // piece within r and continue with the rest
+        while (i < e) {
+            const int64_t r = e - i;
+            int lanes = 1;
+            while (lanes < lmax && TI / (lanes * 2) >= r) lanes *= 2;
+            const int64_t cover = TI / lanes;  // smallest piece >= r
+            if (lanes == lmax || (cover - r) * 8 <= cover) {
+                piece(k, i, r, lanes);
+                break;
+            }
+            piece(k, i, cover / 2, lanes * 2);
+            i += cover / 2;
         }
     }
     std::stable_sort(v.begin(), v.end(), [](const Cand &a, const Cand &b) { return a.cost > b.cost; });
     const int64_t cnt = (int64_t)v.size();
     if (items_out) {
         if (cnt > max_items) return -1;
-        for (int64_t q = 0; q < cnt; ++q) std::memcpy(items_out + 8 * q, &v[q].it, sizeof(BatchItem));
+        for (int64_t q = 0; q < cnt; ++q)
+            std::memcpy(items_out + nb::BATCH_ITEM_INTS * q, &v[q].it, sizeof(BatchItem));
     }
     return cnt;
 }
@@ -1270,20 +1309,37 @@ nb_status nb_batch_plan(nb_ctx *c, int64_t nsys, const int64_t *offsets)
     pick(c, nb::KIND_BATCHED, offsets[nsys], v, divisor);
     if (divisor <= 0) divisor = 4;
     const KernelEntry &k = nb::f32_batched_kernel(v, c->prec == NB_FP32_COMP, false);
-    // When the batch already has more items than resident CTAs, cap an item
-    // at 1/divisor of an even share of the pairs per CTA to shorten the tail
-    // (the tuning entry's split field holds the divisor; 0 = 4).
+    // When the batch has more work than one item per resident CTA, cap an
+    // item at 1/divisor of an even share of the pairs per CTA (j-chunks of
+    // big pieces) to shorten the tail; the tuning entry's split field holds
+    // the divisor (0 = 4).  A plan whose chunks would not fit the context's
+    // partial-sum scratch or counters is redone with a doubled cap.
     double pairs = 0.0;
     for (int64_t q = 0; q < nsys; ++q)
         pairs += (double)(offsets[q + 1] - offsets[q]) * (double)(offsets[q + 1] - offsets[q]);
     const int64_t slots = (int64_t)c->num_sms * occupancy(c, k);
+    const int64_t TI = (int64_t)k.T * k.I;
     int64_t cap = 0;
     if (nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, 0, nullptr, 0) >= slots)
         cap = (int64_t)(pairs / ((double)divisor * (double)std::max<int64_t>(slots, 1))) + 1;
-    const int64_t cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, nullptr, 0);
-    if (cnt < 0) return failf(c, NB_EINVAL, "cannot plan these offsets");
-    std::vector<int32_t> host((size_t)std::max<int64_t>(cnt, 1) * 8);
-    nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, host.data(), cnt);
+    std::vector<int32_t> host;
+    int64_t cnt = 0;
+    for (int attempt = 0;; ++attempt) {
+        cnt = nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, nullptr, 0);
+        if (cnt < 0) return failf(c, NB_EINVAL, "cannot plan these offsets");
+        host.assign((size_t)std::max<int64_t>(cnt, 1) * nb::BATCH_ITEM_INTS, 0);
+        nb_plan_batch_host(nsys, offsets, k.T, k.I, k.J, cap, host.data(), cnt);
+        int64_t ctrs = 0, pslots = 0;
+        for (int64_t q = 0; q < cnt; ++q) {
+            const BatchItem *it = reinterpret_cast<const BatchItem *>(host.data()) + q;
+            if (it->nchunks > 1) {
+                ctrs = std::max<int64_t>(ctrs, it->ctr + 1);
+                pslots = std::max<int64_t>(pslots, (int64_t)it->pbase + it->nchunks);
+            }
+        }
+        if (cap == 0 || (ctrs <= c->n_counters && pslots * TI * 3 <= c->partial_bodies * 4)) break;
+        cap = attempt < 8 ? cap * 2 : 0;
+    }
     if (cnt > c->items_cap) {
         cudaFree(c->items);
         c->items = nullptr;

@@ -402,8 +402,12 @@ def choose_split(n_itiles, n_jtiles, slots, max_split_bodies, tile_bodies) -> in
     return int(load().nb_choose_split(n_itiles, n_jtiles, slots, max_split_bodies, tile_bodies))
 
 
+BATCH_ITEM_INTS = 12
+
+
 def plan_batch_host(offsets, threads, bodies_per_thread, jtile, max_item_pairs=0):
-    """Work items [(i0, i_end, j0, j1, lanes, sys)] the batched kernel would run."""
+    """Work items the batched kernel would run, largest cost first:
+    [(i0, i_end, j0, j1, lanes, sys, ctr, pbase, chunk, nchunks)]."""
     lib = load()
     offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
     nsys = len(offsets) - 1
@@ -411,7 +415,8 @@ def plan_batch_host(offsets, threads, bodies_per_thread, jtile, max_item_pairs=0
                                  int(max_item_pairs), None, 0)
     if cnt < 0:
         raise ValueError("invalid offsets")
-    buf = (ctypes.c_int32 * (8 * max(cnt, 1)))()
+    w = BATCH_ITEM_INTS
+    buf = (ctypes.c_int32 * (w * max(cnt, 1)))()
     lib.nb_plan_batch_host(nsys, offs, threads, bodies_per_thread, jtile, int(max_item_pairs),
                            buf, cnt)
-    return [tuple(buf[8 * q: 8 * q + 6]) for q in range(cnt)]
+    return [tuple(buf[w * q: w * q + 10]) for q in range(cnt)]

@@ -94,29 +94,53 @@ def test_choose_split_degenerate():
 
 @pytest.mark.parametrize("cap", [0, 200_000])
 @pytest.mark.parametrize("T,I,J", [(128, 2, 128), (128, 4, 128), (256, 2, 256), (64, 4, 128),
-                                   (128, 6, 256)])
-def test_plan_batch_covers_every_body_once(T, I, J, cap):
+                                   (128, 6, 256), (64, 6, 128)])
+def test_plan_batch_covers_every_pair_once(T, I, J, cap):
     from paper_1211_2292_gb300 import inputs
     sizes = [0, 1, 2, 64, 100, 255, 256, 257, 8192] + list(inputs.batch_sizes(60, seed=3))
     off = np.concatenate([[0], np.cumsum(sizes)])
     items = nbody.plan_batch_host(off, T, I, J, cap)
-    if cap:
-        # an item's bodies x j-range stay under the cap unless lanes ran out
-        for i0, i_end, j0, j1, lanes, sys in items:
-            assert (T * I // lanes) * (j1 - j0) <= cap or lanes == min(32, T, J)
-    cover = np.zeros(off[-1], dtype=int)
+    TI = T * I
+    lmax = min(32, T, J)
+    jcover = np.zeros(off[-1], dtype=np.int64)  # j bodies met, summed over a body's items
     costs = []
-    for i0, i_end, j0, j1, lanes, sys in items:
-        assert off[sys] == j0 and off[sys + 1] == j1 and j0 <= i0 < i_end <= j1
-        assert lanes in (1, 2, 4, 8, 16, 32) and lanes <= T
-        assert i_end - i0 <= T * I // lanes
-        cover[i0:i_end] += 1
+    pieces = {}
+    for i0, i_end, j0, j1, lanes, sys, ctr, pbase, chunk, nchunks in items:
+        s_, e_ = off[sys], off[sys + 1]
+        assert s_ <= i0 < i_end <= e_ and s_ <= j0 < j1 <= e_
+        assert (j0 - s_) % J == 0  # chunks start on j-tile boundaries
+        assert lanes in (1, 2, 4, 8, 16, 32) and lanes <= lmax
+        assert i_end - i0 <= TI // lanes
+        jcover[i0:i_end] += j1 - j0
         costs.append(-(-(j1 - j0) // J) * J // lanes)
-    assert np.all(cover == 1)
+        if nchunks == 1:
+            assert ctr == -1 and (j0, j1) == (s_, e_)
+        else:
+            pieces.setdefault(ctr, []).append((chunk, nchunks, pbase, i0, i_end, j0, j1))
+        if cap and nchunks == 1:
+            # an unsplit piece stays under the cap unless it is one j-tile
+            assert (TI // lanes) * (j1 - j0) <= cap or j1 - j0 <= J
+    # every body meets every body of its system once
+    assert np.array_equal(jcover, np.repeat(np.diff(off), np.diff(off)))
     assert costs == sorted(costs, reverse=True)
-    # small systems use several lanes per body
-    small = [it for it in items if it[3] - it[2] == 64]
-    assert small and all(it[4] == min(32, T * I // 64) or T * I // it[4] >= 64 for it in small)
+    # chunks of a split piece: one counter, contiguous slots, consecutive j ranges
+    assert sorted(pieces) == list(range(len(pieces)))
+    slots = []
+    for ctr, ch in pieces.items():
+        ch.sort()
+        nch, pbase = ch[0][1], ch[0][2]
+        assert [c[0] for c in ch] == list(range(nch)) and all(c[1:5] == ch[0][1:5] for c in ch)
+        assert all(a[6] == b[5] for a, b in zip(ch, ch[1:]))
+        slots.append((pbase, nch))
+    slots.sort()
+    assert not slots or slots[0][0] == 0
+    assert all(a[0] + a[1] == b[0] for a, b in zip(slots, slots[1:]))
+    if cap:
+        assert pieces  # the 8192-body system is split
+    # remainders go in pieces of TI / lanes bodies: little is left unfilled
+    filled = sum(it[1] - it[0] for it in items if it[8] == 0)
+    slots_ = sum(TI // it[4] for it in items if it[8] == 0)
+    assert filled >= 0.75 * slots_
 
 
 def test_plan_batch_rejects_bad_offsets():

@@ -23,7 +23,7 @@ def _check_systems(a, bodies, off, eps, idx=None):
         assert np.sqrt((err ** 2).mean()) <= 1e-5 and err.max() <= 1e-4, (k, err.max())
 
 
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(11)))
 def test_batched_forces_match_oracle(cuda, variant):
     bodies, off = inputs.plummer_batch(sizes=SIZES, seed=3)
     with nbody.NBody(bodies.n, "fp32_comp") as nb:
@@ -47,11 +47,12 @@ def test_batched_zero_softening(cuda):
 
 def test_batched_bitwise_equals_solo_when_tiles_match(cuda):
     # Batched variant 1 and solo variant 0 share (T, I, J) = (128, 4, 128);
-    # a system larger than one tile runs with one lane per body and no
-    # j-split, so both perform the same operations in the same order.
+    # a system of whole tiles runs with one lane per body and (with few
+    # items) unsplit j ranges, so both perform the same operations in the
+    # same order.
     assert nbody.variants(nbody.KIND_BATCHED, "fp32_comp")[1] == nbody.variants(
         nbody.KIND_FORCE, "fp32_comp")[0]
-    b = inputs.plummer(3000, seed=11)
+    b = inputs.plummer(3072, seed=11)
     x, m = to_dev(b.pos, cuda), to_dev(b.mass, cuda)
     with nbody.NBody(b.n, "fp32_comp") as nb:
         nb.tune_set(nbody.KIND_FORCE, 0, 1 << 40, 0, 1)
@@ -60,6 +61,30 @@ def test_batched_bitwise_equals_solo_when_tiles_match(cuda):
         nb.batch_plan([0, b.n])
         bat = host(nb.forces_batched(x, m, 1.0, 0.01))
     assert np.array_equal(solo, bat)
+
+
+def test_chunked_pieces_equal_the_solo_j_split(cuda):
+    # 400 systems of 2048 bodies: more pieces than resident CTAs, so each
+    # piece's j range is split into chunks (2 to 4 here, by the item cap)
+    # whose partial sums the last chunk adds in order -- the solo kernel's
+    # j-split with the same count, bit for bit.
+    bodies, off = inputs.plummer_batch(sizes=[2048] * 400, seed=14)
+    x, m = to_dev(bodies.pos, cuda), to_dev(bodies.mass, cuda)
+    with nbody.NBody(bodies.n, "fp32_comp") as nb:
+        nb.tune_set(nbody.KIND_BATCHED, 0, 1 << 40, 1, 4)
+        nb.batch_plan(off)
+        a = host(nb.forces_batched(x, m, 1.0, 0.01))
+        nb.sync()
+    with nbody.NBody(2048, "fp32_comp") as nb:
+        for k in (0, 177, 399):
+            s_, e_ = off[k], off[k + 1]
+            match = []
+            for S in (1, 2, 3, 4):
+                nb.tune_set(nbody.KIND_FORCE, 0, 1 << 40, 0, S)
+                if np.array_equal(host(nb.forces(x[s_:e_], m[s_:e_], 1.0, 0.01)), a[s_:e_]):
+                    match.append(S)
+            assert match and match[0] > 1, (k, match)
+    _check_systems(a, bodies, off, 0.01, idx=[0, 5, 177, 250, 399])
 
 
 def test_batched_steps_match_oracle_and_graph(cuda):
