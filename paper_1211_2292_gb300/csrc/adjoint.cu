@@ -288,8 +288,21 @@ __device__ __forceinline__ void vjp_pair(float2 xj, float2 yj, float2 zj, float2
     gm = fma2(dlj, ri3, gm);
 }
 
-template <int T, int I, int J, bool ZEPS>
-__global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
+// Float64 totals of the seven sums per body: in registers, or (TSM) in
+// shared memory, touched once per j-tile, which frees 14 * I registers for
+// more resident warps.
+template <int T, int I, bool TSM>
+struct VjpTotals {
+    double reg[TSM ? 1 : 7][TSM ? 1 : I];
+    double *sh;  // this CTA's [7][I][T] doubles (TSM only)
+    __device__ __forceinline__ double &at(int r, int k)
+    {
+        return TSM ? sh[(r * I + k) * T + threadIdx.x] : reg[TSM ? 0 : r][TSM ? 0 : k];
+    }
+};
+
+template <int T, int I, int J, bool ZEPS, bool TSM = false, int MINB = 0>
+__global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
 {
     static_assert(I % 2 == 0 && J % T == 0, "bad tile shape");
     constexpr int NP = I / 2;
@@ -297,6 +310,7 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
     constexpr int LPT = J / T;
     __shared__ __align__(16) float4 tile[2][4 * J];
     __shared__ float red[6][T / 32];
+    __shared__ double tsh[TSM ? 7 * I * T : 1];
     __shared__ int s_last;
 
     const float4 *Ph = static_cast<const float4 *>(p.PV);
@@ -347,11 +361,12 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
     }
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
     VjpAcc<NP> acc;
-    double tot[7][I];
+    VjpTotals<T, I, TSM> tot;
+    tot.sh = tsh;
 #pragma unroll
     for (int q = 0; q < 7; ++q)
 #pragma unroll
-        for (int k = 0; k < I; ++k) tot[q][k] = 0.0;
+        for (int k = 0; k < I; ++k) tot.at(q, k) = 0.0;
 
     float4 bh[LPT], bl[LPT], bu[LPT];
     if (t0 < t1) {
@@ -404,8 +419,8 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
                                   &acc.qy[q], &acc.qz[q], &acc.gm[q]};
 #pragma unroll
             for (int r = 0; r < 7; ++r) {
-                tot[r][2 * q] += (double)v[r]->x;
-                tot[r][2 * q + 1] += (double)v[r]->y;
+                tot.at(r, 2 * q) += (double)v[r]->x;
+                tot.at(r, 2 * q + 1) += (double)v[r]->y;
             }
         }
         if (t + 1 < t1) vjp_stage_store<T, J>(tile[bsel ^ 1], bh, bl, bu, c);
@@ -435,7 +450,7 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
             if (i < n) {
                 double sums[7];
 #pragma unroll
-                for (int r = 0; r < 7; ++r) sums[r] = tot[r][k];
+                for (int r = 0; r < 7; ++r) sums[r] = tot.at(r, k);
                 emit(i, sums);
             }
         }
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
         if (i < n) {
             double *q = p.partial + ((size_t)js * n + i) * 7;
 #pragma unroll
-            for (int r = 0; r < 7; ++r) q[r] = tot[r][k];
+            for (int r = 0; r < 7; ++r) q[r] = tot.at(r, k);
         }
     }
     __threadfence();
@@ -477,9 +492,10 @@ __global__ void __launch_bounds__(T) vjp_f32_kernel(const VjpParams p)
      {T, I, J, (const void *)vjp_kernel<R, T, I, J, true>}}
 
 typedef KernelEntry Pair[2];
-#define NB_VJP32_ENTRY(T, I, J)                                   \
-    {{T, I, J, (const void *)vjp_f32_kernel<T, I, J, false>},     \
-     {T, I, J, (const void *)vjp_f32_kernel<T, I, J, true>}}
+#define NB_VJP32_ENTRY_X(T, I, J, S, M)                                   \
+    {{T, I, J, (const void *)vjp_f32_kernel<T, I, J, false, S, M>},       \
+     {T, I, J, (const void *)vjp_f32_kernel<T, I, J, true, S, M>}}
+#define NB_VJP32_ENTRY(T, I, J) NB_VJP32_ENTRY_X(T, I, J, false, 0)
 
 const Pair kVjp32[] = {
     NB_VJP32_ENTRY(128, 2, 128),
@@ -487,6 +503,14 @@ const Pair kVjp32[] = {
     NB_VJP32_ENTRY(256, 2, 256),
     NB_VJP32_ENTRY(64, 4, 128),
     NB_VJP32_ENTRY(128, 4, 256),
+    // float64 totals in shared memory, registers capped for 5-6 CTAs/SM (5..8)
+    NB_VJP32_ENTRY_X(128, 2, 128, true, 5),
+    NB_VJP32_ENTRY_X(128, 2, 128, true, 6),
+    NB_VJP32_ENTRY_X(64, 2, 64, true, 12),
+    NB_VJP32_ENTRY_X(64, 2, 128, true, 10),
+    // shorter j-tiles and smaller CTAs with totals in registers (9..10)
+    NB_VJP32_ENTRY(64, 2, 64),
+    NB_VJP32_ENTRY(64, 2, 128),
 };
 const Pair kVjp64[] = {
     NB_VJP_ENTRY(double, 128, 1, 128),
