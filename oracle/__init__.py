@@ -64,6 +64,16 @@ def _bind(lib):
     lib.oracle_bh_groups.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                      i64, _I, _I, _D, _I]
     lib.oracle_bh_groups.restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.oracle_orb.argtypes = [i64, _D, ctypes.c_int, i32p]
+    lib.oracle_orb.restype = ctypes.c_int
+    lib.oracle_bh_sharded.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, i32p, _D, _I, _I]
+    lib.oracle_bh_sharded.restype = ctypes.c_int
+    lib.oracle_bh_let.argtypes = [i64, _D, _D, dbl, ctypes.c_int, f32p, f32p, i64, _I, i32p,
+                                  i32p, _I, _I, _I, f32p, f32p, _I]
+    lib.oracle_bh_let.restype = ctypes.c_int
     lib.oracle_fmm_forces.argtypes = [i64, _D, _D, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                       _D, _I, _I]
     lib.oracle_fmm_forces.restype = ctypes.c_int
@@ -219,6 +229,75 @@ def bh_groups(pos, mass, G, eps, theta, leaf_cap, group, sel):
     if rc != 0:
         raise ValueError("oracle_bh_groups: bad leaf_cap/group or group index")
     return idx, acc, cnt
+
+
+def orb(pos, P):
+    """Processor of each body under orthogonal recursive bisection into P
+    equal-count domains (paper Sec. IV-B; readings in nbody_oracle.c)."""
+    x = _f64(pos)
+    n = x.shape[0]
+    out = np.zeros(n, dtype=np.int32)
+    if _load().oracle_orb(n, _p(x), int(P), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))):
+        raise ValueError("oracle_orb: P must be >= 1")
+    return out
+
+
+def bh_sharded(pos, mass, G, eps, theta, leaf_cap, group, rank, P):
+    """The parallel tree code's accelerations (paper Sec. IV-B): every
+    processor's tree over its own bodies, walked by every processor's groups.
+    Returns acc (n, 3), stats {nodes, leaves, cell_interactions,
+    body_interactions} and per body (cells, bodies met, bodies covered)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    r = np.ascontiguousarray(rank, dtype=np.int32)
+    out = np.zeros((n, 3))
+    st = np.zeros(4, dtype=np.int64)
+    cnt = np.zeros((n, 3), dtype=np.int64)
+    rc = _load().oracle_bh_sharded(n, _p(x), _p(m), float(G), float(eps), float(theta),
+                                   int(leaf_cap), int(group), int(P),
+                                   r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _p(out),
+                                   st.ctypes.data_as(_I), cnt.ctypes.data_as(_I))
+    if rc != 0:
+        raise ValueError("oracle_bh_sharded: bad arguments")
+    stats = dict(zip(("nodes", "leaves", "cell_interactions", "body_interactions"),
+                     (int(v) for v in st)))
+    return out, stats, cnt
+
+
+def bh_let(pos, mass, theta, leaf_cap, box_lo, box_hi):
+    """The tree over (pos, mass) and each node's kind in the locally
+    essential tree sent to a destination whose bodies lie in the float32 box
+    [box_lo, box_hi]: 0 not sent, 1 sent alone, 2 sent with its children,
+    3 a leaf sent with its bodies.  Returns a dict of per-node arrays (build
+    order: kind, level, prefix, child (k, 8), range (k, 2), lo, hi (k, 3)
+    float32) and perm (key order -> body)."""
+    m = _f64(mass)
+    n = m.shape[0]
+    x = _f64(pos, (n, 3))
+    blo = np.ascontiguousarray(box_lo, dtype=np.float32)
+    bhi = np.ascontiguousarray(box_hi, dtype=np.float32)
+    lib = _load()
+    f32p = ctypes.POINTER(ctypes.c_float)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    nn = np.zeros(1, dtype=np.int64)
+    none = ctypes.POINTER(ctypes.c_int64)()
+    if lib.oracle_bh_let(n, _p(x), _p(m), float(theta), int(leaf_cap), blo.ctypes.data_as(f32p),
+                         bhi.ctypes.data_as(f32p), 0, nn.ctypes.data_as(_I), None, None, none,
+                         none, none, None, None, none):
+        raise ValueError("oracle_bh_let: bad arguments")
+    k = int(nn[0])
+    d = {"kind": np.zeros(k, np.int32), "level": np.zeros(k, np.int32),
+         "prefix": np.zeros(k, np.int64), "child": np.zeros((k, 8), np.int64),
+         "range": np.zeros((k, 2), np.int64), "lo": np.zeros((k, 3), np.float32),
+         "hi": np.zeros((k, 3), np.float32), "perm": np.zeros(n, np.int64)}
+    lib.oracle_bh_let(n, _p(x), _p(m), float(theta), int(leaf_cap), blo.ctypes.data_as(f32p),
+                      bhi.ctypes.data_as(f32p), k, nn.ctypes.data_as(_I),
+                      d["kind"].ctypes.data_as(i32p), d["level"].ctypes.data_as(i32p),
+                      d["prefix"].ctypes.data_as(_I), d["child"].ctypes.data_as(_I),
+                      d["range"].ctypes.data_as(_I), d["lo"].ctypes.data_as(f32p),
+                      d["hi"].ctypes.data_as(f32p), d["perm"].ctypes.data_as(_I))
+    return d
 
 
 def fmm_multi_indices(p):

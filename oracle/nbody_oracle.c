@@ -605,6 +605,334 @@ int oracle_bh_groups(int64_t n, const double *x, const double *m, double G, doub
 }
 
 /*
+ * Parallel tree code (paper Sec. IV-B).  The paper divides space by
+ * orthogonal recursive bisection (ORB) into as many non-overlapping
+ * subspaces as processors, each holding about the same number of bodies;
+ * each processor builds a tree over its own bodies and extends it into a
+ * locally essential tree (LET) with the nodes of the other processors' trees
+ * that its bodies need -- a node matters to the bodies in its "influence
+ * ring", those that open its parent yet use the node itself -- and then
+ * computes forces as in the sequential code.  Readings (the paper gives no
+ * splitting rule, ring construction or summation order):
+ *  - ORB: the bodies of a part that p processors share are cut across the
+ *    longest side of their float64 bounding box (the lowest axis on ties);
+ *    the lower part takes floor(p/2) processors and the
+ *    k = floor(count * floor(p/2) / p) bodies first in (coordinate, body
+ *    index) order, the upper part the rest; parts are cut again until each
+ *    holds one processor's bodies;
+ *  - each processor's tree is the tree code's tree (readings above) over its
+ *    own bodies taken in increasing body index, with their own bounding
+ *    cube; bodies walk in groups of consecutive bodies of their own tree's
+ *    key order;
+ *  - a body's acceleration is the sum over every processor's tree of that
+ *    tree's group walk (its own tree first, then the others in processor
+ *    order); a processor's LET holds, of each other tree, what those walks
+ *    meet;
+ *  - the LET of tree s for processor d applies the influence-ring test from
+ *    the destination's side: the root is sent; a sent node that is distant
+ *    enough (the walk's float32 test) from the float32 bounding box of d's
+ *    bodies is accepted by every body of d and is sent alone; otherwise a
+ *    sent leaf is sent with its bodies and a sent cell with all its
+ *    children.  No body inside a box is nearer a cube than the box is (the
+ *    float32 operations are monotonic), so no body of d opens a node sent
+ *    alone, and every node a body of d opens is sent with what is inside.
+ */
+static const double *g_orb_x;
+static int g_orb_axis;
+static int cmp_orb(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    double xi = g_orb_x[3 * i + g_orb_axis], xj = g_orb_x[3 * j + g_orb_axis];
+    if (xi != xj) return xi < xj ? -1 : 1;
+    return i < j ? -1 : (i > j);
+}
+
+static void orb_part(const double *x, int64_t *idx, int64_t cnt, int rank0, int p, int32_t *rank)
+{
+    if (cnt == 0) return;
+    if (p == 1) {
+        for (int64_t k = 0; k < cnt; ++k) rank[idx[k]] = rank0;
+        return;
+    }
+    double lo[3], hi[3];
+    for (int c = 0; c < 3; ++c) lo[c] = hi[c] = x[3 * idx[0] + c];
+    for (int64_t k = 1; k < cnt; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double v = x[3 * idx[k] + c];
+            if (v < lo[c]) lo[c] = v;
+            if (v > hi[c]) hi[c] = v;
+        }
+    int axis = 0;
+    for (int c = 1; c < 3; ++c)
+        if (hi[c] - lo[c] > hi[axis] - lo[axis]) axis = c;
+    g_orb_x = x;
+    g_orb_axis = axis;
+    qsort(idx, (size_t)cnt, sizeof(int64_t), cmp_orb);
+    int p_lo = p / 2;
+    int64_t k = cnt * (int64_t)p_lo / p;
+    orb_part(x, idx, k, rank0, p_lo, rank);
+    orb_part(x, idx + k, cnt - k, rank0 + p_lo, p - p_lo, rank);
+}
+
+/* rank[i] in [0, P): the processor whose ORB domain holds body i. */
+int oracle_orb(int64_t n, const double *x, int P, int32_t *rank)
+{
+    if (P < 1) return -1;
+    if (n <= 0) return 0;
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) idx[i] = i;
+    orb_part(x, idx, n, 0, P, rank);
+    free(idx);
+    return 0;
+}
+
+/* One group of targets (nt bodies: float32 positions xf for the opening
+ * test, float64 positions xt, body indices tid) walks the tree S of the
+ * source bodies xs, ms (body indices sid): each target's sum (without G) is
+ * ADDED to a[3k..] and its list sizes to c[3k..] = {cells, bodies met
+ * directly, bodies inside the cells and met directly}. */
+static void bh_walk_sources(const bh_prep *S, bh_work *W, const double *xs, const double *ms,
+                            const int64_t *sid, int64_t nt, const float *xf, const double *xt,
+                            const int64_t *tid, double eps, double *a, int64_t *c)
+{
+    const bh_tree *t = &S->t;
+    const int64_t *perm = S->perm;
+    int64_t nl = 0, sp = 0;
+    int64_t *stack = W->stack;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        int64_t id = stack[--sp];
+        const bh_node *nd = &t->nodes[id];
+        int all = 1;
+        for (int64_t k = 0; k < nt && all; ++k) {
+            const float *p = xf + 3 * k;
+            float d2 = 0.0f;
+            for (int cc = 0; cc < 3; ++cc) {
+                float aa = nd->lo[cc] - p[cc];
+                float bb = p[cc] - nd->hi[cc];
+                float dd = aa > bb ? aa : bb;
+                dd = dd > 0.0f ? dd : 0.0f;
+                float sq = dd * dd;
+                d2 = d2 + sq;
+            }
+            if (!(d2 >= S->crit2[nd->level])) all = 0;
+        }
+        int leaf = 1;
+        for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
+        if (all || leaf) {
+            if (nl == W->lcap) {
+                W->lcap *= 2;
+                W->lst = (int64_t *)realloc(W->lst, sizeof(int64_t) * (size_t)W->lcap);
+            }
+            W->lst[nl++] = all ? id : ~id;
+        } else {
+            for (int o = 7; o >= 0; --o)
+                if (nd->child[o] >= 0) stack[sp++] = nd->child[o];
+        }
+    }
+    const int64_t *lst = W->lst;
+    for (int64_t k = 0; k < nt; ++k) {
+        const double *xi = xt + 3 * k;
+        double s[3] = {0, 0, 0};
+        int64_t nc = 0, nb = 0, cov = 0;
+        for (int64_t q = 0; q < nl; ++q) {
+            if (lst[q] >= 0) {
+                const bh_node *nd = &t->nodes[lst[q]];
+                double d[3], s2 = eps * eps;
+                for (int cc = 0; cc < 3; ++cc) {
+                    d[cc] = nd->com[cc] - xi[cc];
+                    s2 += d[cc] * d[cc];
+                }
+                double w = nd->M / (s2 * sqrt(s2));
+                for (int cc = 0; cc < 3; ++cc) s[cc] += w * d[cc];
+                ++nc;
+                cov += nd->end - nd->start;
+            } else {
+                const bh_node *nd = &t->nodes[~lst[q]];
+                for (int64_t kk = nd->start; kk < nd->end; ++kk) {
+                    int64_t j = perm[kk];
+                    ++nb;
+                    ++cov;
+                    if (sid[j] == tid[k]) continue;
+                    double d[3], s2 = eps * eps;
+                    for (int cc = 0; cc < 3; ++cc) {
+                        d[cc] = xs[3 * j + cc] - xi[cc];
+                        s2 += d[cc] * d[cc];
+                    }
+                    double w = ms[j] / (s2 * sqrt(s2));
+                    for (int cc = 0; cc < 3; ++cc) s[cc] += w * d[cc];
+                }
+            }
+        }
+        for (int cc = 0; cc < 3; ++cc) a[3 * k + cc] += s[cc];
+        c[3 * k] += nc;
+        c[3 * k + 1] += nb;
+        c[3 * k + 2] += cov;
+    }
+}
+
+/* The bodies of processor s (rank[i] == s), in increasing body index. */
+static int64_t shard_gather(int64_t n, const double *x, const double *m, const int32_t *rank,
+                            int s, double *xs, double *ms, int64_t *sid)
+{
+    int64_t ns = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (rank[i] == s) {
+            for (int c = 0; c < 3; ++c) xs[3 * ns + c] = x[3 * i + c];
+            ms[ns] = m[i];
+            sid[ns] = i;
+            ++ns;
+        }
+    return ns;
+}
+
+/*
+ * Accelerations of the parallel tree code over P processors whose bodies
+ * rank[] assigns (e.g. from oracle_orb): every processor's tree built over
+ * its own bodies, every group of every processor walking every tree.
+ * cnt (optional, [n][3]) receives per body the cells met, the bodies met
+ * directly (the self pair included) and the bodies covered (inside the
+ * cells met, or met directly: each body of the system exactly once).
+ * stats = {nodes of all trees, their leaves, cell interactions, body
+ * interactions}.  Returns -1 for bad arguments.
+ */
+int oracle_bh_sharded(int64_t n, const double *x, const double *m, double G, double eps,
+                      double theta, int leaf_cap, int group, int P, const int32_t *rank,
+                      double *acc, int64_t *stats, int64_t *cnt)
+{
+    if (leaf_cap < 1 || group < 1 || P < 1) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (rank[i] < 0 || rank[i] >= P) return -1;
+    if (n <= 0) return 0;
+    double **xs = (double **)calloc((size_t)P, sizeof(double *));
+    double **ms = (double **)calloc((size_t)P, sizeof(double *));
+    int64_t **sid = (int64_t **)calloc((size_t)P, sizeof(int64_t *));
+    int64_t *ns = (int64_t *)calloc((size_t)P, sizeof(int64_t));
+    bh_prep *S = (bh_prep *)calloc((size_t)P, sizeof(bh_prep));
+    int64_t st[4] = {0, 0, 0, 0};
+    for (int s = 0; s < P; ++s) {
+        xs[s] = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+        ms[s] = (double *)malloc(sizeof(double) * (size_t)n);
+        sid[s] = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+        ns[s] = shard_gather(n, x, m, rank, s, xs[s], ms[s], sid[s]);
+        if (ns[s] > 0) {
+            bh_prepare(&S[s], ns[s], xs[s], ms[s], theta, leaf_cap);
+            st[0] += S[s].t.nnodes;
+            st[1] += S[s].leaves;
+        }
+    }
+    bh_work W;
+    bh_work_init(&W, group);
+    float *xf = (float *)malloc(sizeof(float) * 3 * (size_t)group);
+    double *xt = (double *)malloc(sizeof(double) * 3 * (size_t)group);
+    int64_t *tid = (int64_t *)malloc(sizeof(int64_t) * (size_t)group);
+    double *a = (double *)malloc(sizeof(double) * 3 * (size_t)group);
+    int64_t *c = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)group);
+    for (int r = 0; r < P; ++r) {
+        for (int64_t g0 = 0; g0 < ns[r]; g0 += group) {
+            int64_t g1 = g0 + group < ns[r] ? g0 + group : ns[r];
+            int64_t nt = g1 - g0;
+            for (int64_t k = 0; k < nt; ++k) {
+                int64_t j = S[r].perm[g0 + k];
+                tid[k] = sid[r][j];
+                for (int cc = 0; cc < 3; ++cc) {
+                    xt[3 * k + cc] = xs[r][3 * j + cc];
+                    xf[3 * k + cc] = (float)xs[r][3 * j + cc];
+                    a[3 * k + cc] = 0.0;
+                    c[3 * k + cc] = 0;
+                }
+            }
+            for (int q = 0; q < P; ++q) {
+                int s = q == 0 ? r : (q <= r ? q - 1 : q);  /* own tree, then the others in order */
+                if (ns[s] == 0) continue;
+                bh_walk_sources(&S[s], &W, xs[s], ms[s], sid[s], nt, xf, xt, tid, eps, a, c);
+            }
+            for (int64_t k = 0; k < nt; ++k) {
+                for (int cc = 0; cc < 3; ++cc) acc[3 * tid[k] + cc] = G * a[3 * k + cc];
+                if (cnt)
+                    for (int cc = 0; cc < 3; ++cc) cnt[3 * tid[k] + cc] = c[3 * k + cc];
+                st[2] += c[3 * k];
+                st[3] += c[3 * k + 1];
+            }
+        }
+    }
+    if (stats)
+        for (int q = 0; q < 4; ++q) stats[q] = st[q];
+    free(xf); free(xt); free(tid); free(a); free(c);
+    bh_work_free(&W);
+    for (int s = 0; s < P; ++s) {
+        if (ns[s] > 0) bh_release(&S[s]);
+        free(xs[s]); free(ms[s]); free(sid[s]);
+    }
+    free(xs); free(ms); free(sid); free(ns); free(S);
+    return 0;
+}
+
+/*
+ * The tree over the source bodies (xs, ms) with, per node, its kind in the
+ * LET for a destination whose bodies lie in the float32 box [blo, bhi]
+ * (readings above): 0 not sent, 1 sent alone (accepted by every body in the
+ * box), 2 sent with all its children, 3 a leaf sent with its bodies.  The
+ * nodes are in build order (a parent before its children); *nnodes receives
+ * their number, and when cap >= *nnodes the arrays are filled: kind, level,
+ * prefix (the key bits of the node's cell), child[8] (-1 = none), range[2]
+ * (the node's bodies, positions in key order), lo/hi[3] (float32 cube
+ * corners), and perm[ns] (key order -> source body).  Returns -1 for bad
+ * arguments.
+ */
+int oracle_bh_let(int64_t ns, const double *xs, const double *ms, double theta, int leaf_cap,
+                  const float *blo, const float *bhi, int64_t cap, int64_t *nnodes,
+                  int32_t *kind, int32_t *level, int64_t *prefix, int64_t *child, int64_t *range,
+                  float *lo, float *hi, int64_t *perm)
+{
+    if (leaf_cap < 1 || ns <= 0) return -1;
+    bh_prep S;
+    bh_prepare(&S, ns, xs, ms, theta, leaf_cap);
+    const int64_t nn = S.t.nnodes;
+    *nnodes = nn;
+    if (cap >= nn) {
+        for (int64_t id = 0; id < nn; ++id) kind[id] = 0;
+        kind[0] = -1;  /* sent; classified below (parents come before children) */
+        for (int64_t id = 0; id < nn; ++id) {
+            const bh_node *nd = &S.t.nodes[id];
+            level[id] = nd->level;
+            prefix[id] = nd->prefix;
+            for (int o = 0; o < 8; ++o) child[8 * id + o] = nd->child[o];
+            range[2 * id] = nd->start;
+            range[2 * id + 1] = nd->end;
+            for (int c = 0; c < 3; ++c) {
+                lo[3 * id + c] = nd->lo[c];
+                hi[3 * id + c] = nd->hi[c];
+            }
+            if (kind[id] != -1) continue;
+            float d2 = 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                float aa = nd->lo[c] - bhi[c];
+                float bb = blo[c] - nd->hi[c];
+                float dd = aa > bb ? aa : bb;
+                dd = dd > 0.0f ? dd : 0.0f;
+                float sq = dd * dd;
+                d2 = d2 + sq;
+            }
+            int leaf = 1;
+            for (int o = 0; o < 8; ++o) if (nd->child[o] >= 0) leaf = 0;
+            if (d2 >= S.crit2[nd->level]) {
+                kind[id] = 1;
+            } else if (leaf) {
+                kind[id] = 3;
+            } else {
+                kind[id] = 2;
+                for (int o = 0; o < 8; ++o)
+                    if (nd->child[o] >= 0) kind[nd->child[o]] = -1;
+            }
+        }
+        for (int64_t k = 0; k < ns; ++k) perm[k] = S.perm[k];
+    }
+    bh_release(&S);
+    return 0;
+}
+
+/*
  * Fast multipole method: the O(N) method the paper names as the successor
  * of its tree code (Sec. VI, after Greengard and Rokhlin, ref. [20]).  The
  * paper gives no formulation; the readings here are:

@@ -3,7 +3,8 @@
 Each case plants one mistake in a copy of the oracle's C source (a flipped
 sign, a wrong power of s, a dropped softening term, a swapped index, a wrong
 kick factor, a wrong adjoint term, a wrong expansion term or traversal
-rule of the fast multipole method), builds it, swaps it in for the real
+rule of the fast multipole method, a splitting or sending rule of the
+parallel tree code), builds it, swaps it in for the real
 oracle, and runs the pins of test_oracle_pins.py against it: at least one pin
 must fail.  The real oracle is restored afterwards.  Only the oracle (CPU)
 is mutated.
@@ -17,6 +18,7 @@ import pytest
 import oracle
 import test_oracle_bh as bhpins
 import test_oracle_fmm as fmmpins
+import test_oracle_let as letpins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "nbody_oracle.c")
@@ -74,6 +76,17 @@ MUTANTS = {
                              "z[id][c] = P.box_lo[c] + cell * (double)ic[c];"),
     "fmm inscribed radius": ("T.crit[la][lb] = 0.75 * s * s / (theta * theta);",
                              "T.crit[la][lb] = 0.25 * s * s / (theta * theta);"),
+    "orb shortest axis": ("if (hi[c] - lo[c] > hi[axis] - lo[axis]) axis = c;",
+                          "if (hi[c] - lo[c] < hi[axis] - lo[axis]) axis = c;"),
+    "orb halves regardless of p": ("int64_t k = cnt * (int64_t)p_lo / p;", "int64_t k = cnt / 2;"),
+    "sharded remote trees skipped": ("for (int q = 0; q < P; ++q) {\n                int s = q == 0",
+                                     "for (int q = 0; q < 1; ++q) {\n                int s = q == 0"),
+    "sharded self pair by local index": ("if (sid[j] == tid[k]) continue;",
+                                         "if (j == k) continue;"),
+    "sharded cell not covering its bodies": ("cov += nd->end - nd->start;", "cov += 1;"),
+    "let near box corner": ("float aa = nd->lo[c] - bhi[c];", "float aa = nd->lo[c] - blo[c];"),
+    "let children not sent": ("if (nd->child[o] >= 0) kind[nd->child[o]] = -1;",
+                              "if (nd->child[o] >= 0) kind[nd->child[o]] = 0;"),
 }
 
 PINS = [
@@ -94,6 +107,13 @@ PINS = [
     lambda: fmmpins.test_every_body_meets_every_other_once(0.6),
     fmmpins.test_power_of_two_scaling_is_exact, fmmpins.test_error_falls_with_theta_and_order,
     fmmpins.test_far_cluster_through_expansions_only,
+    lambda: letpins.test_orb_equal_counts_and_bisecting_planes(5, 1000),
+    letpins.test_orb_follows_the_bodies,
+    lambda: letpins.test_one_processor_is_the_tree_code(0.5, 32),
+    lambda: letpins.test_theta_zero_is_the_direct_sum(3),
+    lambda: letpins.test_every_body_is_met_once(0.5, 4),
+    lambda: letpins.test_let_holds_everything_a_remote_body_meets(0.7),
+    letpins.test_let_of_a_far_destination_is_the_root_alone,
 ]
 
 
