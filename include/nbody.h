@@ -372,6 +372,85 @@ nb_status nb_fmm_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const do
 nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
 
 /*
+ * Parallel tree code over P processors (paper Sec. IV-B): orthogonal
+ * recursive bisection (ORB) of space into P equal-count domains, a tree per
+ * processor over its own bodies, and locally essential trees (LET): each
+ * processor sends every other the part of its tree that the other's bodies
+ * need, then computes its bodies' forces as in the sequential code.  These
+ * calls are one processor's share; the collectives between them (sums,
+ * min/max, all-to-all exchanges) belong to the caller's communicator.
+ *
+ * ORB.  A part shared by p processors is cut across the longest side of its
+ * bounding box; the lower part takes floor(p/2) processors and the
+ * k = floor(count floor(p/2) / p) bodies first in (coordinate, body id)
+ * order.  A part is named by its first processor (a "group"); group arrays
+ * are device int32 [n], initially all 0, and after the last cut hold each
+ * body's processor.  ids are device int64 [n], unique over all processors,
+ * in [0, 2^31).  The cut is found without moving bodies by a radix select
+ * on the 96-bit key (order-preserving image of the float64 coordinate, the
+ * 32-bit id), eight bits per round, rounds 0..11 most significant first.
+ *  nb_orb_box: per group g < ngroups (<= NB_ORB_MAX_P), box_out[g] =
+ *    {min xyz, max xyz} of this processor's bodies of g (HOST, float64;
+ *    +inf/-inf when it has none).  Synchronises.
+ *  nb_orb_hist: for the nactive (<= NB_ORB_MAX_P / 2) parts being cut,
+ *    active[r] = the part's group, axis[r] in {0,1,2} its cut axis and
+ *    prefix[2r], prefix[2r+1] the key bits (high 64, low 32) fixed so far:
+ *    hist_out[r][d] (HOST int64) = this processor's bodies of the part whose
+ *    key starts with the first 8 round bits of the prefix and has digit d
+ *    next.  Synchronises.
+ *  nb_orb_cut: bodies of active part r whose key is not below the split
+ *    key (split[2r], split[2r+1]) move to group upper[r] (> active[r]).
+ *  nb_orb_pack: the bodies ordered by rank (stable), into the *_out device
+ *    arrays, and counts_out[r] (HOST) bodies per rank r < P; the send
+ *    buffers of an all-to-all exchange.  Synchronises.
+ *  nb_orb_order: the bodies ordered by id (after an exchange, so that each
+ *    processor's tree and groups do not depend on the exchange's order).
+ * LET.
+ *  nb_let_build: the tree of nb_tree_forces (readings of that call) over
+ *    this processor's n bodies, kept in the context; box_out (HOST, 6
+ *    floats) = the float32 box {min xyz, max xyz} of the bodies, which the
+ *    other processors need for their LETs.  Synchronises.
+ *  nb_let_export: the LET of the local tree for a destination whose bodies
+ *    lie in the float32 box (HOST, 6 floats, from its nb_let_build): the
+ *    root is sent; a sent node distant enough from the box (the walk's
+ *    opening test, so every body inside accepts it) goes alone; otherwise a
+ *    sent leaf goes with its bodies and a sent cell with all its children.
+ *    *size_out receives the LET's size in bytes; with out == NULL only the
+ *    size is computed, otherwise out (device, 16-byte aligned, capacity
+ *    bytes; NB_ENOMEM if too small) receives the LET, a self-contained
+ *    buffer to send as bytes.  Synchronises once.
+ *  nb_let_forces: acc [n][3] (device, the bodies of nb_let_build in their
+ *    order) = G times the walk of the local tree plus the walks of the nlet
+ *    received LETs (lets: HOST array of device pointers, 16-byte aligned, in
+ *    the order to add them), with groups of `group` (32 or 64) bodies and
+ *    the opening angle theta of the exports; counts (optional, device int32
+ *    [n][2]) = cells and bodies met over all trees.  With no LET it is the
+ *    tree code's nb_tree_forces.  nb_tree_stats then reports the summed
+ *    interactions.
+ */
+#define NB_ORB_MAX_P 64
+nb_status nb_orb_box(nb_ctx *ctx, int64_t n, const double *pos, const int32_t *group, int ngroups,
+                     double *box_out);
+nb_status nb_orb_hist(nb_ctx *ctx, int64_t n, const double *pos, const int64_t *id,
+                      const int32_t *group, int nactive, const int32_t *active,
+                      const int32_t *axis, const uint64_t *prefix, int round, int64_t *hist_out);
+nb_status nb_orb_cut(nb_ctx *ctx, int64_t n, const double *pos, const int64_t *id,
+                     int32_t *group, int nactive, const int32_t *active, const int32_t *axis,
+                     const uint64_t *split, const int32_t *upper);
+nb_status nb_orb_pack(nb_ctx *ctx, int64_t n, const int32_t *rank, int P, const double *pos,
+                      const double *vel, const double *mass, const int64_t *id, double *pos_out,
+                      double *vel_out, double *mass_out, int64_t *id_out, int64_t *counts_out);
+nb_status nb_orb_order(nb_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                       const double *mass, const int64_t *id, double *pos_out, double *vel_out,
+                       double *mass_out, int64_t *id_out);
+nb_status nb_let_build(nb_ctx *ctx, int64_t n, const double *pos, const double *mass, int leaf_cap,
+                       float *box_out);
+nb_status nb_let_export(nb_ctx *ctx, double theta, const float *box, void *out, int64_t capacity,
+                        int64_t *size_out);
+nb_status nb_let_forces(nb_ctx *ctx, double G, double eps, double theta, int group, int64_t nlet,
+                        const void *const *lets, double *acc, int32_t *counts);
+
+/*
  * nb_forces_noalloc -- accelerations as nb_forces in the NB_FP32_COMP form
  * (float32 pair terms, Kahan-compensated per-tile sums, float64 output), for
  * callers that cannot allocate device memory: code whose device memory is

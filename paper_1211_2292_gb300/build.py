@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnbody.so")
 
 SOURCES = ["force_f32.cu", "force_f32_b.cu", "force_f32_batched.cu", "force_f64.cu", "force_df.cu",
-           "adjoint.cu", "integrate.cu", "order.cu", "tree.cu", "noalloc.cu", "fmm.cu", "fmm_p2.cu",
+           "adjoint.cu", "integrate.cu", "order.cu", "orb.cu", "tree.cu", "noalloc.cu", "fmm.cu", "fmm_p2.cu",
            "fmm_p3.cu", "fmm_p4.cu", "fmm_p5.cu", "fmm_p6.cu", "nbody_abi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

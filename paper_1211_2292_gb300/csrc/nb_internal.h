@@ -145,6 +145,10 @@ cudaError_t launch_morton_sort(cudaStream_t s, int n, const double *pos, OrderSc
 // sort; sorted keys end in o.keys[0], box_out = {lo_x, lo_y, lo_z, ext}.
 cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScratch &o,
                              int *perm_out, double *box_out, int &kernels);
+// Stable sort of bodies by an integer key below 2^(8 passes) (k32, or k64
+// when k32 is NULL; values below 2^31): perm_out[k] = the k-th body.
+cudaError_t launch_key_sort(cudaStream_t s, int n, const int *k32, const long long *k64,
+                            int passes, OrderScratch &o, int *perm_out, int &kernels);
 // Phi[k], Plo[k] = float32 hi/lo packing of body perm[k] (perm NULL = identity);
 // Phi.w = m, Plo.w = log2(m).
 cudaError_t launch_pack_hilo(cudaStream_t s, int n, const double *pos, const double *mass,
@@ -167,14 +171,17 @@ struct TreeView {
     unsigned long long *stats;  // [4] nodes, leaves, cell and body interactions
 };
 struct TreeWalkParams {
-    TreeView tree;
-    const float4 *P, *Plo;  // bodies in tree order, float32 hi/lo
-    const int *perm;        // tree rank -> body index
-    const double *box;      // {lo_x, lo_y, lo_z, ext}
+    TreeView tree;          // the tree walked (the targets' own, or a received LET)
+    const float4 *P, *Plo;  // target bodies in their own tree's order, float32 hi/lo
+    const int *perm;        // target tree rank -> body index
+    const float4 *sP, *sPlo;  // source bodies the walked tree's leaves index
+    const double *box;      // walked tree's cube {lo_x, lo_y, lo_z, ext}
+    int *queue;             // group queue of the dynamic schedules, zero at launch
     int n;
     int group;              // bodies per walking warp: 32 or 64
     int sched, chunk;       // group schedule: 0 static, 1 dynamic, 2 guided; chunk size
     int num_sms;
+    int accumulate;         // 1: add to acc and counts (vel must be NULL)
     float theta, eps2f;
     double G;
     double *acc, *vel;      // vel != NULL: vel += half_dt * acc
@@ -192,8 +199,55 @@ cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const un
                               const double *box, const double *pos, const double *mass,
                               const int *perm, int leaf_cap, int *err, int &kernels);
 cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps, int &kernels);
-// Where tree.cu keeps each level's node count and first node in TreeView::meta.
-constexpr int TREE_META_COUNT = 0, TREE_META_BASE = 12;
+// Where tree.cu keeps each level's node count and first node, and the walk's
+// group queue, in TreeView::meta.
+constexpr int TREE_META_COUNT = 0, TREE_META_BASE = 12, TREE_META_QUEUE = 25;
+
+// ------------------------------------ locally essential trees (tree.cu)
+// A LET is one contiguous device buffer: a header, then per node the cube
+// corners (.w: child count, first child, as in TreeView), the centre of mass
+// hi/lo pair, the leaf's body range, then the bodies (float32 hi/lo).  Node
+// order is the source tree's (level by level, children of a node
+// consecutive); levels are the source's, so the walk's opening distances
+// come from the header's box.
+struct LetHeader {
+    long long magic, n_nodes, n_bodies, reserved;
+    double box[4];  // the source tree's {lo_x, lo_y, lo_z, ext}
+};
+constexpr long long LET_MAGIC = 0x31305445'4c424e;  // identifies a LET buffer
+struct LetLayout {
+    size_t lo, hi, chi, clo, start, end, P, Plo, total;  // byte offsets; total size
+};
+__host__ __device__ inline size_t let_round16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline LetLayout let_layout(long long nn, long long nb)
+{
+    LetLayout L;
+    L.lo = sizeof(LetHeader);
+    L.hi = L.lo + 16 * (size_t)nn;
+    L.chi = L.hi + 16 * (size_t)nn;
+    L.clo = L.chi + 16 * (size_t)nn;
+    L.start = L.clo + 16 * (size_t)nn;
+    L.end = L.start + let_round16(4 * (size_t)nn);
+    L.P = L.end + let_round16(4 * (size_t)nn);
+    L.Plo = L.P + 16 * (size_t)nb;
+    L.total = L.Plo + 16 * (size_t)nb;
+    return L;
+}
+// Per-node scratch of the LET selection: kind (0 not sent, 1 sent alone,
+// 2 sent with its children, 3 a leaf sent with its bodies), the node's
+// index in the LET and its first body there; totals = {nodes, bodies}.
+struct LetScratch {
+    int *kind, *nidx, *boff, *totals;
+};
+// Kinds and LET indices of the nodes of tree t (built over the bodies whose
+// packed float32 pairs the leaves index) for a destination whose bodies lie
+// in the float32 box [dlo, dhi]; then totals holds {nodes, bodies}.
+cudaError_t launch_let_select(cudaStream_t s, const TreeView &t, const double *box, float theta,
+                              float3 dlo, float3 dhi, const LetScratch &sc, int &kernels);
+// Writes the LET selected by launch_let_select into out (let_layout(totals) bytes).
+cudaError_t launch_let_emit(cudaStream_t s, const TreeView &t, const double *box,
+                            const LetScratch &sc, const float4 *P, const float4 *Plo, void *out,
+                            int &kernels);
 
 // ------------------------------------------------- fast multipole method (fmm.cu)
 // Expansion orders with compiled kernels, and floats per expansion (the
@@ -241,6 +295,39 @@ struct FmmParams {
 // near = false: upward pass, downward levels, near-field work items (the
 // host then reads the meta counters); near = true: the near field.
 cudaError_t launch_fmm(cudaStream_t s, const FmmParams &p, bool near, int &kernels);
+
+// ------------------------------------ orthogonal recursive bisection (orb.cu)
+// Group ids are the first processor of a part; `slot` maps a group id to
+// its row in the per-part tables (-1: the part is not being cut).
+constexpr int ORB_MAX_P = NB_ORB_MAX_P;
+struct OrbTables {
+    int slot[ORB_MAX_P];                 // group id -> active row
+    int axis[ORB_MAX_P / 2];             // per active row: the cut axis
+    int upper[ORB_MAX_P / 2];            // per active row: group id of the upper part
+    unsigned long long key_hi[ORB_MAX_P / 2];  // prefix (hist) or split key (cut), high 64 bits
+    unsigned key_lo[ORB_MAX_P / 2];      // low 32 bits (the body id)
+};
+// box[g][6] (order-preserving images: min xyz, max xyz) of each group's bodies.
+cudaError_t launch_orb_box(cudaStream_t s, int n, const double *pos, const int *group, int ngroups,
+                           unsigned long long *box);
+// hist[row][256]: digit `round` (0..11, most significant first) of the
+// 96-bit key (coordinate image, body id) of the bodies whose key starts
+// with the row's prefix.
+cudaError_t launch_orb_hist(cudaStream_t s, int n, const double *pos, const long long *id,
+                            const int *group, int nactive, const OrbTables &t, int round,
+                            unsigned long long *hist);
+// Bodies of an active part with key >= the row's split key move to `upper`.
+cudaError_t launch_orb_cut(cudaStream_t s, int n, const double *pos, const long long *id,
+                           int *group, const OrbTables &t);
+// out[k] = body perm[k] (any output may be NULL); counts[r] = bodies with rank r.
+cudaError_t launch_gather_bodies(cudaStream_t s, int n, const int *perm, const double *pos,
+                                 const double *vel, const double *mass, const long long *id,
+                                 double *pos_out, double *vel_out, double *mass_out,
+                                 long long *id_out);
+cudaError_t launch_rank_counts(cudaStream_t s, int n, const int *rank, int P,
+                               unsigned long long *counts);
+// Float32 bounding box {min xyz, max xyz} of n packed bodies (their hi parts).
+cudaError_t launch_hi_box(cudaStream_t s, int n, const float4 *P, float *box);
 
 // ------------------------------------------------- O(n) kernels (integrate.cu)
 cudaError_t launch_pack_f32(cudaStream_t s, int n, const double *pos, const double *mass, float4 *P);
@@ -334,6 +421,15 @@ struct nb_ctx {
     nb::FmmView fmm{};
     int fmm_cap = 0;             // nodes the expansion arrays hold
     int fmm_np = 0;              // floats per expansion they hold
+
+    // ORB and LET scratch (allocated on first use)
+    unsigned long long *orb_buf = nullptr;  // boxes [ORB_MAX_P][6], then histograms [ORB_MAX_P/2][256]
+    int *orb_perm = nullptr;                // [n_max] body order of a pack or an id sort
+    nb::LetScratch let{};                   // per tree node (let_cap nodes)
+    int let_cap = 0;
+    float *let_box = nullptr;               // 6 floats out + 6 unsigned of work
+    int *let_queue = nullptr;               // group queue of the LET walks
+    int64_t let_n = 0;                      // bodies of the local tree of nb_let_build
 
     std::map<const void *, int> occ;  // resident CTAs per SM, per kernel
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -556,6 +557,14 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->tree_Plo);
     cudaFree(c->tree_perm);
     cudaFree(c->tree_box);
+    cudaFree(c->orb_buf);
+    cudaFree(c->orb_perm);
+    cudaFree(c->let.kind);
+    cudaFree(c->let.nidx);
+    cudaFree(c->let.boff);
+    cudaFree(c->let.totals);
+    cudaFree(c->let_box);
+    cudaFree(c->let_queue);
     if (c->host_out) cudaFreeHost(c->host_out);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -724,6 +733,23 @@ struct TreeTimer {
     }
 };
 
+// Sort, pack and build the tree over n bodies (kept in the context).
+nb_status tree_build_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos,
+                             const double *mass, int leaf_cap)
+{
+    int k = 0;
+    TreeTimer tm(c, nb::PROF_TREE_BUILD, s);
+    NB_CUDA(c, nb::launch_tree_sort(s, (int)n, pos, c->order, c->tree_perm, c->tree_box, k));
+    c->launches += k;
+    NB_LAUNCHED(c, nb::launch_pack_hilo(s, (int)n, pos, mass, c->tree_perm, c->tree_P,
+                                        c->tree_Plo));
+    NB_CUDA(c, nb::launch_tree_build(s, c->tree, (int)n, c->order.keys[0], c->tree_box, pos, mass,
+                                     c->tree_perm, leaf_cap, c->err, k));
+    c->launches += k;
+    tm.done();
+    return NB_OK;
+}
+
 // Sort, pack, build and walk: acc = G * (tree sum); vel += half_dt * acc when vel.
 nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double *pos,
                               const double *mass, double G, double eps, double theta,
@@ -732,28 +758,22 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
 {
     if (n == 0) return NB_OK;
     int k = 0;
-    {
-        TreeTimer tm(c, nb::PROF_TREE_BUILD, s);
-        NB_CUDA(c, nb::launch_tree_sort(s, (int)n, pos, c->order, c->tree_perm, c->tree_box, k));
-        c->launches += k;
-        NB_LAUNCHED(c, nb::launch_pack_hilo(s, (int)n, pos, mass, c->tree_perm, c->tree_P,
-                                            c->tree_Plo));
-        NB_CUDA(c, nb::launch_tree_build(s, c->tree, (int)n, c->order.keys[0], c->tree_box, pos,
-                                         mass, c->tree_perm, leaf_cap, c->err, k));
-        c->launches += k;
-        tm.done();
-    }
+    NB_TRY(tree_build_enqueue(c, s, n, pos, mass, leaf_cap));
     nb::TreeWalkParams p;
     p.tree = c->tree;
     p.P = c->tree_P;
     p.Plo = c->tree_Plo;
     p.perm = c->tree_perm;
+    p.sP = c->tree_P;
+    p.sPlo = c->tree_Plo;
     p.box = c->tree_box;
+    p.queue = c->tree.meta + nb::TREE_META_QUEUE;
     p.n = (int)n;
     p.group = group;
     p.sched = c->tree_sched;
     p.chunk = c->tree_chunk;
     p.num_sms = c->num_sms;
+    p.accumulate = 0;
     p.theta = (float)theta;
     p.eps2f = (float)(eps * eps);
     p.G = G;
@@ -1646,6 +1666,367 @@ nb_status nb_device_info(nb_ctx *c, int64_t n, int *num_sms, int *ctas_per_sm)
     pick(c, nb::KIND_FORCE, n, v, s);
     if (num_sms) *num_sms = c->num_sms;
     if (ctas_per_sm) *ctas_per_sm = occupancy(c, kernel_for(nb::KIND_FORCE, c->prec, v, false));
+    return NB_OK;
+}
+
+// ----------------------------------------------- ORB and locally essential trees
+namespace {
+
+nb_status ensure_orb(nb_ctx *c)
+{
+    nb_status st = NB_OK;
+    NB_TRY(ensure_order(c));
+    if (!c->orb_buf)
+        c->orb_buf = dev_alloc<unsigned long long>(
+            c, (size_t)nb::ORB_MAX_P * 6 + (size_t)nb::ORB_MAX_P / 2 * 256 + nb::ORB_MAX_P, st);
+    if (st == NB_OK && !c->orb_perm)
+        c->orb_perm = dev_alloc<int>(c, (size_t)std::max<int64_t>(c->n_max, 1), st);
+    return st;
+}
+
+nb_status check_orb_tables(nb_ctx *c, int nactive, const int32_t *active, const int32_t *axis,
+                           const uint64_t *key, const int32_t *upper, nb::OrbTables &t)
+{
+    if (nactive < 0 || nactive > nb::ORB_MAX_P / 2)
+        return failf(c, NB_EINVAL, "nactive = %d outside [0, %d]", nactive, nb::ORB_MAX_P / 2);
+    if (nactive > 0 && (!active || !axis || !key))
+        return failf(c, NB_EINVAL, "active, axis or key table is NULL");
+    for (int g = 0; g < nb::ORB_MAX_P; ++g) t.slot[g] = -1;
+    for (int r = 0; r < nactive; ++r) {
+        if (active[r] < 0 || active[r] >= nb::ORB_MAX_P || t.slot[active[r]] >= 0)
+            return failf(c, NB_EINVAL, "active[%d] = %d is not a distinct group below %d", r,
+                         active[r], nb::ORB_MAX_P);
+        if (axis[r] < 0 || axis[r] > 2) return failf(c, NB_EINVAL, "axis[%d] = %d", r, axis[r]);
+        if (upper && (upper[r] <= active[r] || upper[r] >= nb::ORB_MAX_P))
+            return failf(c, NB_EINVAL, "upper[%d] = %d must lie above %d", r, upper[r], active[r]);
+        t.slot[active[r]] = r;
+        t.axis[r] = axis[r];
+        t.upper[r] = upper ? upper[r] : 0;
+        t.key_hi[r] = key[2 * r];
+        t.key_lo[r] = (unsigned)key[2 * r + 1];
+    }
+    return NB_OK;
+}
+
+// Scratch of the LET selection for the tree's node capacity.
+nb_status ensure_let(nb_ctx *c)
+{
+    nb_status st = NB_OK;
+    if (!c->let_box) c->let_box = dev_alloc<float>(c, 12, st);
+    if (st == NB_OK && !c->let_queue) c->let_queue = dev_alloc<int>(c, 1, st);
+    if (st == NB_OK && !c->let.totals) c->let.totals = dev_alloc<int>(c, 2, st);
+    if (st != NB_OK) return st;
+    if (c->let_cap < c->tree.cap) {
+        cudaFree(c->let.kind);
+        cudaFree(c->let.nidx);
+        cudaFree(c->let.boff);
+        c->let.kind = c->let.nidx = c->let.boff = nullptr;
+        c->let_cap = 0;
+        const size_t m = (size_t)c->tree.cap;
+        c->let.kind = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) c->let.nidx = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) c->let.boff = dev_alloc<int>(c, m, st);
+        if (st != NB_OK) return st;
+        c->let_cap = c->tree.cap;
+    }
+    return NB_OK;
+}
+
+// One walk over tree view t with sources (sP, sPlo) and box, onto the
+// context's local bodies.
+nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float4 *sP,
+                   const float4 *sPlo, const double *box, double G, double eps, double theta,
+                   int group, double *acc, int *counts, int accumulate)
+{
+    NB_CUDA(c, cudaMemsetAsync(c->let_queue, 0, sizeof(int), s));
+    nb::TreeWalkParams p;
+    p.tree = t;
+    p.P = c->tree_P;
+    p.Plo = c->tree_Plo;
+    p.perm = c->tree_perm;
+    p.sP = sP;
+    p.sPlo = sPlo;
+    p.box = box;
+    p.queue = c->let_queue;
+    p.n = (int)c->let_n;
+    p.group = group;
+    p.sched = c->tree_sched;
+    p.chunk = c->tree_chunk;
+    p.num_sms = c->num_sms;
+    p.accumulate = accumulate;
+    p.theta = (float)theta;
+    p.eps2f = (float)(eps * eps);
+    p.G = G;
+    p.acc = acc;
+    p.vel = nullptr;
+    p.half_dt = 0.0;
+    p.counts = counts;
+    p.err = c->err;
+    int k = 0;
+    TreeTimer tm(c, nb::PROF_TREE_WALK, s);
+    NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
+    c->launches += k;
+    tm.done();
+    return NB_OK;
+}
+
+}  // namespace
+
+nb_status nb_orb_box(nb_ctx *c, int64_t n, const double *pos, const int32_t *group, int ngroups,
+                     double *box_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    if (ngroups < 1 || ngroups > nb::ORB_MAX_P)
+        return failf(c, NB_EINVAL, "ngroups = %d outside [1, %d]", ngroups, nb::ORB_MAX_P);
+    if (!box_out) return failf(c, NB_EINVAL, "box_out is NULL");
+    NB_TRY(check_dev(c, pos, (size_t)n * 3 * sizeof(double), "pos"));
+    NB_TRY(check_dev(c, group, (size_t)n * sizeof(int32_t), "group"));
+    NB_TRY(ensure_orb(c));
+    cudaStream_t s = c->stream;
+    NB_LAUNCHED(c, nb::launch_orb_box(s, (int)n, pos, group, ngroups, c->orb_buf));
+    std::vector<unsigned long long> h((size_t)ngroups * 6);
+    NB_CUDA(c, cudaMemcpyAsync(h.data(), c->orb_buf, h.size() * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    for (size_t q = 0; q < h.size(); ++q) {
+        const unsigned long long k = h[q];
+        const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+        double v;
+        std::memcpy(&v, &b, sizeof v);
+        const bool empty = (q % 6 < 3) ? k == ~0ull : k == 0ull;
+        box_out[q] = empty ? ((q % 6 < 3) ? INFINITY : -INFINITY) : v;
+    }
+    return NB_OK;
+}
+
+nb_status nb_orb_hist(nb_ctx *c, int64_t n, const double *pos, const int64_t *id,
+                      const int32_t *group, int nactive, const int32_t *active, const int32_t *axis,
+                      const uint64_t *prefix, int round, int64_t *hist_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    if (round < 0 || round > 11) return failf(c, NB_EINVAL, "round = %d outside [0, 11]", round);
+    if (!hist_out && nactive > 0) return failf(c, NB_EINVAL, "hist_out is NULL");
+    nb::OrbTables t;
+    NB_TRY(check_orb_tables(c, nactive, active, axis, prefix, nullptr, t));
+    NB_TRY(check_dev(c, pos, (size_t)n * 3 * sizeof(double), "pos"));
+    NB_TRY(check_dev(c, id, (size_t)n * sizeof(int64_t), "id"));
+    NB_TRY(check_dev(c, group, (size_t)n * sizeof(int32_t), "group"));
+    NB_TRY(ensure_orb(c));
+    if (nactive == 0) return NB_OK;
+    cudaStream_t s = c->stream;
+    unsigned long long *hist = c->orb_buf + (size_t)nb::ORB_MAX_P * 6;
+    NB_LAUNCHED(c, nb::launch_orb_hist(s, (int)n, pos, (const long long *)id, group, nactive, t,
+                                       round, hist));
+    NB_CUDA(c, cudaMemcpyAsync(hist_out, hist, (size_t)nactive * 256 * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    return NB_OK;
+}
+
+nb_status nb_orb_cut(nb_ctx *c, int64_t n, const double *pos, const int64_t *id, int32_t *group,
+                     int nactive, const int32_t *active, const int32_t *axis,
+                     const uint64_t *split, const int32_t *upper)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    if (nactive > 0 && !upper) return failf(c, NB_EINVAL, "upper is NULL");
+    nb::OrbTables t;
+    NB_TRY(check_orb_tables(c, nactive, active, axis, split, upper, t));
+    NB_TRY(check_dev(c, pos, (size_t)n * 3 * sizeof(double), "pos"));
+    NB_TRY(check_dev(c, id, (size_t)n * sizeof(int64_t), "id"));
+    NB_TRY(check_dev(c, group, (size_t)n * sizeof(int32_t), "group"));
+    if (nactive == 0 || n == 0) return NB_OK;
+    NB_LAUNCHED(c, nb::launch_orb_cut(c->stream, (int)n, pos, (const long long *)id, group, t));
+    return NB_OK;
+}
+
+nb_status nb_orb_pack(nb_ctx *c, int64_t n, const int32_t *rank, int P, const double *pos,
+                      const double *vel, const double *mass, const int64_t *id, double *pos_out,
+                      double *vel_out, double *mass_out, int64_t *id_out, int64_t *counts_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    if (P < 1 || P > nb::ORB_MAX_P) return failf(c, NB_EINVAL, "P = %d outside [1, %d]", P, nb::ORB_MAX_P);
+    if (!counts_out) return failf(c, NB_EINVAL, "counts_out is NULL");
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, rank, (size_t)n * sizeof(int32_t), "rank"));
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, id, (size_t)n * sizeof(int64_t), "id"));
+    NB_TRY(check_dev(c, pos_out, v3, "pos_out"));
+    NB_TRY(check_dev(c, vel_out, v3, "vel_out"));
+    NB_TRY(check_dev(c, mass_out, v1, "mass_out"));
+    NB_TRY(check_dev(c, id_out, (size_t)n * sizeof(int64_t), "id_out"));
+    NB_TRY(ensure_orb(c));
+    cudaStream_t s = c->stream;
+    unsigned long long *cnt = c->orb_buf + (size_t)nb::ORB_MAX_P * 6 + (size_t)nb::ORB_MAX_P / 2 * 256;
+    NB_LAUNCHED(c, nb::launch_rank_counts(s, (int)n, rank, P, cnt));
+    if (n > 0) {
+        int k = 0;
+        NB_CUDA(c, nb::launch_key_sort(s, (int)n, rank, nullptr, 1, c->order, c->orb_perm, k));
+        c->launches += k;
+        NB_LAUNCHED(c, nb::launch_gather_bodies(s, (int)n, c->orb_perm, pos, vel, mass,
+                                                (const long long *)id, pos_out, vel_out, mass_out,
+                                                (long long *)id_out));
+    }
+    NB_CUDA(c, cudaMemcpyAsync(counts_out, cnt, (size_t)P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    int64_t tot = 0;
+    for (int r = 0; r < P; ++r) tot += counts_out[r];
+    if (tot != n) return failf(c, NB_EINVAL, "rank values outside [0, %d)", P);
+    return NB_OK;
+}
+
+nb_status nb_orb_order(nb_ctx *c, int64_t n, const double *pos, const double *vel,
+                       const double *mass, const int64_t *id, double *pos_out, double *vel_out,
+                       double *mass_out, int64_t *id_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    const size_t v3 = (size_t)n * 3 * sizeof(double), v1 = (size_t)n * sizeof(double);
+    NB_TRY(check_dev(c, pos, v3, "pos"));
+    NB_TRY(check_dev(c, vel, v3, "vel"));
+    NB_TRY(check_dev(c, mass, v1, "mass"));
+    NB_TRY(check_dev(c, id, (size_t)n * sizeof(int64_t), "id"));
+    NB_TRY(check_dev(c, pos_out, v3, "pos_out"));
+    NB_TRY(check_dev(c, vel_out, v3, "vel_out"));
+    NB_TRY(check_dev(c, mass_out, v1, "mass_out"));
+    NB_TRY(check_dev(c, id_out, (size_t)n * sizeof(int64_t), "id_out"));
+    if (n == 0) return NB_OK;
+    NB_TRY(ensure_orb(c));
+    cudaStream_t s = c->stream;
+    int k = 0;
+    NB_CUDA(c, nb::launch_key_sort(s, (int)n, nullptr, (const long long *)id, 4, c->order,
+                                   c->orb_perm, k));
+    c->launches += k;
+    NB_LAUNCHED(c, nb::launch_gather_bodies(s, (int)n, c->orb_perm, pos, vel, mass,
+                                            (const long long *)id, pos_out, vel_out, mass_out,
+                                            (long long *)id_out));
+    return NB_OK;
+}
+
+nb_status nb_let_build(nb_ctx *c, int64_t n, const double *pos, const double *mass, int leaf_cap,
+                       float *box_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_n(c, n));
+    if (leaf_cap < 1 || leaf_cap > NB_TREE_MAX_LEAF)
+        return failf(c, NB_EINVAL, "leaf_cap = %d outside [1, %d]", leaf_cap, NB_TREE_MAX_LEAF);
+    if (!box_out) return failf(c, NB_EINVAL, "box_out is NULL");
+    NB_TRY(check_dev(c, pos, (size_t)n * 3 * sizeof(double), "pos"));
+    NB_TRY(check_dev(c, mass, (size_t)n * sizeof(double), "mass"));
+    c->let_n = 0;
+    if (n == 0) {
+        for (int q = 0; q < 6; ++q) box_out[q] = q < 3 ? INFINITY : -INFINITY;
+        return NB_OK;
+    }
+    NB_TRY(ensure_tree(c, leaf_cap));
+    NB_TRY(ensure_let(c));
+    cudaStream_t s = c->stream;
+    NB_TRY(tree_build_enqueue(c, s, n, pos, mass, leaf_cap));
+    NB_LAUNCHED(c, nb::launch_hi_box(s, (int)n, c->tree_P, c->let_box));
+    NB_CUDA(c, cudaMemcpyAsync(box_out, c->let_box, 6 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    c->let_n = n;
+    return NB_OK;
+}
+
+nb_status nb_let_export(nb_ctx *c, double theta, const float *box, void *out, int64_t capacity,
+                        int64_t *size_out)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    if (!box || !size_out) return failf(c, NB_EINVAL, "box or size_out is NULL");
+    if (!std::isfinite(theta) || theta < 0)
+        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
+    for (int q = 0; q < 6; ++q)
+        if (std::isnan(box[q])) return failf(c, NB_EINVAL, "box[%d] is NaN", q);
+    if (c->let_n == 0) return failf(c, NB_EINVAL, "no local tree: call nb_let_build first");
+    NB_TRY(ensure_let(c));
+    cudaStream_t s = c->stream;
+    int k = 0;
+    NB_CUDA(c, nb::launch_let_select(s, c->tree, c->tree_box, (float)theta,
+                                     make_float3(box[0], box[1], box[2]),
+                                     make_float3(box[3], box[4], box[5]), c->let, k));
+    c->launches += k;
+    int tot[2] = {0, 0};
+    NB_CUDA(c, cudaMemcpyAsync(tot, c->let.totals, sizeof tot, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    const nb::LetLayout lay = nb::let_layout(tot[0], tot[1]);
+    *size_out = (int64_t)lay.total;
+    if (!out) return NB_OK;  // size query
+    if (capacity < (int64_t)lay.total)
+        return failf(c, NB_ENOMEM, "LET of %zu bytes exceeds the buffer's %lld", lay.total,
+                     (long long)capacity);
+    if ((uintptr_t)out % 16) return failf(c, NB_EINVAL, "out is not 16-byte aligned");
+    NB_TRY(check_dev(c, out, lay.total, "out"));
+    NB_CUDA(c, nb::launch_let_emit(s, c->tree, c->tree_box, c->let, c->tree_P, c->tree_Plo, out, k));
+    c->launches += k;
+    return NB_OK;
+}
+
+nb_status nb_let_forces(nb_ctx *c, double G, double eps, double theta, int group, int64_t nlet,
+                        const void *const *lets, double *acc, int32_t *counts)
+{
+    if (!c) return NB_EINVAL;
+    DeviceGuard guard(c->device);
+    NB_TRY(check_scalars(c, G, eps));
+    if (!std::isfinite(theta) || theta < 0)
+        return failf(c, NB_EINVAL, "theta must be finite and >= 0");
+    if (group != 32 && group != 64) return failf(c, NB_EINVAL, "group = %d is not 32 or 64", group);
+    if (nlet < 0 || (nlet > 0 && !lets)) return failf(c, NB_EINVAL, "bad nlet or lets");
+    const int64_t n = c->let_n;
+    if (n == 0) return failf(c, NB_EINVAL, "no local tree: call nb_let_build first");
+    NB_TRY(check_dev(c, acc, (size_t)n * 3 * sizeof(double), "acc"));
+    if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 2 * sizeof(int32_t), "counts"));
+    // every received tree's header, checked before anything is launched
+    std::vector<nb::LetHeader> hdr((size_t)nlet);
+    cudaStream_t s = c->stream;
+    for (int64_t q = 0; q < nlet; ++q) {
+        if ((uintptr_t)lets[q] % 16) return failf(c, NB_EINVAL, "lets[%lld] is not 16-byte aligned", (long long)q);
+        NB_TRY(check_dev(c, lets[q], sizeof(nb::LetHeader), "lets[q]"));
+        NB_CUDA(c, cudaMemcpyAsync(&hdr[(size_t)q], lets[q], sizeof(nb::LetHeader),
+                                   cudaMemcpyDeviceToHost, s));
+    }
+    NB_CUDA(c, cudaStreamSynchronize(s));
+    for (int64_t q = 0; q < nlet; ++q) {
+        const nb::LetHeader &h = hdr[(size_t)q];
+        if (h.magic != nb::LET_MAGIC || h.n_nodes < 1 || h.n_bodies < 0 ||
+            h.n_nodes > 0x7fffffffLL || h.n_bodies > 0x7fffffffLL)
+            return failf(c, NB_EINVAL, "lets[%lld] does not hold a LET", (long long)q);
+        NB_TRY(check_dev(c, lets[q], nb::let_layout(h.n_nodes, h.n_bodies).total, "lets[q]"));
+    }
+    NB_TRY(ensure_let(c));
+    NB_CUDA(c, cudaMemsetAsync(c->tree.stats + 2, 0, 2 * sizeof(unsigned long long), s));
+    // the local tree first, then the received ones in order
+    NB_TRY(let_walk(c, s, c->tree, c->tree_P, c->tree_Plo, c->tree_box, G, eps, theta, group, acc,
+                    counts, 0));
+    for (int64_t q = 0; q < nlet; ++q) {
+        const nb::LetHeader &h = hdr[(size_t)q];
+        const nb::LetLayout lay = nb::let_layout(h.n_nodes, h.n_bodies);
+        const unsigned char *b = static_cast<const unsigned char *>(lets[q]);
+        nb::TreeView t{};
+        t.cap = (int)h.n_nodes;
+        t.box_lo = (float4 *)(b + lay.lo);
+        t.box_hi = (float4 *)(b + lay.hi);
+        t.chi = (float4 *)(b + lay.chi);
+        t.clo = (float4 *)(b + lay.clo);
+        t.start = (int *)(b + lay.start);
+        t.end = (int *)(b + lay.end);
+        t.stats = c->tree.stats;
+        NB_TRY(let_walk(c, s, t, (const float4 *)(b + lay.P), (const float4 *)(b + lay.Plo),
+                        (const double *)(b + offsetof(nb::LetHeader, box)), G, eps, theta, group,
+                        acc, counts, 1));
+    }
     return NB_OK;
 }
 

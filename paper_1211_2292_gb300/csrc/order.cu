@@ -266,6 +266,19 @@ __global__ void __launch_bounds__(OTPB) radix_scatter_kernel(int n,
     }
 }
 
+// Keys of a plain integer sort: keys[i] = k32[i] or k64[i] (values below
+// 2^31), vals[i] = i.
+__global__ void __launch_bounds__(OTPB) key_init_kernel(int n, const int *__restrict__ k32,
+                                                         const long long *__restrict__ k64,
+                                                         unsigned *__restrict__ keys,
+                                                         int *__restrict__ vals)
+{
+    for (int i = blockIdx.x * OTPB + threadIdx.x; i < n; i += gridDim.x * OTPB) {
+        keys[i] = k32 ? (unsigned)k32[i] : (unsigned)k64[i];
+        vals[i] = i;
+    }
+}
+
 // Pack body perm[k] at slot k as float32 hi/lo pairs.
 __global__ void __launch_bounds__(OTPB) pack_hilo_kernel(int n, const double *__restrict__ pos,
                                                           const double *__restrict__ mass,
@@ -345,6 +358,29 @@ cudaError_t launch_tree_sort(cudaStream_t s, int n, const double *pos, OrderScra
         radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
         launch_radix_scan(s, o.hist, 256 * nchunks);
         int *vout = pass == 3 ? perm_out : o.vals[cur ^ 1];
+        radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
+                                                     vout, shift, nchunks, o.hist);
+        kernels += 4;
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_sort(cudaStream_t s, int n, const int *k32, const long long *k64,
+                            int passes, OrderScratch &o, int *perm_out, int &kernels)
+{
+    kernels = 0;
+    if (n <= 0) return cudaSuccess;
+    key_init_kernel<<<grid_for(n), OTPB, 0, s>>>(n, k32, k64, o.keys[0], o.vals[0]);
+    ++kernels;
+    const int nchunks = sort_chunks(n);
+    const int blocks = (nchunks + OTPB / 32 - 1) / (OTPB / 32);
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        radix_hist_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], shift, nchunks, o.hist);
+        launch_radix_scan(s, o.hist, 256 * nchunks);
+        int *vout = pass == passes - 1 ? perm_out : o.vals[cur ^ 1];
         radix_scatter_kernel<<<blocks, OTPB, 0, s>>>(n, o.keys[cur], o.vals[cur], o.keys[cur ^ 1],
                                                      vout, shift, nchunks, o.hist);
         kernels += 4;

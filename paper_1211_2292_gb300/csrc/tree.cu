@@ -52,6 +52,8 @@ constexpr int TTPB = 256;
 constexpr int WALK_WARPS = NB_WALK_WARPS;
 
 enum { META_COUNT = 0, META_BASE = 12, META_OVERFLOW = 24, META_QUEUE = 25, META_INTS = 32 };
+static_assert(META_COUNT == TREE_META_COUNT && META_BASE == TREE_META_BASE &&
+                  META_QUEUE == TREE_META_QUEUE, "meta layout shared with nb_internal.h");
 
 inline int grid_cap(int64_t work)
 {
@@ -639,7 +641,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
                 const int body = __shfl_sync(FULL, ls, j & 31) + (pos - __shfl_sync(FULL, lexc, j & 31));
                 const int kk = min(32, T - c0);
                 if (lane < kk) {
-                    const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
+                    const float4 bh = __ldg(p.sP + body), bl = __ldg(p.sPlo + body);
                     list_put<BPL>(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
                                   rel(bh.z, bl.z, cz), bh.w);
                 }
@@ -662,18 +664,28 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         const double gy = p.G * ((double)sy[b] - (double)qy[b]);
         const double gz = p.G * ((double)sz[b] - (double)qz[b]);
         double *a = p.acc + 3 * (size_t)i;
-        a[0] = gx;
-        a[1] = gy;
-        a[2] = gz;
-        if (p.vel) {
-            double *v = p.vel + 3 * (size_t)i;
-            v[0] += p.half_dt * gx;
-            v[1] += p.half_dt * gy;
-            v[2] += p.half_dt * gz;
-        }
-        if (p.counts) {
-            p.counts[2 * (size_t)i] = nc;
-            p.counts[2 * (size_t)i + 1] = nb;
+        if (p.accumulate) {  // a further tree's share (a received LET)
+            a[0] += gx;
+            a[1] += gy;
+            a[2] += gz;
+            if (p.counts) {
+                p.counts[2 * (size_t)i] += nc;
+                p.counts[2 * (size_t)i + 1] += nb;
+            }
+        } else {
+            a[0] = gx;
+            a[1] = gy;
+            a[2] = gz;
+            if (p.vel) {
+                double *v = p.vel + 3 * (size_t)i;
+                v[0] += p.half_dt * gx;
+                v[1] += p.half_dt * gy;
+                v[2] += p.half_dt * gz;
+            }
+            if (p.counts) {
+                p.counts[2 * (size_t)i] = nc;
+                p.counts[2 * (size_t)i + 1] = nb;
+            }
         }
         if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
     }
@@ -704,7 +716,7 @@ __global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB
     }
     const int ngroups = (p.n + 32 * BPL - 1) / (32 * BPL);
     const int nwarps = gridDim.x * WALK_WARPS;
-    int *queue = p.tree.meta + META_QUEUE;
+    int *queue = p.queue;
     int seen = 0;
     for (;;) {
         int c = p.chunk;
@@ -716,6 +728,105 @@ __global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB
         seen = g0 + c;
         const int g1 = min(g0 + c, ngroups);
         for (int g = g0; g < g1; ++g) walk_group<ZEPS, BPL>(p, sh, g);
+    }
+}
+
+// ---------------------------------------------- locally essential trees
+// The LET of this tree for a destination whose bodies lie in the float32
+// box [dlo, dhi] (paper Sec. IV-B, the influence-ring test from the
+// destination's side): the root is sent; a sent node whose cube is distant
+// enough from the box (cube_box_dist2, the walk's own first-stage test, so
+// every body inside the box accepts it) is sent alone; otherwise a sent
+// leaf goes with its bodies and a sent cell with all its children.
+// Level by level, parents first.
+__global__ void __launch_bounds__(TTPB) let_kind_kernel(TreeView t, const double *__restrict__ box,
+                                                        float theta, float3 dlo, float3 dhi, int L,
+                                                        int *__restrict__ kind)
+{
+    const int cnt = t.meta[META_COUNT + L], base = t.meta[META_BASE + L];
+    const float crit2 = open_dist2(box[3], L, theta);
+    const float mn[3] = {dlo.x, dlo.y, dlo.z}, mx[3] = {dhi.x, dhi.y, dhi.z};
+    for (int q = blockIdx.x * TTPB + threadIdx.x; q < cnt; q += gridDim.x * TTPB) {
+        const int u = base + q;
+        int k = 0;
+        if (L == 0 || kind[t.parent[u]] == 2) {
+            if (cube_box_dist2(t.box_lo[u], t.box_hi[u], mn, mx) >= crit2)
+                k = 1;
+            else
+                k = t.nchild[u] == 0 ? 3 : 2;
+        }
+        kind[u] = k;
+    }
+}
+
+// One block: each sent node's index in the LET and each sent leaf's first
+// body there (exclusive scans in node order); totals = {nodes, bodies}.
+__global__ void __launch_bounds__(1024) let_scan_kernel(TreeView t, LetScratch sc)
+{
+    __shared__ int tile[BSCAN_TILE + BSCAN_TILE / 32];
+    __shared__ int wsum[32];
+    const int total = t.meta[META_BASE + 10] + t.meta[META_COUNT + 10];
+    // flags and body counts first go into the output arrays, scanned in place
+    for (int u = threadIdx.x; u < total; u += 1024) {
+        const int k = sc.kind[u];
+        sc.nidx[u] = k != 0;
+        sc.boff[u] = k == 3 ? t.end[u] - t.start[u] : 0;
+    }
+    __syncthreads();
+    const int nn = block_scan_exclusive<int>(sc.nidx, sc.nidx, total, tile, wsum);
+    const int nb = block_scan_exclusive<int>(sc.boff, sc.boff, total, tile, wsum);
+    if (threadIdx.x == 0) {
+        sc.totals[0] = nn;
+        sc.totals[1] = nb;
+    }
+}
+
+__global__ void __launch_bounds__(TTPB) let_emit_kernel(TreeView t, const double *__restrict__ box,
+                                                        LetScratch sc, const float4 *__restrict__ P,
+                                                        const float4 *__restrict__ Plo,
+                                                        unsigned char *__restrict__ out)
+{
+    const int total = t.meta[META_BASE + 10] + t.meta[META_COUNT + 10];
+    const long long nn = sc.totals[0], nb = sc.totals[1];
+    const LetLayout lay = let_layout(nn, nb);
+    float4 *lo = reinterpret_cast<float4 *>(out + lay.lo);
+    float4 *hi = reinterpret_cast<float4 *>(out + lay.hi);
+    float4 *chi = reinterpret_cast<float4 *>(out + lay.chi);
+    float4 *clo = reinterpret_cast<float4 *>(out + lay.clo);
+    int *st = reinterpret_cast<int *>(out + lay.start);
+    int *en = reinterpret_cast<int *>(out + lay.end);
+    float4 *bP = reinterpret_cast<float4 *>(out + lay.P);
+    float4 *bPlo = reinterpret_cast<float4 *>(out + lay.Plo);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        LetHeader h;
+        h.magic = LET_MAGIC;
+        h.n_nodes = nn;
+        h.n_bodies = nb;
+        h.reserved = 0;
+        for (int c = 0; c < 4; ++c) h.box[c] = box[c];
+        *reinterpret_cast<LetHeader *>(out) = h;
+    }
+    for (int u = blockIdx.x * TTPB + threadIdx.x; u < total; u += gridDim.x * TTPB) {
+        const int k = sc.kind[u];
+        if (k == 0) continue;
+        const int v = sc.nidx[u];
+        float4 a = t.box_lo[u], b = t.box_hi[u];
+        // children are kept only for an opened cell; they are consecutive
+        // in both trees, so the first one's LET index locates them all
+        a.w = __int_as_float(k == 2 ? t.nchild[u] : 0);
+        b.w = __int_as_float(k == 2 ? sc.nidx[t.first[u]] : -1);
+        lo[v] = a;
+        hi[v] = b;
+        chi[v] = t.chi[u];
+        clo[v] = t.clo[u];
+        const int b0 = sc.boff[u];
+        const int len = k == 3 ? t.end[u] - t.start[u] : 0;
+        st[v] = b0;
+        en[v] = b0 + len;
+        for (int q = 0; q < len; ++q) {
+            bP[b0 + q] = P[t.start[u] + q];
+            bPlo[b0 + q] = Plo[t.start[u] + q];
+        }
     }
 }
 
@@ -762,6 +873,30 @@ cudaError_t launch_tree_build(cudaStream_t s, const TreeView &t, int n, const un
     tree_moments_kernel<<<grid_cap(t.cap), TTPB, 0, s>>>(t, pos, mass, perm);
     tree_flag_kernel<<<1, 32, 0, s>>>(t, err);
     kernels += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_let_select(cudaStream_t s, const TreeView &t, const double *box, float theta,
+                              float3 dlo, float3 dhi, const LetScratch &sc, int &kernels)
+{
+    kernels = 0;
+    const int g = grid_cap(t.cap);
+    for (int L = 0; L < LEVELS; ++L) {
+        let_kind_kernel<<<g, TTPB, 0, s>>>(t, box, theta, dlo, dhi, L, sc.kind);
+        ++kernels;
+    }
+    let_scan_kernel<<<1, 1024, 0, s>>>(t, sc);
+    ++kernels;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_let_emit(cudaStream_t s, const TreeView &t, const double *box,
+                            const LetScratch &sc, const float4 *P, const float4 *Plo, void *out,
+                            int &kernels)
+{
+    let_emit_kernel<<<grid_cap(t.cap), TTPB, 0, s>>>(t, box, sc, P, Plo,
+                                                     static_cast<unsigned char *>(out));
+    kernels = 1;
     return cudaGetLastError();
 }
 

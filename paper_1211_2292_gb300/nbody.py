@@ -76,6 +76,22 @@ SIGNATURES = {
     "nb_fmm_step": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
                              _c_int, _c_dbl, _c_i64, _c_vp, _c_uint]),
     "nb_forces_noalloc": (_c_int, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_vp, _c_vp]),
+    "nb_orb_box": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_int, ctypes.POINTER(_c_dbl)]),
+    "nb_orb_hist": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_int,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_uint64), _c_int, ctypes.POINTER(_c_i64)]),
+    "nb_orb_cut": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_int,
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)]),
+    "nb_orb_pack": (_c_int, [_c_vp, _c_i64, _c_vp, _c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                             _c_vp, _c_vp, _c_vp, ctypes.POINTER(_c_i64)]),
+    "nb_orb_order": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                              _c_vp]),
+    "nb_let_build": (_c_int, [_c_vp, _c_i64, _c_vp, _c_vp, _c_int, ctypes.POINTER(ctypes.c_float)]),
+    "nb_let_export": (_c_int, [_c_vp, _c_dbl, ctypes.POINTER(ctypes.c_float), _c_vp, _c_i64,
+                               ctypes.POINTER(_c_i64)]),
+    "nb_let_forces": (_c_int, [_c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_i64,
+                               ctypes.POINTER(_c_vp), _c_vp, _c_vp]),
     "nb_choose_split": (_c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_i64]),
     "nb_plan_batch_host": (_c_i64, [_c_i64, ctypes.POINTER(_c_i64), _c_int, _c_int, _c_int,
                                     _c_i64, ctypes.POINTER(ctypes.c_int32), _c_i64]),
@@ -139,6 +155,20 @@ def _ptr_i32(t, name, numel):
             and t.is_contiguous() and t.numel() >= numel):
         raise ValueError(f"{name} must be a contiguous int32 CUDA tensor of {numel} elements")
     return t.data_ptr() if t.numel() else None
+
+
+def _ptr_typed(t, name, dtype, numel):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+            and t.is_contiguous() and t.numel() >= numel):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor of {numel} elements")
+    return t.data_ptr() if t.numel() else None
+
+
+def _host_array(ctype, values):
+    vals = [int(v) for v in values]
+    return (ctype * max(len(vals), 1))(*vals)
 
 
 def _check(ctx, func, status):
@@ -379,6 +409,107 @@ class NBody:
         out = (ctypes.c_int64 * 4)()
         self._call("nb_tree_stats", out)
         return dict(zip(("nodes", "leaves", "cell_interactions", "body_interactions"), out))
+
+    # ------------------------------------- parallel tree code (ORB, LET)
+    def orb_box(self, pos, group, ngroups):
+        """Per group g < ngroups: [min xyz, max xyz] of this context's bodies
+        of g (numpy float64 (ngroups, 6); +inf/-inf when none)."""
+        import numpy as np
+        import torch
+        n = group.shape[0]
+        out = np.zeros((ngroups, 6))
+        self._call("nb_orb_box", n, _ptr(pos, "pos", 3 * n), _ptr_typed(group, "group", torch.int32, n),
+                   int(ngroups), out.ctypes.data_as(ctypes.POINTER(_c_dbl)))
+        return out
+
+    def orb_hist(self, pos, ids, group, active, axis, prefix, rnd):
+        """Digit histograms (numpy int64 (len(active), 256)) of round rnd."""
+        import numpy as np
+        import torch
+        n = group.shape[0]
+        na = len(active)
+        out = np.zeros((max(na, 1), 256), dtype=np.int64)
+        pre = (ctypes.c_uint64 * max(2 * na, 1))(*[int(v) for v in np.asarray(prefix, dtype=np.uint64).ravel()])
+        self._call("nb_orb_hist", n, _ptr(pos, "pos", 3 * n), _ptr_typed(ids, "ids", torch.int64, n),
+                   _ptr_typed(group, "group", torch.int32, n), na,
+                   _host_array(ctypes.c_int32, active), _host_array(ctypes.c_int32, axis), pre,
+                   int(rnd), out.ctypes.data_as(ctypes.POINTER(_c_i64)))
+        return out[:na]
+
+    def orb_cut(self, pos, ids, group, active, axis, split, upper):
+        """Move the bodies of each active part at or above its split key to
+        its upper group (in place on `group`)."""
+        import numpy as np
+        import torch
+        n = group.shape[0]
+        na = len(active)
+        spl = (ctypes.c_uint64 * max(2 * na, 1))(*[int(v) for v in np.asarray(split, dtype=np.uint64).ravel()])
+        self._call("nb_orb_cut", n, _ptr(pos, "pos", 3 * n), _ptr_typed(ids, "ids", torch.int64, n),
+                   _ptr_typed(group, "group", torch.int32, n), na,
+                   _host_array(ctypes.c_int32, active), _host_array(ctypes.c_int32, axis), spl,
+                   _host_array(ctypes.c_int32, upper))
+
+    def orb_pack(self, rank, P, pos, vel, mass, ids):
+        """Bodies ordered by rank (stable) and the counts per rank."""
+        import numpy as np
+        import torch
+        n = rank.shape[0]
+        outs = [torch.empty_like(t) for t in (pos, vel, mass, ids)]
+        counts = np.zeros(P, dtype=np.int64)
+        self._call("nb_orb_pack", n, _ptr_typed(rank, "rank", torch.int32, n), int(P),
+                   _ptr(pos, "pos", 3 * n), _ptr(vel, "vel", 3 * n), _ptr(mass, "mass", n),
+                   _ptr_typed(ids, "ids", torch.int64, n), _ptr(outs[0], "pos_out", 3 * n),
+                   _ptr(outs[1], "vel_out", 3 * n), _ptr(outs[2], "mass_out", n),
+                   _ptr_typed(outs[3], "id_out", torch.int64, n),
+                   counts.ctypes.data_as(ctypes.POINTER(_c_i64)))
+        return (*outs, counts)
+
+    def orb_order(self, pos, vel, mass, ids):
+        """Bodies ordered by id."""
+        import torch
+        n = ids.shape[0]
+        outs = [torch.empty_like(t) for t in (pos, vel, mass, ids)]
+        self._call("nb_orb_order", n, _ptr(pos, "pos", 3 * n), _ptr(vel, "vel", 3 * n),
+                   _ptr(mass, "mass", n), _ptr_typed(ids, "ids", torch.int64, n),
+                   _ptr(outs[0], "pos_out", 3 * n), _ptr(outs[1], "vel_out", 3 * n),
+                   _ptr(outs[2], "mass_out", n), _ptr_typed(outs[3], "id_out", torch.int64, n))
+        return tuple(outs)
+
+    def let_build(self, pos, mass, leaf_cap):
+        """Build the local tree; returns the float32 box of the bodies (6,)."""
+        import numpy as np
+        n = mass.shape[0]
+        box = np.zeros(6, dtype=np.float32)
+        self._call("nb_let_build", n, _ptr(pos, "pos", 3 * n), _ptr(mass, "mass", n),
+                   int(leaf_cap), box.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        self._let_n = n
+        return box
+
+    def let_export(self, theta, box):
+        """The LET of the local tree for a destination box, as a uint8 CUDA tensor."""
+        import numpy as np
+        import torch
+        b = np.ascontiguousarray(box, dtype=np.float32)
+        size = _c_i64()
+        bp = b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        self._call("nb_let_export", float(theta), bp, None, 0, ctypes.byref(size))
+        out = torch.empty(size.value, dtype=torch.uint8, device=f"cuda:{self.device}")
+        self._call("nb_let_export", float(theta), bp, out.data_ptr(), size.value, ctypes.byref(size))
+        return out
+
+    def let_forces(self, G, eps, theta, group, lets, out=None, counts=False):
+        """Accelerations of the local bodies from the local tree and the
+        received LETs (uint8 CUDA tensors, in the order to add them)."""
+        import torch
+        n = self._let_n
+        dev = f"cuda:{self.device}"
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        cnt = torch.empty((n, 2), dtype=torch.int32, device=dev) if counts else None
+        arr = (_c_vp * max(len(lets), 1))(*[t.data_ptr() for t in lets])
+        self._call("nb_let_forces", float(G), float(eps), float(theta), int(group), len(lets), arr,
+                   _ptr(out, "acc", 3 * n), _ptr_i32(cnt, "counts", 2 * n) if counts else None)
+        return (out, cnt) if counts else out
 
     def device_info(self, n):
         sms, occ = ctypes.c_int(), ctypes.c_int()
