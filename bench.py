@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="throughput",
                     choices=["throughput", "batched", "precision", "plain", "differentiation",
-                             "tree", "fmm"])
+                             "tree", "fmm", "let"])
+    ap.add_argument("--procs", type=int, default=8,
+                    help="let workload on one GPU: processes emulated by threads")
     ap.add_argument("--theta", type=float, default=None, help="tree workload: opening angle")
     ap.add_argument("--leaf-cap", type=int, default=None, help="tree workload: leaf capacity")
     ap.add_argument("--order", type=int, default=None, help="fmm workload: expansion order 2..6")
@@ -1007,6 +1009,102 @@ def other_workload(args, ws, rank, local):
     return 0
 
 
+LET_W = {"name": "two-plummer N=1048576, parallel tree code (ORB domains, locally essential "
+                 "trees), Barnes-Hut theta 0.5, leaves <= 16, groups of 64, one force evaluation "
+                 "per step", "seed": 2, "eps": 0.002, "theta": 0.5, "leaf_cap": 16, "group": 64}
+
+
+def let_workload(args, ws, rank, local):
+    """Parallel tree code line (paper Sec. IV-B).  Under torchrun, one process
+    per GPU over NCCL.  On one GPU, --procs processes are emulated by threads
+    whose kernels run one after another on the device: the line then gives
+    the single-GPU cost of the sharded evaluation (every process's ORB,
+    exchange, tree, LET exports and walks), not a multi-GPU time.  value =
+    cell + body interactions of all processes / the force phase's time (tree
+    build, LET export and exchange, walks)."""
+    import numpy as np
+    import torch
+    from paper_1211_2292_gb300 import inputs, let, nbody
+    w = LET_W
+    b = inputs.two_plummer(args.n_per, seed=w["seed"])
+    N = b.n
+    G, eps, th, lc, grp = 1.0, w["eps"], w["theta"], w["leaf_cap"], w["group"]
+    emulated = ws == 1
+    P = args.procs if emulated else ws
+    if not emulated:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if not emulated else 0)
+    torch.cuda.set_device(dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def proc(comm):
+        r = comm.rank
+        lo, hi = r * N // P, (r + 1) * N // P
+        with nbody.NBody(N if emulated else max(2 * (hi - lo), 1), "fp32_comp",
+                         device=dev.index) as nb:
+            x, v, m = (torch.as_tensor(a[lo:hi], device=dev).contiguous()
+                       for a in (b.pos, b.vel, b.mass))
+            ids = torch.arange(lo, hi, dtype=torch.int64, device=dev)
+            e0 = ev()
+            part = let.orb_partition(nb, comm, x, ids)
+            x, v, m, ids = let.exchange(nb, comm, part, x, v, m, ids)
+            e1 = ev()
+            torch.cuda.synchronize(dev)
+            orb_ms = e0.elapsed_time(e1)
+            for _ in range(args.warmup):
+                let.let_forces(nb, comm, x, m, G, eps, th, lc, grp)
+            t = []
+            for _ in range(args.steps):
+                # a collective on each side: the span covers every process's
+                # kernels (on one GPU they share the device's default stream)
+                comm.allreduce(np.zeros(1), "sum")
+                torch.cuda.synchronize(dev)
+                a0 = ev()
+                let.let_forces(nb, comm, x, m, G, eps, th, lc, grp)
+                comm.allreduce(np.zeros(1), "sum")
+                a1 = ev()
+                torch.cuda.synchronize(dev)
+                t.append(a0.elapsed_time(a1))
+            st = nb.tree_stats() if x.shape[0] else {"cell_interactions": 0, "body_interactions": 0}
+            return {"n": int(x.shape[0]), "orb_exchange_ms": orb_ms,
+                    "force_ms": float(np.mean(t)),
+                    "interactions": st["cell_interactions"] + st["body_interactions"]}
+
+    if emulated:
+        res = let.run_threads(P, proc)
+    else:
+        mine = proc(let.TorchComm(device=f"cuda:{local}"))
+        res = [None] * ws
+        torch.distributed.all_gather_object(res, mine)
+    if rank == 0:
+        inter = sum(r["interactions"] for r in res)
+        # the evaluation's span: the slowest process (on one GPU every
+        # process's span covers all processes' kernels)
+        span = max(r["force_ms"] for r in res)
+        line = {"metric": TREE_METRIC, "value": inter / (span / 1e3) / 1e9, "unit": UNIT,
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": span,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded Plummer spheres)",
+                "config": {"workload": w["name"], "n": N, "processes": P,
+                           "processes_emulated_on_one_gpu": emulated,
+                           "theta": th, "leaf_cap": lc, "group": grp},
+                "per_process": res,
+                "note": ("processes emulated by threads on one GPU: their kernels run one "
+                         "after another, so this is the one-GPU cost of the sharded "
+                         "evaluation, not a multi-GPU time" if emulated else
+                         "one process per GPU over NCCL")}
+        print(json.dumps(line), flush=True)
+    if not emulated:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def _relerr(a, ref):
     import numpy as np
     return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
@@ -1128,6 +1226,10 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    if args.workload == "let":
+        if args.warmup < 3:
+            args.warmup = 3
+        return let_workload(args, ws, rank, local)
     if args.workload in ("precision", "plain", "differentiation", "tree", "fmm"):
         if args.warmup < 3:
             args.warmup = 3

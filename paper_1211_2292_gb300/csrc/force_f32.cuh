@@ -67,10 +67,12 @@ __device__ __forceinline__ void write_acc(const ForceParams &p, int i, double ax
 //    s = (r*r)*(m_j*r): 12 float32 operations per pair in total.
 //  * log domain (LOGM = true, wj = log2 m_j): s = 2^(log2 m_j - 1.5 log2 r^2)
 //    with lg2 and ex2 on the MUFU pipe and one fma: 10 float32 operations and
-//    2 MUFU per pair.  Measured on GB300: FFMA2 241 flop/clk/SM, rsqrt and
-//    lg2 16/clk/SM, ex2 32/clk/SM.  The rsqrt form is FMA-bound and the log
-//    form MUFU-bound at the same 10.7 pairs/clk/SM; a thread that runs 2/3 of
-//    its body pairs in the log form balances both pipes at 12 pairs/clk/SM.
+//    2 MUFU per pair.  On GB300 the FMA pipe takes 128 float32 operations per
+//    clock per SM, rsqrt and lg2 16 and ex2 32 MUFU operations (as the
+//    kernels' own pipe counters show), so the rsqrt form is FMA-bound and
+//    the log form MUFU-bound at the same 10.7 pairs/clk/SM; a thread that
+//    runs 2/3 of its body pairs in the log form balances both pipes at
+//    12 pairs/clk/SM.
 //    Needs m_j >= 0 (m_j = 0 gives log2 = -inf, s = 0).
 template <bool ZEPS, bool LOGM>
 __device__ __forceinline__ void interact2(float2 xj, float2 yj, float2 zj, float2 wj, float2 e2,
