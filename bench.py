@@ -9,7 +9,7 @@ evaluations) in the float32 Kahan-compensated form with float64 state.
 Metric: pairwise interactions per second, N^2 per force evaluation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload throughput|batched|precision|plain|differentiation|tree|fmm]
+                  [--workload throughput|batched|precision|plain|differentiation|tree|fmm|let]
 
 The other workloads (single-GPU lines with the same metric): "precision"
 (N = 65,536 Plummer, eps 0.005, FP32 compensated, 1 + 100 steps of dt 5e-4,
@@ -20,7 +20,9 @@ graph launch, checked against the oracle), "differentiation" (N = 16,384,
 "tree" (the default workload's bodies through the Barnes-Hut tree code,
 theta 0.5, leaves of at most 16 bodies: 1 + 10 KDK steps with the tree
 rebuilt for every force evaluation; its metric counts the cell and body
-interactions the walk computes).
+interactions the walk computes), "let" (the same bodies through the parallel
+tree code: ORB domains and locally essential trees over P processes, one per
+GPU under torchrun, or emulated by threads on one GPU).
 
 Multi-GPU (torchrun, one rank per GPU): for "throughput" every rank runs its
 own replica (the single-system path is not sharded); for "batched" the 512
@@ -240,6 +242,38 @@ def reference_arm(args, ws, rank):
         return 0
     import oracle
     from paper_1211_2292_gb300 import inputs
+    if args.workload == "let":
+        w = LET_W
+        b = inputs.two_plummer(TREE["cpu_n_per"], seed=w["seed"])
+        P = args.procs
+        rank_of = oracle.orb(b.pos, P)
+        for _ in range(args.warmup):
+            oracle.bh_sharded(b.pos, b.mass, 1.0, w["eps"], w["theta"], w["leaf_cap"],
+                              w["group"], rank_of, P)
+        tot, inter = 0.0, 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            _, st, _ = oracle.bh_sharded(b.pos, b.mass, 1.0, w["eps"], w["theta"],
+                                         w["leaf_cap"], w["group"], rank_of, P)
+            tot += time.perf_counter() - t0
+            inter += st["cell_interactions"] + st["body_interactions"]
+        value = inter / tot / 1e9
+        sample = (f"the oracle's parallel tree code on two-plummer N={b.n} (same recipe) over "
+                  f"{P} ORB domains, theta {w['theta']}, leaves <= {w['leaf_cap']}, groups of "
+                  f"{w['group']}, per step")
+        line = {
+            "impl": "reference", "metric": TREE_METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer spheres)",
+            "config": {"workload": w["name"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "tree":
         w = TREE
         theta = w["theta"] if args.theta is None else args.theta

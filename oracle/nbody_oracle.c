@@ -743,8 +743,8 @@ static void bh_walk_sources(const bh_prep *S, bh_work *W, const double *xs, cons
                     d[cc] = nd->com[cc] - xi[cc];
                     s2 += d[cc] * d[cc];
                 }
-                double w = nd->M / (s2 * sqrt(s2));
-                for (int cc = 0; cc < 3; ++cc) s[cc] += w * d[cc];
+                double wc = nd->M / (s2 * sqrt(s2));
+                for (int cc = 0; cc < 3; ++cc) s[cc] += wc * d[cc];
                 ++nc;
                 cov += nd->end - nd->start;
             } else {

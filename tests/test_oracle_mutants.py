@@ -84,6 +84,8 @@ MUTANTS = {
     "sharded self pair by local index": ("if (sid[j] == tid[k]) continue;",
                                          "if (j == k) continue;"),
     "sharded cell not covering its bodies": ("cov += nd->end - nd->start;", "cov += 1;"),
+    "sharded cell mass": ("double wc = nd->M / (s2 * sqrt(s2));",
+                          "double wc = 1.0 / (s2 * sqrt(s2));"),
     "let near box corner": ("float aa = nd->lo[c] - bhi[c];", "float aa = nd->lo[c] - blo[c];"),
     "let children not sent": ("if (nd->child[o] >= 0) kind[nd->child[o]] = -1;",
                               "if (nd->child[o] >= 0) kind[nd->child[o]] = 0;"),
