@@ -1094,6 +1094,7 @@ def let_workload(args, ws, rank, local):
             for _ in range(args.warmup):
                 let.let_forces(nb, comm, x, m, G, eps, th, lc, grp)
             t = []
+            nb.profile(True)
             for _ in range(args.steps):
                 # a collective on each side: the span covers every process's
                 # kernels (on one GPU they share the device's default stream)
@@ -1105,9 +1106,23 @@ def let_workload(args, ws, rank, local):
                 a1 = ev()
                 torch.cuda.synchronize(dev)
                 t.append(a0.elapsed_time(a1))
+            nb.profile(False)
+            # the walk kernels alone: the processes in turn (the others wait at
+            # a host barrier, so on one GPU no other work is on the device),
+            # each walking its tree and its received LETs once more
+            _, lets = let.let_forces(nb, comm, x, m, G, eps, th, lc, grp, return_lets=True)
+            wn, wms = 0, 0.0
+            for turn in range(P):
+                comm.allreduce(np.zeros(1), "sum")
+                if turn == comm.rank and x.shape[0]:
+                    torch.cuda.synchronize(dev)
+                    nb.profile(True)
+                    nb.let_forces(G, eps, th, grp, lets)
+                    wn, wms = nb.profile_read(4)
+                    nb.profile(False)
             st = nb.tree_stats() if x.shape[0] else {"cell_interactions": 0, "body_interactions": 0}
             return {"n": int(x.shape[0]), "orb_exchange_ms": orb_ms,
-                    "force_ms": float(np.mean(t)),
+                    "force_ms": float(np.mean(t)), "walk_ms": wms, "walks": wn,
                     "interactions": st["cell_interactions"] + st["body_interactions"]}
 
     if emulated:
@@ -1121,6 +1136,26 @@ def let_workload(args, ws, rank, local):
         # the evaluation's span: the slowest process (on one GPU every
         # process's span covers all processes' kernels)
         span = max(r["force_ms"] for r in res)
+        # the walk kernels' roofline: 20 flops per cell or body interaction
+        # over the walks' summed event time (every process's walks, one after
+        # another on one GPU; the slowest process's on several)
+        walk_ms = (sum if emulated else max)(r["walk_ms"] for r in res)
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = float(load_peaks().get("sm_max_mhz", NOMINAL_SM_MAX_MHZ))
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = FLOPS_PER_INTERACTION * inter / (walk_ms / 1e3) / 1e12
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            bs = inputs.two_plummer(TREE["cpu_n_per"], seed=w["seed"])
+            rk = oracle.orb(bs.pos, P)
+            t0 = time.perf_counter()
+            _, cst, _ = oracle.bh_sharded(bs.pos, bs.mass, G, eps, th, lc, grp, rk, P)
+            el = time.perf_counter() - t0
+            cpu = {"value": (cst["cell_interactions"] + cst["body_interactions"]) / el / 1e9,
+                   "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the oracle's parallel tree code on two-plummer N={bs.n} (same "
+                             f"recipe) over {P} ORB domains: one evaluation, {el:.1f} s"}
         line = {"metric": TREE_METRIC, "value": inter / (span / 1e3) / 1e9, "unit": UNIT,
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": span,
                 "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
@@ -1129,6 +1164,12 @@ def let_workload(args, ws, rank, local):
                            "processes_emulated_on_one_gpu": emulated,
                            "theta": th, "leaf_cap": lc, "group": grp},
                 "per_process": res,
+                "roofline": {"bound": "alu", "kernel": "tree_walk_kernel (local tree and LETs)",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "note": f"{FLOPS_PER_INTERACTION} flops per cell or body "
+                                     "interaction over the walks' event time"},
+                "cpu_baseline": cpu,
                 "note": ("processes emulated by threads on one GPU: their kernels run one "
                          "after another, so this is the one-GPU cost of the sharded "
                          "evaluation, not a multi-GPU time" if emulated else

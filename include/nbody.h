@@ -407,7 +407,9 @@ nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
  *    processor's tree and groups do not depend on the exchange's order).
  * LET.
  *  nb_let_build: the tree of nb_tree_forces (readings of that call) over
- *    this processor's n bodies, kept in the context; box_out (HOST, 6
+ *    this processor's n bodies, kept in the context until the next tree-code
+ *    or FMM call on it (after which nb_let_export and nb_let_forces refuse
+ *    until nb_let_build runs again); box_out (HOST, 6
  *    floats) = the float32 box {min xyz, max xyz} of the bodies, which the
  *    other processors need for their LETs.  Synchronises.
  *  nb_let_export: the LET of the local tree for a destination whose bodies

@@ -758,6 +758,7 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
 {
     if (n == 0) return NB_OK;
     int k = 0;
+    c->let_n = 0;  // the local tree of nb_let_build is replaced
     NB_TRY(tree_build_enqueue(c, s, n, pos, mass, leaf_cap));
     nb::TreeWalkParams p;
     p.tree = c->tree;
@@ -812,6 +813,7 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
 {
     cudaStream_t s = c->stream;
     int k = 0;
+    c->let_n = 0;  // the local tree of nb_let_build is replaced
     {
         TreeTimer tm(c, nb::PROF_TREE_BUILD, s);
         NB_CUDA(c, nb::launch_tree_sort(s, (int)n, pos, c->order, c->tree_perm, c->tree_box, k));

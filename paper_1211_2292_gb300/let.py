@@ -221,13 +221,15 @@ def exchange(ops, comm: Comm, rank, pos, vel, mass, ids):
 
 
 # ------------------------------------------------------------------------ LET
-def let_forces(ops, comm: Comm, pos, mass, G, eps, theta, leaf_cap, group, counts=False):
+def let_forces(ops, comm: Comm, pos, mass, G, eps, theta, leaf_cap, group, counts=False,
+               return_lets=False):
     """Accelerations of this process's bodies (in their order) from its own
     tree and the LETs the other processes send it: each process builds its
     tree, the float32 boxes of all processes' bodies are gathered, each
     process exports one LET per other non-empty process, the LETs are
     exchanged, and each walks its own tree, then the received ones in
-    processor order."""
+    processor order.  With return_lets, (result, received LETs) so that the
+    walks can be repeated on the same trees."""
     import torch
     P, me = comm.size, comm.rank
     n = int(mass.shape[0])
@@ -245,8 +247,10 @@ def let_forces(ops, comm: Comm, pos, mass, G, eps, theta, leaf_cap, group, count
         else:
             sends.append(ops.let_export(theta, boxes[d]))
     recvs = comm.alltoallv(sends)
+    lets = [recvs[s] for s in range(P) if s != me and recvs[s].numel() > 0]
     if n == 0:
         z = torch.empty((0, 3), dtype=torch.float64, device=dev)
-        return (z, torch.empty((0, 2), dtype=torch.int32, device=dev)) if counts else z
-    lets = [recvs[s] for s in range(P) if s != me and recvs[s].numel() > 0]
-    return ops.let_forces(G, eps, theta, group, lets, counts=counts)
+        out = (z, torch.empty((0, 2), dtype=torch.int32, device=dev)) if counts else z
+    else:
+        out = ops.let_forces(G, eps, theta, group, lets, counts=counts)
+    return (out, lets) if return_lets else out

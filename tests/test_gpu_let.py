@@ -122,3 +122,27 @@ def test_argument_checks(cuda):
         junk = torch.zeros(256, dtype=torch.uint8, device=cuda)
         with pytest.raises(nbody.NBodyError):
             nb.let_forces(1.0, 0.01, 0.5, 64, [junk])  # not a LET
+        nb.tree_forces(x, m, 1.0, 0.01, 0.5, 16)  # replaces the local tree
+        with pytest.raises(nbody.NBodyError):
+            nb.let_export(0.5, np.zeros(6, np.float32))
+
+
+def test_ties_in_the_cut_coordinate(cuda):
+    # Many bodies share the cut coordinate (a third coincident, and -0.0
+    # against +0.0): the cut orders them by id, as the oracle does.
+    b = inputs.plummer(2400, seed=95)
+    pos = b.pos.copy()
+    pos[::3] = [0.25, -0.5, 0.125]
+    pos[1::7, 0] = 0.0
+    pos[2::7, 0] = -0.0
+    b = inputs.Bodies(pos, b.vel, b.mass)
+    res = _run(cuda, b, 4, 0.5, 8, 32, 0.01)
+    ref_rank = oracle.orb(b.pos, 4)
+    assert np.array_equal(np.concatenate([r[0] for r in res]), ref_rank)
+    ref, _, ref_cnt = oracle.bh_sharded(b.pos, b.mass, 1.0, 0.01, 0.5, 8, 32, ref_rank, 4)
+    for r, (_, ids, _, acc, cnt) in enumerate(res):
+        mine = np.flatnonzero(ref_rank == r)
+        assert np.array_equal(ids, mine)
+        assert np.array_equal(cnt.astype(np.int64), ref_cnt[mine, :2])
+        e = relerr_per_body(acc, ref[mine])
+        assert np.sqrt((e ** 2).mean()) <= 1e-5 and e.max() <= 1e-4
