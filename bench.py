@@ -835,7 +835,8 @@ def fmm_workload(args, ws, torch, dev, stream, T, flush):
     far_tf = st["expansions"] * m2l_flops(order) / (far_ms / 1e3) / 1e12
     near_tf = FLOPS_PER_INTERACTION * st["direct_pairs"] / (near_ms / 1e3) / 1e12
     phases = {
-        "far": {"kernels": "fmm_up_kernel, fmm_down_kernel x 11 levels, fmm_items_kernel",
+        "far": {"kernels": "fmm_up_kernel, fmm_lists_kernel x 11 levels, fmm_m2l_kernel, "
+                           "fmm_l2l_kernel x 10 levels, fmm_items_kernel",
                 "ms": far_ms, "expansions": st["expansions"], "achieved_tflops": far_tf,
                 "flops_per_expansion": m2l_flops(order)},
         "near": {"kernels": "fmm_near_kernel, fmm_combine_kernel", "ms": near_ms,
@@ -844,12 +845,12 @@ def fmm_workload(args, ws, torch, dev, stream, T, flush):
         "build_ms": build_ms}
     far_dominant = far_ms >= near_ms
     roof = {"bound": "alu",
-            "kernel": "fmm_down_kernel (11 level launches) with the upward pass" if far_dominant
+            "kernel": "far phase: fmm_m2l_kernel with the upward, list and L2L passes" if far_dominant
             else "fmm_near_kernel",
             "achieved": far_tf if far_dominant else near_tf, "peak": peak, "unit": "TFLOP/s",
             "frac": (far_tf if far_dominant else near_tf) / peak,
             "traffic": traffic_from_profile(
-                "fmm_down_two_plummer_n1048576_dram.md" if far_dominant
+                "fmm_far_two_plummer_n1048576_dram.md" if far_dominant
                 else "fmm_near_two_plummer_n1048576_dram.md", "fmm_impl.cuh")
             if (b.n, theta, lc, order) == (1 << 20, 0.6, 64, 6) else None,
             "note": f"far: {m2l_flops(order)} flops per cell-to-cell expansion (its contraction); "

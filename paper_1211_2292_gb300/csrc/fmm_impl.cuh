@@ -31,10 +31,11 @@
 // d^n f_m = q_c d^(n-e_c) f_(m+1) + (n_c - 1) d^(n-2e_c) f_(m+1).
 //
 // Launches: one upward pass (P2M at the leaves, M2M climbing: the last child
-// to arrive sums its parent), one downward launch per level (L2L from the
-// parent, the candidates' classification, M2L with one source per lane, the
-// hand-down lists; leaves walk their candidates' subtrees for their M2L),
-// and one near-field launch over the leaves (the same walk collecting the
+// to arrive sums its parent); one list launch per level (the candidates'
+// classification, the hand-down lists and each cell's list of separated
+// sources; leaves walk their candidates' subtrees); one M2L launch over all
+// cells (one source per lane); one L2L launch per level below the root; and
+// one near-field launch over the leaves (the same walk collecting the
 // leaves to sum directly, float32x2 pair terms over sliced lanes, then L2P).
 #pragma once
 
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(256) fmm_up_kernel(const FmmParams p)
         const int L = t.level[leaf];
         const int4 ci = icentre(t.prefix[leaf], L);
         f.ci[leaf] = ci;
+        f.nd[leaf] = make_int4(0, t.first[leaf], t.start[leaf], t.end[leaf]);
         double z[3];
         centre_of(p.box, ci, z);
         const double inv_e = (double)(1 << L) / ext;
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(256) fmm_up_kernel(const FmmParams p)
             if (atomicAdd(f.arrive + node, 1) != t.nchild[node] - 1) break;
             __threadfence();
             f.ci[node] = icentre(t.prefix[node], t.level[node]);
+            f.nd[node] = make_int4(t.nchild[node], t.first[node], t.start[node], t.end[node]);
 #pragma unroll
             for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
             const int c0 = t.first[node], nch = t.nchild[node];
@@ -429,10 +432,25 @@ __device__ __forceinline__ void push_children(WalkSh &w, bool open, int tgt, int
     __syncwarp();
 }
 
-__device__ __forceinline__ bool separated(int4 a, int4 b, const double (*crit)[LEVELS])
+// The two tests of a pair of cells, both on the integer squared distance
+// D2 of their centres (units of h), as thresholds per pair of levels: D2 is
+// an integer and each float64 test is monotone in it, so one integer
+// comparison decides exactly as the float64 expression would, without the
+// float64 arithmetic in the walks.
+struct CritSh {
+    int sep[LEVELS][LEVELS];  // separated iff D2 >= sep
+    int dir[LEVELS][LEVELS];  // all_direct iff D2 <= dir (-1: never)
+};
+
+__device__ __forceinline__ int dist2(int4 a, int4 b)
 {
     const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    return (double)(dx * dx + dy * dy + dz * dz) >= crit[a.w][b.w];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ bool separated(int4 a, int4 b, const CritSh &c)
+{
+    return dist2(a, b) >= c.sep[a.w][b.w];
 }
 
 // No descendant of the unseparated candidate B can be separated from target
@@ -441,22 +459,59 @@ __device__ __forceinline__ bool separated(int4 a, int4 b, const double (*crit)[L
 // needs more than k e_A / theta.  The margin puts the float64 rounding of
 // both this test and the separation test out of play, so walking B's subtree
 // would meet exactly B's bodies directly.
-__device__ __forceinline__ bool all_direct(int4 a, int4 b, double theta)
+__device__ __forceinline__ bool all_direct(int4 a, int4 b, const CritSh &c)
 {
-    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    const double D = __dsqrt_rn((double)(dx * dx + dy * dy + dz * dz));
-    const double k = 0.8660254037844386;
-    const double eA = (double)(1 << (11 - a.w)), eB = (double)(1 << (11 - b.w));
-    return D + k * eB < (1.0 - 1e-9) * (k * eA / theta);
+    return dist2(a, b) <= c.dir[a.w][b.w];
 }
 
-__device__ __forceinline__ void crit_table(double (*crit)[LEVELS], double theta)
+// The float64 form of all_direct for a squared distance D2 between cells of
+// levels la (target) and lb.
+static __device__ __noinline__ bool all_direct_f64(long long D2, int la, int lb, double theta)
+{
+    const double D = __dsqrt_rn((double)D2);
+    const double k = 0.8660254037844386;
+    const double eA = (double)(1 << (11 - la)), eB = (double)(1 << (11 - lb));
+    return __dadd_rn(D, __dmul_rn(k, eB)) < __dmul_rn(1.0 - 1e-9, __ddiv_rn(__dmul_rn(k, eA), theta));
+}
+
+// Squared distances stay below 3 * 4096^2 (centres lie in [0, 4096)).
+constexpr int D2_MAX = 3 * 4096 * 4096;
+static_assert(sizeof(CritSh) == FMM_CRIT_INTS * sizeof(int), "threshold table size");
+
+// The thresholds for theta, computed once per evaluation (by
+// fmm_init_kernel) into global memory.
+__device__ __forceinline__ void crit_compute(CritSh &c, double theta)
 {
     for (int i = threadIdx.x; i < LEVELS * LEVELS; i += blockDim.x) {
         const int la = i / LEVELS, lb = i % LEVELS;
         const double s = (double)((1 << (11 - la)) + (1 << (11 - lb)));
-        crit[la][lb] = __ddiv_rn(__dmul_rn(__dmul_rn(0.75, s), s), __dmul_rn(theta, theta));
+        const double crit = __ddiv_rn(__dmul_rn(__dmul_rn(0.75, s), s), __dmul_rn(theta, theta));
+        // the least integer >= crit (beyond every distance: never separated)
+        c.sep[la][lb] = crit > (double)D2_MAX ? D2_MAX + 1 : (int)ceil(crit);
+        // the largest D2 passing all_direct_f64: from the real boundary
+        // (sqrt(D2) + k e_B = (1 - 1e-9) k e_A / theta), then stepped to the
+        // exact one
+        const double k = 0.8660254037844386;
+        const double r = (1.0 - 1e-9) * (k * (double)(1 << (11 - la)) / theta) -
+                         k * (double)(1 << (11 - lb));
+        long long t;
+        if (!(r > 0.0))
+            t = -1;
+        else if (r * r > 2.0 * D2_MAX)
+            t = D2_MAX;
+        else
+            t = (long long)(r * r);
+        while (t < D2_MAX && all_direct_f64(t + 1, la, lb, theta)) ++t;
+        while (t >= 0 && !all_direct_f64(t, la, lb, theta)) --t;
+        c.dir[la][lb] = (int)t;
     }
+}
+
+// A block's shared copy of the thresholds (a __syncthreads must follow).
+__device__ __forceinline__ void crit_table(CritSh &c, const int *__restrict__ g)
+{
+    int *d = reinterpret_cast<int *>(&c);
+    for (int i = threadIdx.x; i < (int)(sizeof(CritSh) / sizeof(int)); i += blockDim.x) d[i] = g[i];
 }
 
 __device__ __forceinline__ Consts consts_of(const FmmParams &p)
@@ -469,39 +524,46 @@ __device__ __forceinline__ Consts consts_of(const FmmParams &p)
 }
 
 // ------------------------------------------------------------ downward pass
-// Cells of level L, a warp each (dynamic): local coefficients = the parent's
-// translated + the M2L of the separated candidates; a non-leaf hands the
-// others down, a leaf walks their subtrees for more separated cells.
-// Resident blocks per SM the downward kernel's registers are sized for: four
-// (16 warps) up to order 5 (order 5 spills 84 bytes a thread), two at order 6.
-template <int P>
-constexpr int down_min_blocks() { return P <= 5 ? 4 : 2; }
-
-template <int P>
-__global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
-    fmm_down_kernel(const FmmParams p, int L)
+// Three parts.  (1) Per level L, a warp per cell (dynamic) classifies the
+// candidates its parent handed down: a non-leaf hands the unseparated ones
+// (or their children) to its own children, a leaf walks their subtrees; the
+// separated cells go into the cell's expansion list, in chunks of 32 source
+// ids (one per lane of the later evaluation, -1 past the end) linked from
+// chunk_head.  (2) One launch over all cells sums each cell's list (M2L, a
+// source per lane, the lanes' sums totalled in a fixed order) into L.
+// (3) Per level from the top, L2L adds the parent's translated
+// coefficients.  The chunks hold the sources in the order the
+// classification meets them and each goes to the lane of its position, so
+// every lane's sum, and the result, does not depend on scheduling.
+template <int P, bool LEAVES>
+__global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p, int L)
 {
-    constexpr int N = nterms(P), NP = padded(P);
     __shared__ WalkSh wsh[WARPS];
     __shared__ int mq[WARPS][64];
-    __shared__ double crit[LEVELS][LEVELS];
-    crit_table(crit, p.theta);
+    __shared__ CritSh crit;
+    crit_table(crit, p.f.crit);
     __syncthreads();
     const TreeView &t = p.tree;
     const FmmView &f = p.f;
-    const Consts K = consts_of(p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int cnt = t.meta[TREE_META_COUNT + L], base = t.meta[TREE_META_BASE + L];
+    // the non-leaves of level L, or all leaves (coarsest first: their walks
+    // are the longest)
+    const int cnt = LEAVES ? t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10]
+                           : t.meta[TREE_META_COUNT + L];
+    const int base = LEAVES ? 0 : t.meta[TREE_META_BASE + L];
+    int *queue = f.meta + (LEAVES ? FMM_META_LEAVES_Q : FMM_META_LEVEL + L);
     WalkSh &w = wsh[warp];
     for (;;) {
         int qi = 0;
-        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_LEVEL + L, 1);
+        if (lane == 0) qi = atomicAdd(queue, 1);
         qi = __shfl_sync(FULL, qi, 0);
         if (qi >= cnt) break;
         const int A = base + qi;
+        const int nchA = t.nchild[A];
+        if ((nchA == 0) != LEAVES) continue;  // the other kernel's cell
         const int4 cA = f.ci[A];
-        const int nchA = t.nchild[A], par = t.parent[A];
+        const int par = t.parent[A];
         int inh_off = 0, inh_cnt = 1;  // the root's list: pool[0] = 0
         if (par >= 0) {
             const int2 d = f.down[par];
@@ -509,25 +571,20 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
             inh_cnt = d.y;
         }
         const int *inh = f.pool + inh_off;
-        float acc[N];
-#pragma unroll
-        for (int q = 0; q < N; ++q) acc[q] = 0.0f;
-        int mcnt = 0, own = 0, farb = 0, nearc = 0;
+        int mcnt = 0, own = 0, farb = 0, nearc = 0, prev = -1;
+        if (lane == 0) f.chunk_head[A] = -1;
         // a non-leaf: how many candidates go down (pass 1), and where
         long long off = 0;
         bool fits = true;
-        if (nchA > 0) {
+        if constexpr (!LEAVES) {
             int total = 0;
             for (int c0 = 0; c0 < inh_cnt; c0 += 32) {
                 const int k = c0 + lane;
                 const int B = k < inh_cnt ? __ldg(inh + k) : -1;
                 int outc = 0;
                 if (B >= 0) {
-                    const int4 cB = __ldg(f.ci + B);
-                    if (!separated(cA, cB, crit)) {
-                        const int nchB = t.nchild[B];
-                        outc = (nchB == 0 || cB.w > cA.w) ? 1 : nchB;
-                    }
+                    const int4 cB = __ldg(f.ci + B), nB = __ldg(f.nd + B);
+                    if (!separated(cA, cB, crit)) outc = (nB.x == 0 || cB.w > cA.w) ? 1 : nB.x;
                 }
                 total += warp_sum(outc);
             }
@@ -543,16 +600,16 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
             __syncwarp();
         }
         // Rounds of 32 candidates fill the queue of separated cells; each
-        // time it holds 32 (or the candidates are done) every lane takes one
-        // source's M2L.  A non-leaf classifies its handed-down candidates and
+        // time it holds 32 (or the candidates are done) the first 32 become
+        // a chunk.  A non-leaf classifies its handed-down candidates and
         // writes the others down (pass 2); a leaf walks their subtrees.
         int c0 = 0, cur = 0, cursor = 0;
         bool more = true;
         while (more || mcnt > 0) {
             while (more && mcnt < 32) {
                 bool sep = false;
-                int B = -1;
-                if (nchA > 0) {
+                int B = -1, bodies = 0;
+                if constexpr (!LEAVES) {
                     if (c0 >= inh_cnt) {
                         more = false;
                         break;
@@ -563,13 +620,13 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
                     bool self = false;
                     int outc = 0, firstB = 0;
                     if (B >= 0) {
-                        const int4 cB = __ldg(f.ci + B);
+                        const int4 cB = __ldg(f.ci + B), nB = __ldg(f.nd + B);
                         sep = separated(cA, cB, crit);
+                        bodies = nB.w - nB.z;
                         if (!sep) {
-                            const int nchB = t.nchild[B];
-                            self = nchB == 0 || cB.w > cA.w;
-                            outc = self ? 1 : nchB;
-                            firstB = t.first[B];
+                            self = nB.x == 0 || cB.w > cA.w;
+                            outc = self ? 1 : nB.x;
+                            firstB = nB.y;
                             if (!self && cB.w < cA.w) atomicOr(p.err, ERR_TREE);  // never
                         }
                     }
@@ -590,14 +647,15 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
                     bool open = false;
                     int nchB = 0, firstB = 0, lvB = 0;
                     if (B >= 0) {
-                        const int4 cB = __ldg(f.ci + B);
+                        const int4 cB = __ldg(f.ci + B), nB = __ldg(f.nd + B);
                         sep = separated(cA, cB, crit);
-                        nchB = t.nchild[B];
+                        nchB = nB.x;
+                        bodies = nB.w - nB.z;
                         if (!sep) {
-                            open = nchB > 0 && !all_direct(cA, cB, p.theta);
-                            if (!open) nearc += t.end[B] - t.start[B];
+                            open = nchB > 0 && !all_direct(cA, cB, crit);
+                            if (!open) nearc += bodies;
                         }
-                        firstB = t.first[B];
+                        firstB = nB.y;
                         lvB = cB.w;
                     }
                     push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
@@ -605,7 +663,7 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
                 const unsigned sm = __ballot_sync(FULL, sep);
                 if (sep) {
                     mq[warp][mcnt + __popc(sm & lt)] = B;
-                    farb += t.end[B] - t.start[B];
+                    farb += bodies;
                 }
                 mcnt += __popc(sm);
                 own += __popc(sm);
@@ -613,9 +671,21 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
             }
             const int k = min(mcnt, 32);
             if (k > 0) {
-                if (lane < k) {
-                    const int B = mq[warp][lane];
-                    m2l_add<P>(acc, f.M + (size_t)B * NP, cA, __ldg(f.ci + B), K);
+                int ch = 0;
+                if (lane == 0) ch = atomicAdd(f.meta + FMM_META_CHUNKS, 1);
+                ch = __shfl_sync(FULL, ch, 0);
+                if (ch < f.chunk_cap) {
+                    f.chunk_src[32 * (size_t)ch + lane] = lane < k ? mq[warp][lane] : -1;
+                    if (lane == 0) {
+                        f.chunk_next[ch] = -1;
+                        if (prev < 0)
+                            f.chunk_head[A] = ch;
+                        else
+                            f.chunk_next[prev] = ch;
+                    }
+                    prev = ch;
+                } else if (lane == 0) {
+                    atomicOr(f.meta + FMM_META_OVERFLOW, 2);
                 }
                 __syncwarp();
                 if (lane < mcnt - k) mq[warp][lane] = mq[warp][k + lane];
@@ -623,37 +693,98 @@ __global__ void __launch_bounds__(32 * WARPS, down_min_blocks<P>())
                 __syncwarp();
             }
         }
-        if (nchA == 0) {
+        if constexpr (LEAVES) {
             nearc = warp_sum(nearc);
             if (lane == 0) {
                 f.nearc[A] = nearc;
                 f.leaves[atomicAdd(f.meta + FMM_META_NLEAVES, 1)] = A;
             }
         }
-        // lane 0 totals the lanes' sums (a fixed order), adds the parent's share
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-#pragma unroll
-            for (int off2 = 16; off2 > 0; off2 >>= 1) acc[q] += __shfl_down_sync(FULL, acc[q], off2);
-        }
         farb = warp_sum(farb);
         if (lane == 0) {
             int2 cum = make_int2(own, farb);
             if (par >= 0) {
-                float xp[N];
-                const float *src = f.L + (size_t)par * NP;
-#pragma unroll
-                for (int q = 0; q < N; ++q) xp[q] = src[q];
-                translate_add<P, false>(acc, xp, (int)(t.prefix[A] & 7u));
                 const int2 pc = f.cum[par];
                 cum.x += pc.x;
                 cum.y += pc.y;
             }
-            store_exp<P>(f.L + (size_t)A * NP, acc);
             f.cum[A] = cum;
             if (own) atomicAdd(f.stats + 2, (unsigned long long)own);
         }
         __syncwarp();
+    }
+}
+
+// Resident blocks per SM the expansion-sum kernel's registers are sized
+// for: the lane's running sums and the kernel's derivatives of one source
+// are both live in its contraction.
+template <int P>
+constexpr int m2l_min_blocks() { return P <= 5 ? 4 : 2; }
+
+// A warp per cell (dynamic, deepest cells first): the chunks of its list in
+// order, a source per lane; lane 0 stores the total (zero for an empty list).
+template <int P>
+__global__ void __launch_bounds__(32 * WARPS, m2l_min_blocks<P>()) fmm_m2l_kernel(const FmmParams p)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    if (f.meta[FMM_META_OVERFLOW]) return;  // the lists are incomplete: the host reruns
+    const Consts K = consts_of(p);
+    const int lane = threadIdx.x & 31;
+    const int total = t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10];
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_M2L, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= total) break;
+        const int A = total - 1 - qi;
+        float acc[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = 0.0f;
+        int ch = f.chunk_head[A];
+        if (ch >= 0) {
+            // the next chunk's sources are loaded before this chunk's expansions
+            const int4 cA = f.ci[A];
+            int B = f.chunk_src[32 * (size_t)ch + lane];
+            while (ch >= 0) {
+                const int nx = f.chunk_next[ch];
+                const int Bn = nx >= 0 ? f.chunk_src[32 * (size_t)nx + lane] : -1;
+                if (B >= 0) m2l_add<P>(acc, f.M + (size_t)B * NP, cA, __ldg(f.ci + B), K);
+                ch = nx;
+                B = Bn;
+            }
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(FULL, acc[q], o);
+            }
+        }
+        if (lane == 0) store_exp<P>(f.L + (size_t)A * NP, acc);
+    }
+}
+
+// Cells of level L >= 1, a thread each: L += the parent's coefficients
+// translated to the cell's centre.
+template <int P>
+__global__ void __launch_bounds__(128) fmm_l2l_kernel(const FmmParams p, int L)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    if (f.meta[FMM_META_OVERFLOW]) return;
+    const int cnt = t.meta[TREE_META_COUNT + L], base = t.meta[TREE_META_BASE + L];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+        const int A = base + q, par = t.parent[A];
+        float acc[N], xp[N];
+        const float *dst = f.L + (size_t)A * NP, *src = f.L + (size_t)par * NP;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            acc[k] = dst[k];
+            xp[k] = src[k];
+        }
+        translate_add<P, false>(acc, xp, (int)(t.prefix[A] & 7u));
+        store_exp<P>(f.L + (size_t)A * NP, acc);
     }
 }
 
@@ -785,8 +916,8 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
 {
     __shared__ WalkSh wsh[WARPS];
     __shared__ __align__(16) float4 lists[WARPS][2 * FLUSH];  // 2 * FLUSH sources as pairs
-    __shared__ double crit[LEVELS][LEVELS];
-    crit_table(crit, p.theta);
+    __shared__ CritSh crit;
+    crit_table(crit, p.f.crit);
     __syncthreads();
     const TreeView &t = p.tree;
     const FmmView &f = p.f;
@@ -898,22 +1029,24 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
         while (seen < src_hi && next_round(w, inh, inh_cnt, cursor, lane, B)) {
             bool open = false, direct = false;
             int nchB = 0, firstB = 0, lvB = 0;
+            int4 nB = make_int4(0, 0, 0, 0);
             if (B >= 0) {
                 const int4 cB = __ldg(f.ci + B);
+                nB = __ldg(f.nd + B);
                 if (!separated(cA, cB, crit)) {
-                    nchB = t.nchild[B];
-                    open = nchB > 0 && !all_direct(cA, cB, p.theta);
+                    nchB = nB.x;
+                    open = nchB > 0 && !all_direct(cA, cB, crit);
                     direct = !open;
                 }
-                firstB = t.first[B];
+                firstB = nB.y;
                 lvB = cB.w;
             }
             push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
             if (__ballot_sync(FULL, direct)) {
                 int ls = 0, lsz = 0;
                 if (direct) {
-                    ls = t.start[B];
-                    lsz = t.end[B] - ls;
+                    ls = nB.z;
+                    lsz = nB.w - ls;
                 }
                 const int linc = warp_incl_scan(lsz, lane);
                 const int lexc = linc - lsz;
@@ -1005,8 +1138,9 @@ __global__ void __launch_bounds__(256) fmm_combine_kernel(const FmmParams p)
 }
 
 template <int P>
-__global__ void fmm_init_kernel(FmmView f)
+__global__ void __launch_bounds__(128) fmm_init_kernel(FmmView f, double theta)
 {
+    crit_compute(*reinterpret_cast<CritSh *>(f.crit), theta);
     if (threadIdx.x < FMM_META_INTS) f.meta[threadIdx.x] = 0;
     if (threadIdx.x < 4) f.stats[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) {
@@ -1033,14 +1167,20 @@ cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, bool near, int 
     if (!near) {
         e = cudaMemsetAsync(p.f.arrive, 0, sizeof(int) * (size_t)p.tree.cap, s);
         if (e != cudaSuccess) return e;
-        fmm_init_kernel<P><<<1, 32, 0, s>>>(p.f);
+        fmm_init_kernel<P><<<1, 128, 0, s>>>(p.f, p.theta);
         const int up_grid = (int)std::min<long long>(4096, ((long long)p.tree.cap + 255) / 256);
         fmm_up_kernel<P><<<up_grid, 256, 0, s>>>(p);
-        const int down_grid = resident_grid(fmm_down_kernel<P>, 32 * WARPS, p.num_sms, e);
+        const int lists_grid = resident_grid(fmm_lists_kernel<P, true>, 32 * WARPS, p.num_sms, e);
         if (e != cudaSuccess) return e;
-        for (int L = 0; L < LEVELS; ++L) fmm_down_kernel<P><<<down_grid, 32 * WARPS, 0, s>>>(p, L);
+        const int m2l_grid = resident_grid(fmm_m2l_kernel<P>, 32 * WARPS, p.num_sms, e);
+        if (e != cudaSuccess) return e;
+        for (int L = 0; L < LEVELS; ++L)
+            fmm_lists_kernel<P, false><<<lists_grid, 32 * WARPS, 0, s>>>(p, L);
+        fmm_lists_kernel<P, true><<<lists_grid, 32 * WARPS, 0, s>>>(p, 0);
+        fmm_m2l_kernel<P><<<m2l_grid, 32 * WARPS, 0, s>>>(p);
+        for (int L = 1; L < LEVELS; ++L) fmm_l2l_kernel<P><<<2 * p.num_sms, 128, 0, s>>>(p, L);
         fmm_items_kernel<P><<<1, 1024, 0, s>>>(p);
-        kernels = 3 + LEVELS;
+        kernels = 5 + 2 * LEVELS - 1;
         return cudaGetLastError();
     }
     const bool zeps = p.eps2f == 0.0f;

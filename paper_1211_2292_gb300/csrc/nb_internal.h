@@ -255,10 +255,15 @@ cudaError_t launch_let_emit(cudaStream_t s, const TreeView &t, const double *box
 constexpr int FMM_MIN_ORDER = 2, FMM_MAX_ORDER = 6, FMM_MAX_LEAF = 64;
 int fmm_floats(int order);
 enum : int { FMM_META_LEVEL = 0, FMM_META_NEAR = 11, FMM_META_POOL = 12, FMM_META_OVERFLOW = 13,
-             FMM_META_NLEAVES = 14, FMM_META_ITEMS = 15, FMM_META_PSLOTS = 16, FMM_META_INTS = 20 };
+             FMM_META_NLEAVES = 14, FMM_META_ITEMS = 15, FMM_META_PSLOTS = 16,
+             FMM_META_CHUNKS = 17, FMM_META_M2L = 18, FMM_META_LEAVES_Q = 19, FMM_META_INTS = 20 };
+// FMM_META_OVERFLOW bits: the candidate pool (1), the expansion-list chunks (2).
+constexpr int FMM_CHUNK = 32;  // source ids per expansion-list chunk
+constexpr int FMM_CRIT_INTS = 2 * 11 * 11;  // two thresholds per pair of tree levels
 struct FmmView {
     int order, np;         // expansion order p; floats per expansion
     int4 *ci;              // per node: integer centre in units ext/2048 (.xyz), level (.w)
+    int4 *nd;              // per node: child count, first child, first body, end of bodies
     float *M, *L;          // [cap][np]: scaled moments, scaled local coefficients
     int2 *down;            // per node: (offset, count) in pool of the candidates handed to its children
     int2 *cum;             // per node: source cells acting on it and its ancestors, bodies they hold
@@ -271,7 +276,12 @@ struct FmmView {
     long long part_cap;    // slots part holds
     int *pool;             // candidate lists; pool[0] = 0, the root's own list
     long long pool_cap;
+    int *chunk_head;       // per node: its expansion list's first chunk, -1 for none
+    int *chunk_src;        // [chunk_cap][FMM_CHUNK] source cells, -1 past a list's end
+    int *chunk_next;       // [chunk_cap] the next chunk of the same list, -1 at the end
+    long long chunk_cap;
     int *meta;             // [FMM_META_INTS] queues, pool top, overflow flag, leaf count
+    int *crit;             // [FMM_CRIT_INTS] the cell tests' thresholds for this evaluation's theta
     unsigned long long *stats;  // [4] nodes, leaves, expansions, direct body pairs
 };
 struct FmmParams {

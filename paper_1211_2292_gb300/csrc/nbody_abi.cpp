@@ -512,15 +512,17 @@ void free_tree_nodes(nb_ctx *c)
 void free_fmm(nb_ctx *c)
 {
     nb::FmmView &f = c->fmm;
-    void *arrays[] = {f.ci,    f.M,     f.L,        f.down,     f.cum, f.arrive,
-                      f.leaves, f.nearc, f.item_off, f.part_off, f.part, f.pool};
+    void *arrays[] = {f.ci,       f.nd,       f.M,      f.L,        f.down,     f.cum,
+                      f.arrive,   f.leaves,   f.nearc,  f.item_off, f.part_off,
+                      f.part,     f.pool,     f.chunk_head, f.chunk_src, f.chunk_next};
     for (void *a : arrays) cudaFree(a);
-    f.ci = nullptr;
+    f.ci = f.nd = nullptr;
     f.M = f.L = nullptr;
     f.down = f.cum = nullptr;
     f.arrive = f.leaves = f.nearc = f.item_off = f.part_off = f.pool = nullptr;
+    f.chunk_head = f.chunk_src = f.chunk_next = nullptr;
     f.part = nullptr;
-    f.pool_cap = f.part_cap = 0;
+    f.pool_cap = f.part_cap = f.chunk_cap = 0;
     c->fmm_cap = c->fmm_np = 0;
 }
 
@@ -551,6 +553,7 @@ void free_ctx(nb_ctx *c)
     free_fmm(c);
     cudaFree(c->fmm.meta);
     cudaFree(c->fmm.stats);
+    cudaFree(c->fmm.crit);
     cudaFree(c->tree.meta);
     cudaFree(c->tree.stats);
     cudaFree(c->tree_P);
@@ -644,23 +647,24 @@ nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap, int group)
 
 // Expansion, list and candidate-pool scratch of the fast multipole method
 // for the tree's node capacity and `order`; the pool holds at least
-// pool_need entries.  Growing frees the old arrays (cudaFree synchronises).
-nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
+// pool_need entries and the expansion lists at least chunk_need chunks.
+// Growing frees the old arrays (cudaFree synchronises).
+nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_need)
 {
     nb_status st = NB_OK;
     nb::FmmView &f = c->fmm;
-    if (!f.meta) {
-        f.meta = dev_alloc<int>(c, nb::FMM_META_INTS, st);
-        if (st == NB_OK) f.stats = dev_alloc<unsigned long long>(c, 4, st);
-        if (st != NB_OK) return st;
-    }
+    if (!f.meta) f.meta = dev_alloc<int>(c, nb::FMM_META_INTS, st);
+    if (st == NB_OK && !f.stats) f.stats = dev_alloc<unsigned long long>(c, 4, st);
+    if (st == NB_OK && !f.crit) f.crit = dev_alloc<int>(c, nb::FMM_CRIT_INTS, st);
+    if (st != NB_OK) return st;
     const int np = nb::fmm_floats(order);
     const int cap = c->tree.cap;
     if (cap > c->fmm_cap || np > c->fmm_np) {
-        const long long keep_pool = f.pool_cap;
+        const long long keep_pool = f.pool_cap, keep_chunks = f.chunk_cap;
         free_fmm(c);
         const size_t m = (size_t)cap;
         f.ci = dev_alloc<int4>(c, m, st);
+        if (st == NB_OK) f.nd = dev_alloc<int4>(c, m, st);
         if (st == NB_OK) f.M = dev_alloc<float>(c, m * (size_t)np, st);
         if (st == NB_OK) f.L = dev_alloc<float>(c, m * (size_t)np, st);
         if (st == NB_OK) f.down = dev_alloc<int2>(c, m, st);
@@ -670,6 +674,7 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
         if (st == NB_OK) f.nearc = dev_alloc<int>(c, m, st);
         if (st == NB_OK) f.item_off = dev_alloc<int>(c, m + 1, st);
         if (st == NB_OK) f.part_off = dev_alloc<int>(c, m + 1, st);
+        if (st == NB_OK) f.chunk_head = dev_alloc<int>(c, m, st);
         if (st != NB_OK) {
             free_fmm(c);
             return st;
@@ -677,6 +682,23 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need)
         c->fmm_cap = cap;
         c->fmm_np = np;
         pool_need = std::max(pool_need, keep_pool);
+        chunk_need = std::max(chunk_need, keep_chunks);
+    }
+    if (chunk_need > f.chunk_cap) {
+        if (chunk_need > 0x7fffffffLL / nb::FMM_CHUNK)
+            return failf(c, NB_ENOMEM, "FMM expansion lists of %lld chunks too large", chunk_need);
+        cudaFree(f.chunk_src);
+        cudaFree(f.chunk_next);
+        f.chunk_next = nullptr;
+        f.chunk_src = dev_alloc<int>(c, (size_t)chunk_need * nb::FMM_CHUNK, st);
+        if (st == NB_OK) f.chunk_next = dev_alloc<int>(c, (size_t)chunk_need, st);
+        if (st != NB_OK) {
+            cudaFree(f.chunk_src);
+            f.chunk_src = nullptr;
+            f.chunk_cap = 0;
+            return st;
+        }
+        f.chunk_cap = chunk_need;
     }
     if (pool_need > f.pool_cap) {
         if (pool_need > 0x7fffffffLL)
@@ -867,9 +889,14 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
             return NB_OK;
         }
         if (attempt == 8) return failf(c, NB_ENOMEM, "FMM candidate lists keep overflowing");
-        const long long need = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_POOL],
-                                                   c->fmm.pool_cap) * 2;
-        NB_TRY(ensure_fmm(c, order, need));
+        // the counters hold what was asked for (past the end too); what the
+        // cut-short passes did not reach, the next attempt asks for
+        long long need = c->fmm.pool_cap, chunks = c->fmm.chunk_cap;
+        if (meta[nb::FMM_META_OVERFLOW] & 1)
+            need = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_POOL], need) * 2;
+        if (meta[nb::FMM_META_OVERFLOW] & 2)
+            chunks = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_CHUNKS], chunks) * 2;
+        NB_TRY(ensure_fmm(c, order, need, chunks));
     }
 }
 
@@ -1583,7 +1610,8 @@ nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *m
     if (counts) NB_TRY(check_dev(c, counts, (size_t)n * 3 * sizeof(int32_t), "counts"));
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
-    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max));
+    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max,
+                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max));
     return fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, counts);
 }
 
@@ -1607,7 +1635,8 @@ nb_status nb_fmm_step(nb_ctx *c, int64_t n, double *pos, double *vel, const doub
     NB_TRY(check_dev(c, acc, v3, "acc"));
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
-    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max));
+    NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max,
+                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max));
     if (!(flags & NB_ACC_VALID))
         NB_TRY(fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, nullptr));
     for (int64_t st = 0; st < nsteps; ++st) {
@@ -1628,11 +1657,17 @@ nb_status nb_fmm_reserve(nb_ctx *c, int64_t entries)
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
     nb::FmmView &f = c->fmm;
     cudaFree(f.pool);
-    f.pool = nullptr;
-    f.pool_cap = 0;
+    cudaFree(f.chunk_src);
+    cudaFree(f.chunk_next);
+    f.pool = f.chunk_src = f.chunk_next = nullptr;
+    f.pool_cap = f.chunk_cap = 0;
     nb_status st = NB_OK;
     f.pool = dev_alloc<int>(c, (size_t)entries, st);
     if (st == NB_OK) f.pool_cap = entries;
+    const long long chunks = entries / nb::FMM_CHUNK + 1;
+    if (st == NB_OK) f.chunk_src = dev_alloc<int>(c, (size_t)chunks * nb::FMM_CHUNK, st);
+    if (st == NB_OK) f.chunk_next = dev_alloc<int>(c, (size_t)chunks, st);
+    if (st == NB_OK) f.chunk_cap = chunks;
     return st;
 }
 
