@@ -835,8 +835,9 @@ def fmm_workload(args, ws, torch, dev, stream, T, flush):
     far_tf = st["expansions"] * m2l_flops(order) / (far_ms / 1e3) / 1e12
     near_tf = FLOPS_PER_INTERACTION * st["direct_pairs"] / (near_ms / 1e3) / 1e12
     phases = {
-        "far": {"kernels": "fmm_up_kernel, fmm_lists_kernel x 11 levels, fmm_m2l_kernel, "
-                           "fmm_l2l_kernel x 10 levels, fmm_items_kernel",
+        "far": {"kernels": "fmm_p2m_kernel, fmm_m2m_kernel x 10 levels, fmm_lists_kernel x 11 "
+                           "levels + 1 over the leaves, fmm_m2l_kernel, fmm_l2l_kernel x 10 "
+                           "levels, fmm_items_kernel",
                 "ms": far_ms, "expansions": st["expansions"], "achieved_tflops": far_tf,
                 "flops_per_expansion": m2l_flops(order)},
         "near": {"kernels": "fmm_near_kernel, fmm_combine_kernel", "ms": near_ms,

@@ -30,10 +30,11 @@
 // The derivatives use g = f(|r|^2/2), f^(m) = (-1)^m (2m-1)!! s^-(2m+1) and
 // d^n f_m = q_c d^(n-e_c) f_(m+1) + (n_c - 1) d^(n-2e_c) f_(m+1).
 //
-// Launches: one upward pass (P2M at the leaves, M2M climbing: the last child
-// to arrive sums its parent); one list launch per level (the candidates'
-// classification, the hand-down lists and each cell's list of separated
-// sources; leaves walk their candidates' subtrees); one M2L launch over all
+// Launches: the upward pass (P2M at the leaves in one launch, then M2M one
+// launch per level from the deepest up); one list launch per level over the
+// non-leaf cells (the candidates' classification, the hand-down lists and
+// each cell's list of separated sources), then one over all leaves (each
+// walks its candidates' subtrees for its list); one M2L launch over all
 // cells (one source per lane); one L2L launch per level below the root; and
 // one near-field launch over the leaves (the same walk collecting the
 // leaves to sum directly, float32x2 pair terms over sliced lanes, then L2P).
@@ -96,16 +97,22 @@ __device__ __forceinline__ void sfor(F &&f)
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 // ------------------------------------------------------------ kernel parts
-// T[q] = d^n g'(q) for the slots of order <= P, g' = (|q|^2 + e2)^-1/2.
+// T[q] = c0 sc^|n| d^n g'(q) for the slots of order <= P,
+// g' = (|q|^2 + e2)^-1/2, sc a power of two.  The factors ride on the
+// recursion: with W'[m][n] = c0 sc^|n| d^n f_m it reads
+// W'[m][n] = (sc q_c) W'[m+1][n-e_c] + (n_c - 1) sc^2 W'[m+1][n-2e_c]
+// from the seeds W'[m][0] = c0 f^(m).
 template <int P>
-__device__ __forceinline__ void derivs(float qx, float qy, float qz, float e2, float (&T)[nterms(P)])
+__device__ __forceinline__ void derivs(float qx, float qy, float qz, float e2, float sc, float c0,
+                                       float (&T)[nterms(P)])
 {
     constexpr int N = nterms(P);
-    float W[P + 1][N];  // W[m][slot] = d^n f_m, only m + |n| <= P
+    float W[P + 1][N];  // W[m][slot] = c0 sc^|n| d^n f_m, only m + |n| <= P
     const float s2 = fmaf(qz, qz, fmaf(qy, qy, fmaf(qx, qx, e2)));
     const float is = rsqrt_mufu(s2);
     const float is2 = is * is;
-    W[0][0] = is;
+    const float sx = sc * qx, sy = sc * qy, sz = sc * qz, sc2 = sc * sc;
+    W[0][0] = is * c0;
     sfor<1, P + 1>([&](auto mI) {
         constexpr int m = decltype(mI)::value;
         W[m][0] = -(float)(2 * m - 1) * W[m - 1][0] * is2;
@@ -118,11 +125,11 @@ __device__ __forceinline__ void derivs(float qx, float qy, float qz, float e2, f
         constexpr int q1 = slot_of(a - (ax == 0), b - (ax == 1), c - (ax == 2));
         constexpr int q2 =
             na >= 2 ? slot_of(a - 2 * (ax == 0), b - 2 * (ax == 1), c - 2 * (ax == 2)) : -1;
-        const float r = ax == 0 ? qx : (ax == 1 ? qy : qz);
+        const float r = ax == 0 ? sx : (ax == 1 ? sy : sz);
         sfor<0, P - k + 1>([&](auto mI) {
             constexpr int m = decltype(mI)::value;
             float v = r * W[m + 1][q1];
-            if constexpr (q2 >= 0) v = fmaf((float)(na - 1), W[m + 1][q2], v);
+            if constexpr (q2 >= 0) v = fmaf((float)(na - 1) * sc2, W[m + 1][q2], v);
             W[m][q] = v;
         });
     });
@@ -147,18 +154,10 @@ __device__ __forceinline__ void m2l_add(float (&acc)[nterms(P)], const float *__
     const int D2 = dx * dx + dy * dy + dz * dz;  // >= 1 for distinct cells
     const int E = (31 - __clz(D2)) >> 1;         // floor(log2 sqrt(D2))
     const float sc = pow2f(-E);
-    float T[N];
-    derivs<P>((float)dx * sc, (float)dy * sc, (float)dz * sc, K.eps2_h * sc * sc, T);
-    // U_m = sA^|m| T_m / rho, sA = e_A / rho = 2^(11 - L_A - E)
+    // U_m = sA^|m| T'_m / rho, sA = e_A / rho = 2^(11 - L_A - E), 1/rho = inv_h sc
     const float sA = pow2f(11 - cA.w - E);
-    float pa[P + 1];
-    pa[0] = K.inv_h * sc;
-#pragma unroll
-    for (int j = 1; j <= P; ++j) pa[j] = pa[j - 1] * sA;
-    sfor<0, N>([&](auto mI) {
-        constexpr int m = decltype(mI)::value;
-        T[m] *= pa[mi_of(m, 0) + mi_of(m, 1) + mi_of(m, 2)];
-    });
+    float T[N];
+    derivs<P>((float)dx * sc, (float)dy * sc, (float)dz * sc, K.eps2_h * sc * sc, sA, K.inv_h * sc, T);
     const float g = pow2f(cA.w - cB.w);
     float pg[P + 1];
     pg[0] = 1.0f;
@@ -280,11 +279,15 @@ __device__ __forceinline__ void store_exp(float *dst, const float (&v)[nterms(P)
 }
 
 // ------------------------------------------------------------ upward pass
-// A thread per leaf forms its moments from its bodies, then climbs: at each
-// parent it counts itself in, and only the last child to arrive goes on to
-// translate the children's moments (in child order) into the parent's.
+// P2M: a thread per leaf forms its moments from its bodies (the next body's
+// position loaded while this one's monomials are added).  M2M: one launch
+// per level from the deepest up, a warp per cell with children: a child per
+// lane translates the child's moments, and the lanes' terms are totalled in
+// a fixed order.
+constexpr int UP_WARPS = 4;
+
 template <int P>
-__global__ void __launch_bounds__(256) fmm_up_kernel(const FmmParams p)
+__global__ void __launch_bounds__(32 * UP_WARPS) fmm_p2m_kernel(const FmmParams p)
 {
     constexpr int N = nterms(P), NP = padded(P);
     const TreeView &t = p.tree;
@@ -296,43 +299,75 @@ __global__ void __launch_bounds__(256) fmm_up_kernel(const FmmParams p)
         if (t.nchild[leaf] != 0) continue;
         const int L = t.level[leaf];
         const int4 ci = icentre(t.prefix[leaf], L);
+        const int k0 = t.start[leaf], k1 = t.end[leaf];
         f.ci[leaf] = ci;
-        f.nd[leaf] = make_int4(0, t.first[leaf], t.start[leaf], t.end[leaf]);
+        f.nd[leaf] = make_int4(0, t.first[leaf], k0, k1);
         double z[3];
         centre_of(p.box, ci, z);
         const double inv_e = (double)(1 << L) / ext;
         float Mc[N];
 #pragma unroll
         for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
-        for (int k = t.start[leaf]; k < t.end[leaf]; ++k) {
-            const int j = p.perm[k];
-            const float m = (float)p.mass[j];
+        double x[3] = {0.0, 0.0, 0.0}, mj = 0.0;
+        if (k0 < k1) {
+            const int j = p.perm[k0];
+            x[0] = p.pos[3 * (size_t)j];
+            x[1] = p.pos[3 * (size_t)j + 1];
+            x[2] = p.pos[3 * (size_t)j + 2];
+            mj = p.mass[j];
+        }
+        for (int k = k0; k < k1; ++k) {
+            const float m = (float)mj;
             float pw[3][P + 1];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                scaled_powers<P>((float)((z[c] - p.pos[3 * (size_t)j + c]) * inv_e), pw[c]);
+            for (int c = 0; c < 3; ++c) scaled_powers<P>((float)((z[c] - x[c]) * inv_e), pw[c]);
+            if (k + 1 < k1) {
+                const int j = p.perm[k + 1];
+                x[0] = p.pos[3 * (size_t)j];
+                x[1] = p.pos[3 * (size_t)j + 1];
+                x[2] = p.pos[3 * (size_t)j + 2];
+                mj = p.mass[j];
+            }
             sfor<0, N>([&](auto qI) {
                 constexpr int q = decltype(qI)::value;
                 Mc[q] = fmaf(m * pw[0][mi_of(q, 0)], pw[1][mi_of(q, 1)] * pw[2][mi_of(q, 2)], Mc[q]);
             });
         }
         store_exp<P>(f.M + (size_t)leaf * NP, Mc);
-        for (int node = t.parent[leaf]; node >= 0; node = t.parent[node]) {
-            __threadfence();
-            if (atomicAdd(f.arrive + node, 1) != t.nchild[node] - 1) break;
-            __threadfence();
-            f.ci[node] = icentre(t.prefix[node], t.level[node]);
-            f.nd[node] = make_int4(t.nchild[node], t.first[node], t.start[node], t.end[node]);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * UP_WARPS) fmm_m2m_kernel(const FmmParams p, int L)
+{
+    constexpr int N = nterms(P), NP = padded(P);
+    const TreeView &t = p.tree;
+    const FmmView &f = p.f;
+    const int lane = threadIdx.x & 31;
+    const int cnt = t.meta[TREE_META_COUNT + L], base = t.meta[TREE_META_BASE + L];
+    for (int q0 = blockIdx.x * UP_WARPS + (threadIdx.x >> 5); q0 < cnt; q0 += gridDim.x * UP_WARPS) {
+        const int node = base + q0;
+        const int nch = t.nchild[node];
+        if (nch == 0) continue;
+        const int c0 = t.first[node];
+        float Mc[N];
 #pragma unroll
-            for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
-            const int c0 = t.first[node], nch = t.nchild[node];
-            for (int c = c0; c < c0 + nch; ++c) {
-                float xc[N];
-                const float *src = f.M + (size_t)c * NP;
+        for (int q = 0; q < N; ++q) Mc[q] = 0.0f;
+        if (lane < nch) {
+            float xc[N];
+            const float *src = f.M + (size_t)(c0 + lane) * NP;
 #pragma unroll
-                for (int q = 0; q < N; ++q) xc[q] = __ldcg(src + q);
-                translate_add<P, true>(Mc, xc, (int)(t.prefix[c] & 7u));
-            }
+            for (int q = 0; q < N; ++q) xc[q] = src[q];
+            translate_add<P, true>(Mc, xc, (int)(t.prefix[c0 + lane] & 7u));
+        }
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) Mc[q] += __shfl_down_sync(FULL, Mc[q], o);
+        }
+        if (lane == 0) {
+            f.ci[node] = icentre(t.prefix[node], L);
+            f.nd[node] = make_int4(nch, c0, t.start[node], t.end[node]);
             store_exp<P>(f.M + (size_t)node * NP, Mc);
         }
     }
@@ -523,6 +558,37 @@ __device__ __forceinline__ Consts consts_of(const FmmParams &p)
     return K;
 }
 
+// Append the first k entries of a warp's queue q (qcnt entries, at most 64)
+// as a chunk of 32 (pad past k) to a linked chunk list: `prev` is the
+// list's last chunk so far (-1 for none, then *head is set); a store that
+// is full sets `bit` in *overflow instead and drops the entries.
+template <class T>
+__device__ __forceinline__ void flush_chunk(T *q, int &qcnt, int k, T pad, T *store, int *next,
+                                            int *head, long long cap, int *ctr, int *overflow,
+                                            int bit, int &prev, int lane)
+{
+    int ch = 0;
+    if (lane == 0) ch = atomicAdd(ctr, 1);
+    ch = __shfl_sync(FULL, ch, 0);
+    if (ch < cap) {
+        store[32 * (size_t)ch + lane] = lane < k ? q[lane] : pad;
+        if (lane == 0) {
+            next[ch] = -1;
+            if (prev < 0)
+                *head = ch;
+            else
+                next[prev] = ch;
+        }
+        prev = ch;
+    } else if (lane == 0) {
+        atomicOr(overflow, bit);
+    }
+    __syncwarp();
+    if (lane < qcnt - k) q[lane] = q[k + lane];
+    qcnt -= k;
+    __syncwarp();
+}
+
 // ------------------------------------------------------------ downward pass
 // Three parts.  (1) Per level L, a warp per cell (dynamic) classifies the
 // candidates its parent handed down: a non-leaf hands the unseparated ones
@@ -670,28 +736,10 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
                 __syncwarp();
             }
             const int k = min(mcnt, 32);
-            if (k > 0) {
-                int ch = 0;
-                if (lane == 0) ch = atomicAdd(f.meta + FMM_META_CHUNKS, 1);
-                ch = __shfl_sync(FULL, ch, 0);
-                if (ch < f.chunk_cap) {
-                    f.chunk_src[32 * (size_t)ch + lane] = lane < k ? mq[warp][lane] : -1;
-                    if (lane == 0) {
-                        f.chunk_next[ch] = -1;
-                        if (prev < 0)
-                            f.chunk_head[A] = ch;
-                        else
-                            f.chunk_next[prev] = ch;
-                    }
-                    prev = ch;
-                } else if (lane == 0) {
-                    atomicOr(f.meta + FMM_META_OVERFLOW, 2);
-                }
-                __syncwarp();
-                if (lane < mcnt - k) mq[warp][lane] = mq[warp][k + lane];
-                mcnt -= k;
-                __syncwarp();
-            }
+            if (k > 0)
+                flush_chunk(mq[warp], mcnt, k, -1, f.chunk_src, f.chunk_next, f.chunk_head + A,
+                            f.chunk_cap, f.meta + FMM_META_CHUNKS, f.meta + FMM_META_OVERFLOW, 2,
+                            prev, lane);
         }
         if constexpr (LEAVES) {
             nearc = warp_sum(nearc);
@@ -1165,11 +1213,12 @@ cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, bool near, int 
     kernels = 0;
     cudaError_t e = cudaSuccess;
     if (!near) {
-        e = cudaMemsetAsync(p.f.arrive, 0, sizeof(int) * (size_t)p.tree.cap, s);
-        if (e != cudaSuccess) return e;
         fmm_init_kernel<P><<<1, 128, 0, s>>>(p.f, p.theta);
-        const int up_grid = (int)std::min<long long>(4096, ((long long)p.tree.cap + 255) / 256);
-        fmm_up_kernel<P><<<up_grid, 256, 0, s>>>(p);
+        const int p2m_grid = (int)std::min<long long>(
+            8 * p.num_sms, ((long long)p.tree.cap + 32 * UP_WARPS - 1) / (32 * UP_WARPS));
+        fmm_p2m_kernel<P><<<p2m_grid, 32 * UP_WARPS, 0, s>>>(p);
+        for (int L = LEVELS - 2; L >= 0; --L)
+            fmm_m2m_kernel<P><<<8 * p.num_sms, 32 * UP_WARPS, 0, s>>>(p, L);
         const int lists_grid = resident_grid(fmm_lists_kernel<P, true>, 32 * WARPS, p.num_sms, e);
         if (e != cudaSuccess) return e;
         const int m2l_grid = resident_grid(fmm_m2l_kernel<P>, 32 * WARPS, p.num_sms, e);
@@ -1180,7 +1229,7 @@ cudaError_t launch_fmm_order(cudaStream_t s, const FmmParams &p, bool near, int 
         fmm_m2l_kernel<P><<<m2l_grid, 32 * WARPS, 0, s>>>(p);
         for (int L = 1; L < LEVELS; ++L) fmm_l2l_kernel<P><<<2 * p.num_sms, 128, 0, s>>>(p, L);
         fmm_items_kernel<P><<<1, 1024, 0, s>>>(p);
-        kernels = 5 + 2 * LEVELS - 1;
+        kernels = 5 + 3 * LEVELS - 2;
         return cudaGetLastError();
     }
     const bool zeps = p.eps2f == 0.0f;

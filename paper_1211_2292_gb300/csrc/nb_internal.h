@@ -267,7 +267,6 @@ struct FmmView {
     float *M, *L;          // [cap][np]: scaled moments, scaled local coefficients
     int2 *down;            // per node: (offset, count) in pool of the candidates handed to its children
     int2 *cum;             // per node: source cells acting on it and its ancestors, bodies they hold
-    int *arrive;           // upward-pass arrival counters (zeroed before each pass)
     int *leaves;           // leaf ids, in the order the downward pass meets them
     int *nearc;            // per node (leaves): bodies met directly
     int *item_off;         // per leaf index: first near-field work item (exclusive scan)

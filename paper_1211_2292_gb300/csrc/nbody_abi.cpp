@@ -513,13 +513,13 @@ void free_fmm(nb_ctx *c)
 {
     nb::FmmView &f = c->fmm;
     void *arrays[] = {f.ci,       f.nd,       f.M,      f.L,        f.down,     f.cum,
-                      f.arrive,   f.leaves,   f.nearc,  f.item_off, f.part_off,
+                      f.leaves,   f.nearc,    f.item_off, f.part_off,
                       f.part,     f.pool,     f.chunk_head, f.chunk_src, f.chunk_next};
     for (void *a : arrays) cudaFree(a);
     f.ci = f.nd = nullptr;
     f.M = f.L = nullptr;
     f.down = f.cum = nullptr;
-    f.arrive = f.leaves = f.nearc = f.item_off = f.part_off = f.pool = nullptr;
+    f.leaves = f.nearc = f.item_off = f.part_off = f.pool = nullptr;
     f.chunk_head = f.chunk_src = f.chunk_next = nullptr;
     f.part = nullptr;
     f.pool_cap = f.part_cap = f.chunk_cap = 0;
@@ -645,6 +645,32 @@ nb_status check_tree_args(nb_ctx *c, double theta, int leaf_cap, int group)
     return NB_OK;
 }
 
+// Chunked list store (chunks of FMM_CHUNK entries and their links) of at
+// least `need` chunks.
+template <class T>
+nb_status ensure_chunks(nb_ctx *c, long long need, T *&store, int *&next, long long &cap,
+                        const char *what)
+{
+    if (need <= cap) return NB_OK;
+    if (need > 0x7fffffffLL / nb::FMM_CHUNK)
+        return failf(c, NB_ENOMEM, "FMM %s of %lld chunks too large", what, need);
+    cudaFree(store);
+    cudaFree(next);
+    store = nullptr;
+    next = nullptr;
+    cap = 0;
+    nb_status st = NB_OK;
+    store = dev_alloc<T>(c, (size_t)need * nb::FMM_CHUNK, st);
+    if (st == NB_OK) next = dev_alloc<int>(c, (size_t)need, st);
+    if (st != NB_OK) {
+        cudaFree(store);
+        store = nullptr;
+        return st;
+    }
+    cap = need;
+    return NB_OK;
+}
+
 // Expansion, list and candidate-pool scratch of the fast multipole method
 // for the tree's node capacity and `order`; the pool holds at least
 // pool_need entries and the expansion lists at least chunk_need chunks.
@@ -669,7 +695,6 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_
         if (st == NB_OK) f.L = dev_alloc<float>(c, m * (size_t)np, st);
         if (st == NB_OK) f.down = dev_alloc<int2>(c, m, st);
         if (st == NB_OK) f.cum = dev_alloc<int2>(c, m, st);
-        if (st == NB_OK) f.arrive = dev_alloc<int>(c, m, st);
         if (st == NB_OK) f.leaves = dev_alloc<int>(c, m, st);
         if (st == NB_OK) f.nearc = dev_alloc<int>(c, m, st);
         if (st == NB_OK) f.item_off = dev_alloc<int>(c, m + 1, st);
@@ -684,22 +709,7 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_
         pool_need = std::max(pool_need, keep_pool);
         chunk_need = std::max(chunk_need, keep_chunks);
     }
-    if (chunk_need > f.chunk_cap) {
-        if (chunk_need > 0x7fffffffLL / nb::FMM_CHUNK)
-            return failf(c, NB_ENOMEM, "FMM expansion lists of %lld chunks too large", chunk_need);
-        cudaFree(f.chunk_src);
-        cudaFree(f.chunk_next);
-        f.chunk_next = nullptr;
-        f.chunk_src = dev_alloc<int>(c, (size_t)chunk_need * nb::FMM_CHUNK, st);
-        if (st == NB_OK) f.chunk_next = dev_alloc<int>(c, (size_t)chunk_need, st);
-        if (st != NB_OK) {
-            cudaFree(f.chunk_src);
-            f.chunk_src = nullptr;
-            f.chunk_cap = 0;
-            return st;
-        }
-        f.chunk_cap = chunk_need;
-    }
+    NB_TRY(ensure_chunks(c, chunk_need, f.chunk_src, f.chunk_next, f.chunk_cap, "expansion lists"));
     if (pool_need > f.pool_cap) {
         if (pool_need > 0x7fffffffLL)
             return failf(c, NB_ENOMEM, "FMM candidate lists of %lld entries too large", pool_need);
@@ -892,10 +902,9 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
         // the counters hold what was asked for (past the end too); what the
         // cut-short passes did not reach, the next attempt asks for
         long long need = c->fmm.pool_cap, chunks = c->fmm.chunk_cap;
-        if (meta[nb::FMM_META_OVERFLOW] & 1)
-            need = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_POOL], need) * 2;
-        if (meta[nb::FMM_META_OVERFLOW] & 2)
-            chunks = std::max<long long>((long long)(unsigned)meta[nb::FMM_META_CHUNKS], chunks) * 2;
+        const int over = meta[nb::FMM_META_OVERFLOW];
+        if (over & 1) need = std::max<long long>((unsigned)meta[nb::FMM_META_POOL], need) * 2;
+        if (over & 2) chunks = std::max<long long>((unsigned)meta[nb::FMM_META_CHUNKS], chunks) * 2;
         NB_TRY(ensure_fmm(c, order, need, chunks));
     }
 }
@@ -1656,19 +1665,16 @@ nb_status nb_fmm_reserve(nb_ctx *c, int64_t entries)
         return failf(c, NB_EINVAL, "pool of %lld entries outside [1, 2^31)", (long long)entries);
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
     nb::FmmView &f = c->fmm;
-    cudaFree(f.pool);
-    cudaFree(f.chunk_src);
-    cudaFree(f.chunk_next);
+    void *old[] = {f.pool, f.chunk_src, f.chunk_next};
+    for (void *a : old) cudaFree(a);
     f.pool = f.chunk_src = f.chunk_next = nullptr;
     f.pool_cap = f.chunk_cap = 0;
     nb_status st = NB_OK;
     f.pool = dev_alloc<int>(c, (size_t)entries, st);
-    if (st == NB_OK) f.pool_cap = entries;
+    if (st != NB_OK) return st;
+    f.pool_cap = entries;
     const long long chunks = entries / nb::FMM_CHUNK + 1;
-    if (st == NB_OK) f.chunk_src = dev_alloc<int>(c, (size_t)chunks * nb::FMM_CHUNK, st);
-    if (st == NB_OK) f.chunk_next = dev_alloc<int>(c, (size_t)chunks, st);
-    if (st == NB_OK) f.chunk_cap = chunks;
-    return st;
+    return ensure_chunks(c, chunks, f.chunk_src, f.chunk_next, f.chunk_cap, "expansion lists");
 }
 
 nb_status nb_fmm_stats(nb_ctx *c, int64_t *out)
