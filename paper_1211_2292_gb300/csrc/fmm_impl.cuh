@@ -620,14 +620,11 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
     const int base = LEAVES ? 0 : t.meta[TREE_META_BASE + L];
     int *queue = f.meta + (LEAVES ? FMM_META_LEAVES_Q : FMM_META_LEVEL + L);
     WalkSh &w = wsh[warp];
-    for (;;) {
-        int qi = 0;
-        if (lane == 0) qi = atomicAdd(queue, 1);
-        qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= cnt) break;
+    // one cell: its list (and, for a non-leaf, its hand-down list)
+    auto visit = [&](int qi) {
         const int A = base + qi;
         const int nchA = t.nchild[A];
-        if ((nchA == 0) != LEAVES) continue;  // the other kernel's cell
+        if ((nchA == 0) != LEAVES) return;  // the other kernel's cell
         const int4 cA = f.ci[A];
         const int par = t.parent[A];
         int inh_off = 0, inh_cnt = 1;  // the root's list: pool[0] = 0
@@ -760,6 +757,27 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
             if (own) atomicAdd(f.stats + 2, (unsigned long long)own);
         }
         __syncwarp();
+    };
+    if constexpr (LEAVES) {
+        // a block's warps take neighbouring cells together: their walks meet
+        // mostly the same nodes, which the later ones then find in L1
+        __shared__ int blk_base;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) blk_base = atomicAdd(queue, WARPS);
+            __syncthreads();
+            const int b0 = blk_base;
+            if (b0 >= cnt) break;
+            if (b0 + warp < cnt) visit(b0 + warp);
+        }
+    } else {
+        for (;;) {
+            int qi = 0;
+            if (lane == 0) qi = atomicAdd(queue, 1);
+            qi = __shfl_sync(FULL, qi, 0);
+            if (qi >= cnt) break;
+            visit(qi);
+        }
     }
 }
 
