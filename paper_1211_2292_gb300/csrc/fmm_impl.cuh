@@ -758,26 +758,17 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
         }
         __syncwarp();
     };
-    if constexpr (LEAVES) {
-        // a block's warps take neighbouring cells together: their walks meet
-        // mostly the same nodes, which the later ones then find in L1
-        __shared__ int blk_base;
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) blk_base = atomicAdd(queue, WARPS);
-            __syncthreads();
-            const int b0 = blk_base;
-            if (b0 >= cnt) break;
-            if (b0 + warp < cnt) visit(b0 + warp);
-        }
-    } else {
-        for (;;) {
-            int qi = 0;
-            if (lane == 0) qi = atomicAdd(queue, 1);
-            qi = __shfl_sync(FULL, qi, 0);
-            if (qi >= cnt) break;
-            visit(qi);
-        }
+    // a block's warps take neighbouring cells together: their candidates
+    // (siblings share their parent's hand-down list) and walks meet mostly
+    // the same nodes, which the later ones then find in L1
+    __shared__ int blk_base;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) blk_base = atomicAdd(queue, WARPS);
+        __syncthreads();
+        const int b0 = blk_base;
+        if (b0 >= cnt) break;
+        if (b0 + warp < cnt) visit(b0 + warp);
     }
 }
 
