@@ -558,18 +558,27 @@ __device__ __forceinline__ Consts consts_of(const FmmParams &p)
     return K;
 }
 
+// Chunks a warp reserves at a time (one atomic per batch rather than per
+// chunk: the atomic's round trip was on every flush's path).
+constexpr int CHUNK_BATCH = 16;
+
 // Append the first k entries of a warp's queue q (qcnt entries, at most 64)
 // as a chunk of 32 (pad past k) to a linked chunk list: `prev` is the
-// list's last chunk so far (-1 for none, then *head is set); a store that
-// is full sets `bit` in *overflow instead and drops the entries.
+// list's last chunk so far (-1 for none, then *head is set); the chunk comes
+// from the warp's reserved range [cnext, cend), refilled from *ctr; a store
+// that is full sets `bit` in *overflow instead and drops the entries.
 template <class T>
 __device__ __forceinline__ void flush_chunk(T *q, int &qcnt, int k, T pad, T *store, int *next,
                                             int *head, long long cap, int *ctr, int *overflow,
-                                            int bit, int &prev, int lane)
+                                            int bit, int &prev, int &cnext, int &cend, int lane)
 {
-    int ch = 0;
-    if (lane == 0) ch = atomicAdd(ctr, 1);
-    ch = __shfl_sync(FULL, ch, 0);
+    if (cnext == cend) {
+        int r = 0;
+        if (lane == 0) r = atomicAdd(ctr, CHUNK_BATCH);
+        cnext = __shfl_sync(FULL, r, 0);
+        cend = cnext + CHUNK_BATCH;
+    }
+    const int ch = cnext++;
     if (ch < cap) {
         store[32 * (size_t)ch + lane] = lane < k ? q[lane] : pad;
         if (lane == 0) {
@@ -620,6 +629,7 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
     const int base = LEAVES ? 0 : t.meta[TREE_META_BASE + L];
     int *queue = f.meta + (LEAVES ? FMM_META_LEAVES_Q : FMM_META_LEVEL + L);
     WalkSh &w = wsh[warp];
+    int cnext = 0, cend = 0;  // this warp's reserved expansion-list chunks
     // one cell: its list (and, for a non-leaf, its hand-down list)
     auto visit = [&](int qi) {
         const int A = base + qi;
@@ -736,7 +746,7 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
             if (k > 0)
                 flush_chunk(mq[warp], mcnt, k, -1, f.chunk_src, f.chunk_next, f.chunk_head + A,
                             f.chunk_cap, f.meta + FMM_META_CHUNKS, f.meta + FMM_META_OVERFLOW, 2,
-                            prev, lane);
+                            prev, cnext, cend, lane);
         }
         if constexpr (LEAVES) {
             nearc = warp_sum(nearc);
