@@ -800,11 +800,13 @@ __global__ void __launch_bounds__(32 * WARPS, m2l_min_blocks<P>()) fmm_m2l_kerne
     const Consts K = consts_of(p);
     const int lane = threadIdx.x & 31;
     const int total = t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10];
+    // the next cell's queue ticket is taken while this one's expansions run
+    int ticket = 0;
+    if (lane == 0) ticket = atomicAdd(f.meta + FMM_META_M2L, 1);
     for (;;) {
-        int qi = 0;
-        if (lane == 0) qi = atomicAdd(f.meta + FMM_META_M2L, 1);
-        qi = __shfl_sync(FULL, qi, 0);
+        const int qi = __shfl_sync(FULL, ticket, 0);
         if (qi >= total) break;
+        if (lane == 0) ticket = atomicAdd(f.meta + FMM_META_M2L, 1);
         const int A = total - 1 - qi;
         float acc[N];
 #pragma unroll
