@@ -47,7 +47,7 @@ constexpr int TTPB = 256;
 #define NB_WALK_MINB1 8
 #endif
 #ifndef NB_WALK_MINB2
-#define NB_WALK_MINB2 7
+#define NB_WALK_MINB2 6
 #endif
 constexpr int WALK_WARPS = NB_WALK_WARPS;
 
