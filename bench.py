@@ -585,9 +585,15 @@ def measure_forms(torch, dev, tune, table, peak_tflops, tree_bodies=None, tuning
                       "ms_per_eval": build + far + near, "build_ms": build, "far_ms": far,
                       "near_ms": near, "expansions": st["expansions"],
                       "direct_pairs": st["direct_pairs"],
+                      "far_frac_of_fp32_peak": st["expansions"] * m2l_flops(f_["order"])
+                      / (far / 1e3) / 1e12 / peak_tflops,
+                      "near_frac_of_fp32_peak": FLOPS_PER_INTERACTION * st["direct_pairs"]
+                      / (near / 1e3) / 1e12 / peak_tflops,
                       "bodies_per_s": n / ((build + far + near) / 1e3) / 1e9, "unit": FMM_UNIT,
                       "note": "one tree build + fast multipole evaluation of the throughput "
-                              "workload's bodies; error and parity in bench.py --workload fmm"}
+                              "workload's bodies; far: flops of the expansions' contractions "
+                              f"({m2l_flops(f_['order'])} each), near: 20 per pair; error and "
+                              "parity in bench.py --workload fmm"}
     return out
 
 

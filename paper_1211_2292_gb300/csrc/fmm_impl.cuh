@@ -923,18 +923,17 @@ __global__ void __launch_bounds__(1024) fmm_items_kernel(FmmParams p)
     }
 }
 
-// G (near + far) into acc for the body at tree rank k of leaf A; the far
-// field is the gradient of A's local expansion (L2P).
+// G (near + far) into acc for the body at tree rank k of leaf A (centre z,
+// inverse edge inv_e); the far field is the gradient of A's local expansion
+// (L2P).
 template <int P>
-__device__ __forceinline__ void write_body(const FmmParams &p, int A, int4 cA, int k, double nx,
-                                           double ny, double nz, int nnear)
+__device__ __forceinline__ void write_body(const FmmParams &p, int A, const double (&z)[3],
+                                           double inv_e, int k, double nx, double ny, double nz,
+                                           int nnear)
 {
     constexpr int NP = padded(P);
     const FmmView &f = p.f;
-    double z[3];
-    centre_of(p.box, cA, z);
     const float *Lc = f.L + (size_t)A * NP;
-    const double inv_e = (double)(1 << cA.w) / p.box[3];
     const int i = p.perm[k];
     float pw[3][P + 1];
 #pragma unroll
@@ -1155,12 +1154,13 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
                 ns3[b][c] = v;
             }
         if (slice == 0) {
+            const double inv_e = (double)(1 << cA.w) / p.box[3];
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 if (!(b == 0 ? v0 : v1)) continue;
                 const int k = s0 + b0 + T * b;
                 if (ns == 1) {
-                    write_body<P>(p, A, cA, k, ns3[b][0], ns3[b][1], ns3[b][2], nearc);
+                    write_body<P>(p, A, z, inv_e, k, ns3[b][0], ns3[b][1], ns3[b][2], nearc);
                 } else {
                     double *d = f.part + 3 * ((size_t)f.part_off[qi] + (size_t)sc * nbt +
                                               (size_t)(k - t.start[A]));
@@ -1193,6 +1193,9 @@ __global__ void __launch_bounds__(256) fmm_combine_kernel(const FmmParams p)
         const int4 cA = f.ci[A];
         const int nbt = t.end[A] - t.start[A];
         const double *base = f.part + 3 * (size_t)f.part_off[qi];
+        double z[3];
+        centre_of(p.box, cA, z);
+        const double inv_e = (double)(1 << cA.w) / p.box[3];
         for (int b = lane; b < nbt; b += 32) {
             double s[3] = {0.0, 0.0, 0.0};
             for (int sc = 0; sc < ns; ++sc) {
@@ -1201,7 +1204,7 @@ __global__ void __launch_bounds__(256) fmm_combine_kernel(const FmmParams p)
                 s[1] += d[1];
                 s[2] += d[2];
             }
-            write_body<P>(p, A, cA, t.start[A] + b, s[0], s[1], s[2], nearc);
+            write_body<P>(p, A, z, inv_e, t.start[A] + b, s[0], s[1], s[2], nearc);
         }
     }
 }
