@@ -170,6 +170,16 @@ struct TreeView {
     float4 *chi, *clo;    // centre of mass hi/lo float32 pair; chi.w = mass
     unsigned long long *stats;  // [4] nodes, leaves, cell and body interactions
 };
+// A further tree walked after TreeWalkParams::tree in the same launch (a
+// received LET): its walk data, the bodies its leaves index, its cube.
+struct WalkSource {
+    const float4 *box_lo, *box_hi, *chi, *clo;
+    const int *start, *end;
+    const float4 *sP, *sPlo;
+    const double *box;
+};
+constexpr int WALK_MAX_MORE = 63;  // further trees per launch
+
 struct TreeWalkParams {
     TreeView tree;          // the tree walked (the targets' own, or a received LET)
     const float4 *P, *Plo;  // target bodies in their own tree's order, float32 hi/lo
@@ -188,6 +198,8 @@ struct TreeWalkParams {
     double half_dt;
     int *counts;            // optional [n][2]: cells, bodies met per body
     int *err;
+    const WalkSource *more;  // device [nmore]: trees walked after `tree`, their sums added
+    int nmore;               // in order (as separate accumulating walks would), 0..WALK_MAX_MORE
 };
 int tree_meta_ints();
 // Upper bound on the node count of a tree over n bodies with leaves of at
@@ -438,6 +450,7 @@ struct nb_ctx {
     int let_cap = 0;
     float *let_box = nullptr;               // 6 floats out + 6 unsigned of work
     int *let_queue = nullptr;               // group queue of the LET walks
+    nb::WalkSource *let_src = nullptr;      // [WALK_MAX_MORE] the received trees of one walk
     int64_t let_n = 0;                      // bodies of the local tree of nb_let_build
 
     std::map<const void *, int> occ;  // resident CTAs per SM, per kernel

@@ -568,6 +568,7 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->let.totals);
     cudaFree(c->let_box);
     cudaFree(c->let_queue);
+    cudaFree(c->let_src);
     if (c->host_out) cudaFreeHost(c->host_out);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -815,6 +816,8 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
     p.half_dt = half_dt;
     p.counts = counts;
     p.err = c->err;
+    p.more = nullptr;
+    p.nmore = 0;
     TreeTimer tm(c, nb::PROF_TREE_WALK, s);
     NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
     c->launches += k;
@@ -1757,6 +1760,7 @@ nb_status ensure_let(nb_ctx *c)
     nb_status st = NB_OK;
     if (!c->let_box) c->let_box = dev_alloc<float>(c, 12, st);
     if (st == NB_OK && !c->let_queue) c->let_queue = dev_alloc<int>(c, 1, st);
+    if (st == NB_OK && !c->let_src) c->let_src = dev_alloc<nb::WalkSource>(c, nb::WALK_MAX_MORE, st);
     if (st == NB_OK && !c->let.totals) c->let.totals = dev_alloc<int>(c, 2, st);
     if (st != NB_OK) return st;
     if (c->let_cap < c->tree.cap) {
@@ -1775,11 +1779,12 @@ nb_status ensure_let(nb_ctx *c)
     return NB_OK;
 }
 
-// One walk over tree view t with sources (sP, sPlo) and box, onto the
-// context's local bodies.
+// One walk launch over tree view t with sources (sP, sPlo) and box, then
+// the nmore trees at more (device), onto the context's local bodies.
 nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float4 *sP,
-                   const float4 *sPlo, const double *box, double G, double eps, double theta,
-                   int group, double *acc, int *counts, int accumulate)
+                   const float4 *sPlo, const double *box, const nb::WalkSource *more,
+                   int nmore, double G, double eps, double theta, int group, double *acc,
+                   int *counts, int accumulate)
 {
     NB_CUDA(c, cudaMemsetAsync(c->let_queue, 0, sizeof(int), s));
     nb::TreeWalkParams p;
@@ -1805,6 +1810,8 @@ nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float
     p.half_dt = 0.0;
     p.counts = counts;
     p.err = c->err;
+    p.more = more;
+    p.nmore = nmore;
     int k = 0;
     TreeTimer tm(c, nb::PROF_TREE_WALK, s);
     NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
@@ -2050,25 +2057,43 @@ nb_status nb_let_forces(nb_ctx *c, double G, double eps, double theta, int group
     }
     NB_TRY(ensure_let(c));
     NB_CUDA(c, cudaMemsetAsync(c->tree.stats + 2, 0, 2 * sizeof(unsigned long long), s));
-    // the local tree first, then the received ones in order
-    NB_TRY(let_walk(c, s, c->tree, c->tree_P, c->tree_Plo, c->tree_box, G, eps, theta, group, acc,
-                    counts, 0));
+    // the local tree first, then the received ones in order: the local tree
+    // and up to WALK_MAX_MORE received ones per launch
+    std::vector<nb::WalkSource> src((size_t)nlet);
     for (int64_t q = 0; q < nlet; ++q) {
         const nb::LetHeader &h = hdr[(size_t)q];
         const nb::LetLayout lay = nb::let_layout(h.n_nodes, h.n_bodies);
         const unsigned char *b = static_cast<const unsigned char *>(lets[q]);
+        src[(size_t)q] = nb::WalkSource{(const float4 *)(b + lay.lo),  (const float4 *)(b + lay.hi),
+                                        (const float4 *)(b + lay.chi), (const float4 *)(b + lay.clo),
+                                        (const int *)(b + lay.start),  (const int *)(b + lay.end),
+                                        (const float4 *)(b + lay.P),   (const float4 *)(b + lay.Plo),
+                                        (const double *)(b + offsetof(nb::LetHeader, box))};
+    }
+    const int first = (int)std::min<int64_t>(nlet, nb::WALK_MAX_MORE);
+    if (first > 0)  // from pageable memory: staged before the call returns
+        NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data(), first * sizeof(nb::WalkSource),
+                                   cudaMemcpyHostToDevice, s));
+    NB_TRY(let_walk(c, s, c->tree, c->tree_P, c->tree_Plo, c->tree_box, c->let_src, first, G, eps,
+                    theta, group, acc, counts, 0));
+    for (int64_t q0 = first; q0 < nlet; q0 += 1 + nb::WALK_MAX_MORE) {
+        // a further launch: tree q0, then up to WALK_MAX_MORE more, added on
+        const int more = (int)std::min<int64_t>(nlet - q0 - 1, nb::WALK_MAX_MORE);
+        if (more > 0)
+            NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data() + q0 + 1,
+                                       more * sizeof(nb::WalkSource), cudaMemcpyHostToDevice, s));
+        const nb::WalkSource &w = src[(size_t)q0];
         nb::TreeView t{};
-        t.cap = (int)h.n_nodes;
-        t.box_lo = (float4 *)(b + lay.lo);
-        t.box_hi = (float4 *)(b + lay.hi);
-        t.chi = (float4 *)(b + lay.chi);
-        t.clo = (float4 *)(b + lay.clo);
-        t.start = (int *)(b + lay.start);
-        t.end = (int *)(b + lay.end);
+        t.cap = (int)hdr[(size_t)q0].n_nodes;
+        t.box_lo = const_cast<float4 *>(w.box_lo);
+        t.box_hi = const_cast<float4 *>(w.box_hi);
+        t.chi = const_cast<float4 *>(w.chi);
+        t.clo = const_cast<float4 *>(w.clo);
+        t.start = const_cast<int *>(w.start);
+        t.end = const_cast<int *>(w.end);
         t.stats = c->tree.stats;
-        NB_TRY(let_walk(c, s, t, (const float4 *)(b + lay.P), (const float4 *)(b + lay.Plo),
-                        (const double *)(b + offsetof(nb::LetHeader, box)), G, eps, theta, group,
-                        acc, counts, 1));
+        NB_TRY(let_walk(c, s, t, w.sP, w.sPlo, w.box, c->let_src, more, G, eps, theta, group, acc,
+                        counts, 1));
     }
     return NB_OK;
 }

@@ -425,27 +425,26 @@ __device__ __forceinline__ int warp_span_of(int incl, int pos)
 // body.  Each level's stack holds at most 32 ranges, the children of one
 // round's nodes, since a level is refilled only once every deeper level is
 // empty.  Whenever FLUSH sources are listed, every lane adds them to its bodies.
-template <int BPL>
+template <int BPL, bool MULTI>
 struct WalkShared {
     float4 list[WALK_WARPS][LIST_CAP * BPL];  // float4 slots of the lists
     int2 ranges[WALK_WARPS][LEVELS][32];
-    float crit2[LEVELS];
+    float crit2[MULTI ? 1 + WALK_MAX_MORE : 1][LEVELS];  // per walked tree
 };
 
 // The walk of group g (bodies [g * 32 * BPL, ...) in key order) by one warp.
-template <bool ZEPS, int BPL>
-__device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<BPL> &sh, int g)
+template <bool ZEPS, int BPL, bool MULTI>
+__device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<BPL, MULTI> &sh,
+                                           int g)
 {
     constexpr int GROUP = 32 * BPL;
     constexpr int LIST_F4 = LIST_CAP * BPL;
-    const TreeView &t = p.tree;
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n;
     const int base = g * GROUP;
     if (base >= n) return;  // whole warp past the end
     const int nvalid = min(GROUP, n - base);
-    const float *crit2 = sh.crit2;
     float4(*list_s)[LIST_F4] = sh.list;
 
     bool valid[BPL];
@@ -506,6 +505,21 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
     int2(*rs)[32] = sh.ranges[warp];
     const unsigned lt = (1u << lane) - 1u;
 
+    // Each tree's sum per body, G (s - c) from its Kahan pair, added in tree
+    // order in float64 (as separate accumulating walks would add them).
+    double tg[BPL][3];
+    int nc = 0, nb = 0;
+    const int ntrees = MULTI ? 1 + p.nmore : 1;
+    for (int tq = 0; tq < ntrees; ++tq) {
+    WalkSource t;
+    if (!MULTI || tq == 0) {
+        t = WalkSource{p.tree.box_lo, p.tree.box_hi, p.tree.chi, p.tree.clo,
+                       p.tree.start,  p.tree.end,    p.sP,      p.sPlo,
+                       p.box};
+    } else {
+        t = p.more[tq - 1];
+    }
+    const float *crit2 = sh.crit2[MULTI ? tq : 0];
     float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
     // Kahan (sum, carry) per body and axis: BPL = 1 folds both halves of the
     // float32x2 accumulators into one body; BPL = 2 keeps .x and .y apart.
@@ -543,7 +557,6 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         __syncwarp();
     };
 
-    int nc = 0, nb = 0;
     int lsize = lane == 0 ? 1 : 0;  // lane L holds the size of level L's stack
     if (lane == 0) rs[0][0] = make_int2(0, 1);
     __syncwarp();
@@ -641,7 +654,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
                 const int body = __shfl_sync(FULL, ls, j & 31) + (pos - __shfl_sync(FULL, lexc, j & 31));
                 const int kk = min(32, T - c0);
                 if (lane < kk) {
-                    const float4 bh = __ldg(p.sP + body), bl = __ldg(p.sPlo + body);
+                    const float4 bh = __ldg(t.sP + body), bl = __ldg(t.sPlo + body);
                     list_put<BPL>(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
                                   rel(bh.z, bl.z, cz), bh.w);
                 }
@@ -656,13 +669,21 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         list_eval<ZEPS, BPL>(L4, BPL == 1 ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay, az);
         fold();
     }
+    __syncwarp();  // the next tree reuses this warp's list and stacks
+#pragma unroll
+    for (int b = 0; b < BPL; ++b) {
+        const double d[3] = {p.G * ((double)sx[b] - (double)qx[b]),
+                             p.G * ((double)sy[b] - (double)qy[b]),
+                             p.G * ((double)sz[b] - (double)qz[b])};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tg[b][c] = (!MULTI || tq == 0) ? d[c] : __dadd_rn(tg[b][c], d[c]);
+    }
+    }  // trees
 #pragma unroll
     for (int b = 0; b < BPL; ++b) {
         if (!valid[b]) continue;
         const int i = p.perm[base + 32 * b + lane];
-        const double gx = p.G * ((double)sx[b] - (double)qx[b]);
-        const double gy = p.G * ((double)sy[b] - (double)qy[b]);
-        const double gz = p.G * ((double)sz[b] - (double)qz[b]);
+        const double gx = tg[b][0], gy = tg[b][1], gz = tg[b][2];
         double *a = p.acc + 3 * (size_t)i;
         if (p.accumulate) {  // a further tree's share (a received LET)
             a[0] += gx;
@@ -690,8 +711,8 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
     }
     if (lane == 0) {  // nc, nb are the same for the group's nvalid bodies
-        atomicAdd(t.stats + 2, (unsigned long long)nc * nvalid);
-        atomicAdd(t.stats + 3, (unsigned long long)nb * nvalid);
+        atomicAdd(p.tree.stats + 2, (unsigned long long)nc * nvalid);
+        atomicAdd(p.tree.stats + 3, (unsigned long long)nb * nvalid);
     }
     __syncwarp();  // the next group reuses this warp's lists and stacks
 }
@@ -701,17 +722,20 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
 // grid covering all groups; dynamic, a grid of resident warps taking `chunk`
 // groups at a time from an atomic counter; guided, the same with chunks of
 // max(chunk, remaining / (2 x warps)).
-template <bool ZEPS, int BPL>
+template <bool ZEPS, int BPL, bool MULTI>
 __global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB_WALK_MINB2)
     tree_walk_kernel(const TreeWalkParams p)
 {
-    __shared__ WalkShared<BPL> sh;
-    if (threadIdx.x < LEVELS) sh.crit2[threadIdx.x] = open_dist2(p.box[3], threadIdx.x, p.theta);
+    __shared__ WalkShared<BPL, MULTI> sh;
+    for (int q = threadIdx.x; q < (MULTI ? 1 + p.nmore : 1) * LEVELS; q += blockDim.x) {
+        const int tq = q / LEVELS, L = q % LEVELS;
+        sh.crit2[tq][L] = open_dist2(tq == 0 ? p.box[3] : p.more[tq - 1].box[3], L, p.theta);
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WALK_WARPS + warp;
     if (p.sched == 0) {
-        walk_group<ZEPS, BPL>(p, sh, gw);
+        walk_group<ZEPS, BPL, MULTI>(p, sh, gw);
         return;
     }
     const int ngroups = (p.n + 32 * BPL - 1) / (32 * BPL);
@@ -727,7 +751,7 @@ __global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB
         if (g0 >= ngroups) break;
         seen = g0 + c;
         const int g1 = min(g0 + c, ngroups);
-        for (int g = g0; g < g1; ++g) walk_group<ZEPS, BPL>(p, sh, g);
+        for (int g = g0; g < g1; ++g) walk_group<ZEPS, BPL, MULTI>(p, sh, g);
     }
 }
 
@@ -906,9 +930,14 @@ cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps,
     if (p.n <= 0) return cudaSuccess;
     const int G = p.group;
     const int groups = (p.n + G - 1) / G;
+    // (a separate instance walks further trees: the single-tree walk keeps
+    // its own registers and shared memory)
     void (*fn)(const TreeWalkParams) =
-        G == 32 ? (zeps ? tree_walk_kernel<true, 1> : tree_walk_kernel<false, 1>)
-                : (zeps ? tree_walk_kernel<true, 2> : tree_walk_kernel<false, 2>);
+        p.nmore > 0
+            ? (G == 32 ? (zeps ? tree_walk_kernel<true, 1, true> : tree_walk_kernel<false, 1, true>)
+                       : (zeps ? tree_walk_kernel<true, 2, true> : tree_walk_kernel<false, 2, true>))
+            : (G == 32 ? (zeps ? tree_walk_kernel<true, 1, false> : tree_walk_kernel<false, 1, false>)
+                       : (zeps ? tree_walk_kernel<true, 2, false> : tree_walk_kernel<false, 2, false>));
     int blocks = (groups + WALK_WARPS - 1) / WALK_WARPS;
     if (p.sched != 0) {  // resident blocks only
         int per_sm = 0;

@@ -146,3 +146,28 @@ def test_ties_in_the_cut_coordinate(cuda):
         assert np.array_equal(cnt.astype(np.int64), ref_cnt[mine, :2])
         e = relerr_per_body(acc, ref[mine])
         assert np.sqrt((e ** 2).mean()) <= 1e-5 and e.max() <= 1e-4
+
+
+def test_more_trees_than_one_launch_takes(cuda):
+    # 70 copies of one LET: the local tree and 63 received ones go in the
+    # first launch, the rest in a second; counts add exactly and each copy
+    # adds the same float64 sum
+    b = inputs.two_plummer(3000, seed=96)
+    rank = oracle.orb(b.pos, 2)
+    src, dst = rank == 0, rank == 1
+    with nbody.NBody(b.n, "fp32_comp") as other:
+        other.let_build(to_dev(b.pos[src], cuda), to_dev(b.mass[src], cuda), 16)
+        xd = b.pos[dst].astype(np.float32)
+        let_buf = other.let_export(0.5, np.concatenate([xd.min(0), xd.max(0)]))
+        other.sync()
+        with nbody.NBody(b.n, "fp32_comp") as nb:
+            nb.let_build(to_dev(b.pos[dst], cuda), to_dev(b.mass[dst], cuda), 16)
+            runs = {}
+            for k in (0, 1, 70):
+                a, c = nb.let_forces(1.0, 0.01, 0.5, 64, [let_buf] * k, counts=True)
+                nb.sync()
+                runs[k] = (host(a), host(c).astype(np.int64))
+    (a0, c0), (a1, c1), (a70, c70) = runs[0], runs[1], runs[70]
+    assert np.array_equal(c70, c0 + 70 * (c1 - c0))
+    d = a1 - a0
+    assert np.allclose(a70, a0 + 70 * d, rtol=0, atol=1e-11 * np.abs(a70).max())
