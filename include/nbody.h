@@ -343,12 +343,13 @@ nb_status nb_tree_schedule(nb_ctx *ctx, int sched, int chunk);
  * ancestors, the bodies those cells hold, and the bodies it meets directly
  * (itself included); the last two sum to n.  Float32 arithmetic in every
  * precision mode, float64 output.  Allocates on first use (the tree scratch
- * of nb_tree_forces, plus 2 np + 17 4-byte words per tree node, np the
+ * of nb_tree_forces, plus 2 np + 18 4-byte words per tree node, np the
  * (order+1)(order+2)(order+3)/6 expansion coefficients rounded up to a
  * multiple of 4; a pool of candidate lists, 4 (2^20 + 32 n_max) bytes to start;
- * and the cells' expansion lists, 132 (4096 + 2 n_max) bytes to start).
- * Synchronises the context's stream at the end: if a list outgrew its
- * store, the store is doubled and the passes run again.
+ * the cells' expansion lists, 132 (4096 + 2 n_max) bytes to start; and the
+ * leaves' lists of directly summed cells, 260 (4096 + n_max / 4) bytes to
+ * start).  Synchronises the context's stream at the end: if a list outgrew
+ * its store, the store is doubled and the passes run again.
  * Non-finite results are reported by nb_sync.
  *
  * nb_fmm_stats: {nodes, leaves, cell-to-cell expansions, direct body pairs
@@ -368,11 +369,11 @@ nb_status nb_fmm_stats(nb_ctx *ctx, int64_t *out);
 nb_status nb_fmm_step(nb_ctx *ctx, int64_t n, double *pos, double *vel, const double *mass,
                       double G, double eps, double theta, int order, int leaf_cap, double dt,
                       int64_t nsteps, double *acc, unsigned flags);
-/* Replace the candidate pool by one of `entries` ints (1 <= entries < 2^31)
- * and the store of the cells' expansion lists by one of entries / 32 + 1
- * chunks of 32 source ids, e.g. to size them for a known workload;
- * synchronises the stream.  A store too small still gives the same results:
- * the passes grow it and run again. */
+/* Replace the candidate pool by one of `entries` ints (1 <= entries < 2^31),
+ * and the stores of the cells' expansion lists and of the leaves' lists of
+ * directly summed cells by entries / 32 + 1 chunks of 32 each, e.g. to size
+ * them for a known workload; synchronises the stream.  A store too small
+ * still gives the same results: the passes grow it and run again. */
 nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
 
 /*

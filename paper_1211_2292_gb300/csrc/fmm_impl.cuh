@@ -615,6 +615,7 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
 {
     __shared__ WalkSh wsh[WARPS];
     __shared__ int mq[WARPS][64];
+    __shared__ int2 dq[WARPS][LEAVES ? 64 : 1];  // a leaf's directly summed cells: body ranges
     __shared__ CritSh crit;
     crit_table(crit, p.f.crit);
     __syncthreads();
@@ -629,7 +630,8 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
     const int base = LEAVES ? 0 : t.meta[TREE_META_BASE + L];
     int *queue = f.meta + (LEAVES ? FMM_META_LEAVES_Q : FMM_META_LEVEL + L);
     WalkSh &w = wsh[warp];
-    int cnext = 0, cend = 0;  // this warp's reserved expansion-list chunks
+    int cnext = 0, cend = 0;    // this warp's reserved expansion-list chunks
+    int rcnext = 0, rcend = 0;  // and direct-range chunks
     // one cell: its list (and, for a non-leaf, its hand-down list)
     auto visit = [&](int qi) {
         const int A = base + qi;
@@ -644,8 +646,11 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
             inh_cnt = d.y;
         }
         const int *inh = f.pool + inh_off;
-        int mcnt = 0, own = 0, farb = 0, nearc = 0, prev = -1;
-        if (lane == 0) f.chunk_head[A] = -1;
+        int mcnt = 0, own = 0, farb = 0, nearc = 0, prev = -1, dcnt = 0, dprev = -1;
+        if (lane == 0) {
+            f.chunk_head[A] = -1;
+            if (LEAVES) f.rhead[A] = -1;
+        }
         // a non-leaf: how many candidates go down (pass 1), and where
         long long off = 0;
         bool fits = true;
@@ -717,8 +722,9 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
                         more = false;
                         break;
                     }
-                    bool open = false;
+                    bool open = false, direct = false;
                     int nchB = 0, firstB = 0, lvB = 0;
+                    int2 rng = make_int2(0, 0);
                     if (B >= 0) {
                         const int4 cB = __ldg(f.ci + B), nB = __ldg(f.nd + B);
                         sep = separated(cA, cB, crit);
@@ -726,12 +732,23 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
                         bodies = nB.w - nB.z;
                         if (!sep) {
                             open = nchB > 0 && !all_direct(cA, cB, crit);
-                            if (!open) nearc += bodies;
+                            direct = !open;
+                            rng = make_int2(nB.z, nB.w);
+                            if (direct) nearc += bodies;
                         }
                         firstB = nB.y;
                         lvB = cB.w;
                     }
                     push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
+                    // the directly summed cells, in walk order, for the near field
+                    const unsigned dm = __ballot_sync(FULL, direct);
+                    if (direct) dq[warp][dcnt + __popc(dm & lt)] = rng;
+                    dcnt += __popc(dm);
+                    __syncwarp();
+                    if (dcnt >= 32)
+                        flush_chunk(dq[warp], dcnt, 32, make_int2(0, 0), f.rchunk, f.rnext,
+                                    f.rhead + A, f.rchunk_cap, f.meta + FMM_META_RCHUNKS,
+                                    f.meta + FMM_META_OVERFLOW, 4, dprev, rcnext, rcend, lane);
                 }
                 const unsigned sm = __ballot_sync(FULL, sep);
                 if (sep) {
@@ -749,6 +766,10 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_lists_kernel(const FmmParams p
                             prev, cnext, cend, lane);
         }
         if constexpr (LEAVES) {
+            if (dcnt > 0)
+                flush_chunk(dq[warp], dcnt, dcnt, make_int2(0, 0), f.rchunk, f.rnext, f.rhead + A,
+                            f.rchunk_cap, f.meta + FMM_META_RCHUNKS, f.meta + FMM_META_OVERFLOW,
+                            4, dprev, rcnext, rcend, lane);
             nearc = warp_sum(nearc);
             if (lane == 0) {
                 f.nearc[A] = nearc;
@@ -970,9 +991,9 @@ __device__ __forceinline__ void write_body(const FmmParams &p, int A, const doub
     if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
 }
 
-// A warp per work item (dynamic): the leaf's candidates' subtrees walked
-// again, in the downward pass's order, for the bodies it meets directly
-// (pruned subtrees as whole body ranges); the item's slice of them is
+// A warp per work item (dynamic): the body ranges of the cells the leaf's
+// walk met directly, in the order the walk recorded them; the item's slice
+// of those bodies is
 // listed (coordinates relative to the leaf's centre) and every FLUSH of them
 // added onto its bodies: two bodies per lane (b and b + T, T = nb / 2 rounded
 // up to a power of two), lane = b + T * slice, the 32 / T slices sharing the
@@ -982,11 +1003,7 @@ __device__ __forceinline__ void write_body(const FmmParams &p, int A, const doub
 template <int P, bool ZEPS>
 __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
 {
-    __shared__ WalkSh wsh[WARPS];
     __shared__ __align__(16) float4 lists[WARPS][2 * FLUSH];  // 2 * FLUSH sources as pairs
-    __shared__ CritSh crit;
-    crit_table(crit, p.f.crit);
-    __syncthreads();
     const TreeView &t = p.tree;
     const FmmView &f = p.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -995,7 +1012,6 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
         f.stats[0] = (unsigned long long)(t.meta[TREE_META_BASE + 10] + t.meta[TREE_META_COUNT + 10]);
         f.stats[1] = (unsigned long long)nleaves;
     }
-    WalkSh &w = wsh[warp];
     float *Lf = reinterpret_cast<float *>(lists[warp]);
     const float4 *L4 = lists[warp];
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
@@ -1015,20 +1031,12 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
         }
         const int qi = lo, A = f.leaves[qi];
         const int4 cA = f.ci[A];
-        const int par = t.parent[A];
         const int nearc = f.nearc[A], ns = src_slices(nearc);
         const int j = it - f.item_off[qi], bc = j / ns, sc = j % ns;
         const int nbt = t.end[A] - t.start[A];
         const int s0 = t.start[A] + 64 * bc, nb = min(64, t.end[A] - s0);
         const int per = (nearc + ns - 1) / ns;
         const int src_lo = sc * per, src_hi = min(nearc, src_lo + per);
-        int inh_off = 0, inh_cnt = 1;
-        if (par >= 0) {
-            const int2 d = f.down[par];
-            inh_off = d.x;
-            inh_cnt = d.y;
-        }
-        const int *inh = f.pool + inh_off;
         double z[3];
         centre_of(p.box, cA, z);
         const float cx = (float)z[0], cy = (float)z[1], cz = (float)z[2];
@@ -1091,51 +1099,29 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
             cnt -= FLUSH;
             __syncwarp();
         };
-        if (lane < LEVELS) w.lsz[lane] = 0;
-        __syncwarp();
-        int cursor = 0, B = -1;
-        while (seen < src_hi && next_round(w, inh, inh_cnt, cursor, lane, B)) {
-            bool open = false, direct = false;
-            int nchB = 0, firstB = 0, lvB = 0;
-            int4 nB = make_int4(0, 0, 0, 0);
-            if (B >= 0) {
-                const int4 cB = __ldg(f.ci + B);
-                nB = __ldg(f.nd + B);
-                if (!separated(cA, cB, crit)) {
-                    nchB = nB.x;
-                    open = nchB > 0 && !all_direct(cA, cB, crit);
-                    direct = !open;
+        for (int rc = f.rhead[A]; rc >= 0 && seen < src_hi;) {
+            const int2 r = f.rchunk[32 * (size_t)rc + lane];  // (0, 0) past the list's end
+            rc = f.rnext[rc];
+            const int ls = r.x, lsz = r.y - r.x;
+            const int linc = warp_incl_scan(lsz, lane);
+            const int lexc = linc - lsz;
+            const int tot = __shfl_sync(FULL, linc, 31);
+            // this chunk's direct sources are [seen, seen + tot) in walk order
+            const int a0 = max(src_lo - seen, 0), a1 = min(src_hi - seen, tot);
+            for (int c0 = a0; c0 < a1; c0 += 32) {
+                const int pos = c0 + lane;
+                const int jj = warp_span_of(linc, pos) & 31;
+                const int body = __shfl_sync(FULL, ls, jj) + (pos - __shfl_sync(FULL, lexc, jj));
+                const int kk = min(32, a1 - c0);
+                if (lane < kk) {
+                    const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
+                    list_put(Lf, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
+                             rel(bh.z, bl.z, cz), bh.w);
                 }
-                firstB = nB.y;
-                lvB = cB.w;
+                cnt += kk;
+                if (cnt >= FLUSH) flush();
             }
-            push_children(w, open, lvB + 1, firstB, nchB, lane, p.err);
-            if (__ballot_sync(FULL, direct)) {
-                int ls = 0, lsz = 0;
-                if (direct) {
-                    ls = nB.z;
-                    lsz = nB.w - ls;
-                }
-                const int linc = warp_incl_scan(lsz, lane);
-                const int lexc = linc - lsz;
-                const int tot = __shfl_sync(FULL, linc, 31);
-                // this round's direct sources are [seen, seen + tot) in walk order
-                const int a0 = max(src_lo - seen, 0), a1 = min(src_hi - seen, tot);
-                for (int c0 = a0; c0 < a1; c0 += 32) {
-                    const int pos = c0 + lane;
-                    const int jj = warp_span_of(linc, pos) & 31;
-                    const int body = __shfl_sync(FULL, ls, jj) + (pos - __shfl_sync(FULL, lexc, jj));
-                    const int kk = min(32, a1 - c0);
-                    if (lane < kk) {
-                        const float4 bh = __ldg(p.P + body), bl = __ldg(p.Plo + body);
-                        list_put(Lf, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
-                                 rel(bh.z, bl.z, cz), bh.w);
-                    }
-                    cnt += kk;
-                    if (cnt >= FLUSH) flush();
-                }
-                seen += tot;
-            }
+            seen += tot;
         }
         if (cnt > 0) {
             if (lane == 0 && (cnt & 1)) list_put(Lf, cnt, 0.f, 0.f, 0.f, 0.f);

@@ -268,8 +268,10 @@ constexpr int FMM_MIN_ORDER = 2, FMM_MAX_ORDER = 6, FMM_MAX_LEAF = 64;
 int fmm_floats(int order);
 enum : int { FMM_META_LEVEL = 0, FMM_META_NEAR = 11, FMM_META_POOL = 12, FMM_META_OVERFLOW = 13,
              FMM_META_NLEAVES = 14, FMM_META_ITEMS = 15, FMM_META_PSLOTS = 16,
-             FMM_META_CHUNKS = 17, FMM_META_M2L = 18, FMM_META_LEAVES_Q = 19, FMM_META_INTS = 20 };
-// FMM_META_OVERFLOW bits: the candidate pool (1), the expansion-list chunks (2).
+             FMM_META_CHUNKS = 17, FMM_META_M2L = 18, FMM_META_LEAVES_Q = 19, FMM_META_RCHUNKS = 20,
+             FMM_META_INTS = 24 };
+// FMM_META_OVERFLOW bits: the candidate pool (1), the expansion-list chunks
+// (2), the direct-range chunks (4).
 constexpr int FMM_CHUNK = 32;  // source ids per expansion-list chunk
 constexpr int FMM_CRIT_INTS = 2 * 11 * 11;  // two thresholds per pair of tree levels
 struct FmmView {
@@ -291,6 +293,10 @@ struct FmmView {
     int *chunk_src;        // [chunk_cap][FMM_CHUNK] source cells, -1 past a list's end
     int *chunk_next;       // [chunk_cap] the next chunk of the same list, -1 at the end
     long long chunk_cap;
+    int *rhead;            // per leaf: first chunk of its directly summed cells, -1 for none
+    int2 *rchunk;          // [rchunk_cap][FMM_CHUNK] those cells' body ranges, (0, 0) past the end
+    int *rnext;            // [rchunk_cap] the next chunk of the same list, -1 at the end
+    long long rchunk_cap;
     int *meta;             // [FMM_META_INTS] queues, pool top, overflow flag, leaf count
     int *crit;             // [FMM_CRIT_INTS] the cell tests' thresholds for this evaluation's theta
     unsigned long long *stats;  // [4] nodes, leaves, expansions, direct body pairs

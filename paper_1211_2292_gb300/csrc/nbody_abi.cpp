@@ -514,15 +514,18 @@ void free_fmm(nb_ctx *c)
     nb::FmmView &f = c->fmm;
     void *arrays[] = {f.ci,       f.nd,       f.M,      f.L,        f.down,     f.cum,
                       f.leaves,   f.nearc,    f.item_off, f.part_off,
-                      f.part,     f.pool,     f.chunk_head, f.chunk_src, f.chunk_next};
+                      f.part,     f.pool,     f.chunk_head, f.chunk_src, f.chunk_next,
+                      f.rhead,    f.rchunk,   f.rnext};
     for (void *a : arrays) cudaFree(a);
     f.ci = f.nd = nullptr;
     f.M = f.L = nullptr;
     f.down = f.cum = nullptr;
     f.leaves = f.nearc = f.item_off = f.part_off = f.pool = nullptr;
     f.chunk_head = f.chunk_src = f.chunk_next = nullptr;
+    f.rhead = f.rnext = nullptr;
+    f.rchunk = nullptr;
     f.part = nullptr;
-    f.pool_cap = f.part_cap = f.chunk_cap = 0;
+    f.pool_cap = f.part_cap = f.chunk_cap = f.rchunk_cap = 0;
     c->fmm_cap = c->fmm_np = 0;
 }
 
@@ -674,9 +677,11 @@ nb_status ensure_chunks(nb_ctx *c, long long need, T *&store, int *&next, long l
 
 // Expansion, list and candidate-pool scratch of the fast multipole method
 // for the tree's node capacity and `order`; the pool holds at least
-// pool_need entries and the expansion lists at least chunk_need chunks.
-// Growing frees the old arrays (cudaFree synchronises).
-nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_need)
+// pool_need entries, the expansion lists at least chunk_need chunks and the
+// leaves' direct-range lists at least rchunk_need.  Growing frees the old
+// arrays (cudaFree synchronises).
+nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_need,
+                     long long rchunk_need)
 {
     nb_status st = NB_OK;
     nb::FmmView &f = c->fmm;
@@ -687,7 +692,8 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_
     const int np = nb::fmm_floats(order);
     const int cap = c->tree.cap;
     if (cap > c->fmm_cap || np > c->fmm_np) {
-        const long long keep_pool = f.pool_cap, keep_chunks = f.chunk_cap;
+        const long long keep_pool = f.pool_cap, keep_chunks = f.chunk_cap,
+                        keep_rchunks = f.rchunk_cap;
         free_fmm(c);
         const size_t m = (size_t)cap;
         f.ci = dev_alloc<int4>(c, m, st);
@@ -701,6 +707,7 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_
         if (st == NB_OK) f.item_off = dev_alloc<int>(c, m + 1, st);
         if (st == NB_OK) f.part_off = dev_alloc<int>(c, m + 1, st);
         if (st == NB_OK) f.chunk_head = dev_alloc<int>(c, m, st);
+        if (st == NB_OK) f.rhead = dev_alloc<int>(c, m, st);
         if (st != NB_OK) {
             free_fmm(c);
             return st;
@@ -709,8 +716,10 @@ nb_status ensure_fmm(nb_ctx *c, int order, long long pool_need, long long chunk_
         c->fmm_np = np;
         pool_need = std::max(pool_need, keep_pool);
         chunk_need = std::max(chunk_need, keep_chunks);
+        rchunk_need = std::max(rchunk_need, keep_rchunks);
     }
     NB_TRY(ensure_chunks(c, chunk_need, f.chunk_src, f.chunk_next, f.chunk_cap, "expansion lists"));
+    NB_TRY(ensure_chunks(c, rchunk_need, f.rchunk, f.rnext, f.rchunk_cap, "direct-range lists"));
     if (pool_need > f.pool_cap) {
         if (pool_need > 0x7fffffffLL)
             return failf(c, NB_ENOMEM, "FMM candidate lists of %lld entries too large", pool_need);
@@ -904,11 +913,12 @@ nb_status fmm_forces_run(nb_ctx *c, int64_t n, const double *pos, const double *
         if (attempt == 8) return failf(c, NB_ENOMEM, "FMM candidate lists keep overflowing");
         // the counters hold what was asked for (past the end too); what the
         // cut-short passes did not reach, the next attempt asks for
-        long long need = c->fmm.pool_cap, chunks = c->fmm.chunk_cap;
+        long long need = c->fmm.pool_cap, chunks = c->fmm.chunk_cap, rchunks = c->fmm.rchunk_cap;
         const int over = meta[nb::FMM_META_OVERFLOW];
         if (over & 1) need = std::max<long long>((unsigned)meta[nb::FMM_META_POOL], need) * 2;
         if (over & 2) chunks = std::max<long long>((unsigned)meta[nb::FMM_META_CHUNKS], chunks) * 2;
-        NB_TRY(ensure_fmm(c, order, need, chunks));
+        if (over & 4) rchunks = std::max<long long>((unsigned)meta[nb::FMM_META_RCHUNKS], rchunks) * 2;
+        NB_TRY(ensure_fmm(c, order, need, chunks, rchunks));
     }
 }
 
@@ -1623,7 +1633,8 @@ nb_status nb_fmm_forces(nb_ctx *c, int64_t n, const double *pos, const double *m
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
     NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max,
-                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max));
+                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max,
+                      c->fmm.rchunk ? 1 : 4096LL + c->n_max / 4));
     return fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, counts);
 }
 
@@ -1648,7 +1659,8 @@ nb_status nb_fmm_step(nb_ctx *c, int64_t n, double *pos, double *vel, const doub
     if (n == 0) return NB_OK;
     NB_TRY(ensure_tree(c, leaf_cap));
     NB_TRY(ensure_fmm(c, order, c->fmm.pool ? 1 : (long long)(1 << 20) + 32LL * c->n_max,
-                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max));
+                      c->fmm.chunk_src ? 1 : 4096LL + 2LL * c->n_max,
+                      c->fmm.rchunk ? 1 : 4096LL + c->n_max / 4));
     if (!(flags & NB_ACC_VALID))
         NB_TRY(fmm_forces_run(c, n, pos, mass, G, eps, theta, order, leaf_cap, acc, nullptr));
     for (int64_t st = 0; st < nsteps; ++st) {
@@ -1668,16 +1680,18 @@ nb_status nb_fmm_reserve(nb_ctx *c, int64_t entries)
         return failf(c, NB_EINVAL, "pool of %lld entries outside [1, 2^31)", (long long)entries);
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
     nb::FmmView &f = c->fmm;
-    void *old[] = {f.pool, f.chunk_src, f.chunk_next};
+    void *old[] = {f.pool, f.chunk_src, f.chunk_next, f.rchunk, f.rnext};
     for (void *a : old) cudaFree(a);
-    f.pool = f.chunk_src = f.chunk_next = nullptr;
-    f.pool_cap = f.chunk_cap = 0;
+    f.pool = f.chunk_src = f.chunk_next = f.rnext = nullptr;
+    f.rchunk = nullptr;
+    f.pool_cap = f.chunk_cap = f.rchunk_cap = 0;
     nb_status st = NB_OK;
     f.pool = dev_alloc<int>(c, (size_t)entries, st);
     if (st != NB_OK) return st;
     f.pool_cap = entries;
     const long long chunks = entries / nb::FMM_CHUNK + 1;
-    return ensure_chunks(c, chunks, f.chunk_src, f.chunk_next, f.chunk_cap, "expansion lists");
+    NB_TRY(ensure_chunks(c, chunks, f.chunk_src, f.chunk_next, f.chunk_cap, "expansion lists"));
+    return ensure_chunks(c, chunks, f.rchunk, f.rnext, f.rchunk_cap, "direct-range lists");
 }
 
 nb_status nb_fmm_stats(nb_ctx *c, int64_t *out)
