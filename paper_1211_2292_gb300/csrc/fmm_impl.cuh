@@ -991,6 +991,69 @@ __device__ __forceinline__ void write_body(const FmmParams &p, int A, const doub
     if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
 }
 
+// (s, c) += (so, co) for Kahan pairs holding s - c: the sums' rounding
+// error goes into the carry (the two-sum of s and so).
+__device__ __forceinline__ void kahan_merge(float &s, float &c, float so, float co)
+{
+    const float t = s + so;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (so - bp);
+    s = t;
+    c = (c + co) - e;
+}
+
+// write_body for a near field held as float32 Kahan pairs (s - c): the L2P
+// in float32 from the body's hi/lo position relative to the centre's hi/lo
+// pair (zh, zl) times 1/e, the far field added into the pair, one float64
+// conversion at the end.
+template <int P>
+__device__ __forceinline__ void write_body_kahan(const FmmParams &p, int A, const float (&zh)[3],
+                                                 const float (&zl)[3], float inv_e, int k,
+                                                 float (&ks)[3], float (&kc)[3], int nnear)
+{
+    constexpr int NP = padded(P);
+    const FmmView &f = p.f;
+    const float *Lc = f.L + (size_t)A * NP;
+    const int i = p.perm[k];
+    const float4 h = __ldg(p.P + k), l = __ldg(p.Plo + k);
+    const float hx[3] = {h.x, h.y, h.z}, lx[3] = {l.x, l.y, l.z};
+    float pw[3][P + 1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) scaled_powers<P>(((hx[c] - zh[c]) + (lx[c] - zl[c])) * inv_e, pw[c]);
+    float fa[3] = {0.f, 0.f, 0.f};
+    sfor<0, nterms(P - 1)>([&](auto kI) {
+        constexpr int q = decltype(kI)::value;
+        constexpr int a = mi_of(q, 0), b = mi_of(q, 1), c = mi_of(q, 2);
+        const float wv = pw[0][a] * pw[1][b] * pw[2][c];
+        fa[0] = fmaf(__ldg(Lc + slot_of(a + 1, b, c)), wv, fa[0]);
+        fa[1] = fmaf(__ldg(Lc + slot_of(a, b + 1, c)), wv, fa[1]);
+        fa[2] = fmaf(__ldg(Lc + slot_of(a, b, c + 1)), wv, fa[2]);
+    });
+    double g[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        kahan_add(ks[c], kc[c], fa[c] * inv_e);
+        g[c] = p.G * ((double)ks[c] - (double)kc[c]);
+    }
+    double *a = p.acc + 3 * (size_t)i;
+    a[0] = g[0];
+    a[1] = g[1];
+    a[2] = g[2];
+    if (p.vel) {  // a step's closing half-kick
+        double *v = p.vel + 3 * (size_t)i;
+        v[0] += p.half_dt * g[0];
+        v[1] += p.half_dt * g[1];
+        v[2] += p.half_dt * g[2];
+    }
+    if (p.counts) {
+        const int2 cm = f.cum[A];
+        p.counts[3 * (size_t)i] = cm.x;
+        p.counts[3 * (size_t)i + 1] = cm.y;
+        p.counts[3 * (size_t)i + 2] = nnear;
+    }
+    if (!finite3(g[0], g[1], g[2])) atomicOr(p.err, ERR_NONFINITE);
+}
+
 // A warp per work item (dynamic): the body ranges of the cells the leaf's
 // walk met directly, in the order the walk recorded them; the item's slice
 // of those bodies is
@@ -1129,30 +1192,37 @@ __global__ void __launch_bounds__(32 * WARPS) fmm_near_kernel(const FmmParams p)
             eval((cnt + 1) >> 1);
             fold();
         }
-        // combine the slices (lane b0 of slice 0 ends with the total)
-        double ns3[2][3];
+        // combine the slices' Kahan pairs in float32 (lane b0 of slice 0 ends
+        // with the total): float64 work is scarce on this part
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double v = (double)ks[b][c] - (double)kc[b][c];
-                for (int off = 16; off >= T; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-                ns3[b][c] = v;
-            }
+            for (int c = 0; c < 3; ++c)
+                for (int off = 16; off >= T; off >>= 1) {
+                    const float so = __shfl_down_sync(FULL, ks[b][c], off);
+                    const float co = __shfl_down_sync(FULL, kc[b][c], off);
+                    kahan_merge(ks[b][c], kc[b][c], so, co);
+                }
         if (slice == 0) {
-            const double inv_e = (double)(1 << cA.w) / p.box[3];
+            // 1/e = (2048 / ext) 2^(L - 11): the float32 1/h scaled exactly
+            const float inv_e = (float)(2048.0 / p.box[3]) * pow2f(cA.w - 11);
+            float zh[3], zl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                zh[c] = (float)z[c];
+                zl[c] = (float)(z[c] - (double)zh[c]);
+            }
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 if (!(b == 0 ? v0 : v1)) continue;
                 const int k = s0 + b0 + T * b;
                 if (ns == 1) {
-                    write_body<P>(p, A, z, inv_e, k, ns3[b][0], ns3[b][1], ns3[b][2], nearc);
+                    write_body_kahan<P>(p, A, zh, zl, inv_e, k, ks[b], kc[b], nearc);
                 } else {
                     double *d = f.part + 3 * ((size_t)f.part_off[qi] + (size_t)sc * nbt +
                                               (size_t)(k - t.start[A]));
-                    d[0] = ns3[b][0];
-                    d[1] = ns3[b][1];
-                    d[2] = ns3[b][2];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) d[c] = (double)ks[b][c] - (double)kc[b][c];
                 }
             }
         }
