@@ -47,7 +47,7 @@ constexpr int TTPB = 256;
 #define NB_WALK_MINB1 8
 #endif
 #ifndef NB_WALK_MINB2
-#define NB_WALK_MINB2 6
+#define NB_WALK_MINB2 5
 #endif
 constexpr int WALK_WARPS = NB_WALK_WARPS;
 
@@ -328,21 +328,31 @@ __device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const floa
 
 // Interaction list of a warp: up to LIST_CAP sources (cells or bodies) as
 // (x, y, z, m), coordinates relative to the group's centre, laid out for
-// float32x2 arithmetic.  With one body per lane (BPL = 1) two sources share
-// an instruction: a pair of sources is {x0, x1, y0, y1}, {z0, z1, m0, m1}.
-// With two bodies per lane (BPL = 2) one source meets both bodies: a source
-// is stored twice over, {x, x, y, y}, {z, z, m, m}.
+// float32x2 arithmetic.  Paired layout: two sources share an instruction,
+// a pair of sources is {x0, x1, y0, y1}, {z0, z1, m0, m1} (one body per
+// lane, or each of a lane's two bodies in turn).  Doubled layout (two
+// bodies per lane, NB_WALK_PAIRED 0): one source meets both bodies, stored
+// twice over, {x, x, y, y}, {z, z, m, m}.
 #ifndef NB_WALK_FLUSH
 #define NB_WALK_FLUSH 64
+#endif
+#ifndef NB_WALK_PAIRED
+#define NB_WALK_PAIRED 1
 #endif
 constexpr int FLUSH = NB_WALK_FLUSH;  // sources evaluated per flush (a multiple of 32)
 constexpr int LIST_CAP = 2 * FLUSH;
 constexpr int LEVELS = 11;
 
 template <int BPL>
+__host__ __device__ constexpr bool paired_list() { return BPL == 1 || NB_WALK_PAIRED; }
+// float4 slots of a list of LIST_CAP sources
+template <int BPL>
+__host__ __device__ constexpr int list_f4() { return paired_list<BPL>() ? LIST_CAP : LIST_CAP * 2; }
+
+template <int BPL>
 __device__ __forceinline__ void list_put(float *L, int q, float x, float y, float z, float m)
 {
-    if (BPL == 1) {
+    if (paired_list<BPL>()) {
         float *b = L + 8 * (q >> 1) + (q & 1);
         b[0] = x;
         b[2] = y;
@@ -373,18 +383,25 @@ __device__ __forceinline__ void pair_terms(float2 dx, float2 dy, float2 dz, floa
     az = fma2(dz, s, az);
 }
 
-// Add the first `cnt` listed sources (cnt even for BPL = 1) onto this lane's
-// bodies.  BPL = 1: nx = (-x_i, -x_i); BPL = 2: nx = (-x_i0, -x_i1).
+// Add the first `cnt` listed sources (cnt even for the paired layout) onto
+// this lane's bodies.  Paired layout: nx = (-x_i, -x_i) per body (the second
+// body's in nx2, its sums in a2); doubled layout: nx = (-x_i0, -x_i1).
 template <bool ZEPS, int BPL>
 __device__ __forceinline__ void list_eval(const float4 *L4, int cnt, float2 nx, float2 ny,
-                                          float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az)
+                                          float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                          float2 nx2, float2 ny2, float2 nz2, float2 &bx,
+                                          float2 &by, float2 &bz)
 {
-    const int steps = BPL == 1 ? cnt >> 1 : cnt;
+    constexpr bool TWO = BPL == 2 && paired_list<BPL>();
+    const int steps = paired_list<BPL>() ? cnt >> 1 : cnt;
 #pragma unroll 4
     for (int q = 0; q < steps; ++q) {
         const float4 A = L4[2 * q], B = L4[2 * q + 1];
-        pair_terms<ZEPS>(add2(make_float2(A.x, A.y), nx), add2(make_float2(A.z, A.w), ny),
-                         add2(make_float2(B.x, B.y), nz), make_float2(B.z, B.w), e2, ax, ay, az);
+        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+        const float2 sz = make_float2(B.x, B.y), sm = make_float2(B.z, B.w);
+        pair_terms<ZEPS>(add2(sx, nx), add2(sy, ny), add2(sz, nz), sm, e2, ax, ay, az);
+        if constexpr (TWO)
+            pair_terms<ZEPS>(add2(sx, nx2), add2(sy, ny2), add2(sz, nz2), sm, e2, bx, by, bz);
     }
 }
 
@@ -427,7 +444,7 @@ __device__ __forceinline__ int warp_span_of(int incl, int pos)
 // empty.  Whenever FLUSH sources are listed, every lane adds them to its bodies.
 template <int BPL, bool MULTI>
 struct WalkShared {
-    float4 list[WALK_WARPS][LIST_CAP * BPL];  // float4 slots of the lists
+    float4 list[WALK_WARPS][list_f4<BPL>()];  // float4 slots of the lists
     int2 ranges[WALK_WARPS][LEVELS][32];
     float crit2[MULTI ? 1 + WALK_MAX_MORE : 1][LEVELS];  // per walked tree
 };
@@ -438,7 +455,8 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
                                            int g)
 {
     constexpr int GROUP = 32 * BPL;
-    constexpr int LIST_F4 = LIST_CAP * BPL;
+    constexpr int LIST_F4 = list_f4<BPL>();
+    constexpr bool TWO = BPL == 2 && paired_list<BPL>();  // a lane's two bodies in turn
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n;
@@ -483,9 +501,13 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         yi[b] = rel(h[b].y, lo_[b].y, cy);
         zi[b] = rel(h[b].z, lo_[b].z, cz);
     }
-    const float2 nx = BPL == 1 ? make_float2(-xi[0], -xi[0]) : make_float2(-xi[0], -xi[BPL - 1]);
-    const float2 ny = BPL == 1 ? make_float2(-yi[0], -yi[0]) : make_float2(-yi[0], -yi[BPL - 1]);
-    const float2 nz = BPL == 1 ? make_float2(-zi[0], -zi[0]) : make_float2(-zi[0], -zi[BPL - 1]);
+    const bool bc = BPL == 1 || TWO;  // the first body broadcast over a source pair
+    const float2 nx = bc ? make_float2(-xi[0], -xi[0]) : make_float2(-xi[0], -xi[BPL - 1]);
+    const float2 ny = bc ? make_float2(-yi[0], -yi[0]) : make_float2(-yi[0], -yi[BPL - 1]);
+    const float2 nz = bc ? make_float2(-zi[0], -zi[0]) : make_float2(-zi[0], -zi[BPL - 1]);
+    const float2 nx2 = make_float2(-xi[BPL - 1], -xi[BPL - 1]);
+    const float2 ny2 = make_float2(-yi[BPL - 1], -yi[BPL - 1]);
+    const float2 nz2 = make_float2(-zi[BPL - 1], -zi[BPL - 1]);
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
     // the group's first and last bodies, for the quick rejection
     const int lastb = (nvalid - 1) >> 5, lastl = (nvalid - 1) & 31;
@@ -520,20 +542,29 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         t = p.more[tq - 1];
     }
     const float *crit2 = sh.crit2[MULTI ? tq : 0];
-    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-    // Kahan (sum, carry) per body and axis: BPL = 1 folds both halves of the
-    // float32x2 accumulators into one body; BPL = 2 keeps .x and .y apart.
+    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax, bx = ax, by = ax, bz = ax;
+    // Kahan (sum, carry) per body and axis: the paired layout folds both
+    // halves of a body's float32x2 accumulators into it (the second body's
+    // are bx..bz); the doubled layout keeps .x and .y apart.
     float sx[BPL], sy[BPL], sz[BPL], qx[BPL], qy[BPL], qz[BPL];
 #pragma unroll
     for (int b = 0; b < BPL; ++b) sx[b] = sy[b] = sz[b] = qx[b] = qy[b] = qz[b] = 0.f;
     auto fold = [&]() {
-        if (BPL == 1) {
+        if (paired_list<BPL>()) {
             kahan_add(sx[0], qx[0], ax.x);
             kahan_add(sx[0], qx[0], ax.y);
             kahan_add(sy[0], qy[0], ay.x);
             kahan_add(sy[0], qy[0], ay.y);
             kahan_add(sz[0], qz[0], az.x);
             kahan_add(sz[0], qz[0], az.y);
+            if (TWO) {
+                kahan_add(sx[BPL - 1], qx[BPL - 1], bx.x);
+                kahan_add(sx[BPL - 1], qx[BPL - 1], bx.y);
+                kahan_add(sy[BPL - 1], qy[BPL - 1], by.x);
+                kahan_add(sy[BPL - 1], qy[BPL - 1], by.y);
+                kahan_add(sz[BPL - 1], qz[BPL - 1], bz.x);
+                kahan_add(sz[BPL - 1], qz[BPL - 1], bz.y);
+            }
         } else {
             kahan_add(sx[0], qx[0], ax.x);
             kahan_add(sy[0], qy[0], ay.x);
@@ -542,13 +573,13 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
             kahan_add(sy[BPL - 1], qy[BPL - 1], ay.y);
             kahan_add(sz[BPL - 1], qz[BPL - 1], az.y);
         }
-        ax = ay = az = make_float2(0.f, 0.f);
+        ax = ay = az = bx = by = bz = make_float2(0.f, 0.f);
     };
     int cnt = 0;  // listed sources (warp-uniform)
     // FLUSH sources listed: add them, move the rest (< FLUSH) to the front
     auto flush = [&]() {
         __syncwarp();
-        list_eval<ZEPS, BPL>(L4, FLUSH, nx, ny, nz, e2, ax, ay, az);
+        list_eval<ZEPS, BPL>(L4, FLUSH, nx, ny, nz, e2, ax, ay, az, nx2, ny2, nz2, bx, by, bz);
         fold();
         __syncwarp();
 #pragma unroll
@@ -663,10 +694,11 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
             }
         }
     }
-    if (cnt > 0) {  // the rest (BPL = 1: padded to a pair with a massless source)
-        if (BPL == 1 && lane == 0 && (cnt & 1)) list_put<BPL>(L, cnt, 0.f, 0.f, 0.f, 0.f);
+    if (cnt > 0) {  // the rest (paired layout: padded to a pair with a massless source)
+        if (paired_list<BPL>() && lane == 0 && (cnt & 1)) list_put<BPL>(L, cnt, 0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        list_eval<ZEPS, BPL>(L4, BPL == 1 ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay, az);
+        list_eval<ZEPS, BPL>(L4, paired_list<BPL>() ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay,
+                             az, nx2, ny2, nz2, bx, by, bz);
         fold();
     }
     __syncwarp();  // the next tree reuses this warp's list and stacks
