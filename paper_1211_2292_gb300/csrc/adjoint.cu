@@ -12,16 +12,19 @@
 //
 // float32 kernel (vjp_f32_kernel): float32x2 lanes over pairs of i-bodies,
 // positions as hi/lo pairs in coordinates relative to the i-tile's centre
-// (as in the force kernel), the direct w form accumulated as
-//   P_k = sum_j w/s^3,  Q_k = sum_j d (d.w)/s^5,  gx_k = G (P_k - 3 Q_k),
-//   M_k = sum_j (mu_j . d)/s^3,  gm_k = -G M_k,
-// 29 float32 operations (14.5 float32x2 issues) and one rsqrt per pair.
-// (Splitting w into m_k sum mu_j/s^3 - mu_k sum m_j/s^3 would save three
-// operations but rounds against large coherent sums when w is small, as for
-// smooth cotangent fields.)  The self pair is masked out exactly in the
-// j-tiles that overlap the CTA's own bodies, since fl(m_k mu_k) - fl(m_k mu_k)
-// through an fma leaves a rounding residue that 1/eps^3 would magnify.
-// Each tile's float32 partials are added into float64 totals.
+// (as in the force kernel).  With b = w - 3 d (d.w)/s^2 the lane accumulates
+//   B_k = sum_j b/s^3,  gx_k = G B_k,   M_k = sum_j (mu_j . d)/s^3,  gm_k = -G M_k.
+// Scaled form: w/m_k = mu_j - m_j v_k with v_k = mu_k/m_k formed once per
+// i-body, 26 float32 operations (13 float32x2 issues) and one rsqrt per pair,
+// the factor m_k applied to the float64 total.  Direct form (bodies of zero
+// mass, or a tile whose scaled sums overflow): w = m_k mu_j - m_j mu_k, 29
+// operations.  Both keep the difference per pair; splitting w into
+// m_k sum mu_j/s^3 - mu_k sum m_j/s^3 would round against large coherent sums
+// when w is small, as for smooth cotangent fields.  The self pair is masked
+// out exactly in the j-tiles that overlap the CTA's own bodies, since the
+// pair's w is a rounding residue that 1/eps^3 would magnify.  Each tile's
+// float32 partials are added into float64 totals; the j-splits divide the
+// bodies (not the tiles) evenly.
 //
 // float64 kernel (vjp_kernel<double>): the direct form above, all float64.
 #include <cuda_runtime.h>
@@ -230,25 +233,38 @@ __device__ __forceinline__ void vjp_stage_store(float4 *tile, const float4 (&bh)
     }
 }
 
-// Per-pair-lane state of the float32 VJP.
+// Per-pair-lane state of the float32 VJP: sum b/s^3 (three components) and
+// sum (mu_j . d)/s^3.
 template <int NP>
 struct VjpAcc {
-    float2 px[NP], py[NP], pz[NP], qx[NP], qy[NP], qz[NP], gm[NP];
+    float2 gx[NP], gy[NP], gz[NP], gm[NP];
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int p = 0; p < NP; ++p)
-            px[p] = py[p] = pz[p] = qx[p] = qy[p] = qz[p] = gm[p] = make_float2(0.f, 0.f);
+        for (int p = 0; p < NP; ++p) gx[p] = gy[p] = gz[p] = gm[p] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ bool finite(int p) const
+    {
+        const float2 s = add2(add2(gx[p], gy[p]), add2(gz[p], gm[p]));
+        return isfinite(s.x) && isfinite(s.y);
     }
 };
 
-template <bool ZEPS, bool MASK>
+// One j-body against a float32x2 lane of two i-bodies: with the pair weight w,
+// b = w - 3 d (d.w)/s^2 and the lane adds b/s^3 and (mu_j . d)/s^3.
+//   GEN (direct form):  w = m_k mu_j - m_j mu_k, from sk = -mu_k
+//       (29 float32 operations);
+//   else (scaled form): w = mu_j - m_j v_k with v_k = mu_k/m_k, from
+//       sk = -v_k: the same weight over m_k, which the caller multiplies
+//       back (26 float32 operations).
+// Both keep the difference per pair, so a smooth cotangent field (small w)
+// loses nothing to cancellation.
+template <bool ZEPS, bool MASK, bool GEN>
 __device__ __forceinline__ void vjp_pair(float2 xj, float2 yj, float2 zj, float2 mj, float2 ujx,
                                          float2 ujy, float2 ujz, float2 e2, float2 nx, float2 ny,
-                                         float2 nz, float2 mk, float2 nukx, float2 nuky,
-                                         float2 nukz, bool self_a, bool self_b, float2 &px,
-                                         float2 &py, float2 &pz, float2 &qx, float2 &qy,
-                                         float2 &qz, float2 &gm)
+                                         float2 nz, float2 mk, float2 skx, float2 sky, float2 skz,
+                                         bool self_a, bool self_b, float2 &gx, float2 &gy,
+                                         float2 &gz, float2 &gm)
 {
     const float2 dx = add2(xj, nx), dy = add2(yj, ny), dz = add2(zj, nz);
     float2 r2 = fma2(dx, dx, e2);
@@ -267,40 +283,48 @@ __device__ __forceinline__ void vjp_pair(float2 xj, float2 yj, float2 zj, float2
     }
     const float2 ri2 = mul2(ri, ri);
     const float2 ri3 = mul2(ri2, ri);
-    const float2 q5 = mul2(ri3, ri2);
-    // w = m_k mu_j - m_j mu_k
-    const float2 wx = fma2(mk, ujx, mul2(mj, nukx));
-    const float2 wy = fma2(mk, ujy, mul2(mj, nuky));
-    const float2 wz = fma2(mk, ujz, mul2(mj, nukz));
+    const float2 m3ri2 = mul2(ri2, make_float2(-3.f, -3.f));
+    float2 wx, wy, wz;
+    if (GEN) {
+        wx = fma2(mk, ujx, mul2(mj, skx));
+        wy = fma2(mk, ujy, mul2(mj, sky));
+        wz = fma2(mk, ujz, mul2(mj, skz));
+    } else {
+        wx = fma2(mj, skx, ujx);
+        wy = fma2(mj, sky, ujy);
+        wz = fma2(mj, skz, ujz);
+    }
     float2 dw = mul2(dx, wx);
     dw = fma2(dy, wy, dw);
     dw = fma2(dz, wz, dw);
-    const float2 c = mul2(dw, q5);
-    px = fma2(wx, ri3, px);
-    py = fma2(wy, ri3, py);
-    pz = fma2(wz, ri3, pz);
-    qx = fma2(dx, c, qx);
-    qy = fma2(dy, c, qy);
-    qz = fma2(dz, c, qz);
+    const float2 t = mul2(dw, m3ri2);
+    gx = fma2(fma2(dx, t, wx), ri3, gx);
+    gy = fma2(fma2(dy, t, wy), ri3, gy);
+    gz = fma2(fma2(dz, t, wz), ri3, gz);
     float2 dlj = mul2(dx, ujx);
     dlj = fma2(dy, ujy, dlj);
     dlj = fma2(dz, ujz, dlj);
     gm = fma2(dlj, ri3, gm);
 }
 
-// Float64 totals of the seven sums per body: in registers, or (TSM) in
-// shared memory, touched once per j-tile, which frees 14 * I registers for
+// Float64 totals of the four sums per body: in registers, or (TSM) in
+// shared memory, touched once per j-tile, which frees 8 * I registers for
 // more resident warps.
 template <int T, int I, bool TSM>
 struct VjpTotals {
-    double reg[TSM ? 1 : 7][TSM ? 1 : I];
-    double *sh;  // this CTA's [7][I][T] doubles (TSM only)
+    double reg[TSM ? 1 : 4][TSM ? 1 : I];
+    double *sh;  // this CTA's [4][I][T] doubles (TSM only)
     __device__ __forceinline__ double &at(int r, int k)
     {
         return TSM ? sh[(r * I + k) * T + threadIdx.x] : reg[TSM ? 0 : r][TSM ? 0 : k];
     }
 };
 
+// The CTA takes the scaled form (totals in units of m_k) unless one of its
+// bodies has m_k <= 0 or a non-finite mu_k/m_k; then every tile takes the
+// direct form (totals in absolute units).  A lane whose scaled tile sums are
+// not finite (m_j mu_k/m_k beyond the float32 range) evaluates that tile
+// again in the direct form and adds it divided by m_k.
 template <int T, int I, int J, bool ZEPS, bool TSM = false, int MINB = 0>
 __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
 {
@@ -310,7 +334,7 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     constexpr int LPT = J / T;
     __shared__ __align__(16) float4 tile[2][4 * J];
     __shared__ float red[6][T / 32];
-    __shared__ double tsh[TSM ? 7 * I * T : 1];
+    __shared__ double tsh[TSM ? 4 * I * T : 1];
     __shared__ int s_last;
 
     const float4 *Ph = static_cast<const float4 *>(p.PV);
@@ -320,16 +344,25 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     const int it = blockIdx.x % n_itiles;
     const int js = blockIdx.x / n_itiles;
     const int i0 = it * TILE_I;
-    int t0, t1;
-    split_range((n + J - 1) / J, p.nsplit, js, t0, t1);
+    // j-split js covers bodies [jbeg, jend): equal shares to the body, so that
+    // the CTAs of one wave carry equal work; its last tile is zero-padded to
+    // a multiple of four bodies
+    const int jbeg = (int)(((long long)n * js) / p.nsplit);
+    const int jend = (int)(((long long)n * (js + 1)) / p.nsplit);
+    const int ntl = (jend - jbeg + J - 1) / J;
 
-    // i-bodies: k-th body of the thread is i0 + tid + k*T; pair p = (2p, 2p+1)
-    float2 nx[NP], ny[NP], nz[NP], mk[NP], nukx[NP], nuky[NP], nukz[NP];
-    int ia[NP], ib[NP];
+    // the first j-tile's loads are in flight while the i-bodies are read
+    float4 bh[LPT], bl[LPT], bu[LPT];
+    if (ntl > 0) vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, jbeg, jend);
+
+    // i-bodies: k-th body of the thread is i0 + tid + k*T; pair q = (2q, 2q+1)
+    float2 nx[NP], ny[NP], nz[NP], skx[NP], sky[NP], skz[NP];
     float3 c;
+    bool gen;
     {
         float4 h[I], l[I], u[I];
         float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        bool bad = false;
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             const int i = i0 + threadIdx.x + k * T;
@@ -342,8 +375,12 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
                 mn[0] = fminf(mn[0], h[k].x); mx[0] = fmaxf(mx[0], h[k].x);
                 mn[1] = fminf(mn[1], h[k].y); mx[1] = fmaxf(mx[1], h[k].y);
                 mn[2] = fminf(mn[2], h[k].z); mx[2] = fmaxf(mx[2], h[k].z);
+                const float m = h[k].w;
+                bad |= !(m > 0.f && isfinite(u[k].x / m) && isfinite(u[k].y / m) &&
+                         isfinite(u[k].z / m));
             }
         }
+        gen = __syncthreads_or(bad) != 0;
         c = block_center<T>(mn, mx, red);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -351,12 +388,16 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
             nx[q] = make_float2(-rel(h[a].x, l[a].x, c.x), -rel(h[b].x, l[b].x, c.x));
             ny[q] = make_float2(-rel(h[a].y, l[a].y, c.y), -rel(h[b].y, l[b].y, c.y));
             nz[q] = make_float2(-rel(h[a].z, l[a].z, c.z), -rel(h[b].z, l[b].z, c.z));
-            mk[q] = make_float2(h[a].w, h[b].w);
-            nukx[q] = make_float2(-u[a].x, -u[b].x);
-            nuky[q] = make_float2(-u[a].y, -u[b].y);
-            nukz[q] = make_float2(-u[a].z, -u[b].z);
-            ia[q] = i0 + threadIdx.x + a * T;
-            ib[q] = i0 + threadIdx.x + b * T;
+            if (gen) {
+                skx[q] = make_float2(-u[a].x, -u[b].x);
+                sky[q] = make_float2(-u[a].y, -u[b].y);
+                skz[q] = make_float2(-u[a].z, -u[b].z);
+            } else {  // padding bodies (zero mass and cotangent) take sk = 0
+                const float ma = h[a].w > 0.f ? h[a].w : 1.f, mb = h[b].w > 0.f ? h[b].w : 1.f;
+                skx[q] = make_float2(-(u[a].x / ma), -(u[b].x / mb));
+                sky[q] = make_float2(-(u[a].y / ma), -(u[b].y / mb));
+                skz[q] = make_float2(-(u[a].z / ma), -(u[b].z / mb));
+            }
         }
     }
     const float2 e2 = make_float2(p.eps2f, p.eps2f);
@@ -364,75 +405,107 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     VjpTotals<T, I, TSM> tot;
     tot.sh = tsh;
 #pragma unroll
-    for (int q = 0; q < 7; ++q)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int k = 0; k < I; ++k) tot.at(q, k) = 0.0;
 
-    float4 bh[LPT], bl[LPT], bu[LPT];
-    if (t0 < t1) {
-        vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, t0 * J, n);
-        vjp_stage_store<T, J>(tile[0], bh, bl, bu, c);
-    }
+    if (ntl > 0) vjp_stage_store<T, J>(tile[0], bh, bl, bu, c);
     __syncthreads();
-    for (int t = t0; t < t1; ++t) {
-        const int bsel = (t - t0) & 1;
-        if (t + 1 < t1) vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, (t + 1) * J, n);
+    for (int t = 0; t < ntl; ++t) {
+        const int bsel = t & 1;
+        if (t + 1 < ntl) vjp_stage_load<T, J>(bh, bl, bu, Ph, Pl, Pu, jbeg + (t + 1) * J, jend);
         acc.zero();
         const float4 *s = tile[bsel];
-        const int jb = t * J;
+        const int jb = jbeg + t * J;
+        const int jn = min(J, (jend - jb + 3) & ~3);  // zero-padded bodies add nothing
         const bool self_tile = jb < i0 + TILE_I && i0 < jb + J;
-        if (self_tile) {
+        if (!gen && self_tile) {
 #pragma unroll 2
-            for (int jj = 0; jj < J; ++jj) {
+            for (int jj = 0; jj < jn; ++jj) {
                 const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
                              q3 = s[4 * jj + 3];
                 const int jg = jb + jj;
 #pragma unroll
-                for (int q = 0; q < NP; ++q)
-                    vjp_pair<ZEPS, true>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
-                                         make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
-                                         make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
-                                         make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q], mk[q],
-                                         nukx[q], nuky[q], nukz[q], jg == ia[q], jg == ib[q],
-                                         acc.px[q], acc.py[q], acc.pz[q], acc.qx[q], acc.qy[q],
-                                         acc.qz[q], acc.gm[q]);
+                for (int q = 0; q < NP; ++q) {
+                    const int ia = i0 + threadIdx.x + 2 * q * T;
+                    vjp_pair<ZEPS, true, false>(
+                        make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                        make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
+                        make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                        make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q], e2, skx[q], sky[q],
+                        skz[q], jg == ia, jg == ia + T, acc.gx[q], acc.gy[q], acc.gz[q],
+                        acc.gm[q]);
+                }
             }
-        } else {
-#pragma unroll 4
-            for (int jj = 0; jj < J; ++jj) {
-                const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
-                             q3 = s[4 * jj + 3];
+        } else if (!gen) {
+            for (int j4 = 0; j4 < jn; j4 += 4) {
 #pragma unroll
-                for (int q = 0; q < NP; ++q)
-                    vjp_pair<ZEPS, false>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
-                                          make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
-                                          make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
-                                          make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q],
-                                          mk[q], nukx[q], nuky[q], nukz[q], false, false,
-                                          acc.px[q], acc.py[q], acc.pz[q], acc.qx[q], acc.qy[q],
-                                          acc.qz[q], acc.gm[q]);
+                for (int jj = j4; jj < j4 + 4; ++jj) {
+                    const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
+                                 q3 = s[4 * jj + 3];
+#pragma unroll
+                    for (int q = 0; q < NP; ++q)
+                        vjp_pair<ZEPS, false, false>(
+                            make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                            make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
+                            make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                            make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q], e2, skx[q],
+                            sky[q], skz[q], false, false, acc.gx[q], acc.gy[q], acc.gz[q],
+                            acc.gm[q]);
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float2 *v[7] = {&acc.px[q], &acc.py[q], &acc.pz[q], &acc.qx[q],
-                                  &acc.qy[q], &acc.qz[q], &acc.gm[q]};
+            if (!gen && acc.finite(q)) {
+                const float2 *v[4] = {&acc.gx[q], &acc.gy[q], &acc.gz[q], &acc.gm[q]};
 #pragma unroll
-            for (int r = 0; r < 7; ++r) {
-                tot.at(r, 2 * q) += (double)v[r]->x;
-                tot.at(r, 2 * q + 1) += (double)v[r]->y;
+                for (int r = 0; r < 4; ++r) {
+                    tot.at(r, 2 * q) += (double)v[r]->x;
+                    tot.at(r, 2 * q + 1) += (double)v[r]->y;
+                }
+                continue;
             }
+            // the direct form for this lane and tile
+            const int ia = i0 + threadIdx.x + 2 * q * T, ib = ia + T;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ua = ia < n ? __ldg(Pu + ia) : z, ub = ib < n ? __ldg(Pu + ib) : z;
+            const float ma = ia < n ? __ldg(Ph + ia).w : 0.f, mb = ib < n ? __ldg(Ph + ib).w : 0.f;
+            const float2 mk = make_float2(ma, mb);
+            const float2 ukx = make_float2(-ua.x, -ub.x), uky = make_float2(-ua.y, -ub.y),
+                         ukz = make_float2(-ua.z, -ub.z);
+            float2 g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
+            for (int jj = 0; jj < jn; ++jj) {
+                const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
+                             q3 = s[4 * jj + 3];
+                const int jg = jb + jj;
+                vjp_pair<ZEPS, true, true>(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                                           make_float2(q1.x, q1.y), make_float2(q1.z, q1.w),
+                                           make_float2(q2.x, q2.y), make_float2(q2.z, q2.w),
+                                           make_float2(q3.x, q3.y), e2, nx[q], ny[q], nz[q], mk,
+                                           ukx, uky, ukz, jg == ia, jg == ib, g0, g1, g2, g3);
+            }
+            // units of the CTA's totals: m_k (scaled form) or absolute
+            const double sa = gen || !(ma > 0.f) ? 1.0 : 1.0 / (double)ma;
+            const double sb = gen || !(mb > 0.f) ? 1.0 : 1.0 / (double)mb;
+            tot.at(0, 2 * q) += (double)g0.x * sa;
+            tot.at(1, 2 * q) += (double)g1.x * sa;
+            tot.at(2, 2 * q) += (double)g2.x * sa;
+            tot.at(3, 2 * q) += (double)g3.x;
+            tot.at(0, 2 * q + 1) += (double)g0.y * sb;
+            tot.at(1, 2 * q + 1) += (double)g1.y * sb;
+            tot.at(2, 2 * q + 1) += (double)g2.y * sb;
+            tot.at(3, 2 * q + 1) += (double)g3.y;
         }
-        if (t + 1 < t1) vjp_stage_store<T, J>(tile[bsel ^ 1], bh, bl, bu, c);
+        if (t + 1 < ntl) vjp_stage_store<T, J>(tile[bsel ^ 1], bh, bl, bu, c);
         __syncthreads();
     }
 
-    // gx = G (P - 3 Q), gm = -G M
+    // gx = G m_k sum b/s^3 (G sum b/s^3 in the direct form), gm = -G M
     auto emit = [&](int i, const double *sums) {
-        const double x = p.G * (sums[0] - 3.0 * sums[3]);
-        const double y = p.G * (sums[1] - 3.0 * sums[4]);
-        const double z = p.G * (sums[2] - 3.0 * sums[5]);
-        const double g = -p.G * sums[6];
+        const double f = gen ? p.G : p.G * (double)__ldg(Ph + i).w;
+        const double x = f * sums[0], y = f * sums[1], z = f * sums[2];
+        const double g = -p.G * sums[3];
         double *o = p.gx + 3 * (size_t)i;
         if (p.accumulate) {
             o[0] += x; o[1] += y; o[2] += z;
@@ -448,9 +521,9 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
         for (int k = 0; k < I; ++k) {
             const int i = i0 + threadIdx.x + k * T;
             if (i < n) {
-                double sums[7];
+                double sums[4];
 #pragma unroll
-                for (int r = 0; r < 7; ++r) sums[r] = tot.at(r, k);
+                for (int r = 0; r < 4; ++r) sums[r] = tot.at(r, k);
                 emit(i, sums);
             }
         }
@@ -460,9 +533,9 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     for (int k = 0; k < I; ++k) {
         const int i = i0 + threadIdx.x + k * T;
         if (i < n) {
-            double *q = p.partial + ((size_t)js * n + i) * 7;
-#pragma unroll
-            for (int r = 0; r < 7; ++r) q[r] = tot.at(r, k);
+            double2 *q = reinterpret_cast<double2 *>(p.partial + ((size_t)js * n + i) * 4);
+            q[0] = make_double2(tot.at(0, k), tot.at(1, k));
+            q[1] = make_double2(tot.at(2, k), tot.at(3, k));
         }
     }
     __threadfence();
@@ -471,18 +544,26 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // The splits' sums in split order; the loads of several splits and both
+    // bodies are in flight together (this runs at the end of the launch).
+    double sums[I][4];
+#pragma unroll
+    for (int k = 0; k < I; ++k) sums[k][0] = sums[k][1] = sums[k][2] = sums[k][3] = 0.0;
+#pragma unroll 4
+    for (int q = 0; q < p.nsplit; ++q) {
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int i = min(i0 + threadIdx.x + k * T, n - 1);  // rows past n: not emitted
+            const double2 *r =
+                reinterpret_cast<const double2 *>(p.partial + ((size_t)q * n + i) * 4);
+            const double2 a = __ldcg(r), b = __ldcg(r + 1);
+            sums[k][0] += a.x; sums[k][1] += a.y; sums[k][2] += b.x; sums[k][3] += b.y;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < I; ++k) {
         const int i = i0 + threadIdx.x + k * T;
-        if (i < n) {
-            double sums[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (int q = 0; q < p.nsplit; ++q) {
-                const double *r = p.partial + ((size_t)q * n + i) * 7;
-#pragma unroll
-                for (int u = 0; u < 7; ++u) sums[u] += __ldcg(r + u);
-            }
-            emit(i, sums);
-        }
+        if (i < n) emit(i, sums[k]);
     }
     if (threadIdx.x == 0) p.counters[it] = 0u;
 }
@@ -511,6 +592,11 @@ const Pair kVjp32[] = {
     // shorter j-tiles and smaller CTAs with totals in registers (9..10)
     NB_VJP32_ENTRY(64, 2, 64),
     NB_VJP32_ENTRY(64, 2, 128),
+    // float64 totals in shared memory, 7 or 8 CTAs/SM (11..12); four bodies
+    // per thread at 4 CTAs/SM (13)
+    NB_VJP32_ENTRY_X(128, 2, 128, true, 7),
+    NB_VJP32_ENTRY_X(128, 2, 128, true, 8),
+    NB_VJP32_ENTRY_X(128, 4, 128, true, 4),
 };
 const Pair kVjp64[] = {
     NB_VJP_ENTRY(double, 128, 1, 128),

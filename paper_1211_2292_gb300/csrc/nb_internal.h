@@ -93,7 +93,7 @@ struct VjpParams {
     double *gx;           // [n][3]
     double *gm;           // [n]
     int accumulate;       // 0: overwrite gx/gm with G*sum; 1: add G*sum
-    double *partial;      // [nsplit][n][4] (float64 kernel) or [nsplit][n][7] (float32)
+    double *partial;      // [nsplit][n][4]
     unsigned *counters;
     int *err;
 };

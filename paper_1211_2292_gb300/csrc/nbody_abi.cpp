@@ -379,7 +379,7 @@ nb_status vjp_packed(nb_ctx *c, cudaStream_t s, int64_t n, double G, double eps,
     int v, forced;
     pick(c, nb::KIND_VJP, n, v, forced);
     const KernelEntry &k = kernel_for(nb::KIND_VJP, c->prec, v, zeps);
-    const int S = splits_for(c, k, n, forced, is_f64(c) ? 4 : 7);
+    const int S = splits_for(c, k, n, forced, 4);
     nb::VjpParams p;
     p.PV = c->pack;
     p.Plo = is_f64(c) ? nullptr : lo_half(c);

@@ -41,7 +41,7 @@ def test_vjp_variants_and_splits(cuda, prec):
     rgx, rgm = oracle.force_vjp(b.pos, b.mass, lam, 1.0, 0.02)
     tol = 1e-12 if prec == "fp64" else 5e-5
     for v in range(len(nbody.variants(nbody.KIND_VJP, prec))):
-        for split in (1, 4):
+        for split in (1, 4, 7):
             with nbody.NBody(1500, prec) as nb:
                 nb.tune_set(nbody.KIND_VJP, 0, 1 << 40, v, split)
                 gx, gm = nb.forces_backward(to_dev(b.pos, cuda), to_dev(b.mass, cuda), 1.0, 0.02,
@@ -61,6 +61,49 @@ def test_vjp_smooth_cotangent_fp32(cuda):
         gx, gm = nb.forces_backward(to_dev(b.pos, cuda), to_dev(b.mass, cuda), 1.0, 0.01,
                                     to_dev(lam, cuda))
     assert _rel(host(gx), rgx) <= 5e-5 and _rel(host(gm), rgm) <= 5e-5
+
+
+def _vjp32(cuda, pos, mass, lam, G, eps, variant=None):
+    with nbody.NBody(len(mass), "fp32_comp") as nb:
+        if variant is not None:
+            nb.tune_set(nbody.KIND_VJP, 0, 1 << 40, variant, 0)
+        gx, gm = nb.forces_backward(to_dev(pos, cuda), to_dev(mass, cuda), G, eps,
+                                    to_dev(lam, cuda))
+        nb.sync()
+        return host(gx), host(gm)
+
+
+@pytest.mark.parametrize("variant", [0, 5])
+def test_vjp_massless_bodies_fp32(cuda, variant):
+    # Bodies of zero mass: the float32 kernel cannot form mu_k/m_k, so every
+    # CTA holding one takes the m_k mu_j - m_j mu_k form; the others keep the
+    # mu_j - m_j mu_k/m_k form.  Both against the oracle.
+    b = inputs.plummer(1500, seed=49)
+    mass = b.mass.copy()
+    mass[:300:7] = 0.0  # the first CTAs hold massless bodies, the later ones none
+    lam = np.random.default_rng(49).normal(size=(b.n, 3))
+    rgx, rgm = oracle.force_vjp(b.pos, mass, lam, 1.0, 0.01)
+    gx, gm = _vjp32(cuda, b.pos, mass, lam, 1.0, 0.01, variant)
+    assert _rel(gx, rgx) <= 5e-5 and _rel(gm, rgm) <= 5e-5
+
+
+@pytest.mark.parametrize("variant", [0, 5])
+def test_vjp_tiny_mass_large_cotangent_fp32(cuda, variant):
+    # m_j mu_k/m_k beyond the float32 range for a light body k with a large
+    # cotangent next to heavy bodies j (mu_k/m_k itself finite): the lanes
+    # whose tile sums overflow evaluate that tile again in the
+    # m_k mu_j - m_j mu_k form, which stays finite, as the oracle does.
+    b = inputs.plummer(1000, seed=50)
+    mass = b.mass.copy()
+    mass[[10, 400]] = 10.0
+    mass[600] = 1e-30
+    lam = np.random.default_rng(50).normal(size=(b.n, 3))
+    lam[600] = [1e8, -2e8, 5e7]
+    assert np.isfinite(np.float32(lam[600, 1]) / np.float32(mass[600]))
+    rgx, rgm = oracle.force_vjp(b.pos, mass, lam, 1.0, 0.01)
+    gx, gm = _vjp32(cuda, b.pos, mass, lam, 1.0, 0.01, variant)
+    assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gm))
+    assert _rel(gx, rgx) <= 5e-5 and _rel(gm, rgm) <= 5e-5
 
 
 def test_vjp_zero_softening(cuda):
