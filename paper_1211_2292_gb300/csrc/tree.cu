@@ -26,8 +26,8 @@
 //
 // Walk arithmetic: float32 pair terms in coordinates relative to the
 // group's centre (hi/lo packed positions and centres of mass, as in the
-// direct-sum kernel), float32 partial sums over every FLUSH listed sources
-// folded into Kahan (sum, carry) pairs.
+// direct-sum kernel), float32 partial sums over every NB_WALK_FOLD_EVERY
+// flushes of FLUSH listed sources folded into Kahan (sum, carry) pairs.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -326,9 +326,12 @@ __device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const floa
     return d2;
 }
 
-// Interaction list of a warp: up to LIST_CAP sources (cells or bodies) as
-// (x, y, z, m), coordinates relative to the group's centre, laid out for
-// float32x2 arithmetic.  Paired layout: two sources share an instruction,
+// Interaction list of a warp: a ring of LIST_CAP sources (cells or bodies)
+// as (x, y, z, m), coordinates relative to the group's centre, laid out for
+// float32x2 arithmetic.  A flush evaluates the FLUSH sources of the half the
+// ring's head is in and moves the head to the other half; at most
+// FLUSH - 1 + 32 sources are ever listed, so new ones never reach the half
+// being evaluated.  Paired layout: two sources share an instruction,
 // a pair of sources is {x0, x1, y0, y1}, {z0, z1, m0, m1} (one body per
 // lane, or each of a lane's two bodies in turn).  Doubled layout (two
 // bodies per lane, NB_WALK_PAIRED 0): one source meets both bodies, stored
@@ -338,6 +341,9 @@ __device__ __forceinline__ float cube_box_dist2(float4 lo, float4 hi, const floa
 #endif
 #ifndef NB_WALK_PAIRED
 #define NB_WALK_PAIRED 1
+#endif
+#ifndef NB_WALK_FOLD_EVERY
+#define NB_WALK_FOLD_EVERY 4  // flushes between Kahan folds of the float32 partials
 #endif
 constexpr int FLUSH = NB_WALK_FLUSH;  // sources evaluated per flush (a multiple of 32)
 constexpr int LIST_CAP = 2 * FLUSH;
@@ -446,6 +452,7 @@ template <int BPL, bool MULTI>
 struct WalkShared {
     float4 list[WALK_WARPS][list_f4<BPL>()];  // float4 slots of the lists
     int2 ranges[WALK_WARPS][LEVELS][32];
+    int lslot[MULTI ? 1 : WALK_WARPS][32];  // a chunk's leaf starts: body index minus position
     float crit2[MULTI ? 1 + WALK_MAX_MORE : 1][LEVELS];  // per walked tree
 };
 
@@ -526,6 +533,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
     const float4 *L4 = list_s[warp];
     int2(*rs)[32] = sh.ranges[warp];
     const unsigned lt = (1u << lane) - 1u;
+    int head = 0;  // the list ring's current half (0 or FLUSH)
 
     // Each tree's sum per body, G (s - c) from its Kahan pair, added in tree
     // order in float64 (as separate accumulating walks would add them).
@@ -576,14 +584,14 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         ax = ay = az = bx = by = bz = make_float2(0.f, 0.f);
     };
     int cnt = 0;  // listed sources (warp-uniform)
-    // FLUSH sources listed: add them, move the rest (< FLUSH) to the front
+    int nflush = 0;
+    // FLUSH sources listed from the head on: add them, head to the other half
     auto flush = [&]() {
         __syncwarp();
-        list_eval<ZEPS, BPL>(L4, FLUSH, nx, ny, nz, e2, ax, ay, az, nx2, ny2, nz2, bx, by, bz);
-        fold();
-        __syncwarp();
-#pragma unroll
-        for (int c = lane; c < LIST_F4 / 2; c += 32) list_s[warp][c] = list_s[warp][LIST_F4 / 2 + c];
+        list_eval<ZEPS, BPL>(L4 + (paired_list<BPL>() ? head : 2 * head), FLUSH, nx, ny, nz, e2,
+                             ax, ay, az, nx2, ny2, nz2, bx, by, bz);
+        if (++nflush % NB_WALK_FOLD_EVERY == 0) fold();
+        head ^= FLUSH;
         cnt -= FLUSH;
         __syncwarp();
     };
@@ -602,7 +610,10 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         const int incl = warp_incl_scan(r.y, lane);
         const int excl = incl - r.y;
         const int take = min(__shfl_sync(FULL, incl, 31), 32);
-        const int src = warp_span_of(incl, lane);  // range holding this lane's node
+        // the range holding this lane's node: the last range starting at or
+        // before it (ranges 0..R-1 are non-empty, so their starts increase)
+        const unsigned starts = __reduce_or_sync(FULL, lane < R && excl < 32 ? 1u << excl : 0u);
+        const int src = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
         const int first_src = __shfl_sync(FULL, r.x, src), excl_src = __shfl_sync(FULL, excl, src);
         const int node = lane < take ? first_src + (lane - excl_src) : -1;
         const unsigned done = __ballot_sync(FULL, lane < R && incl <= 32);
@@ -660,8 +671,8 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         if (am) {
             if (accept) {
                 const float4 ch = __ldg(t.chi + node), cl = __ldg(t.clo + node);
-                list_put<BPL>(L, cnt + __popc(am & lt), rel(ch.x, cl.x, cx), rel(ch.y, cl.y, cy),
-                              rel(ch.z, cl.z, cz), ch.w);
+                list_put<BPL>(L, (head + cnt + __popc(am & lt)) & (LIST_CAP - 1),
+                              rel(ch.x, cl.x, cx), rel(ch.y, cl.y, cy), rel(ch.z, cl.z, cz), ch.w);
             }
             cnt += __popc(am);
             nc += __popc(am);
@@ -679,28 +690,47 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
             const int lexc = linc - lsz;
             const int T = __shfl_sync(FULL, linc, 31);
             nb += T;
+            int carry = 0;  // the offset of the leaf running into the chunk
             for (int c0 = 0; c0 < T; c0 += 32) {
                 const int pos = c0 + lane;
-                const int j = warp_span_of(linc, pos);
-                const int body = __shfl_sync(FULL, ls, j & 31) + (pos - __shfl_sync(FULL, lexc, j & 31));
+                int body;
+                if constexpr (MULTI) {  // (the slots cost this instance spills)
+                    const int j = warp_span_of(linc, pos);
+                    body = __shfl_sync(FULL, ls, j & 31) + (pos - __shfl_sync(FULL, lexc, j & 31));
+                } else {
+                    // the leaf holding position pos: the last one starting at
+                    // or before it, in this chunk (its slot) or earlier (carry)
+                    const bool st = lsz > 0 && lexc >= c0 && lexc < c0 + 32;
+                    if (st) sh.lslot[warp][lexc - c0] = ls - lexc;
+                    const unsigned S = __reduce_or_sync(FULL, st ? 1u << (lexc - c0) : 0u);
+                    __syncwarp();
+                    const unsigned below = S & (0xffffffffu >> (31 - lane));
+                    const int off = below ? sh.lslot[warp][31 - __clz(below)] : carry;
+                    carry = __shfl_sync(FULL, off, 31);
+                    body = off + pos;
+                }
                 const int kk = min(32, T - c0);
                 if (lane < kk) {
                     const float4 bh = __ldg(t.sP + body), bl = __ldg(t.sPlo + body);
-                    list_put<BPL>(L, cnt + lane, rel(bh.x, bl.x, cx), rel(bh.y, bl.y, cy),
-                                  rel(bh.z, bl.z, cz), bh.w);
+                    list_put<BPL>(L, (head + cnt + lane) & (LIST_CAP - 1), rel(bh.x, bl.x, cx),
+                                  rel(bh.y, bl.y, cy), rel(bh.z, bl.z, cz), bh.w);
                 }
                 cnt += kk;
                 if (cnt >= FLUSH) flush();
+                __syncwarp();  // the slots are rewritten for the next chunk
             }
         }
     }
-    if (cnt > 0) {  // the rest (paired layout: padded to a pair with a massless source)
-        if (paired_list<BPL>() && lane == 0 && (cnt & 1)) list_put<BPL>(L, cnt, 0.f, 0.f, 0.f, 0.f);
+    if (cnt > 0) {  // the rest, within the head's half (paired layout: padded to a
+                    // pair with a massless source)
+        if (paired_list<BPL>() && lane == 0 && (cnt & 1))
+            list_put<BPL>(L, head + cnt, 0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        list_eval<ZEPS, BPL>(L4, paired_list<BPL>() ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay,
+        list_eval<ZEPS, BPL>(L4 + (paired_list<BPL>() ? head : 2 * head),
+                             paired_list<BPL>() ? (cnt + 1) & ~1 : cnt, nx, ny, nz, e2, ax, ay,
                              az, nx2, ny2, nz2, bx, by, bz);
-        fold();
     }
+    if (nflush % NB_WALK_FOLD_EVERY != 0 || cnt > 0) fold();
     __syncwarp();  // the next tree reuses this warp's list and stacks
 #pragma unroll
     for (int b = 0; b < BPL; ++b) {
