@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
     const int i0 = it * TILE_I;
     // j-split js covers bodies [jbeg, jend): equal shares to the body, so that
     // the CTAs of one wave carry equal work; its last tile is zero-padded to
-    // a multiple of four bodies
+    // a multiple of the tile loop's step (8 bodies for I = 2, else 4)
     const int jbeg = (int)(((long long)n * js) / p.nsplit);
     const int jend = (int)(((long long)n * (js + 1)) / p.nsplit);
     const int ntl = (jend - jbeg + J - 1) / J;
@@ -417,7 +417,9 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
         acc.zero();
         const float4 *s = tile[bsel];
         const int jb = jbeg + t * J;
-        const int jn = min(J, (jend - jb + 3) & ~3);  // zero-padded bodies add nothing
+        // zero-padded bodies add nothing; the tile loop takes U bodies at a time
+        constexpr int U = I == 2 ? 8 : 4;
+        const int jn = min(J, (jend - jb + U - 1) & ~(U - 1));
         const bool self_tile = jb < i0 + TILE_I && i0 < jb + J;
         if (!gen && self_tile) {
 #pragma unroll 2
@@ -438,9 +440,9 @@ __global__ void __launch_bounds__(T, MINB) vjp_f32_kernel(const VjpParams p)
                 }
             }
         } else if (!gen) {
-            for (int j4 = 0; j4 < jn; j4 += 4) {
+            for (int j4 = 0; j4 < jn; j4 += U) {
 #pragma unroll
-                for (int jj = j4; jj < j4 + 4; ++jj) {
+                for (int jj = j4; jj < j4 + U; ++jj) {
                     const float4 q0 = s[4 * jj], q1 = s[4 * jj + 1], q2 = s[4 * jj + 2],
                                  q3 = s[4 * jj + 3];
 #pragma unroll
