@@ -433,8 +433,10 @@ nb_status nb_fmm_reserve(nb_ctx *ctx, int64_t entries);
  *    the opening angle theta of the exports; counts (optional, device int32
  *    [n][2]) = cells and bodies met over all trees.  With no LET it is the
  *    tree code's nb_tree_forces.  nb_tree_stats then reports the summed
- *    interactions.  Up to 64 trees are walked in one launch, each group of
- *    bodies walking them in turn and adding their float64 sums in order.
+ *    interactions.  Up to 64 trees are walked in one launch, one task per
+ *    (group of bodies, tree), the group's float64 sums added in tree order;
+ *    the context keeps per-tree sums for that (24 bytes per body and tree,
+ *    grown on demand).
  */
 #define NB_ORB_MAX_P 64
 nb_status nb_orb_box(nb_ctx *ctx, int64_t n, const double *pos, const int32_t *group, int ngroups,

@@ -198,8 +198,15 @@ struct TreeWalkParams {
     double half_dt;
     int *counts;            // optional [n][2]: cells, bodies met per body
     int *err;
-    const WalkSource *more;  // device [nmore]: trees walked after `tree`, their sums added
-    int nmore;               // in order (as separate accumulating walks would), 0..WALK_MAX_MORE
+    const WalkSource *more;  // device [1 + nmore] when nmore > 0: `tree` (again) and the trees
+    int nmore;               // walked after it, their sums added in order (as separate
+                             // accumulating walks would); nmore 0..WALK_MAX_MORE
+    // Split mode (nmore > 0): one task per group and span of tspan trees; each
+    // writes its span's sums, the group's last task adds them in tree order.
+    int tspan;               // trees per task (1: every tree's sum added in turn)
+    double *tpart;           // [spans][groups * group][3] per-span sums, group order
+    int *tcnt;               // [spans][groups][2] per-span cells, bodies met
+    unsigned *tctr;          // [groups] tasks arrived; zero between launches
 };
 int tree_meta_ints();
 // Upper bound on the node count of a tree over n bodies with leaves of at
@@ -456,7 +463,11 @@ struct nb_ctx {
     int let_cap = 0;
     float *let_box = nullptr;               // 6 floats out + 6 unsigned of work
     int *let_queue = nullptr;               // group queue of the LET walks
-    nb::WalkSource *let_src = nullptr;      // [WALK_MAX_MORE] the received trees of one walk
+    nb::WalkSource *let_src = nullptr;      // [1 + WALK_MAX_MORE] the trees of one multi-tree walk
+    double *let_tpart = nullptr;            // split LET walk: per-tree sums
+    int *let_tcnt = nullptr;                //   per-tree counts
+    unsigned *let_tctr = nullptr;           //   per-group arrivals (kept zero)
+    int64_t let_tpart_cap = 0, let_tcnt_cap = 0, let_tctr_cap = 0;
     int64_t let_n = 0;                      // bodies of the local tree of nb_let_build
 
     std::map<const void *, int> occ;  // resident CTAs per SM, per kernel

@@ -572,6 +572,9 @@ void free_ctx(nb_ctx *c)
     cudaFree(c->let_box);
     cudaFree(c->let_queue);
     cudaFree(c->let_src);
+    cudaFree(c->let_tpart);
+    cudaFree(c->let_tcnt);
+    cudaFree(c->let_tctr);
     if (c->host_out) cudaFreeHost(c->host_out);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -827,6 +830,10 @@ nb_status tree_forces_enqueue(nb_ctx *c, cudaStream_t s, int64_t n, const double
     p.err = c->err;
     p.more = nullptr;
     p.nmore = 0;
+    p.tspan = 1;
+    p.tpart = nullptr;
+    p.tcnt = nullptr;
+    p.tctr = nullptr;
     TreeTimer tm(c, nb::PROF_TREE_WALK, s);
     NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
     c->launches += k;
@@ -1774,7 +1781,8 @@ nb_status ensure_let(nb_ctx *c)
     nb_status st = NB_OK;
     if (!c->let_box) c->let_box = dev_alloc<float>(c, 12, st);
     if (st == NB_OK && !c->let_queue) c->let_queue = dev_alloc<int>(c, 1, st);
-    if (st == NB_OK && !c->let_src) c->let_src = dev_alloc<nb::WalkSource>(c, nb::WALK_MAX_MORE, st);
+    if (st == NB_OK && !c->let_src)
+        c->let_src = dev_alloc<nb::WalkSource>(c, 1 + nb::WALK_MAX_MORE, st);
     if (st == NB_OK && !c->let.totals) c->let.totals = dev_alloc<int>(c, 2, st);
     if (st != NB_OK) return st;
     if (c->let_cap < c->tree.cap) {
@@ -1793,8 +1801,39 @@ nb_status ensure_let(nb_ctx *c)
     return NB_OK;
 }
 
+// Scratch of the split LET walk for ntrees trees over `groups` groups of
+// `group` bodies (grown, never shrunk; the arrival counters start at zero
+// and every launch leaves them at zero).
+nb_status ensure_let_split(nb_ctx *c, int ntrees, int64_t groups, int group)
+{
+    nb_status st = NB_OK;
+    const int64_t part = (int64_t)ntrees * groups * group * 3, cnt = (int64_t)ntrees * groups * 2;
+    if (c->let_tpart_cap < part) {
+        cudaFree(c->let_tpart);
+        c->let_tpart = dev_alloc<double>(c, (size_t)part, st);
+        c->let_tpart_cap = st == NB_OK ? part : 0;
+        if (st != NB_OK) return st;
+    }
+    if (c->let_tcnt_cap < cnt) {
+        cudaFree(c->let_tcnt);
+        c->let_tcnt = dev_alloc<int>(c, (size_t)cnt, st);
+        c->let_tcnt_cap = st == NB_OK ? cnt : 0;
+        if (st != NB_OK) return st;
+    }
+    if (c->let_tctr_cap < groups) {
+        cudaFree(c->let_tctr);
+        c->let_tctr = dev_alloc<unsigned>(c, (size_t)groups, st);
+        c->let_tctr_cap = 0;
+        if (st != NB_OK) return st;
+        NB_CUDA(c, cudaMemset(c->let_tctr, 0, (size_t)groups * sizeof(unsigned)));
+        c->let_tctr_cap = groups;
+    }
+    return NB_OK;
+}
+
 // One walk launch over tree view t with sources (sP, sPlo) and box, then
-// the nmore trees at more (device), onto the context's local bodies.
+// the nmore trees at more (device), onto the context's local bodies; with
+// received trees, one task per (group, tree).
 nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float4 *sP,
                    const float4 *sPlo, const double *box, const nb::WalkSource *more,
                    int nmore, double G, double eps, double theta, int group, double *acc,
@@ -1826,6 +1865,17 @@ nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float
     p.err = c->err;
     p.more = more;
     p.nmore = nmore;
+    p.tspan = 1;
+    p.tpart = nullptr;
+    p.tcnt = nullptr;
+    p.tctr = nullptr;
+    if (nmore > 0 && p.n > 0) {
+        const int64_t groups = (p.n + group - 1) / group;
+        NB_TRY(ensure_let_split(c, 1 + nmore, groups, group));
+        p.tpart = c->let_tpart;
+        p.tcnt = c->let_tcnt;
+        p.tctr = c->let_tctr;
+    }
     int k = 0;
     TreeTimer tm(c, nb::PROF_TREE_WALK, s);
     NB_CUDA(c, nb::launch_tree_walk(s, p, p.eps2f == 0.0f, k));
@@ -2084,19 +2134,25 @@ nb_status nb_let_forces(nb_ctx *c, double G, double eps, double theta, int group
                                         (const float4 *)(b + lay.P),   (const float4 *)(b + lay.Plo),
                                         (const double *)(b + offsetof(nb::LetHeader, box))};
     }
+    // a multi-tree launch reads every tree it walks, the first included, from
+    // let_src: the local tree, then the received ones
+    src.insert(src.begin(), nb::WalkSource{c->tree.box_lo, c->tree.box_hi, c->tree.chi,
+                                           c->tree.clo, c->tree.start, c->tree.end, c->tree_P,
+                                           c->tree_Plo, c->tree_box});
     const int first = (int)std::min<int64_t>(nlet, nb::WALK_MAX_MORE);
     if (first > 0)  // from pageable memory: staged before the call returns
-        NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data(), first * sizeof(nb::WalkSource),
+        NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data(), (1 + first) * sizeof(nb::WalkSource),
                                    cudaMemcpyHostToDevice, s));
     NB_TRY(let_walk(c, s, c->tree, c->tree_P, c->tree_Plo, c->tree_box, c->let_src, first, G, eps,
                     theta, group, acc, counts, 0));
     for (int64_t q0 = first; q0 < nlet; q0 += 1 + nb::WALK_MAX_MORE) {
         // a further launch: tree q0, then up to WALK_MAX_MORE more, added on
         const int more = (int)std::min<int64_t>(nlet - q0 - 1, nb::WALK_MAX_MORE);
-        if (more > 0)
-            NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data() + q0 + 1,
-                                       more * sizeof(nb::WalkSource), cudaMemcpyHostToDevice, s));
-        const nb::WalkSource &w = src[(size_t)q0];
+        if (more > 0)  // (src[0] is the local tree: received tree q is src[1 + q])
+            NB_CUDA(c, cudaMemcpyAsync(c->let_src, src.data() + 1 + q0,
+                                       (1 + more) * sizeof(nb::WalkSource),
+                                       cudaMemcpyHostToDevice, s));
+        const nb::WalkSource &w = src[(size_t)(1 + q0)];
         nb::TreeView t{};
         t.cap = (int)hdr[(size_t)q0].n_nodes;
         t.box_lo = const_cast<float4 *>(w.box_lo);

@@ -459,7 +459,7 @@ struct WalkShared {
 // The walk of group g (bodies [g * 32 * BPL, ...) in key order) by one warp.
 template <bool ZEPS, int BPL, bool MULTI>
 __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<BPL, MULTI> &sh,
-                                           int g)
+                                           int g, int tq_only)
 {
     constexpr int GROUP = 32 * BPL;
     constexpr int LIST_F4 = list_f4<BPL>();
@@ -540,14 +540,17 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
     double tg[BPL][3];
     int nc = 0, nb = 0;
     const int ntrees = MULTI ? 1 + p.nmore : 1;
-    for (int tq = 0; tq < ntrees; ++tq) {
+    // split mode: this task walks trees [tq_only * tspan, ... + tspan)
+    const int tq_lo = MULTI && tq_only >= 0 ? tq_only * p.tspan : 0;
+    const int tq_hi = MULTI && tq_only >= 0 ? min(tq_lo + p.tspan, ntrees) : ntrees;
+    for (int tq = tq_lo; tq < tq_hi; ++tq) {
     WalkSource t;
-    if (!MULTI || tq == 0) {
+    if (!MULTI) {
         t = WalkSource{p.tree.box_lo, p.tree.box_hi, p.tree.chi, p.tree.clo,
                        p.tree.start,  p.tree.end,    p.sP,      p.sPlo,
                        p.box};
-    } else {
-        t = p.more[tq - 1];
+    } else {  // every tree of a multi-tree walk, the first included, from `more`
+        t = p.more[tq];
     }
     const float *crit2 = sh.crit2[MULTI ? tq : 0];
     float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax, bx = ax, by = ax, bz = ax;
@@ -738,9 +741,51 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
                              p.G * ((double)sy[b] - (double)qy[b]),
                              p.G * ((double)sz[b] - (double)qz[b])};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) tg[b][c] = (!MULTI || tq == 0) ? d[c] : __dadd_rn(tg[b][c], d[c]);
+        for (int c = 0; c < 3; ++c) tg[b][c] = (!MULTI || tq == tq_lo) ? d[c] : __dadd_rn(tg[b][c], d[c]);
     }
     }  // trees
+    bool stats_done = false;
+    if (MULTI && tq_only >= 0) {
+        // this task's sums and counts; the group's last task adds all tasks'
+        // in tree order (with one tree per task, as the walk over every tree
+        // in turn does) and writes
+        const int ngroups = (n + GROUP - 1) / GROUP;
+        const size_t npad = (size_t)ngroups * GROUP;
+#pragma unroll
+        for (int b = 0; b < BPL; ++b) {
+            double *q = p.tpart + ((size_t)tq_only * npad + base + 32 * b + lane) * 3;
+            q[0] = tg[b][0];
+            q[1] = tg[b][1];
+            q[2] = tg[b][2];
+        }
+        if (lane == 0) {
+            p.tcnt[((size_t)tq_only * ngroups + g) * 2] = nc;
+            p.tcnt[((size_t)tq_only * ngroups + g) * 2 + 1] = nb;
+            atomicAdd(p.tree.stats + 2, (unsigned long long)nc * nvalid);
+            atomicAdd(p.tree.stats + 3, (unsigned long long)nb * nvalid);
+        }
+        stats_done = true;
+        __threadfence();
+        __syncwarp();
+        unsigned last = 0;
+        const int nspans = (ntrees + p.tspan - 1) / p.tspan;
+        if (lane == 0) last = atomicAdd(p.tctr + g, 1u) == (unsigned)(nspans - 1);
+        if (!__shfl_sync(FULL, last, 0)) return;
+        __threadfence();
+        nc = nb = 0;
+        for (int tq = 0; tq < nspans; ++tq) {
+#pragma unroll
+            for (int b = 0; b < BPL; ++b) {
+                const double *q = p.tpart + ((size_t)tq * npad + base + 32 * b + lane) * 3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    tg[b][c] = tq == 0 ? __ldcg(q + c) : __dadd_rn(tg[b][c], __ldcg(q + c));
+            }
+            nc += __ldcg(p.tcnt + ((size_t)tq * ngroups + g) * 2);
+            nb += __ldcg(p.tcnt + ((size_t)tq * ngroups + g) * 2 + 1);
+        }
+        if (lane == 0) p.tctr[g] = 0u;  // every task of the group has arrived
+    }
 #pragma unroll
     for (int b = 0; b < BPL; ++b) {
         if (!valid[b]) continue;
@@ -772,7 +817,7 @@ __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<B
         }
         if (!finite3(gx, gy, gz)) atomicOr(p.err, ERR_NONFINITE);
     }
-    if (lane == 0) {  // nc, nb are the same for the group's nvalid bodies
+    if (lane == 0 && !stats_done) {  // nc, nb are the same for the group's nvalid bodies
         atomicAdd(p.tree.stats + 2, (unsigned long long)nc * nvalid);
         atomicAdd(p.tree.stats + 3, (unsigned long long)nb * nvalid);
     }
@@ -791,29 +836,38 @@ __global__ void __launch_bounds__(32 * WALK_WARPS, BPL == 1 ? NB_WALK_MINB1 : NB
     __shared__ WalkShared<BPL, MULTI> sh;
     for (int q = threadIdx.x; q < (MULTI ? 1 + p.nmore : 1) * LEVELS; q += blockDim.x) {
         const int tq = q / LEVELS, L = q % LEVELS;
-        sh.crit2[tq][L] = open_dist2(tq == 0 ? p.box[3] : p.more[tq - 1].box[3], L, p.theta);
+        sh.crit2[tq][L] = open_dist2(MULTI ? p.more[tq].box[3] : p.box[3], L, p.theta);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WALK_WARPS + warp;
+    const int ngroups = (p.n + 32 * BPL - 1) / (32 * BPL);
+    // tasks: the groups, or with further trees (split mode) the (group,
+    // tree) pairs, tree-major
+    const int ntasks = MULTI ? ngroups * ((1 + p.nmore + p.tspan - 1) / p.tspan) : ngroups;
+    auto task = [&](int t) {
+        if constexpr (MULTI)
+            walk_group<ZEPS, BPL, MULTI>(p, sh, t % ngroups, t / ngroups);
+        else
+            walk_group<ZEPS, BPL, MULTI>(p, sh, t, -1);
+    };
     if (p.sched == 0) {
-        walk_group<ZEPS, BPL, MULTI>(p, sh, gw);
+        if (gw < ntasks) task(gw);
         return;
     }
-    const int ngroups = (p.n + 32 * BPL - 1) / (32 * BPL);
     const int nwarps = gridDim.x * WALK_WARPS;
     int *queue = p.queue;
     int seen = 0;
     for (;;) {
         int c = p.chunk;
-        if (p.sched == 2) c = max(c, (ngroups - seen) / (2 * nwarps));
+        if (p.sched == 2) c = max(c, (ntasks - seen) / (2 * nwarps));
         int g0 = 0;
         if (lane == 0) g0 = atomicAdd(queue, c);
         g0 = __shfl_sync(0xffffffffu, g0, 0);
-        if (g0 >= ngroups) break;
+        if (g0 >= ntasks) break;
         seen = g0 + c;
-        const int g1 = min(g0 + c, ngroups);
-        for (int g = g0; g < g1; ++g) walk_group<ZEPS, BPL, MULTI>(p, sh, g);
+        const int g1 = min(g0 + c, ntasks);
+        for (int g = g0; g < g1; ++g) task(g);
     }
 }
 
@@ -991,7 +1045,10 @@ cudaError_t launch_tree_walk(cudaStream_t s, const TreeWalkParams &p, bool zeps,
     kernels = 0;
     if (p.n <= 0) return cudaSuccess;
     const int G = p.group;
-    const int groups = (p.n + G - 1) / G;
+    if (p.nmore > 0 && (!p.tpart || !p.tcnt || !p.tctr || p.tspan < 1))
+        return cudaErrorInvalidValue;
+    const int groups =  // tasks
+        (p.n + G - 1) / G * (p.nmore > 0 ? (1 + p.nmore + p.tspan - 1) / p.tspan : 1);
     // (a separate instance walks further trees: the single-tree walk keeps
     // its own registers and shared memory)
     void (*fn)(const TreeWalkParams) =
