@@ -456,7 +456,9 @@ struct WalkShared {
     float crit2[MULTI ? 1 + WALK_MAX_MORE : 1][LEVELS];  // per walked tree
 };
 
-// The walk of group g (bodies [g * 32 * BPL, ...) in key order) by one warp.
+// The walk of group g (bodies [g * 32 * BPL, ...) in key order) by one warp:
+// over the one tree (tq_only = -1), or (MULTI) over span tq_only of the trees
+// in p.more, the group's last span then writing the sums of all of them.
 template <bool ZEPS, int BPL, bool MULTI>
 __device__ __forceinline__ void walk_group(const TreeWalkParams &p, WalkShared<BPL, MULTI> &sh,
                                            int g, int tq_only)
