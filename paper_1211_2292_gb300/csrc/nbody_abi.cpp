@@ -1802,9 +1802,9 @@ nb_status ensure_let(nb_ctx *c)
 }
 
 // Scratch of the split LET walk for ntrees trees over `groups` groups of
-// `group` bodies (grown, never shrunk; the arrival counters start at zero
-// and every launch leaves them at zero).
-nb_status ensure_let_split(nb_ctx *c, int ntrees, int64_t groups, int group)
+// `group` bodies (grown, never shrunk; the arrival counters are zeroed on
+// stream s when allocated and every launch leaves them at zero).
+nb_status ensure_let_split(nb_ctx *c, cudaStream_t s, int ntrees, int64_t groups, int group)
 {
     nb_status st = NB_OK;
     const int64_t part = (int64_t)ntrees * groups * group * 3, cnt = (int64_t)ntrees * groups * 2;
@@ -1825,7 +1825,7 @@ nb_status ensure_let_split(nb_ctx *c, int ntrees, int64_t groups, int group)
         c->let_tctr = dev_alloc<unsigned>(c, (size_t)groups, st);
         c->let_tctr_cap = 0;
         if (st != NB_OK) return st;
-        NB_CUDA(c, cudaMemset(c->let_tctr, 0, (size_t)groups * sizeof(unsigned)));
+        NB_CUDA(c, cudaMemsetAsync(c->let_tctr, 0, (size_t)groups * sizeof(unsigned), s));
         c->let_tctr_cap = groups;
     }
     return NB_OK;
@@ -1871,7 +1871,7 @@ nb_status let_walk(nb_ctx *c, cudaStream_t s, const nb::TreeView &t, const float
     p.tctr = nullptr;
     if (nmore > 0 && p.n > 0) {
         const int64_t groups = (p.n + group - 1) / group;
-        NB_TRY(ensure_let_split(c, 1 + nmore, groups, group));
+        NB_TRY(ensure_let_split(c, s, 1 + nmore, groups, group));
         p.tpart = c->let_tpart;
         p.tcnt = c->let_tcnt;
         p.tctr = c->let_tctr;
